@@ -1,0 +1,365 @@
+"""Residual and exact Jacobian of the P4D DFN discretization (FP64, plain).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+What is computed, following the paper:
+* electrode level (section 3, "Spatial discretization for the electrode-level
+  equations", eqs. ce-weak, phie-weak, phis-weak): continuous Q1 finite
+  elements on a structured box mesh, every volume integral by 2x2x2 Gauss
+  quadrature, the reaction terms by vertex (lumped) quadrature;
+* particle level (section 3, "Spatial discretization of the particle
+  equation", eqs. L1, L2, Lh, L0, LR, FD): the finite-difference radial
+  operator per electrode node, weighted by the node's lumped electrode
+  volume as in the weak form of Appendix A (eq. particle-weak);
+* backward Euler in time (section 3, "Temporal discretization");
+* Butler-Volmer kinetics (section 2, "Interfacial kinetics").
+
+Readings taken where the paper is silent or inconsistent (each also listed in
+the design notes of the repository):
+* the particle state lives on electrode *nodes* (one particle per node);
+* the surface flux term of eq. LR enters with a minus sign (derived from
+  the flux condition -D dc/dr = i_n/F);
+* discharge uses a negative applied current density in eq. phis-weak;
+* the diffusion-potential term of eq. phie-weak keeps the printed sign
+  (parameter ``diffpot_sign``, default +1);
+* the separator regularisation of phi_s is taken to its sigma -> 0 limit:
+  phi_s exists only at electrode nodes; other nodes and the grounded face
+  carry identity rows, and their phi_s values are lifted to zero wherever
+  another row reads them;
+* a = 3 eps_s / R_s (matches the tables: 1.5e5 = 3*0.5/1e-5,
+  1.8e5 = 3*0.6/1e-5).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+G0 = 0.5 - 0.5 / np.sqrt(3.0)
+G1 = 0.5 + 0.5 / np.sqrt(3.0)
+
+
+class DomainError(ValueError):
+    """A concentration left the domain of the kinetics (c_surf outside
+    (0, c_max) or c_e <= 0)."""
+
+
+def _reference_q1():
+    """Q1 basis values and reference derivatives at the 2x2x2 Gauss points of
+    the unit cube.  Local node l = a + 2b + 4c, Gauss point q likewise."""
+    pts = (G0, G1)
+    N = np.zeros((8, 8))
+    dN = np.zeros((8, 8, 3))
+    phi = (lambda t: 1.0 - t, lambda t: t)
+    dphi = (-1.0, 1.0)
+    for q in range(8):
+        xq, yq, zq = pts[q & 1], pts[(q >> 1) & 1], pts[(q >> 2) & 1]
+        for l in range(8):
+            a, b, c = l & 1, (l >> 1) & 1, (l >> 2) & 1
+            N[q, l] = phi[a](xq) * phi[b](yq) * phi[c](zq)
+            dN[q, l, 0] = dphi[a] * phi[b](yq) * phi[c](zq)
+            dN[q, l, 1] = phi[a](xq) * dphi[b] * phi[c](zq)
+            dN[q, l, 2] = phi[a](xq) * phi[b](yq) * dphi[c]
+    return N, dN
+
+
+NREF, DREF = _reference_q1()
+# Gauss weights on the unit cube are all 1/8.
+MREF = NREF.T @ NREF / 8.0                                 # unit-cube mass
+KREF = np.stack([DREF[:, :, d].T @ DREF[:, :, d] / 8.0 for d in range(3)])  # per-axis stiffness
+
+
+def radial_operator(r, D, F):
+    """Tridiagonal coefficients of the radial operator L_h (eqs. L1, L2, Lh,
+    L0, LR) for node radii r[..., nc] (r[...,0] = 0, r[...,-1] = R) and
+    diffusivity D[...].
+
+    Returns (lo, di, up, beta): L_h(c)_i = lo_i c_{i-1} + di_i c_i + up_i c_{i+1}
+    for the no-flux part, and the surface row additionally carries
+    -beta * i_n with beta = 2 (1 + dr/R) / (F dr), dr = r_N - r_{N-1}.
+    """
+    r = np.asarray(r, float)
+    D = np.asarray(D, float)[..., None]
+    nc = r.shape[-1]
+    lo = np.zeros(r.shape)
+    di = np.zeros(r.shape)
+    up = np.zeros(r.shape)
+    # centre (eq. L0): 6 D / dr1^2 (c2 - c1)
+    dr1 = r[..., 1] - r[..., 0]
+    di[..., 0] = -6.0 * D[..., 0] / dr1 ** 2
+    up[..., 0] = 6.0 * D[..., 0] / dr1 ** 2
+    # interior (eqs. L1 + L2) with dr_i = r_{i+1} - r_i, dr_{i-1} = r_i - r_{i-1}
+    for i in range(1, nc - 1):
+        dri = r[..., i + 1] - r[..., i]
+        drm = r[..., i] - r[..., i - 1]
+        th = dri / drm
+        ri = r[..., i]
+        Di = D[..., 0]
+        a1 = 2.0 * Di / (ri * dri * (1.0 + th))          # L1 prefactor
+        a2 = 2.0 * Di / (dri * drm * (1.0 + th))         # L2 prefactor
+        up[..., i] = a1 + a2
+        lo[..., i] = -a1 * th ** 2 + a2 * th
+        di[..., i] = -a1 * (1.0 - th ** 2) - a2 * (1.0 + th)
+    # surface (eq. LR): 2 D / dr^2 (c_{N-1} - c_N) - 2 i_n/(F dr) (1 + dr/R)
+    drN = r[..., -1] - r[..., -2]
+    lo[..., -1] = 2.0 * D[..., 0] / drN ** 2
+    di[..., -1] = -2.0 * D[..., 0] / drN ** 2
+    beta = 2.0 * (1.0 + drN / r[..., -1]) / (F * drN)
+    return lo, di, up, beta
+
+
+class Disc:
+    """Mesh bookkeeping and coefficients of one cell."""
+
+    def __init__(self, mesh, params):
+        self.mesh = mesh
+        self.p = dict(params)
+        nx, ny, nz = int(mesh["nx"]), int(mesh["ny"]), int(mesh["nz"])
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.nnx, self.nny, self.nnz = nx + 1, ny + 1, nz + 1
+        self.nn = self.nnx * self.nny * self.nnz
+        self.nelem = nx * ny * nz
+        k, j, i = [a.ravel() for a in np.indices((nz, ny, nx))]
+        conn = np.empty((self.nelem, 8), np.int64)
+        for l in range(8):
+            a, b, c = l & 1, (l >> 1) & 1, (l >> 2) & 1
+            conn[:, l] = (i + a) + self.nnx * ((j + b) + self.nny * (k + c))
+        self.conn = conn
+        hx, hy, hz = (np.asarray(mesh[h], float) for h in ("hx", "hy", "hz"))
+        self.h = np.stack([hx[i], hy[j], hz[k]], axis=1)          # (nelem, 3)
+        self.vol = self.h.prod(axis=1)
+        region = np.asarray(mesh["region"])
+        self.region = region
+        an_el, ca_el = region == 0, region == 2
+        el = an_el | ca_el
+        self.el = el
+        node_an = np.zeros(self.nn, bool)
+        node_ca = np.zeros(self.nn, bool)
+        node_an[conn[an_el].ravel()] = True
+        node_ca[conn[ca_el].ravel()] = True
+        if np.any(node_an & node_ca):
+            raise ValueError("anode and cathode elements share a node")
+        self.enodes = np.flatnonzero(node_an | node_ca)
+        self.NE = self.enodes.size
+        self.eidx = np.full(self.nn, -1, np.int64)
+        self.eidx[self.enodes] = np.arange(self.NE)
+        self.etype = np.where(node_an[self.enodes], 0, 1)
+        eps = np.asarray(mesh["eps"], float)
+        eps_s = np.asarray(mesh["eps_s"], float)
+        Mn = np.zeros(self.nn)
+        Sn = np.zeros(self.nn)
+        np.add.at(Mn, conn[el].ravel(), np.repeat(self.vol[el] / 8.0, 8))
+        np.add.at(Sn, conn[el].ravel(), np.repeat(eps_s[el] * self.vol[el] / 8.0, 8))
+        self.M = Mn[self.enodes]
+        self.S = Sn[self.enodes]
+        self.Rs = np.asarray(mesh["Rs"], float)[self.enodes]
+        self.Ds = np.asarray(mesh["Ds"], float)[self.enodes]
+        self.A = 3.0 * self.S / self.Rs
+        p = self.p
+        an = self.etype == 0
+        self.kr = np.where(an, p["k_n"], p["k_p"])
+        self.cmax = np.where(an, p["cmax_n"], p["cmax_p"])
+        self.u0 = np.where(an, p["ocp_n"][0], p["ocp_p"][0])
+        self.u1 = np.where(an, p["ocp_n"][1], p["ocp_p"][1])
+        b = p["brug"]
+        sig_reg = np.where(an_el, p["sigma_n"], np.where(ca_el, p["sigma_p"], 0.0))
+        self.sig = np.where(el, eps_s ** b * sig_reg, 0.0)
+        self.kap = eps ** b * p["kappa"]
+        self.Deff = eps ** b * p["De"]
+        self.eps = eps
+        # applied-current face Gamma_p (z = Lz), grounded face Gamma_n (z = 0)
+        fj, fi = [a.ravel() for a in np.indices((ny, nx))]
+        area = hx[fi] * hy[fj]
+        gp = np.asarray(mesh["gamma_p"]).astype(bool)
+        gn = np.asarray(mesh["gamma_n"]).astype(bool)
+        self.gpw = np.zeros(self.nn)
+        self.dirichlet = np.zeros(self.nn, bool)
+        for a in (0, 1):
+            for bb in (0, 1):
+                top = (fi + a) + self.nnx * ((fj + bb) + self.nny * nz)
+                bot = (fi + a) + self.nnx * (fj + bb)
+                np.add.at(self.gpw, top[gp], area[gp] / 4.0)
+                self.dirichlet[bot[gn]] = True
+        self.act = np.zeros(self.nn, bool)
+        self.act[self.enodes] = True
+        self.act[self.dirichlet] = False
+        self.nc = int(mesh["nc"])
+        self.r = self.Rs[:, None] * np.asarray(mesh["rgrid"], float)[None, :]
+        self.lo, self.di, self.up, self.beta = radial_operator(self.r, self.Ds, p["F"])
+        self.ndof = 3 * self.nn + self.NE * self.nc
+
+    # ------------------------------------------------------------------ state
+    def state_from_case(self, st):
+        """Compact a generator state (c_s given per node) to electrode rows."""
+        return dict(phis=np.asarray(st["phis"], float).copy(),
+                    phie=np.asarray(st["phie"], float).copy(),
+                    ce=np.asarray(st["ce"], float).copy(),
+                    cs=np.asarray(st["cs_node"], float)[self.enodes].copy(),
+                    ce_prev=np.asarray(st["ce_prev"], float).copy(),
+                    cs_prev=np.asarray(st["cs_prev_node"], float)[self.enodes].copy())
+
+    def pack(self, st):
+        return np.concatenate([st["phis"], st["phie"], st["ce"], st["cs"].ravel()])
+
+    def unpack(self, x):
+        nn = self.nn
+        return dict(phis=x[:nn], phie=x[nn:2 * nn], ce=x[2 * nn:3 * nn],
+                    cs=x[3 * nn:].reshape(self.NE, self.nc))
+
+    def with_values(self, st, x):
+        out = dict(st)
+        out.update({k: v.copy() for k, v in self.unpack(x).items()})
+        return out
+
+    # --------------------------------------------------------------- helpers
+    def _lap(self, ue):
+        """Unit-coefficient Q1 stiffness applied element-wise: (nelem, 8)."""
+        out = np.zeros_like(ue)
+        for d in range(3):
+            out += (self.vol / self.h[:, d] ** 2)[:, None] * (ue @ KREF[d])
+        return out
+
+    def _scatter(self, vals):
+        return np.bincount(self.conn.ravel(), weights=vals.ravel(), minlength=self.nn)
+
+    def kinetics(self, phis_l, phie, ce, cs_surf):
+        """Butler-Volmer at the electrode nodes (section 2, "Interfacial
+        kinetics").  Returns i_n and its partial derivatives with respect to
+        phi_s, c_e and c_surf (d/dphi_e = -d/dphi_s)."""
+        p = self.p
+        ph_s, ph_e, c_e = phis_l[self.enodes], phie[self.enodes], ce[self.enodes]
+        if np.any(c_e <= 0) or np.any(cs_surf <= 0) or np.any(cs_surf >= self.cmax):
+            raise DomainError("concentration outside the kinetics domain")
+        al = p["alpha"]
+        f = p["F"] / (p["R"] * p["T"])
+        theta = cs_surf / self.cmax
+        eta = ph_s - ph_e - (self.u0 + self.u1 * theta)
+        i0 = self.kr * c_e ** al * (self.cmax - cs_surf) ** al * cs_surf ** (1.0 - al)
+        ea = np.exp(al * f * eta)
+        ec = np.exp(-(1.0 - al) * f * eta)
+        i_n = i0 * (ea - ec)
+        g_eta = i0 * f * (al * ea + (1.0 - al) * ec)
+        g_c = al * i_n / c_e
+        g_s = i_n * ((1.0 - al) / cs_surf - al / (self.cmax - cs_surf)) - g_eta * self.u1 / self.cmax
+        return i_n, g_eta, g_c, g_s
+
+    def _gauss_c(self, ce):
+        """c_e and grad c_e at the Gauss points: (nelem, 8), (nelem, 8, 3)."""
+        ce_e = ce[self.conn]
+        cq = ce_e @ NREF.T
+        gq = np.einsum("qld,el->eqd", DREF, ce_e) / self.h[:, None, :]
+        return cq, gq
+
+    def _kp(self):
+        p = self.p
+        return p["diffpot_sign"] * self.kap * 2.0 * p["R"] * p["T"] * (1.0 - p["tplus"]) / p["F"]
+
+    # -------------------------------------------------------------- residual
+    def residual(self, st):
+        """Monolithic residual [R_phis; R_phie; R_ce; R_cs] (section 4 eq. of
+        the block residual)."""
+        p = self.p
+        dt = p["dt"]
+        phis_l = np.where(self.act, st["phis"], 0.0)
+        phie, ce, cs = st["phie"], st["ce"], st["cs"]
+        cq, gq = self._gauss_c(ce)
+        if np.any(cq <= 0):
+            raise DomainError("c_e <= 0 at a quadrature point")
+        # electronic charge (eq. phis-weak)
+        R_s = self._scatter(self.sig[:, None] * self._lap(phis_l[self.conn]))
+        # ionic charge (eq. phie-weak), diffusion-potential term by Gauss quadrature
+        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn]))
+        flux = gq / cq[..., None]                                   # grad c / c
+        nl = np.einsum("eqd,qld->el", flux / self.h[:, None, :], DREF) * (self._kp() * self.vol / 8.0)[:, None]
+        R_e += self._scatter(nl)
+        # electrolyte transport (eq. ce-weak), consistent mass
+        dce = (ce - st["ce_prev"])[self.conn]
+        R_c = self._scatter((self.eps * self.vol)[:, None] * (dce @ MREF) / dt
+                            + self.Deff[:, None] * self._lap(ce[self.conn]))
+        # reactions (vertex quadrature)
+        i_n, *_ = self.kinetics(phis_l, phie, ce, cs[:, -1])
+        tau = (1.0 - p["tplus"]) / p["F"]
+        en = self.enodes
+        R_s[en] += self.A * i_n
+        R_e[en] -= self.A * i_n
+        R_c[en] -= tau * self.A * i_n
+        R_s -= p["i_app"] * self.gpw
+        R_s[~self.act] = st["phis"][~self.act]
+        # particles (eqs. FD, particle-weak)
+        L = self.di * cs
+        L[:, 1:] += self.lo[:, 1:] * cs[:, :-1]
+        L[:, :-1] += self.up[:, :-1] * cs[:, 1:]
+        L[:, -1] -= self.beta * i_n
+        R_p = self.M[:, None] * ((cs - st["cs_prev"]) / dt - L)
+        return np.concatenate([R_s, R_e, R_c, R_p.ravel()])
+
+    # -------------------------------------------------------------- Jacobian
+    def jacobian(self, st):
+        """Exact derivative of ``residual`` as a CSR matrix (section 4 eq.
+        blocks)."""
+        p = self.p
+        dt = p["dt"]
+        nn, NE, nc = self.nn, self.NE, self.nc
+        phis_l = np.where(self.act, st["phis"], 0.0)
+        phie, ce, cs = st["phie"], st["ce"], st["cs"]
+        rows, cols, vals = [], [], []
+
+        def add(r, c, v):
+            rows.append(np.asarray(r).ravel())
+            cols.append(np.asarray(c).ravel())
+            vals.append(np.broadcast_to(v, np.shape(r)).ravel() if np.ndim(v) == 0 else np.asarray(v).ravel())
+
+        R8 = np.broadcast_to(self.conn[:, :, None], (self.nelem, 8, 8))
+        C8 = np.broadcast_to(self.conn[:, None, :], (self.nelem, 8, 8))
+        Ke = np.zeros((self.nelem, 8, 8))
+        for d in range(3):
+            Ke += (self.vol / self.h[:, d] ** 2)[:, None, None] * KREF[d][None]
+        Me = self.vol[:, None, None] * MREF[None]
+        # phi_s - phi_s (active rows and columns only)
+        keep = self.el[:, None, None] & self.act[R8] & self.act[C8]
+        add(R8[keep], C8[keep], (self.sig[:, None, None] * Ke)[keep])
+        # phi_e - phi_e
+        add(nn + R8, nn + C8, self.kap[:, None, None] * Ke)
+        # phi_e - c_e: derivative of the diffusion-potential term
+        cq, gq = self._gauss_c(ce)
+        gN = DREF[None] / self.h[:, None, None, :]                   # (e, q, l, d)
+        GG = np.einsum("eqld,eqmd->eqlm", gN, gN)
+        t1 = np.einsum("eqlm,eq->elm", GG, 1.0 / cq)
+        gcN = np.einsum("eqd,eqld->eql", gq, gN)                     # grad c . grad N_l
+        t2 = np.einsum("qm,eql,eq->elm", NREF, gcN, 1.0 / cq ** 2)
+        Be = (self._kp() * self.vol / 8.0)[:, None, None] * (t1 - t2)
+        add(nn + R8, 2 * nn + C8, Be)
+        # c_e - c_e
+        add(2 * nn + R8, 2 * nn + C8, (self.eps / dt)[:, None, None] * Me + self.Deff[:, None, None] * Ke)
+        # identity rows of phi_s
+        ina = np.flatnonzero(~self.act)
+        add(ina, ina, 1.0)
+        # reactions
+        i_n, ge, gc, gs = self.kinetics(phis_l, phie, ce, cs[:, -1])
+        tau = (1.0 - p["tplus"]) / p["F"]
+        en = self.enodes
+        a_ = self.act[en]
+        csN = 3 * nn + np.arange(NE) * nc + (nc - 1)
+        A = self.A
+        Mb = self.M * self.beta
+        # rows: (row index, row weight) for phi_s, phi_e, c_e, c_s(N)
+        for rix, w, only_act in ((en, A, True), (nn + en, -A, False),
+                                 (2 * nn + en, -tau * A, False), (csN, Mb, False)):
+            m = a_ if only_act else np.ones(NE, bool)
+            ms = m & a_
+            add(rix[ms], en[ms], (w * ge)[ms])                # d/dphi_s (lifted)
+            add(rix[m], nn + en[m], -(w * ge)[m])             # d/dphi_e
+            add(rix[m], 2 * nn + en[m], (w * gc)[m])          # d/dc_e
+            add(rix[m], csN[m], (w * gs)[m])                  # d/dc_surf
+        # particle tridiagonals: M (I/dt - L_h)
+        base = 3 * nn + np.arange(NE)[:, None] * nc + np.arange(nc)[None, :]
+        Mcol = self.M[:, None]
+        add(base, base, Mcol * (1.0 / dt - self.di))
+        add(base[:, 1:], base[:, :-1], -Mcol * self.lo[:, 1:])
+        add(base[:, :-1], base[:, 1:], -Mcol * self.up[:, :-1])
+        J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.ndof, self.ndof)).tocsr()
+        J.sum_duplicates()
+        return J
+
+    # ------------------------------------------------------------- utilities
+    def field_slices(self):
+        nn = self.nn
+        return [slice(0, nn), slice(nn, 2 * nn), slice(2 * nn, 3 * nn), slice(3 * nn, self.ndof)]

@@ -1,0 +1,225 @@
+"""Seeded generators for the synthetic cells (see package docstring)."""
+import math
+import numpy as np
+
+# Physical constants and material data (paper, Appendix "Model Parameters":
+# constants, electrolyte, cathode, anode and separator tables).  D_s, D_e,
+# kappa, sigma and eps_e follow the homogeneous-cube workload definition.
+PARAMS_DEFAULT = dict(
+    F=96485.33, R=8.31446, T=298.15, tplus=0.4, brug=1.5,
+    De=7.5e-10, kappa=1.0,
+    sigma_n=100.0, sigma_p=10.0,
+    k_n=2e-5, k_p=6e-7,
+    cmax_n=2.5e4, cmax_p=5.12e4,
+    alpha=0.5,
+    # linear OCP U(theta) = c0 + c1*theta (secants, see ocp_linear_secants)
+    ocp_n=(0.229016, -0.067279), ocp_p=(4.948384, -1.535617),
+    dt=10.0, i_app=-40.2022,
+    diffpot_sign=1.0,
+    shell_sigma_t_p=0.0, shell_sigma_t_n=0.0,
+)
+
+CASES = ("tiny", "cube8", "cube128", "hetero128")
+
+
+def ocp_linear_secants():
+    """Secant lines of the paper's OCP curves (Appendix, eqs. for LiCoO2 and
+    graphite) over the stoichiometry ranges the seeded states draw from:
+    anode theta in [0.5, 0.8], cathode theta in [0.4, 0.6].  Returns
+    ((c0_n, c1_n), (c0_p, c1_p))."""
+    def u_p(th):
+        t = 1.062 * th
+        return (2.16216 + 0.07645 * math.tanh(30.834 - 54.4806 * t)
+                + 2.1581 * math.tanh(52.294 - 50.294 * t)
+                - 0.14169 * math.tanh(11.0923 - 19.8543 * t)
+                + 0.2051 * math.tanh(1.4684 - 5.4888 * t)
+                + 0.2531 * math.tanh((-t + 0.56478) / 0.1316)
+                - 0.02167 * math.tanh((t - 0.525) / 0.006))
+
+    def u_n(th):
+        return (0.194 + 1.5 * math.exp(-120.0 * th)
+                + 0.0351 * math.tanh((th - 0.286) / 0.083)
+                - 0.0045 * math.tanh((th - 0.849) / 0.119)
+                - 0.035 * math.tanh((th - 0.9233) / 0.05)
+                - 0.0147 * math.tanh((th - 0.5) / 0.034)
+                - 0.102 * math.tanh((th - 0.194) / 0.142)
+                - 0.022 * math.tanh((th - 0.9) / 0.0164)
+                - 0.011 * math.tanh((th - 0.124) / 0.0226)
+                + 0.0155 * math.tanh((th - 0.105) / 0.029))
+
+    def secant(f, a, b):
+        s = (f(b) - f(a)) / (b - a)
+        return (f(a) - s * a, s)
+    return secant(u_n, 0.5, 0.8), secant(u_p, 0.4, 0.6)
+
+
+def theoretical_iapp(Lx, Ly, Ln, Lp, eps_s_n, eps_s_p, cmax_n, cmax_p, F, crate=1.0):
+    """Applied current density for a C-rate from the theoretical capacity
+    (paper, Appendix: Q_i = F eps_s,i V_i c_max,i / 3600, Q = min, I = C Q).
+    Returned negative: discharge makes the cathode reaction cathodic."""
+    area = Lx * Ly
+    q_n = F / 3600.0 * eps_s_n * area * Ln * cmax_n
+    q_p = F / 3600.0 * eps_s_p * area * Lp * cmax_p
+    return -crate * min(q_n, q_p) / area
+
+
+def _layers(n_an, n_sep, n_ca, L_an, L_sep, L_ca):
+    hz = np.concatenate([np.full(n_an, L_an / n_an), np.full(n_sep, L_sep / n_sep),
+                         np.full(n_ca, L_ca / n_ca)])
+    reg_z = np.concatenate([np.zeros(n_an, np.uint8), np.ones(n_sep, np.uint8),
+                            np.full(n_ca, 2, np.uint8)])
+    return hz, reg_z
+
+
+def _node_types(nx, ny, nz, region):
+    """Anode/cathode flags per node (used only to pick which stoichiometry
+    range a node's seeded state is drawn from)."""
+    r = region.reshape(nz, ny, nx)
+    an = np.zeros((nz + 1, ny + 1, nx + 1), bool)
+    ca = np.zeros_like(an)
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                an[dk:dk + nz, dj:dj + ny, di:di + nx] |= (r == 0)
+                ca[dk:dk + nz, dj:dj + ny, di:di + nx] |= (r == 2)
+    return an.ravel(), ca.ravel()
+
+
+def make_box_case(nx, ny, nz_layers, L_lat, L_layers, nc, seed, *, params=None,
+                  hetero=False, rs_cv=0.0, state="seeded", Rs=5e-6, Ds=1e-14,
+                  eps_e=0.3, eps_s=(0.6, 0.5)):
+    """Layered anode/separator/cathode box.
+
+    state="seeded": linearization state with c_e = 1000(1 + U(-0.05, 0.05)),
+    anode theta ~ U(0.5, 0.8), cathode theta ~ U(0.4, 0.6) per node, c_s
+    uniform in r, previous step equal to the state and open-circuit
+    potentials (phi_s = 0 in the anode, phi_e = -U_n(0.65),
+    phi_s = U_p(0.5) - U_n(0.65) in the cathode).
+    state="initial": c_e = 1000, theta_n = 0.8, theta_p = 0.6, open circuit.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = dict(PARAMS_DEFAULT)
+    if params:
+        p.update(params)
+    n_an, n_sep, n_ca = nz_layers
+    L_an, L_sep, L_ca = L_layers
+    nz = n_an + n_sep + n_ca
+    hx = np.full(nx, L_lat / nx)
+    hy = np.full(ny, L_lat / ny)
+    hz, reg_z = _layers(n_an, n_sep, n_ca, L_an, L_sep, L_ca)
+    nelem = nx * ny * nz
+    region = np.repeat(reg_z, nx * ny).astype(np.uint8)
+    eps = np.where(region == 1, 1.0, eps_e).astype(np.float64)
+    eps_s_arr = np.where(region == 0, eps_s[0], np.where(region == 2, eps_s[1], 0.0))
+    if hetero:
+        eps, eps_s_arr = _hetero_fields(nx, ny, nz, hx, hy, hz, region, rng)
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    Rs_node = np.full(nn, Rs)
+    if rs_cv > 0:
+        s2 = math.log(1 + rs_cv ** 2)
+        Rs_node = np.exp(math.log(Rs) - s2 / 2 + math.sqrt(s2) * rng.standard_normal(nn))
+        Rs_node = np.clip(Rs_node, 1e-6, 20e-6)
+    Ds_node = np.full(nn, Ds)
+    gamma_p = np.ones(nx * ny, np.uint8)
+    gamma_n = np.ones(nx * ny, np.uint8)
+    if "i_app" not in (params or {}):
+        p["i_app"] = theoretical_iapp(L_lat, L_lat, L_an, L_ca, eps_s[0], eps_s[1],
+                                      p["cmax_n"], p["cmax_p"], p["F"])
+    an, ca = _node_types(nx, ny, nz, region)
+    (c0n, c1n), (c0p, c1p) = p["ocp_n"], p["ocp_p"]
+    if state == "seeded":
+        ce = 1000.0 * (1.0 + rng.uniform(-0.05, 0.05, nn))
+        th_n = rng.uniform(0.5, 0.8, nn)
+        th_p = rng.uniform(0.4, 0.6, nn)
+        thn_ref, thp_ref = 0.65, 0.5
+    else:
+        ce = np.full(nn, 1000.0)
+        th_n = np.full(nn, 0.8)
+        th_p = np.full(nn, 0.6)
+        thn_ref, thp_ref = 0.8, 0.6
+    cs_node = np.zeros((nn, nc))
+    cs_node[an] = (th_n[an] * p["cmax_n"])[:, None]
+    cs_node[ca] = (th_p[ca] * p["cmax_p"])[:, None]
+    un_ref = c0n + c1n * thn_ref
+    up_ref = c0p + c1p * thp_ref
+    phis = np.zeros(nn)
+    phis[ca] = up_ref - un_ref
+    phie = np.full(nn, -un_ref)
+    mesh = dict(nx=nx, ny=ny, nz=nz, hx=hx, hy=hy, hz=hz, region=region, eps=eps,
+                eps_s=eps_s_arr, Rs=Rs_node, Ds=Ds_node, gamma_p=gamma_p,
+                gamma_n=gamma_n, nc=nc, rgrid=np.linspace(0.0, 1.0, nc))
+    st = dict(phis=phis, phie=phie, ce=ce, cs_node=cs_node, ce_prev=ce.copy(),
+              cs_prev_node=cs_node.copy())
+    return dict(mesh=mesh, params=p, state=st, seed=seed)
+
+
+def _hetero_fields(nx, ny, nz, hx, hy, hz, region, rng, corr=8, mean=0.3, cv=0.2):
+    """Lognormal porosity with correlation length `corr` elements: Gaussian
+    samples on a coarse grid of `corr`-element spacing, trilinearly
+    interpolated to element centres, smoothed by a few Jacobi sweeps of
+    (I - h_c^2 Lap) g~ = g on the element grid, normalised to zero mean and
+    unit variance, then eps = exp(mu + s g~) with mean 0.3 and CV 0.2 in the
+    electrodes (clamped to [0.05, 0.7]); eps_s = 1 - eps - eps_b with binder
+    fractions 0.1 (anode) and 0.2 (cathode)."""
+    cz, cy, cx = nz // corr + 2, ny // corr + 2, nx // corr + 2
+    g = rng.standard_normal((cz, cy, cx))
+    zc = (np.arange(nz) + 0.5) / corr
+    yc = (np.arange(ny) + 0.5) / corr
+    xc = (np.arange(nx) + 0.5) / corr
+    def interp1(arr, coords, axis):
+        i0 = np.floor(coords).astype(int)
+        t = coords - i0
+        a = np.take(arr, i0, axis=axis)
+        b = np.take(arr, i0 + 1, axis=axis)
+        shape = [1, 1, 1]
+        shape[axis] = -1
+        t = t.reshape(shape)
+        return a * (1 - t) + b * t
+    f = interp1(interp1(interp1(g, zc, 0), yc, 1), xc, 2)
+    # smoothing: damped Jacobi on (I - hc^2 Lap) with hc = corr (element units)
+    h2 = float(corr) ** 2
+    gt = f.copy()
+    for _ in range(40):
+        lap = -6 * gt
+        for ax in range(3):
+            lap += np.roll(gt, 1, ax) + np.roll(gt, -1, ax)
+        res = f - (gt - h2 * lap)
+        gt = gt + 0.8 * res / (1 + 6 * h2)
+    gt = (gt - gt.mean()) / gt.std()
+    s2 = math.log(1 + cv ** 2)
+    mu = math.log(mean) - s2 / 2
+    eps_field = np.clip(np.exp(mu + math.sqrt(s2) * gt), 0.05, 0.7).ravel()
+    eps = np.where(region == 1, 1.0, eps_field)
+    eps_b = np.where(region == 0, 0.1, np.where(region == 2, 0.2, 0.0))
+    eps_s = np.where((region == 0) | (region == 2), 1.0 - eps - eps_b, 0.0)
+    return eps, eps_s
+
+
+def make_tiny_case(nx=2, ny=2, layers=(2, 1, 2), nc=4, seed=7, **kw):
+    """Small box for brute-force checks (lateral 20 um, 20/10/20 um thick)."""
+    return make_box_case(nx, ny, layers, 20e-6, (20e-6, 10e-6, 20e-6), nc, seed, **kw)
+
+
+def make_case(name, **kw):
+    """Named workloads.
+
+    cube8:      8x8x24 elements (10/4/10), 100 um lateral, 100/25/100 um,
+                N_c = 10, seeded linearization state (seed 1001).
+    cube128:    128x128x96 (40/16/40), same physics, N_c = 20 (seed 1002).
+    hetero128:  cube128 mesh with lognormal porosity (mean 0.3, CV 0.2,
+                correlation 8 elements) and lognormal particle radius
+                (mean 5 um, CV 0.3) (seed 1003).
+    tiny:       2x2x5 (2/1/2), N_c = 4 (seed 7).
+    """
+    if name == "tiny":
+        return make_tiny_case(**kw)
+    if name == "cube8":
+        return make_box_case(8, 8, (10, 4, 10), 100e-6, (100e-6, 25e-6, 100e-6), 10,
+                             kw.pop("seed", 1001), **kw)
+    if name == "cube128":
+        return make_box_case(128, 128, (40, 16, 40), 100e-6, (100e-6, 25e-6, 100e-6), 20,
+                             kw.pop("seed", 1002), **kw)
+    if name == "hetero128":
+        return make_box_case(128, 128, (40, 16, 40), 100e-6, (100e-6, 25e-6, 100e-6), 20,
+                             kw.pop("seed", 1003), hetero=True, rs_cv=0.3, **kw)
+    raise KeyError(name)
