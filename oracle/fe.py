@@ -21,7 +21,12 @@ the design notes of the repository):
   the flux condition -D dc/dr = i_n/F);
 * discharge uses a negative applied current density in eq. phis-weak;
 * the diffusion-potential term of eq. phie-weak keeps the printed sign
-  (parameter ``diffpot_sign``, default +1);
+  (parameter ``diffpot_sign``, default +1) and is discretized through the
+  identity grad(c_e)/c_e = grad(ln c_e) with ln c_e replaced by its Q1
+  nodal interpolant (the quadrature of the quotient is not specified by the
+  paper): the term becomes the kappa_eff-weighted stiffness matrix applied
+  to the nodal values of ln c_e, so it stays in divergence form and its
+  Jacobian block is K_kappa diag(gamma / c_e);
 * the separator regularisation of phi_s is taken to its sigma -> 0 limit:
   phi_s exists only at electrode nodes; other nodes and the grounded face
   carry identity rows, and their phi_s values are lifted to zero wherever
@@ -240,16 +245,9 @@ class Disc:
         g_s = i_n * ((1.0 - al) / cs_surf - al / (self.cmax - cs_surf)) - g_eta * self.u1 / self.cmax
         return i_n, g_eta, g_c, g_s
 
-    def _gauss_c(self, ce):
-        """c_e and grad c_e at the Gauss points: (nelem, 8), (nelem, 8, 3)."""
-        ce_e = ce[self.conn]
-        cq = ce_e @ NREF.T
-        gq = np.einsum("qld,el->eqd", DREF, ce_e) / self.h[:, None, :]
-        return cq, gq
-
-    def _kp(self):
+    def _gamma(self):
         p = self.p
-        return p["diffpot_sign"] * self.kap * 2.0 * p["R"] * p["T"] * (1.0 - p["tplus"]) / p["F"]
+        return p["diffpot_sign"] * 2.0 * p["R"] * p["T"] * (1.0 - p["tplus"]) / p["F"]
 
     # -------------------------------------------------------------- residual
     def residual(self, st):
@@ -259,16 +257,14 @@ class Disc:
         dt = p["dt"]
         phis_l = np.where(self.act, st["phis"], 0.0)
         phie, ce, cs = st["phie"], st["ce"], st["cs"]
-        cq, gq = self._gauss_c(ce)
-        if np.any(cq <= 0):
-            raise DomainError("c_e <= 0 at a quadrature point")
+        if np.any(ce <= 0):
+            raise DomainError("c_e <= 0")
         # electronic charge (eq. phis-weak)
         R_s = self._scatter(self.sig[:, None] * self._lap(phis_l[self.conn]))
-        # ionic charge (eq. phie-weak), diffusion-potential term by Gauss quadrature
-        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn]))
-        flux = gq / cq[..., None]                                   # grad c / c
-        nl = np.einsum("eqd,qld->el", flux / self.h[:, None, :], DREF) * (self._kp() * self.vol / 8.0)[:, None]
-        R_e += self._scatter(nl)
+        # ionic charge (eq. phie-weak); diffusion potential through the Q1
+        # interpolant of ln c_e
+        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn])
+                            + self._gamma() * self.kap[:, None] * self._lap(np.log(ce)[self.conn]))
         # electrolyte transport (eq. ce-weak), consistent mass
         dce = (ce - st["ce_prev"])[self.conn]
         R_c = self._scatter((self.eps * self.vol)[:, None] * (dce @ MREF) / dt
@@ -317,14 +313,8 @@ class Disc:
         add(R8[keep], C8[keep], (self.sig[:, None, None] * Ke)[keep])
         # phi_e - phi_e
         add(nn + R8, nn + C8, self.kap[:, None, None] * Ke)
-        # phi_e - c_e: derivative of the diffusion-potential term
-        cq, gq = self._gauss_c(ce)
-        gN = DREF[None] / self.h[:, None, None, :]                   # (e, q, l, d)
-        GG = np.einsum("eqld,eqmd->eqlm", gN, gN)
-        t1 = np.einsum("eqlm,eq->elm", GG, 1.0 / cq)
-        gcN = np.einsum("eqd,eqld->eql", gq, gN)                     # grad c . grad N_l
-        t2 = np.einsum("qm,eql,eq->elm", NREF, gcN, 1.0 / cq ** 2)
-        Be = (self._kp() * self.vol / 8.0)[:, None, None] * (t1 - t2)
+        # phi_e - c_e: derivative of the diffusion-potential term, K_kappa diag(gamma / c_e)
+        Be = (self._gamma() * self.kap)[:, None, None] * Ke / ce[self.conn][:, None, :]
         add(nn + R8, 2 * nn + C8, Be)
         # c_e - c_e
         add(2 * nn + R8, 2 * nn + C8, (self.eps / dt)[:, None, None] * Me + self.Deff[:, None, None] * Ke)

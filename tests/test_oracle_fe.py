@@ -128,7 +128,6 @@ def _p2d_residual(z_h, region, p, nc, R, D, u, prev, eps_e=0.3, eps_s=(0.6, 0.5)
     phis_l = np.where(act, phis, 0.0)
     Rs = np.zeros(nn); Re = np.zeros(nn); Rc = np.zeros(nn)
     Mw = np.zeros(nn); Sw = np.zeros(nn)
-    g = [0.5 - 0.5 / np.sqrt(3), 0.5 + 0.5 / np.sqrt(3)]
     kp = p["diffpot_sign"] * 2 * p["R"] * p["T"] * (1 - p["tplus"]) / p["F"]
     for e in range(nz):
         h = z_h[e]
@@ -144,10 +143,7 @@ def _p2d_residual(z_h, region, p, nc, R, D, u, prev, eps_e=0.3, eps_s=(0.6, 0.5)
         Rs[ix] += sig * k2 @ phis_l[ix]
         Re[ix] += kap * k2 @ phie[ix]
         Rc[ix] += eps * m2 @ (ce[ix] - cep[ix]) / p["dt"] + De * k2 @ ce[ix]
-        for q in g:
-            cq = ce[e] * (1 - q) + ce[e + 1] * q
-            gq = (ce[e + 1] - ce[e]) / h
-            Re[ix] += 0.5 * h * kap * kp * gq / cq * np.array([-1 / h, 1 / h])
+        Re[ix] += kap * kp * k2 @ np.log(ce[ix])
         if el:
             Mw[ix] += h / 2
             Sw[ix] += es * h / 2
