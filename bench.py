@@ -1,0 +1,401 @@
+"""Benchmark: Newton linear solves/s and FGMRES iterations/s to a 1e-8
+relative residual on the 128x128x96 homogeneous cube (40/16/40 elements,
+N_c = 20, ~32M unknowns), mixed precision (FP32 multigrid/particle
+preconditioner inside FP64 FGMRES) vs the all-FP64 GPU path.
+
+One step = one Newton linear solve of the hot path: nonlinear residual,
+linearization update (kinetics, particle Schur scalars, multigrid operators)
+and the block-preconditioned FGMRES solve, on a seeded linearization state.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+Under torchrun (N > 1) every rank solves its own cell (independent problems,
+weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton linear solves/s & FGMRES iters/s to 1e-8 rel. residual; mixed vs FP64"
+WORKLOAD = "cube128"
+# unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
+# the 82 electrode node layers (41 anode + 41 cathode)
+CUBE128_DOF = 3 * 129 * 129 * 97 + 20 * 82 * 129 * 129
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nme, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_workload(name):
+    from p4d_inputs import make_case
+    return make_case(name)
+
+
+def gpu_leg(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2602_07225_gb300 import P4DSolver
+    from paper_2602_07225_gb300 import build as pbuild
+
+    pbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_workload(args.workload)
+    opts_mixed = dict(precision=1, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600)
+    s = P4DSolver(case, device=dev, **opts_mixed)
+    st = s.state_tensors(case["state"])
+    ndof = s.ndof
+
+    def step(solver, state):
+        b = solver.residual(state)
+        b.neg_()
+        solver.jacobian_update(state)
+        x, info = solver.solve(b)
+        return x, info
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        x, info = step(s, st)
+    torch.cuda.synchronize()
+    barrier()
+    iters = 0
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            x, info = step(s, st)
+            iters += info["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        it = torch.tensor([iters], device=dev, dtype=torch.float64)
+        dist.all_reduce(it)
+        iters_all = it.item()
+    else:
+        iters_all = iters
+    ms_per_step = ms / args.steps
+    solves_per_s = world * args.steps / (ms / 1e3)
+    iters_per_s = iters_all / (ms / 1e3)
+    last_info = info
+
+    # ---- end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    host = {k: v.cpu().pin_memory() for k, v in st.items()}
+    x_host = torch.empty(ndof, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = ndof * 8
+    dev_bufs = {k: torch.empty_like(v) for k, v in st.items()}
+
+    def e2e_step():
+        for k in host:
+            dev_bufs[k].copy_(host[k], non_blocking=True)
+        x, info = step(s, dev_bufs)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        return info
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    # ---- roofline: dominant kernel timed live (FP64 coupled JVP through the C ABI)
+    roof = roofline_jvp(s, st, dev)
+    kern = kernel_breakdown(lambda: step(s, st))
+
+    # ---- FP64 GPU path for the same step
+    fp64 = None
+    if not args.no_fp64:
+        s64 = P4DSolver(case, device=dev, precision=0, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600)
+        for _ in range(2):
+            _, i64 = step(s64, st)
+        torch.cuda.synchronize()
+        k64 = max(2, args.steps // 2)
+        it64 = 0
+        e0.record(stream)
+        for _ in range(k64):
+            _, i64 = step(s64, st)
+            it64 += i64["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        fp64 = {"solves_per_s": 1e3 / ms64, "fgmres_iters_per_s": it64 / (ms64 * k64 / 1e3),
+                "iters_per_solve": it64 / k64, "ms_per_step": ms64, "rel_res": i64["rel_res"]}
+        s64.close()
+    return dict(ms_per_step=ms_per_step, solves_per_s=solves_per_s, iters_per_s=iters_per_s,
+                iters_per_solve=iters / args.steps, ndof=ndof, info=last_info, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h,
+                clocks=clk.summary(), roof=roof, fp64=fp64, kern=kern, nn=s.nn, NE=s.NE, nc=s.nc)
+
+
+def kernel_breakdown(step_fn):
+    """Kernels of one step, recorded by the CUDA activity tracer (one extra,
+    untimed step): launch count and device time per kernel name."""
+    import torch
+    from torch.profiler import profile, ProfilerActivity
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step_fn()
+        torch.cuda.synchronize()
+    agg = {}
+    for ev in prof.events():
+        if ev.device_type != torch.autograd.DeviceType.CUDA:
+            continue
+        name = ev.name
+        if "Memcpy" in name or "Memset" in name:
+            continue
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += ev.device_time_total if hasattr(ev, "device_time_total") else ev.cuda_time_total
+    total = sum(v[1] for v in agg.values())
+    rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
+    mine = sum(v[0] for k, v in agg.items() if "p4d" in k or k.startswith("void p4d") or "k_" in k)
+    return {"launches_per_step": mine, "all_launches_per_step": sum(v[0] for v in agg.values()),
+            "top": [{"kernel": k[:90], "launches": v[0], "us": round(v[1], 1),
+                     "share": round(v[1] / total, 4) if total else None} for k, v in rows[:12]]}
+
+
+def roofline_jvp(s, st, dev):
+    """Average duration of the FP64 coupled JVP (full layout) over repeated
+    launches on the solver's stream, and its algorithmic bytes: the three
+    27-point FP64 stencils, x and y over every unknown, the per-node factor
+    gamma/c_e and the electrode-node coupling scalars."""
+    import torch
+    x = torch.randn(s.ndof, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        s.jvp(x, out=y)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        s.jvp(x, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nn, NE, nc = s.nn, s.NE, s.nc
+    bytes_ = 3 * 27 * 8 * nn + 2 * 8 * s.ndof + 8 * nn + (8 * 9) * NE
+    return {"kernel": "coupled JVP (k_jvp_macro + k_jvp_particle)", "ms": ms, "bytes": bytes_,
+            "gbs": bytes_ / (ms * 1e-3) / 1e9}
+
+
+def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0):
+    """The oracle's plain block-preconditioned FGMRES on a bounded sample of
+    the workload: a 16x16 lateral column block of the 128x128x96 cube (same
+    z layering, spacings, N_c and physics), scaled to the full workload by
+    the number of unknowns (linear solves/s x sample DoF / full DoF)."""
+    import numpy as np
+    from p4d_inputs import make_box_case
+    from oracle.fe import Disc
+    from oracle.krylov import LinearSolve
+    L = 100e-6 * sample_lat / 128
+    case = make_box_case(sample_lat, sample_lat, (40, 16, 40), L, (100e-6, 25e-6, 100e-6), 20, 1002)
+    d = Disc(case["mesh"], case["params"])
+    st = d.state_from_case(case["state"])
+    t0 = time.perf_counter()
+    n = 0
+    its_tot = 0
+    while True:
+        ls = LinearSolve(d, st)
+        _, its, _ = ls.fgmres(rtol=1e-8)
+        n += 1
+        its_tot += its
+        if time.perf_counter() - t0 > seconds_hint * 0.5 or n >= 3:
+            break
+    dt = (time.perf_counter() - t0) / n
+    return {"sample_dof": d.ndof, "s_per_solve": dt, "iters_per_solve": its_tot / n, "solves": n,
+            "scaled_solves_per_s": (1.0 / dt) * d.ndof / full_dof}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "gpu":
+            dist.init_process_group("nccl")
+        else:
+            if rank != 0:
+                return
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reference_main(args)
+        return
+    r = gpu_leg(args, rank, world, local)
+    if rank != 0:
+        return
+    pk, src = peaks()
+    peak = pk.get("hbm_gbs", 6800.0)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        try:
+            import multiprocessing as mp
+            cores = os.cpu_count()
+            c = cpu_oracle_leg(r["ndof"])
+            cpu = {"value": c["scaled_solves_per_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": "oracle FGMRES (BJ, V(2,2), FP64) on a 16x16x96 column block of the cube128 "
+                             "workload (%d unknowns, %.1f s/solve, %.1f its/solve), scaled by unknowns"
+                             % (c["sample_dof"], c["s_per_solve"], c["iters_per_solve"])}
+        except Exception as e:  # pragma: no cover
+            cpu = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "failed: %s" % e}
+    out = {
+        "metric": METRIC,
+        "value": r["solves_per_s"],
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 outer / f32 preconditioner",
+        "data": "synthetic",
+        "config": {"workload": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40), N_c=20, "
+                               "seeded linearization state, REDUCED Schur mode, block Jacobi, V(2,2) Chebyshev, "
+                               "FGMRES(30) rtol 1e-8",
+                   "unknowns": r["ndof"], "l2": "inputs larger than L2 (Krylov basis and stencils > 129 MB)"},
+        "fgmres_iters_per_s": r["iters_per_s"],
+        "iters_per_solve": r["iters_per_solve"],
+        "dof_iters_per_s": r["iters_per_s"] * r["ndof"],
+        "rel_res": r["info"]["rel_res"],
+        "fp64_path": r["fp64"],
+        "e2e": {"value": 1e3 / r["e2e_ms"], "unit": "solves/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["kern"]["launches_per_step"] * args.steps,
+        "kernels_per_step": r["kern"]["top"],
+        "roofline": {"bound": "hbm", "achieved": r["roof"]["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": r["roof"]["gbs"] / peak, "traffic": None, "kernel": r["roof"]["kernel"],
+                     "peak_source": src},
+        "cpu_baseline": cpu,
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(out))
+
+
+def reference_main(args):
+    """--impl reference: the FP64 oracle (plain block-preconditioned FGMRES),
+    on the host cores, on bounded samples of the same workload."""
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    its = []
+    for _ in range(max(1, args.steps)):
+        c = cpu_oracle_leg(CUBE128_DOF, seconds_hint=10.0)
+        vals.append(c["scaled_solves_per_s"])
+        its.append(c["iters_per_solve"])
+        if time.perf_counter() - t0 > 150:
+            break
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 0,
+           "steps": len(vals), "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "cube128 (bounded 16x16x96 column samples, scaled by unknowns)"},
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "16x16x96 column block of cube128 per step"},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

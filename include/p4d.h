@@ -1,0 +1,195 @@
+/*
+ * p4d.h -- C ABI of the GB300 (sm_103a) block-preconditioned Newton-Krylov
+ * hot path of the pseudo-4D Doyle-Fuller-Newman (P4D DFN) battery model
+ * (Roy et al., "Scalable Preconditioners for the Pseudo-4D DFN Lithium-ion
+ * Battery Model", arXiv 2602.07225).
+ *
+ * Problem (paper sections 2-4): the backward-Euler step of the coupled
+ * electrode-level Q1 finite-element equations for phi_s, phi_e, c_e
+ * (eqs. phis-weak, phie-weak, ce-weak) and the per-particle radial finite
+ * differences for c_s (eqs. L1, L2, L0, LR, FD), linked by Butler-Volmer
+ * kinetics, is solved by Newton's method; every Newton linear system
+ * J(u) delta = -R(u) (section 4, eq. blocks) is solved by FGMRES,
+ * right-preconditioned by the block preconditioner of section 4
+ * (eqs. PJ / PGS): the particle blocks are inverted exactly per electrode
+ * node and eliminated onto the electrode fields by a Schur complement; the
+ * electrode-level blocks get one geometric multigrid V-cycle each.
+ *
+ * Geometry: a structured tensor-product hex mesh of nx*ny*nz elements.
+ * Node (i,j,k), 0<=i<=nx, ..., has index i + (nx+1)*(j + (ny+1)*k); element
+ * (i,j,k) has index i + nx*(j + ny*k).  The anode sits on the z = 0 side
+ * (grounded face Gamma_n, Dirichlet phi_s = 0 on the faces flagged in
+ * gamma_n), the cathode on the z = Lz side (applied current on the faces
+ * flagged in gamma_p).
+ *
+ * Unknown vector ("full layout", FP64, length ndof = 3*nnode + nelec*nc):
+ *   [ phi_s(nnode) | phi_e(nnode) | c_e(nnode) | c_s(nelec, nc) ]
+ * c_s is stored node-major: particle of electrode node e (0 <= e < nelec,
+ * electrode nodes numbered in increasing node index), radial node i
+ * (0 = centre, nc-1 = surface) at 3*nnode + e*nc + i.  phi_s carries an
+ * identity row at every node that is not an electrode node or that lies on
+ * Gamma_n; those values are read as 0 by every other row.
+ *
+ * Conventions
+ *  - Memory: pointers marked [host] are host memory, [device] are device
+ *    memory of the current CUDA device.  The caller owns every pointer it
+ *    passes; the library only reads/writes them during the call (or, for
+ *    asynchronous calls, until the handle's stream reaches that point).
+ *    The library owns its workspace, allocated in p4d_setup and freed in
+ *    p4d_destroy; no other call allocates device memory.
+ *  - Streams: work is issued on the stream given to p4d_setup (NULL = the
+ *    legacy default stream).  p4d_fgmres_solve / p4d_adjoint_solve
+ *    synchronize that stream before returning; the other calls are
+ *    asynchronous unless stated.
+ *  - Errors: every call returns a p4d_status; no device traps.  On
+ *    P4D_ERR_CUDA the handle should be destroyed.
+ *  - Threads: a handle is used by one host thread at a time; distinct
+ *    handles are independent.
+ */
+#ifndef P4D_H
+#define P4D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct p4d_ctx* p4d_handle;
+
+typedef enum {
+  P4D_OK = 0,
+  P4D_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, unsupported option */
+  P4D_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  P4D_ERR_OOM = 3,           /* device allocation failed (p4d_setup only) */
+  P4D_ERR_NOT_CONVERGED = 4, /* Krylov or Newton hit maxit; output = best iterate */
+  P4D_ERR_BREAKDOWN = 5,     /* Krylov breakdown before convergence */
+  P4D_ERR_NONFINITE = 6,     /* NaN/Inf met in a residual or Krylov scalar */
+  P4D_ERR_DOMAIN = 7,        /* c_surf outside (0, c_max) or c_e <= 0 */
+  P4D_ERR_TIMEOUT = 8        /* a bounded device-side wait expired */
+} p4d_status;
+
+/* Mesh and material layout (all [host]; copied during p4d_setup). */
+typedef struct {
+  int32_t nx, ny, nz;              /* elements per axis, each >= 1 */
+  const double* hx;                /* [nx] element widths along x (m) */
+  const double* hy;                /* [ny] */
+  const double* hz;                /* [nz] */
+  const uint8_t* region;           /* [nelem] 0 anode, 1 separator, 2 cathode, 3 electrolyte-only */
+  const double* eps;               /* [nelem] porosity eps (electrolyte volume fraction) */
+  const double* eps_s;             /* [nelem] active-material volume fraction (0 off-electrode) */
+  const double* Rs;                /* [nnode] particle radius (m), read at electrode nodes */
+  const double* Ds;                /* [nnode] solid diffusivity (m^2/s), read at electrode nodes */
+  const uint8_t* gamma_p;          /* [nx*ny] 1 = face (i,j) of the z = Lz boundary carries i_app */
+  const uint8_t* gamma_n;          /* [nx*ny] 1 = face (i,j) of the z = 0 boundary is grounded */
+  const double* rgrid;             /* [nc] radial nodes / R_s, rgrid[0] = 0, rgrid[nc-1] = 1, increasing */
+  int32_t nc;                      /* radial nodes per particle, 3 <= nc <= 32 */
+} p4d_mesh;
+
+/* Physics and solver options. */
+typedef struct {
+  /* constants (paper Appendix "Model Parameters") */
+  double F, R, T, tplus, brug, De, kappa;
+  double sigma_n, sigma_p, k_n, k_p, cmax_n, cmax_p, alpha;
+  double ocp_n[2], ocp_p[2];       /* linear OCP U(theta) = c0 + c1*theta per electrode */
+  double dt;                       /* backward-Euler step (s) */
+  double i_app;                    /* applied current density on Gamma_p (A/m^2), < 0 for discharge */
+  double diffpot_sign;             /* sign of the diffusion-potential term of eq. phie-weak (+1 as printed) */
+  /* solver */
+  int32_t precision;    /* 0: FP64 preconditioner; 1: FP32 preconditioner; 2: FP32 with BF16 coarse-level stencils */
+  int32_t combine;      /* 0: block Jacobi (eq. PJ); 1: block Gauss-Seidel (eq. PGS) */
+  int32_t order[3];     /* BGS order over {0 phi_s, 1 phi_e, 2 c_e}; default {1, 0, 2} */
+  int32_t restart;      /* FGMRES restart length m, 1 <= m <= 128 (paper: 30; 100 for the jelly roll) */
+  int32_t maxit;        /* maximum FGMRES iterations per solve */
+  int32_t mode;         /* 0: FULL (Krylov on all unknowns); 1: REDUCED (Krylov on the Schur system) */
+  int32_t cheb_degree;  /* Chebyshev smoothing steps before and after the coarse correction (>= 1) */
+  int32_t coarse_max;   /* coarsen while a level has more than this many nodes (>= 8) */
+  double cheb_ratio;    /* Chebyshev interval [lam/ratio, lam] on D^-1 A */
+  double rtol;          /* relative residual target of FGMRES in the scaled norm */
+} p4d_params;
+
+/* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */
+typedef struct {
+  const double *phis, *phie, *ce, *cs;
+  const double *ce_prev, *cs_prev;   /* previous backward-Euler time level */
+} p4d_state;
+
+/* Solve report ([host], written when the solve returns). */
+typedef struct {
+  int32_t iters;          /* FGMRES iterations (preconditioner applications) */
+  int32_t restarts;       /* restart cycles started */
+  int32_t status;         /* p4d_status of the solve */
+  int32_t reorth;         /* iterations that needed a second Gram-Schmidt pass */
+  double rel_res;         /* final ||s.(b - J x)|| / ||s.b|| (true residual, scaled norm) */
+  double rel_res_block[4];/* the same restricted to phi_s, phi_e, c_e, c_s rows */
+  double ms_total;        /* device time of the solve (CUDA events) */
+} p4d_info;
+
+/* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,
+   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10). */
+void p4d_params_default(p4d_params* p);
+
+/* Build a handle for one cell (paper sections 3-4): validates the mesh,
+   classifies nodes (electrode nodes = nodes of anode/cathode elements;
+   anode and cathode elements must not share a node), assembles the fixed
+   Q1 stiffness/mass stencils, plans the multigrid hierarchy and allocates
+   all workspace.  If state != NULL the Jacobian is linearized at it (as
+   p4d_jacobian_update).  stream: a cudaStream_t or NULL.
+   Errors: INVALID_ARG (sizes, options, anode/cathode contact), OOM, CUDA. */
+p4d_status p4d_setup(const p4d_mesh* mesh, const p4d_params* params, const p4d_state* state,
+                     void* stream, p4d_handle* out);
+
+/* Release all device memory of the handle (NULL is ignored). */
+void p4d_destroy(p4d_handle h);
+
+/* Sizes: nodes, electrode nodes, total unknowns, radial nodes ([host] outputs, any may be NULL). */
+p4d_status p4d_get_sizes(p4d_handle h, int64_t* nnode, int64_t* nelec, int64_t* ndof, int32_t* nc);
+
+/* Node index of every electrode node, increasing ([host] int32 array of nelec). */
+p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out);
+
+/* Change solver options (combine, order, restart, maxit, rtol, cheb_ratio,
+   cheb_degree, mode).  precision and coarse_max cannot change (INVALID_ARG). */
+p4d_status p4d_set_params(p4d_handle h, const p4d_params* params);
+
+/* Nonlinear residual R(u) (paper section 4, block residual [R_phis; R_phie;
+   R_ce; R_cs]) at `state` into r_out [device, ndof].  DOMAIN if a
+   concentration leaves the kinetics domain (r_out then undefined).
+   Synchronizes the stream (to report DOMAIN). */
+p4d_status p4d_residual(p4d_handle h, const p4d_state* state, double* r_out);
+
+/* Linearize at `state` (paper section 4, eq. blocks): Butler-Volmer
+   derivatives per electrode node, particle tridiagonals and their Schur
+   scalars, the Jacobi scaling, the Schur-corrected multigrid operators of
+   every level and the coarsest-level inverses.  Synchronizes the stream
+   (to report DOMAIN). */
+p4d_status p4d_jacobian_update(p4d_handle h, const p4d_state* state);
+
+/* y = J x (transpose = 0) or y = J^T x (transpose = 1), unscaled, full
+   layout, [device] x and y of ndof doubles, x != y.  Requires a prior
+   p4d_jacobian_update. */
+p4d_status p4d_jvp(p4d_handle h, const double* x, double* y, int transpose);
+
+/* z = P^-1 r, the block preconditioner of section 4 in the unscaled full
+   layout (transpose = 1: P^-T, used by the adjoint), [device] r, z of ndof
+   doubles, r != z. */
+p4d_status p4d_precond_apply(p4d_handle h, const double* r, double* z, int transpose);
+
+/* Solve J x = b by right-preconditioned FGMRES(m) to
+   ||s.(b - J x)|| <= rtol ||s.b|| (s: Jacobi scaling with per-field
+   balancing, see the design notes), [device] b and x (in: initial guess,
+   out: solution) of ndof doubles.  info may be NULL.  Returns OK,
+   NOT_CONVERGED (x = last iterate), BREAKDOWN or NONFINITE. */
+p4d_status p4d_fgmres_solve(p4d_handle h, const double* b, double* x, p4d_info* info);
+
+/* Adjoint solve J^T lam = g with the transposed block preconditioner,
+   same conventions as p4d_fgmres_solve. */
+p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_info* info);
+
+/* Human-readable name of a status. */
+const char* p4d_status_string(p4d_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P4D_H */

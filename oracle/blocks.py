@@ -171,6 +171,45 @@ class BlockPrecond:
                 done.append(f)
         return np.concatenate(z)
 
+    def macro_apply_transpose(self, rm):
+        """Transpose of macro_apply: the V-cycles are symmetric, block
+        Gauss-Seidel becomes upper triangular (reverse order, transposed
+        couplings)."""
+        if self.schur_lu is not None:
+            raise NotImplementedError
+        nn = self.disc.nn
+        r = [rm[f * nn:(f + 1) * nn] for f in range(3)]
+        z = [None] * 3
+        if self.combine == "additive":
+            for f in range(3):
+                z[f] = self.solvers[f](r[f])
+        else:
+            done = []
+            for f in reversed(self.order):
+                rhs = r[f].copy()
+                for g in done:
+                    rhs -= self.blocks[g][f].T @ z[g]
+                z[f] = self.solvers[f](rhs)
+                done.append(f)
+        return np.concatenate(z)
+
+    def apply_transpose(self, r):
+        """P^-T r: the transpose of ``apply`` (particle solves with T^T,
+        A_mc and A_cm exchanged and transposed)."""
+        m = 3 * self.disc.nn
+        NE, nc = self.disc.NE, self.disc.nc
+        loT = np.zeros_like(self.lo)
+        upT = np.zeros_like(self.up)
+        loT[:, 1:] = self.up[:, :-1]
+        upT[:, :-1] = self.lo[:, 1:]
+        rm, rc = r[:m], r[m:].reshape(NE, nc)
+        yc = thomas(loT, self.di, upT, rc)
+        rm2 = rm - self.Acm.T @ yc.ravel()
+        zm = self.macro_apply_transpose(rm2)
+        t = (self.Amc.T @ zm).reshape(NE, nc)
+        zc = yc - thomas(loT, self.di, upT, t)
+        return np.concatenate([zm, zc.ravel()])
+
     def apply(self, r):
         m = 3 * self.disc.nn
         NE, nc = self.disc.NE, self.disc.nc

@@ -108,7 +108,10 @@ class GMG:
 
     def vcycle(self, b, level=0):
         if level == self.nlevels - 1:
-            return sla.lu_solve(self.lu, b)
+            x = sla.lu_solve(self.lu, b)
+            if level == 0:
+                x[~self.mask0] = 0.0
+            return x
         A = self.A[level]
         x = chebyshev(A, self.dinv[level], b, np.zeros_like(b), self.degree, self.lam[level], self.ratio)
         r = b - A @ x

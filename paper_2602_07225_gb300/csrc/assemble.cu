@@ -1,0 +1,382 @@
+// Fixed stencil assembly, linearization (Butler-Volmer derivatives, particle
+// Schur scalars, Jacobi scaling) and the nonlinear residual.
+//
+// Q1 on boxes: for an element of widths (hx, hy, hz) and local corners
+// a, a' in {0,1} per axis, the 1D factors are
+//   stiffness  s(a,a') / h  with s = +1 (a == a'), -1 (a != a')
+//   mass       h m(a,a')    with m = 1/3 (a == a'), 1/6 (a != a')
+// so the element stiffness entry is vol * (s_x/hx^2 m_y m_z + m_x s_y/hy^2 m_z
+// + m_x m_y s_z/hz^2) and the mass entry vol * m_x m_y m_z (exact integrals of
+// the trilinear basis).  Per node the contributions of its <= 8 elements are
+// gathered into 27-point stencils (paper section 3, eqs. ce-weak, phie-weak,
+// phis-weak); these depend only on the mesh and dt and are built once.
+#include <cmath>
+#include <vector>
+#include "p4d_common.cuh"
+
+namespace p4d {
+namespace {
+
+struct Phys {
+  double brug, sigma_n, sigma_p, kappa, De, dt;
+};
+
+__global__ void k_assemble(Grid g, int nx, int ny, int nz, const double* __restrict__ hx,
+                           const double* __restrict__ hy, const double* __restrict__ hz,
+                           const uint8_t* __restrict__ region, const double* __restrict__ eps,
+                           const double* __restrict__ eps_s, const uint8_t* __restrict__ label, Phys ph,
+                           double* __restrict__ Jst, double* __restrict__ sfix) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int i = (int)(n % g.nnx);
+  const int j = (int)((n / g.nnx) % g.nny);
+  const int k = (int)(n / ((int64_t)g.nnx * g.nny));
+  double Ks[27], Kk[27], Cc[27], Mm[27];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) Ks[o] = Kk[o] = Cc[o] = Mm[o] = 0.0;
+  const bool act = label[n] & kLabActive;
+  double sdrop = 0.0, mlump = 0.0;
+  for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < 2; ++q)
+      for (int p = 0; p < 2; ++p) {
+        const int ei = i - 1 + p, ej = j - 1 + q, ek = k - 1 + s;
+        if (ei < 0 || ej < 0 || ek < 0 || ei >= nx || ej >= ny || ek >= nz) continue;
+        const int64_t e = ei + (int64_t)nx * (ej + (int64_t)ny * ek);
+        const double a = hx[ei], b = hy[ej], cz = hz[ek];
+        const double vol = a * b * cz;
+        const uint8_t r = region[e];
+        const double sig = (r == 0 || r == 2) ? pow(eps_s[e], ph.brug) * (r == 0 ? ph.sigma_n : ph.sigma_p) : 0.0;
+        const double epb = pow(eps[e], ph.brug);
+        const double kap = epb * ph.kappa;
+        const double Dd = epb * ph.De;
+        const double mcoef = eps[e] / ph.dt;
+        const int an = 1 - p, bn = 1 - q, cn = 1 - s;
+        for (int cc = 0; cc < 2; ++cc)
+          for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa) {
+              const int dx = p - 1 + aa, dy = q - 1 + bb, dz = s - 1 + cc;
+              const int o = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+              const double sx = aa == an ? 1.0 : -1.0, mx = aa == an ? 1.0 / 3.0 : 1.0 / 6.0;
+              const double sy = bb == bn ? 1.0 : -1.0, my = bb == bn ? 1.0 / 3.0 : 1.0 / 6.0;
+              const double sz = cc == cn ? 1.0 : -1.0, mz = cc == cn ? 1.0 / 3.0 : 1.0 / 6.0;
+              const double kf = vol * (sx / (a * a) * my * mz + mx * sy / (b * b) * mz + mx * my * sz / (cz * cz));
+              const double mf = vol * mx * my * mz;
+              if (sig > 0.0 && act) {
+                const int64_t nb = n + dx + (int64_t)g.nnx * (dy + (int64_t)g.nny * dz);
+                if (label[nb] & kLabActive) Ks[o] += sig * kf;
+                else sdrop -= sig * kf;
+              }
+              Kk[o] += kap * kf;
+              Cc[o] += mcoef * mf + Dd * kf;
+              Mm[o] += mcoef * mf;
+              mlump += mcoef * mf;
+            }
+      }
+  const int64_t nn = g.nn;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    Jst[(0 * 27 + o) * nn + n] = Ks[o];
+    Jst[(1 * 27 + o) * nn + n] = Kk[o];
+    Jst[(2 * 27 + o) * nn + n] = Cc[o];
+    Jst[(3 * 27 + o) * nn + n] = Mm[o];
+  }
+  sfix[0 * nn + n] = act ? sdrop : 1.0;
+  sfix[1 * nn + n] = 0.0;
+  sfix[2 * nn + n] = mlump;
+}
+
+// max |centre| over the nodes of one field (for the FP32 scaling)
+__global__ void k_maxdiag(const double* __restrict__ st, int64_t nn, unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(st[13 * nn + n]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+struct Kin {
+  double F, Rg, T, alpha, tau, i_app, gamma;
+  double k[2], cmax[2], u0[2], u1[2];
+};
+
+// Butler-Volmer (paper section 2, "Interfacial kinetics") at one electrode
+// node; returns false outside the domain of the exchange current.
+__device__ inline bool kinetics(const Kin& kn, int et, double phis, double phie, double ce, double cs,
+                                double& in, double& ge, double& gc, double& gs) {
+  const double cmax = kn.cmax[et];
+  if (!(ce > 0.0) || !(cs > 0.0) || !(cs < cmax)) {
+    in = ge = gc = gs = 0.0;
+    return false;
+  }
+  const double f = kn.F / (kn.Rg * kn.T);
+  const double al = kn.alpha;
+  const double eta = phis - phie - (kn.u0[et] + kn.u1[et] * cs / cmax);
+  double i0;
+  if (al == 0.5) i0 = kn.k[et] * sqrt(ce) * sqrt(cmax - cs) * sqrt(cs);
+  else i0 = kn.k[et] * pow(ce, al) * pow(cmax - cs, al) * pow(cs, 1.0 - al);
+  const double ea = exp(al * f * eta);
+  const double ec = exp(-(1.0 - al) * f * eta);
+  in = i0 * (ea - ec);
+  ge = i0 * f * (al * ea + (1.0 - al) * ec);
+  gc = al * in / ce;
+  gs = in * ((1.0 - al) / cs - al / (cmax - cs)) - ge * kn.u1[et] / cmax;
+  return true;
+}
+
+__global__ void k_node_ln(int64_t nn, const double* __restrict__ ce, double gamma, double* __restrict__ lnce,
+                          double* __restrict__ gdc, unsigned* flags) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const double c = ce[n];
+  if (!(c > 0.0)) {
+    atomicOr(flags, kFlagDomain);
+    lnce[n] = 0.0;
+    if (gdc) gdc[n] = 0.0;
+    return;
+  }
+  lnce[n] = log(c);
+  if (gdc) gdc[n] = gamma / c;
+}
+
+// Linearization per electrode node: kinetics derivatives, last pivot of the
+// particle tridiagonal T_j = M_j (I/dt - kap_j Lref) + e_N e_N^T M_j beta_j g_s
+// (z_j = 1 / pivot = (T_j^-1)_NN) and zeta_j = 1 - z_j g_s M_j beta_j.
+__global__ void k_linearize(int64_t NE, int nc, Kin kn, double dt, const int32_t* __restrict__ enode,
+                            const uint8_t* __restrict__ label, const uint8_t* __restrict__ etype,
+                            const double* __restrict__ phis, const double* __restrict__ phie,
+                            const double* __restrict__ ce, const double* __restrict__ cs,
+                            const double* __restrict__ Mj, const double* __restrict__ kapj,
+                            const double* __restrict__ betaj, const double* __restrict__ rref,
+                            double* __restrict__ in_, double* __restrict__ ge, double* __restrict__ gc,
+                            double* __restrict__ gs, double* __restrict__ zj, double* __restrict__ zeta,
+                            unsigned* flags) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= NE) return;
+  const int64_t n = enode[j];
+  const bool act = label[n] & kLabActive;
+  double a, b, c, d;
+  if (!kinetics(kn, etype[j], act ? phis[n] : 0.0, phie[n], ce[n], cs[j * nc + nc - 1], a, b, c, d))
+    atomicOr(flags, kFlagDomain);
+  in_[j] = a; ge[j] = b; gc[j] = c; gs[j] = d;
+  const double kap = kapj[j], M = Mj[j];
+  const double* lo = rref;
+  const double* di = rref + nc;
+  const double* up = rref + 2 * nc;
+  // scaled by 1/M: T/M = I/dt - kap Lref + e_N e_N^T beta g_s
+  double piv = 1.0 / dt - kap * di[0];
+  for (int i = 1; i < nc; ++i) {
+    double dii = 1.0 / dt - kap * di[i];
+    if (i == nc - 1) dii += betaj[j] * d;
+    const double l = -kap * lo[i];
+    const double u = -kap * up[i - 1];
+    piv = dii - l * u / piv;
+  }
+  const double z = 1.0 / (M * piv);
+  zj[j] = z;
+  zeta[j] = 1.0 - z * d * M * betaj[j];
+}
+
+// sqrt of the Jacobian diagonal per row (Krylov scaling).
+__global__ void k_diag(Grid g, int64_t NE, int nc, double tau, double dt, const double* __restrict__ Jst,
+                       const uint8_t* __restrict__ label, const int32_t* __restrict__ eidx,
+                       const double* __restrict__ Aj, const double* __restrict__ Mj,
+                       const double* __restrict__ kapj, const double* __restrict__ betaj,
+                       const double* __restrict__ rref, const double* __restrict__ ge,
+                       const double* __restrict__ gc, const double* __restrict__ gs, double* __restrict__ sqd) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nn = g.nn;
+  double d;
+  if (t < nn) {
+    const int64_t n = t;
+    const int32_t e = eidx[n];
+    d = (label[n] & kLabActive) ? Jst[(0 * 27 + 13) * nn + n] + Aj[e] * ge[e] : 1.0;
+    sqd[n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+    d = Jst[(1 * 27 + 13) * nn + n] + (e >= 0 ? Aj[e] * ge[e] : 0.0);
+    sqd[nn + n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+    d = Jst[(2 * 27 + 13) * nn + n] - (e >= 0 ? tau * Aj[e] * gc[e] : 0.0);
+    sqd[2 * nn + n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+  } else if (t < nn + NE * nc) {
+    const int64_t q = t - nn;
+    const int64_t e = q / nc;
+    const int i = (int)(q % nc);
+    d = Mj[e] * (1.0 / dt - kapj[e] * rref[nc + i]);
+    if (i == nc - 1) d += Mj[e] * betaj[e] * gs[e];
+    sqd[3 * nn + q] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+  }
+}
+
+template <typename F>
+__device__ inline double stencil_apply(const double* __restrict__ st, int64_t nn, const Grid& g, int64_t n,
+                                       int i, int j, int k, F val) {
+  double acc = 0.0;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
+    const int64_t m = n + dx + (int64_t)g.nnx * (dy + (int64_t)g.nny * dz);
+    acc += st[o * nn + n] * val(m);
+  }
+  return acc;
+}
+
+// Nonlinear residual (paper section 4, block residual) -- macro rows.
+__global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
+                                 const uint8_t* __restrict__ label, const int32_t* __restrict__ eidx,
+                                 const double* __restrict__ Aj, const double* __restrict__ gpw,
+                                 const double* __restrict__ phis, const double* __restrict__ phie,
+                                 const double* __restrict__ ce, const double* __restrict__ ce_prev,
+                                 const double* __restrict__ lnce, const double* __restrict__ rin,
+                                 double* __restrict__ r) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nn = g.nn;
+  if (n >= nn) return;
+  const int i = (int)(n % g.nnx);
+  const int j = (int)((n / g.nnx) % g.nny);
+  const int k = (int)(n / ((int64_t)g.nnx * g.nny));
+  const int32_t e = eidx[n];
+  const double ain = e >= 0 ? Aj[e] * rin[e] : 0.0;
+  const bool act = label[n] & kLabActive;
+  // phi_s: lifted stencil (entries to inactive nodes are zero)
+  if (act) {
+    const double s = stencil_apply(Jst + 0 * 27 * nn, nn, g, n, i, j, k, [&](int64_t m) {
+      return (label[m] & kLabActive) ? phis[m] : 0.0;
+    });
+    r[n] = s + ain - kn.i_app * gpw[n];
+  } else {
+    r[n] = phis[n];
+  }
+  const double se = stencil_apply(Jst + 1 * 27 * nn, nn, g, n, i, j, k,
+                                  [&](int64_t m) { return phie[m] + kn.gamma * lnce[m]; });
+  r[nn + n] = se - ain;
+  // mass part on (c_e - c_e_prev), diffusion part (C - M_eps/dt) on c_e: no cancellation between
+  // the two time levels
+  double sc = 0.0;
+  {
+    const double* Cc = Jst + 2 * 27 * nn;
+    const double* Mm = Jst + 3 * 27 * nn;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int ii = i + dx, jj = j + dy, kk = k + dz;
+      if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
+      const int64_t m = n + dx + (int64_t)g.nnx * (dy + (int64_t)g.nny * dz);
+      const double mo = Mm[o * nn + n];
+      sc += mo * (ce[m] - ce_prev[m]) + (Cc[o * nn + n] - mo) * ce[m];
+    }
+  }
+  r[2 * nn + n] = sc - kn.tau * ain;
+}
+
+__global__ void k_kinetics_only(int64_t NE, int nc, Kin kn, const int32_t* __restrict__ enode,
+                                const uint8_t* __restrict__ label, const uint8_t* __restrict__ etype,
+                                const double* __restrict__ phis, const double* __restrict__ phie,
+                                const double* __restrict__ ce, const double* __restrict__ cs,
+                                double* __restrict__ rin, unsigned* flags) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= NE) return;
+  const int64_t n = enode[j];
+  const bool act = label[n] & kLabActive;
+  double a, b, c, d;
+  if (!kinetics(kn, etype[j], act ? phis[n] : 0.0, phie[n], ce[n], cs[j * nc + nc - 1], a, b, c, d))
+    atomicOr(flags, kFlagDomain);
+  rin[j] = a;
+}
+
+// Particle rows: R_cs = M [(c - c_prev)/dt - kap Lref c] + e_N M beta i_n.
+__global__ void k_residual_particle(int64_t NE, int nc, double dt, const double* __restrict__ cs,
+                                    const double* __restrict__ cs_prev, const double* __restrict__ Mj,
+                                    const double* __restrict__ kapj, const double* __restrict__ betaj,
+                                    const double* __restrict__ rref, const double* __restrict__ rin,
+                                    double* __restrict__ r) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= NE * nc) return;
+  const int64_t e = q / nc;
+  const int i = (int)(q % nc);
+  const double* c = cs + e * nc;
+  double L = rref[nc + i] * c[i];
+  if (i > 0) L += rref[i] * c[i - 1];
+  if (i < nc - 1) L += rref[2 * nc + i] * c[i + 1];
+  double v = Mj[e] * ((c[i] - cs_prev[q]) / dt - kapj[e] * L);
+  if (i == nc - 1) v += Mj[e] * betaj[e] * rin[e];
+  r[q] = v;
+}
+
+Kin make_kin(const p4d_params& p) {
+  Kin k;
+  k.F = p.F; k.Rg = p.R; k.T = p.T; k.alpha = p.alpha; k.tau = (1.0 - p.tplus) / p.F;
+  k.i_app = p.i_app;
+  k.gamma = p.diffpot_sign * 2.0 * p.R * p.T * (1.0 - p.tplus) / p.F;
+  k.k[0] = p.k_n; k.k[1] = p.k_p;
+  k.cmax[0] = p.cmax_n; k.cmax[1] = p.cmax_p;
+  k.u0[0] = p.ocp_n[0]; k.u0[1] = p.ocp_p[0];
+  k.u1[0] = p.ocp_n[1]; k.u1[1] = p.ocp_p[1];
+  return k;
+}
+
+}  // namespace
+
+p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, const uint8_t* region) {
+  const int64_t nn = c->g.nn;
+  P4D_TRYS(dalloc_t(c, &c->Jst, (size_t)4 * 27 * nn));
+  P4D_TRYS(dalloc_t(c, &c->sfix, (size_t)3 * nn));
+  Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt};
+  k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
+                                                       eps, eps_s, c->label, ph, c->Jst, c->sfix);
+  P4D_TRY(cudaGetLastError());
+  unsigned long long* mx = nullptr;
+  P4D_TRYS(dalloc_t(c, &mx, 3));
+  P4D_TRY(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), c->stream));
+  for (int f = 0; f < 3; ++f)
+    k_maxdiag<<<4 * 152, kBlock, 0, c->stream>>>(c->Jst + (size_t)f * 27 * nn, nn, mx + f);
+  unsigned long long h[3];
+  P4D_TRY(cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  for (int f = 0; f < 3; ++f) {
+    double v;
+    memcpy(&v, &h[f], sizeof(double));
+    // power of two so that scaling is exact
+    c->scale_f[f] = v > 0 ? std::ldexp(1.0, -std::ilogb(v)) : 1.0;
+  }
+  return P4D_OK;
+}
+
+p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
+  const int64_t nn = c->g.nn, NE = c->NE;
+  const int nc = c->nc;
+  Kin kn = make_kin(c->prm);
+  P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
+  k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce, c->gdc, c->flags);
+  if (NE > 0)
+    k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->prm.dt, c->enode, c->label, c->etype,
+                                                        st->phis, st->phie, st->ce, st->cs, c->Mj, c->kapj,
+                                                        c->betaj, c->rref, c->in_, c->ge, c->gc, c->gs, c->zj,
+                                                        c->zeta, c->flags);
+  k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, c->prm.dt, c->Jst, c->label,
+                                                          c->eidx, c->Aj, c->Mj, c->kapj, c->betaj, c->rref,
+                                                          c->ge, c->gc, c->gs, c->sqd);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status residual(p4d_ctx* c, const p4d_state* st, double* r) {
+  const int64_t nn = c->g.nn, NE = c->NE;
+  const int nc = c->nc;
+  Kin kn = make_kin(c->prm);
+  P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
+  k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce_r, nullptr, c->flags);
+  if (NE > 0)
+    k_kinetics_only<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype, st->phis,
+                                                            st->phie, st->ce, st->cs, c->rin, c->flags);
+  k_residual_macro<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, kn, c->Jst, c->label, c->eidx, c->Aj, c->gpw,
+                                                             st->phis, st->phie, st->ce, st->ce_prev,
+                                                             c->lnce_r, c->rin, r);
+  if (NE > 0)
+    k_residual_particle<<<nblocks(NE * nc), kBlock, 0, c->stream>>>(NE, nc, c->prm.dt, st->cs, st->cs_prev, c->Mj,
+                                                                    c->kapj, c->betaj, c->rref, c->rin,
+                                                                    r + 3 * nn);
+  P4D_TRY(cudaGetLastError());
+  return check_flags(c);
+}
+
+}  // namespace p4d

@@ -1,0 +1,466 @@
+// Right-preconditioned flexible GMRES(m) (Saad 1993) in FP64 on the scaled
+// system s.J.s x^ = s.b (s_i = w_f / sqrt(J_ii)); the preconditioned
+// directions are stored unscaled (z_k = P^-1 (s^-1 v_k)), so that
+// x = x0 + sum_k y_k z_k and the operator is applied as s.(J z_k).
+//
+// Orthogonalisation: classical Gram-Schmidt with one full reorthogonalisation
+// ("twice is enough"), each pass a fused multi-dot over the basis with a
+// fixed-shape two-stage reduction (deterministic order).  The Hessenberg
+// column, Givens rotations and residual estimate are updated on the device by
+// one thread; the host reads one scalar per iteration.
+#include <cmath>
+#include <cstring>
+#include "p4d_common.cuh"
+
+namespace p4d {
+namespace {
+
+constexpr int kRedBlocks = 4 * 152;   // reduction grid: a multiple of the SM count
+constexpr int kRedThreads = 256;
+
+// partial[blk][i] = sum over the block's elements of V[i][n] * w[n] (i < kp1);
+// if with_ww, partial[blk][kp1] = sum w[n]^2.
+__global__ void __launch_bounds__(kRedThreads) k_mdot(const double* __restrict__ V, int64_t ldv, int kp1,
+                                                      const double* __restrict__ w, int64_t len, int with_ww,
+                                                      double* __restrict__ partial, int pstride) {
+  __shared__ double red[kRedThreads / 32][130];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nd = kp1 + (with_ww ? 1 : 0);
+  for (int i = threadIdx.x; i < (kRedThreads / 32) * 130; i += blockDim.x) (&red[0][0])[i] = 0.0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) * 4; base < len; base += stride) {
+    double wv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t n = base + threadIdx.x + (int64_t)q * blockDim.x;
+      wv[q] = n < len ? w[n] : 0.0;
+    }
+    for (int i = 0; i < nd; ++i) {
+      double acc = 0.0;
+      if (i < kp1) {
+        const double* v = V + (int64_t)i * ldv;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t n = base + threadIdx.x + (int64_t)q * blockDim.x;
+          if (n < len) acc += v[n] * wv[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += wv[q] * wv[q];
+      }
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) red[warp][i] += acc;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    double s = 0.0;
+    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[wv][i];
+    partial[(int64_t)blockIdx.x * pstride + i] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int pstride, int nd,
+                                  double* __restrict__ out) {
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * pstride + i];
+    out[i] = s;
+  }
+}
+
+// w[n] -= sum_i h[i] V[i][n]   (h on the device)
+__global__ void k_maxpy(const double* __restrict__ V, int64_t ldv, int kp1, const double* __restrict__ h,
+                        double* __restrict__ w, int64_t len, double sign) {
+  __shared__ double hs[130];
+  for (int i = threadIdx.x; i < kp1; i += blockDim.x) hs[i] = sign * h[i];
+  __syncthreads();
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[n];
+    for (int i = 0; i < kp1; ++i) acc -= hs[i] * V[(int64_t)i * ldv + n];
+    w[n] = acc;
+  }
+}
+
+// y = x * f(*sp): mode 0 f = s, mode 1 f = 1/s, mode 2 f = 1/sqrt(s) (0 if s == 0)
+__global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int64_t len,
+                        const double* __restrict__ sp, int mode) {
+  const double v = *sp;
+  const double s = mode == 0 ? v : (v != 0.0 ? (mode == 1 ? 1.0 / v : 1.0 / sqrt(v)) : 0.0);
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x)
+    y[n] = x[n] * s;
+}
+
+// Per-field squared norms of (b / sqrt(d)) over the 4 fields (c_s optional).
+__global__ void k_field_norms(const double* __restrict__ b, const double* __restrict__ sqd, int64_t nn, int64_t len,
+                              double* __restrict__ partial) {
+  __shared__ double red[4][kRedThreads / 32];
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
+    const int f = n < 3 * nn ? (int)(n / nn) : 3;
+    const double v = b[n] / sqd[n];
+    acc[f] += v * v;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int f = 0; f < 4; ++f) {
+    double a = acc[f];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) red[f][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[threadIdx.x][wv];
+    partial[blockIdx.x * 4 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_weights(const double* __restrict__ partial, int nblk, double* __restrict__ wf, double* bn2) {
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[b * 4 + f];
+    wf[f] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    bn2[f] = s;
+    tot += s > 0.0 ? 1.0 : 0.0;
+  }
+  bn2[4] = tot;
+}
+
+// Per-field squared norms of an already scaled vector.
+__global__ void k_field_norms_plain(const double* __restrict__ r, int64_t nn, int64_t len, double* __restrict__ partial) {
+  __shared__ double red[4][kRedThreads / 32];
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
+    const int f = n < 3 * nn ? (int)(n / nn) : 3;
+    acc[f] += r[n] * r[n];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int f = 0; f < 4; ++f) {
+    double a = acc[f];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) red[f][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[threadIdx.x][wv];
+    partial[blockIdx.x * 4 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_sum4(const double* __restrict__ partial, int nblk, double* out) {
+  if (threadIdx.x >= 4) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[b * 4 + threadIdx.x];
+  out[threadIdx.x] = s;
+}
+
+// Hessenberg layout in hs: H[(m+1) x m] column-major, cs[m], sn[m], g[m+1], y[m], misc
+struct HLay {
+  int m;
+  int H, cs, sn, g, y, misc;
+};
+HLay hlay(int m) {
+  HLay L;
+  L.m = m;
+  L.H = 0;
+  L.cs = (m + 1) * m;
+  L.sn = L.cs + m;
+  L.g = L.sn + m;
+  L.y = L.g + m + 1;
+  L.misc = L.y + m;
+  return L;
+}
+// misc: [0] h1 (m+1) ... we keep separate small arrays after misc:
+//   misc+0 .. misc+m       : h1 (first-pass coefficients, then column)
+//   misc+m+1 .. misc+2m+1  : h2 (second pass)
+//   misc+2m+2              : ||w||^2 after the second pass (or first pass)
+//   misc+2m+3              : residual estimate |g_{k+1}|
+//   misc+2m+4              : status (0 ok, 1 breakdown, 2 nonfinite)
+//   misc+2m+5              : beta (initial residual norm)
+
+__global__ void k_init_cycle(double* hs, HLay L, int64_t unused) {
+  if (threadIdx.x != 0) return;
+  const double* nrm2 = hs + L.misc + 2 * L.m + 2;
+  const double beta = sqrt(*nrm2);
+  for (int i = 0; i <= L.m; ++i) hs[L.g + i] = 0.0;
+  hs[L.g] = beta;
+  hs[L.misc + 2 * L.m + 5] = beta;
+  hs[L.misc + 2 * L.m + 3] = beta;
+}
+
+// Column k: h = h1 + h2, h_{k+1,k} = ||w||, previous rotations, new rotation.
+__global__ void k_givens(double* hs, HLay L, int k) {
+  if (threadIdx.x != 0) return;
+  const int m = L.m;
+  double* H = hs + L.H;
+  double* cs = hs + L.cs;
+  double* sn = hs + L.sn;
+  double* g = hs + L.g;
+  const double* h1 = hs + L.misc;
+  const double* h2 = hs + L.misc + m + 1;
+  const double nw = sqrt(hs[L.misc + 2 * m + 2]);
+  double* col = H + (int64_t)k * (m + 1);
+  for (int i = 0; i <= k; ++i) col[i] = h1[i] + h2[i];
+  col[k + 1] = nw;
+  for (int i = 0; i < k; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[k], col[k + 1]);
+  double status = 0.0;
+  if (!(den > 0.0) || !isfinite(den)) {
+    cs[k] = 1.0; sn[k] = 0.0;
+    status = isfinite(den) ? 1.0 : 2.0;
+  } else {
+    cs[k] = col[k] / den;
+    sn[k] = col[k + 1] / den;
+    col[k] = den;
+    col[k + 1] = 0.0;
+  }
+  g[k + 1] = -sn[k] * g[k];
+  g[k] = cs[k] * g[k];
+  hs[L.misc + 2 * m + 3] = fabs(g[k + 1]);
+  if (nw == 0.0 && status == 0.0) status = 1.0;   // happy breakdown: exact solution in the space
+  if (!isfinite(g[k + 1])) status = 2.0;
+  hs[L.misc + 2 * m + 4] = status;
+}
+
+__global__ void k_backsolve(double* hs, HLay L, int kk) {
+  if (threadIdx.x != 0) return;
+  const int m = L.m;
+  const double* H = hs + L.H;
+  const double* g = hs + L.g;
+  double* y = hs + L.y;
+  for (int i = kk - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < kk; ++j) s -= H[(int64_t)j * (m + 1) + i] * y[j];
+    const double d = H[(int64_t)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// Reduced-mode condensation / back-substitution helpers (per node).
+__global__ void k_condense(Grid g, int nc, double tau, const int32_t* __restrict__ eidx,
+                           const uint8_t* __restrict__ label, const double* __restrict__ Aj,
+                           const double* __restrict__ Mj, const double* __restrict__ betaj,
+                           const double* __restrict__ ge, const double* __restrict__ gc,
+                           const double* __restrict__ gs, const double* __restrict__ b,
+                           const double* __restrict__ yc, double* __restrict__ bm, int trans) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nn = g.nn;
+  if (n >= nn) return;
+  const int32_t e = eidx[n];
+  double r0 = b[n], r1 = b[nn + n], r2 = b[2 * nn + n];
+  if (e >= 0) {
+    const bool act = label[n] & kLabActive;
+    const double A = Aj[e];
+    const double yN = yc[(int64_t)e * nc + nc - 1];
+    if (!trans) {
+      const double gsv = gs[e];
+      if (act) r0 -= A * gsv * yN;
+      r1 -= -A * gsv * yN;
+      r2 -= -tau * A * gsv * yN;
+    } else {
+      const double mb = Mj[e] * betaj[e];
+      if (act) r0 -= mb * ge[e] * yN;
+      r1 -= mb * (-ge[e]) * yN;
+      r2 -= mb * gc[e] * yN;
+    }
+  }
+  bm[n] = r0;
+  bm[nn + n] = r1;
+  bm[2 * nn + n] = r2;
+}
+
+__global__ void k_surface_coupling(int64_t NE, double tau, const int32_t* __restrict__ enode, int64_t nn,
+                                   const uint8_t* __restrict__ label, const double* __restrict__ Aj,
+                                   const double* __restrict__ Mj, const double* __restrict__ betaj,
+                                   const double* __restrict__ ge, const double* __restrict__ gc,
+                                   const double* __restrict__ gs, const double* __restrict__ xm,
+                                   double* __restrict__ tN, int trans) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= NE) return;
+  const int64_t n = enode[e];
+  const bool act = label[n] & kLabActive;
+  if (!trans) {
+    tN[e] = Mj[e] * betaj[e] * ((act ? ge[e] * xm[n] : 0.0) - ge[e] * xm[nn + n] + gc[e] * xm[2 * nn + n]);
+  } else {
+    const double A = Aj[e];
+    tN[e] = gs[e] * ((act ? A * xm[n] : 0.0) - A * xm[nn + n] - tau * A * xm[2 * nn + n]);
+  }
+}
+
+struct Reducer {
+  p4d_ctx* c;
+  int nblk(int64_t len) const {
+    const int64_t want = (len + (int64_t)kRedThreads * 4 - 1) / ((int64_t)kRedThreads * 4);
+    return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, want));
+  }
+  // out[0..kp1) = V^T w, out[kp1] = w.w (optional)
+  void mdot(const double* V, int64_t ldv, int kp1, const double* w, int64_t len, bool ww, double* out) {
+    const int nb = nblk(len);
+    const int ps = 132;
+    k_mdot<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, kp1, w, len, ww ? 1 : 0, c->part, ps);
+    k_reduce_partials<<<1, 256, 0, c->stream>>>(c->part, nb, ps, kp1 + (ww ? 1 : 0), out);
+  }
+};
+
+}  // namespace
+
+p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
+  const int64_t nn = c->g.nn;
+  const bool full = c->prm.mode == 0;
+  const int64_t len = full ? c->ndof : 3 * nn;
+  const int m = std::min(c->prm.restart, c->mcap);
+  const HLay L = hlay(c->mcap);
+  double* hs = c->hs;
+  Reducer R{c};
+  cudaEvent_t ev0, ev1;
+  P4D_TRY(cudaEventCreate(&ev0));
+  P4D_TRY(cudaEventCreate(&ev1));
+  P4D_TRY(cudaEventRecord(ev0, c->stream));
+  const double tau = (1.0 - c->prm.tplus) / c->prm.F;
+  const unsigned gb = (unsigned)std::min<int64_t>(4 * 152 * 4, (int64_t)nblocks(len));
+
+  // per-field weights from the full right-hand side
+  {
+    const int nb = kRedBlocks;
+    k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->sqd, nn, c->ndof, c->part);
+    k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->wf, hs + L.misc + 2 * L.m + 8);
+  }
+  const double* bk = b;            // Krylov right-hand side (unscaled)
+  if (!full) {
+    // b_m' = b_m - A_mc T^-1 b_c
+    P4D_TRYS(particle_solve64(c, b + 3 * nn, c->tmp + 3 * nn, nullptr, trans));
+    k_condense<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->nc, tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj,
+                                                      c->ge, c->gc, c->gs, b, c->tmp + 3 * nn, c->bred, trans);
+    bk = c->bred;
+  }
+  // ||s.b_k|| = sqrt(sum_f w_f^2 ||(b_k / sqrt(d))_f||^2)
+  double bnorm = 0.0;
+  {
+    k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(bk, c->sqd, nn, len, c->part);
+    k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
+    P4D_TRY(cudaMemcpyAsync(c->hs_h, hs + L.misc + 2 * L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
+    P4D_TRY(cudaStreamSynchronize(c->stream));
+    const double* bn2 = c->hs_h;        // full-b field norms^2 (weights)
+    const double* bk2 = c->hs_h + 8;    // Krylov-rhs field norms^2
+    for (int f = 0; f < (full ? 4 : 3); ++f) {
+      const double wf = bn2[f] > 0 ? 1.0 / std::sqrt(bn2[f]) : 1.0;
+      bnorm += wf * wf * bk2[f];
+    }
+    bnorm = std::sqrt(bnorm);
+  }
+  int iters = 0, restarts = 0, reorth = 0;
+  p4d_status st = P4D_ERR_NOT_CONVERGED;
+  double est = 1.0;
+  if (bnorm == 0.0) {
+    P4D_TRY(cudaMemsetAsync(x, 0, sizeof(double) * c->ndof, c->stream));
+    st = P4D_OK;
+    est = 0.0;
+  }
+  double* misc = hs + L.misc;
+  while (st == P4D_ERR_NOT_CONVERGED && iters < c->prm.maxit) {
+    ++restarts;
+    // V0 = s.(b_k - A x)
+    if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
+    else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
+    R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
+    k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, 0);
+    k_scale<<<gb, kBlock, 0, c->stream>>>(c->V, c->V, len, misc + 2 * L.m + 5, 1);
+    P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    P4D_TRY(cudaStreamSynchronize(c->stream));
+    const double beta = c->hs_h[0];
+    est = beta / bnorm;
+    if (!std::isfinite(beta)) { st = P4D_ERR_NONFINITE; break; }
+    if (beta <= c->prm.rtol * bnorm) { st = P4D_OK; break; }
+    int kk = 0;
+    for (int k = 0; k < m && iters < c->prm.maxit; ++k) {
+      double* vk = c->V + (int64_t)k * len;
+      double* zk = c->Z + (int64_t)k * len;
+      double* w = c->V + (int64_t)(k + 1) * len;
+      if (full) P4D_TRYS(precond_full(c, vk, zk, trans, true));
+      else P4D_TRYS(precond_macro(c, vk, zk, trans, true));
+      if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
+      else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
+      // CGS, twice
+      R.mdot(c->V, len, k + 1, w, len, false, misc);
+      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc, w, len, 1.0);
+      R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1);
+      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0);
+      ++reorth;
+      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2);
+      k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
+      // v_{k+1} = w / h_{k+1,k}
+      k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
+      P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      P4D_TRY(cudaStreamSynchronize(c->stream));
+      ++iters;
+      kk = k + 1;
+      est = c->hs_h[0] / bnorm;
+      const double stt = c->hs_h[1];
+      if (stt == 2.0) { st = P4D_ERR_NONFINITE; break; }
+      if (est <= c->prm.rtol) { st = P4D_OK; break; }
+      if (stt == 1.0) { st = P4D_OK; break; }
+    }
+    if (kk > 0) {
+      k_backsolve<<<1, 1, 0, c->stream>>>(hs, L, kk);
+      // x += Z y  (k_maxpy computes w -= sum h_i V_i; use sign -1)
+      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->Z, len, kk, hs + L.y, x, len, -1.0);
+    }
+    if (st == P4D_ERR_NONFINITE) break;
+    if (st == P4D_OK) {
+      // confirm with the true residual
+      if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
+      else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
+      R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
+      P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      P4D_TRY(cudaStreamSynchronize(c->stream));
+      est = std::sqrt(c->hs_h[0]) / bnorm;
+      if (!(est <= c->prm.rtol) && iters < c->prm.maxit) st = P4D_ERR_NOT_CONVERGED;
+      if (!std::isfinite(est)) st = P4D_ERR_NONFINITE;
+    }
+  }
+  if (!full) {
+    // x_c = T^-1 (b_c - A_cm x_m)
+    k_surface_coupling<<<nblocks(std::max<int64_t>(1, c->NE)), kBlock, 0, c->stream>>>(
+        c->NE, tau, c->enode, nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, x, c->tloc, trans);
+    P4D_TRYS(particle_solve64(c, b + 3 * nn, x + 3 * nn, c->tloc, trans));
+  }
+  // final true residual of the full system in the scaled norm
+  P4D_TRYS(jvp_full(c, x, c->r0, trans, b, true));
+  k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
+  k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, misc + 2 * L.m + 24);
+  P4D_TRY(cudaEventRecord(ev1, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 8, sizeof(double) * 24, cudaMemcpyDeviceToHost, c->stream));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = iters;
+    info->restarts = restarts;
+    info->status = st;
+    info->reorth = reorth;
+    const double* bn2 = c->hs_h;          // field norms^2 of b/sqd (weights: 1/sqrt)
+    const double* rr = c->hs_h + 16;      // field norms^2 of s.(b - Jx)
+    double tot_r = 0.0, tot_b = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      info->rel_res_block[f] = bn2[f] > 0 ? std::sqrt(rr[f]) : std::sqrt(rr[f]);
+      tot_r += rr[f];
+      tot_b += bn2[f] > 0 ? 1.0 : 0.0;
+    }
+    info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
+    info->ms_total = ms;
+  }
+  return st;
+}
+
+}  // namespace p4d

@@ -1,0 +1,857 @@
+// Geometric multigrid on the Schur-reduced electrode blocks (paper section 4:
+// one V-cycle approximates each electrode-level block inverse; the paper uses
+// BoomerAMG, here the structured hex grid gives the hierarchy directly).
+//
+// Hierarchies h: 0 phi_s anode, 1 phi_s cathode, 2 phi_e, 3 c_e.  The two
+// electrodes' phi_s never couple, and the thin separator leaves no coarse
+// grid that could represent both electrodes' near-constant modes, so phi_s
+// gets one masked hierarchy per electrode (they share the level-0 arrays).
+//
+// Per level: trilinear prolongation P (rows of masked-out fine nodes zero),
+// Galerkin operators A_{l+1} = P^T A_l P split into a fixed part (built once
+// at setup from the fixed stencils) and a linearization-dependent part
+// (Schur/reaction row sums, rebuilt per Newton step), Chebyshev smoothing on
+// D^-1 A over [lam/ratio, lam] (lam: Gershgorin bound), and an explicit FP64
+// inverse on the coarsest level.  Stencils are in difference form (slot 13
+// = row sum), see p4d_common.cuh.
+#include <algorithm>
+#include <cmath>
+#include "p4d_common.cuh"
+
+namespace p4d {
+namespace {
+
+template <typename T> __device__ __forceinline__ T fromd(double v);
+template <> __device__ __forceinline__ double fromd<double>(double v) { return v; }
+template <> __device__ __forceinline__ float fromd<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 fromd<__nv_bfloat16>(double v) {
+  return __float2bfloat16((float)v);
+}
+template <typename T> __device__ __forceinline__ float tof(T v) { return (float)v; }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+struct LevelDims {
+  int nnx, nny, nnz;
+  int64_t n;
+};
+
+struct HList {
+  int h[kNH];
+};
+
+__device__ __forceinline__ void node_ijk(const LevelDims& d, int64_t n, int& i, int& j, int& k) {
+  i = (int)(n % d.nnx);
+  j = (int)((n / d.nnx) % d.nny);
+  k = (int)(n / ((int64_t)d.nnx * d.nny));
+}
+
+// Fine nodes of the support of coarse node C along one axis: f = 2C + t for a
+// coarsened axis (t in {-1,0,1}, weight 1 or 1/2), f = C otherwise.
+__device__ __forceinline__ int supp_lo(int coarsen) { return coarsen ? -1 : 0; }
+__device__ __forceinline__ int supp_hi(int coarsen) { return coarsen ? 1 : 0; }
+__device__ __forceinline__ double wt(int t) { return t == 0 ? 1.0 : 0.5; }
+
+// Coarse parents of fine index f along one axis: returns count (1 or 2),
+// parents p[] and weights w[].
+__device__ __forceinline__ int parents(int f, int coarsen, int* p, double* w) {
+  if (!coarsen) { p[0] = f; w[0] = 1.0; return 1; }
+  if ((f & 1) == 0) { p[0] = f >> 1; w[0] = 1.0; return 1; }
+  p[0] = f >> 1; p[1] = (f >> 1) + 1; w[0] = w[1] = 0.5; return 2;
+}
+
+// ---------------------------------------------------------------- masks
+__global__ void k_mask0(int64_t nn, const uint8_t* __restrict__ label, uint8_t* m0, uint8_t* m1, uint8_t* m2,
+                        uint8_t* m3) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const uint8_t l = label[n];
+  const bool act = l & kLabActive;
+  m0[n] = act && (l & kLabAnode);
+  m1[n] = act && (l & kLabCathode);
+  m2[n] = 1;
+  m3[n] = 1;
+}
+
+__global__ void k_mask_coarse(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const uint8_t> fm,
+                              Ptr4<uint8_t> cm) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (C >= cd.n) return;
+  int I, J, K;
+  node_ijk(cd, C, I, J, K);
+  uint8_t any = 0;
+  for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
+    for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
+      for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
+        const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
+        if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+        any |= fm.p[h][fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk)];
+      }
+  cm.p[h][C] = any ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- Galerkin
+// Source operator in difference form: off-diagonals O[o][n] (o != 13) and
+// row sums s[n] (slot 13, or a separate array at level 0).
+struct SrcOp {
+  const double* st;      // [27][n] (slot 13 ignored when rs != nullptr)
+  const double* rs;      // optional separate row sums [n]
+};
+
+// A_c = P^T diag(m) A diag(m) P for one hierarchy; writes difference form.
+// identity_out: coarse nodes without support get an identity row (fixed part)
+// or a zero row (variable part).
+__global__ void k_rap(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const double> fst,
+                      Ptr4<const double> frs, Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out,
+                      int identity_out) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (C >= cd.n) return;
+  double acc[27];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  double rsum = 0.0;
+  int I, J, K;
+  node_ijk(cd, C, I, J, K);
+  const double* st = fst.p[h];
+  const double* rs = frs.p[h];
+  const uint8_t* m = fm.p[h];
+  const int64_t fn = fd.n;
+  if (cm.p[h][C]) {
+    for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
+      for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
+        for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
+          const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
+          if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+          const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
+          if (!m[f]) continue;
+          const double wf = (cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0);
+          const double sf = rs ? rs[f] : st[13 * fn + f];
+          rsum += wf * sf;
+          // full-form diagonal of row f
+          double diag = sf;
+          for (int o = 0; o < 27; ++o)
+            if (o != 13) diag -= st[o * fn + f];
+          for (int o = 0; o < 27; ++o) {
+            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+            const int gi = fi + dx, gj = fj + dy, gk = fk + dz;
+            if (gi < 0 || gj < 0 || gk < 0 || gi >= fd.nnx || gj >= fd.nny || gk >= fd.nnz) continue;
+            const int64_t gidx = gi + (int64_t)fd.nnx * (gj + (int64_t)fd.nny * gk);
+            if (!m[gidx]) continue;
+            const double a = (o == 13 ? diag : st[o * fn + f]) * wf;
+            if (a == 0.0) continue;
+            int px[2], py[2], pz[2];
+            double wx[2], wy[2], wz[2];
+            const int nx_ = parents(gi, cx, px, wx), ny_ = parents(gj, cy, py, wy), nz_ = parents(gk, cz, pz, wz);
+            for (int c3 = 0; c3 < nz_; ++c3)
+              for (int c2 = 0; c2 < ny_; ++c2)
+                for (int c1 = 0; c1 < nx_; ++c1) {
+                  const int oo = (px[c1] - I + 1) + 3 * (py[c2] - J + 1) + 9 * (pz[c3] - K + 1);
+                  acc[oo] += a * wx[c1] * wy[c2] * wz[c3];
+                }
+          }
+        }
+  }
+  double* o_ = out.p[h];
+  const int64_t cn = cd.n;
+  if (!cm.p[h][C]) {
+    for (int o = 0; o < 27; ++o) o_[o * cn + C] = 0.0;
+    o_[13 * cn + C] = identity_out ? 1.0 : 0.0;
+    return;
+  }
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : acc[o];
+}
+
+// V_1 = P^T diag(m s) P (level-0 variable part is diagonal).
+__global__ void k_rap_diag(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const double> s,
+                           Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (C >= cd.n) return;
+  double acc[27];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  double rsum = 0.0;
+  int I, J, K;
+  node_ijk(cd, C, I, J, K);
+  const uint8_t* m = fm.p[h];
+  if (cm.p[h][C]) {
+    for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
+      for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
+        for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
+          const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
+          if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+          const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
+          if (!m[f]) continue;
+          const double wf = (cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0);
+          const double a = wf * s.p[h][f];
+          rsum += a;
+          int px[2], py[2], pz[2];
+          double wx[2], wy[2], wz[2];
+          const int nx_ = parents(fi, cx, px, wx), ny_ = parents(fj, cy, py, wy), nz_ = parents(fk, cz, pz, wz);
+          for (int c3 = 0; c3 < nz_; ++c3)
+            for (int c2 = 0; c2 < ny_; ++c2)
+              for (int c1 = 0; c1 < nx_; ++c1) {
+                const int oo = (px[c1] - I + 1) + 3 * (py[c2] - J + 1) + 9 * (pz[c3] - K + 1);
+                acc[oo] += a * wx[c1] * wy[c2] * wz[c3];
+              }
+        }
+  }
+  double* o_ = out.p[h];
+  const int64_t cn = cd.n;
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (cm.p[h][C] ? acc[o] : 0.0);
+}
+
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// Level 0: variable row sums, storage stencil slot 13, inverse diagonal, lam.
+template <typename TS, typename T>
+__global__ void k_level0_update(Grid g, double tau, const double* __restrict__ Jst, const double* __restrict__ sfix,
+                                const uint8_t* __restrict__ label, const int32_t* __restrict__ eidx,
+                                const double* __restrict__ Aj, const double* __restrict__ ge,
+                                const double* __restrict__ gc, const double* __restrict__ zeta, double s0,
+                                double s1, double s2, TS* st0, TS* st1, TS* st2, T* di0, T* di1, T* di2,
+                                double* __restrict__ svar, double* lam) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nn = g.nn;
+  if (n >= nn) return;
+  const int32_t e = eidx[n];
+  const uint8_t l = label[n];
+  const bool act = l & kLabActive;
+  double sv[3] = {0.0, 0.0, 0.0};
+  if (e >= 0) {
+    const double zA = zeta[e] * Aj[e];
+    if (act) sv[0] = zA * ge[e];
+    sv[1] = zA * ge[e];
+    sv[2] = -tau * zA * gc[e];
+  }
+  TS* sts[3] = {st0, st1, st2};
+  T* dis[3] = {di0, di1, di2};
+  const double sc[3] = {s0, s1, s2};
+  for (int f = 0; f < 3; ++f) {
+    const double* st = Jst + (size_t)f * 27 * nn;
+    const double s = sfix[f * nn + n] + sv[f];
+    double diag = s, absoff = 0.0;
+    if (f == 0 && !act) {
+      diag = 1.0;
+    } else {
+      for (int o = 0; o < 27; ++o)
+        if (o != 13) {
+          diag -= st[o * nn + n];
+          absoff += fabs(st[o * nn + n]);
+        }
+    }
+    svar[f * nn + n] = sv[f];
+    sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
+    if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);   // keep the smoother finite on a degenerate row
+    dis[f][n] = fromd<T>(1.0 / (sc[f] * diag));
+    const double gl = (absoff + fabs(diag)) / diag;
+    int h = f + 1;
+    if (f == 0) {
+      if (!act) continue;
+      h = (l & kLabAnode) ? 0 : 1;
+    }
+    atomic_max_pos(lam + h, gl);
+  }
+}
+
+// Level >= 1: A = F + V into storage precision, inverse diagonal and lam.
+template <typename TS, typename T>
+__global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const double> V, Ptr4<TS> st,
+                                Ptr4<T> dinv, Ptr4<const uint8_t> mask, double sc0, double sc1, double sc2,
+                                double sc3, double* lam) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (n >= d.n) return;
+  const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
+  const double* f = F.p[h];
+  const double* v = V.p[h];
+  double diag = 0.0, absoff = 0.0, s = 0.0;
+  for (int o = 0; o < 27; ++o) {
+    const double a = f[o * d.n + n] + v[o * d.n + n];
+    st.p[h][o * d.n + n] = fromd<TS>(sc * a);
+    if (o == 13) s = a;
+    else { diag -= a; absoff += fabs(a); }
+  }
+  diag += s;
+  if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
+  dinv.p[h][n] = fromd<T>(1.0 / (sc * diag));
+  if (mask.p[h][n]) atomic_max_pos(lam + h, (absoff + fabs(diag)) / diag);
+}
+
+// Dense scaled coarsest operator [n][n] (row major) from difference form.
+__global__ void k_dense(LevelDims d, Ptr4<const double> F, Ptr4<const double> V, double sc0, double sc1,
+                        double sc2, double sc3, double* out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (n >= d.n) return;
+  const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
+  double* A = out + (size_t)h * d.n * d.n;
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
+  for (int64_t m = 0; m < d.n; ++m) A[n * d.n + m] = 0.0;
+  double diag = 0.0;
+  for (int o = 0; o < 27; ++o) {
+    const double a = F.p[h][o * d.n + n] + V.p[h][o * d.n + n];
+    if (o == 13) { diag += a; continue; }
+    diag -= a;
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= d.nnx || jj >= d.nny || kk >= d.nnz) continue;
+    A[n * d.n + (ii + (int64_t)d.nnx * (jj + (int64_t)d.nny * kk))] = sc * a;
+  }
+  A[n * d.n + n] = sc * diag;
+}
+
+// Single-level hierarchy: dense scaled level-0 operator of hierarchy h from
+// the fixed stencil (off-diagonals), fixed + variable row sums and the mask
+// (masked-out rows/columns become identity).
+__global__ void k_dense0(Grid g, const double* __restrict__ Jst, const double* __restrict__ sfix,
+                         const double* __restrict__ svar, Ptr4<const uint8_t> mask, double sc0, double sc1,
+                         double sc2, double* out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  const int64_t nn = g.nn;
+  if (n >= nn) return;
+  const int f = h == 0 || h == 1 ? 0 : h - 1;
+  const double sc = f == 0 ? sc0 : (f == 1 ? sc1 : sc2);
+  double* A = out + (size_t)h * nn * nn;
+  for (int64_t m = 0; m < nn; ++m) A[n * nn + m] = 0.0;
+  if (!mask.p[h][n]) {
+    A[n * nn + n] = 1.0;
+    return;
+  }
+  const int i = (int)(n % g.nnx), j = (int)((n / g.nnx) % g.nny), k = (int)(n / ((int64_t)g.nnx * g.nny));
+  const double* st = Jst + (size_t)f * 27 * nn;
+  double diag = sfix[f * nn + n] + svar[f * nn + n];
+  for (int o = 0; o < 27; ++o) {
+    if (o == 13) continue;
+    const double a = st[o * nn + n];
+    diag -= a;
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
+    const int64_t m = ii + (int64_t)g.nnx * (jj + (int64_t)g.nny * kk);
+    if (mask.p[h][m]) A[n * nn + m] = sc * a;
+  }
+  A[n * nn + n] = sc * diag;
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting, one block per matrix.
+__global__ void k_gauss_jordan(int n, double* mats, double* work) {
+  double* A = mats + (size_t)blockIdx.x * n * n;
+  double* Inv = work + (size_t)blockIdx.x * n * n;
+  __shared__ int piv;
+  __shared__ double pval;
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) Inv[t] = (t / n == t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int col = 0; col < n; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      double best = fabs(A[(size_t)col * n + col]);
+      for (int r = col + 1; r < n; ++r) {
+        const double v = fabs(A[(size_t)r * n + col]);
+        if (v > best) { best = v; p = r; }
+      }
+      piv = p;
+      pval = A[(size_t)p * n + col];
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != col)
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        double a = A[(size_t)col * n + t]; A[(size_t)col * n + t] = A[(size_t)p * n + t]; A[(size_t)p * n + t] = a;
+        double b = Inv[(size_t)col * n + t]; Inv[(size_t)col * n + t] = Inv[(size_t)p * n + t]; Inv[(size_t)p * n + t] = b;
+      }
+    __syncthreads();
+    const double inv_p = pval != 0.0 ? 1.0 / pval : 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      A[(size_t)col * n + t] *= inv_p;
+      Inv[(size_t)col * n + t] *= inv_p;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+      const int r = (int)(t / n), cc = (int)(t % n);
+      if (r == col) continue;
+      const double f = A[(size_t)r * n + col];
+      if (cc != col) A[(size_t)r * n + cc] -= f * A[(size_t)col * n + cc];
+      Inv[(size_t)r * n + cc] -= f * Inv[(size_t)col * n + cc];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != col) A[(size_t)r * n + col] = 0.0;
+    __syncthreads();
+  }
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) A[t] = Inv[t];
+}
+
+// ---------------------------------------------------------------- cycle kernels
+template <typename TS, typename T>
+struct LvlPtrs {
+  const TS* st[kNH];
+  const T* dinv[kNH];
+  const uint8_t* mask[kNH];
+  const T* x[kNH];
+  T* xo[kNH];
+  const T* b[kNH];
+  T* r[kNH];
+  T* d[kNH];
+};
+
+template <typename TS, typename T>
+__device__ __forceinline__ T apply_row(const TS* __restrict__ st, const T* __restrict__ x, const LevelDims& dd,
+                                       int64_t n, int i, int j, int k) {
+  const T xn = x[n];
+  T acc = (T)tof(st[13 * dd.n + n]) * xn;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    if (o == 13) continue;
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
+    const int64_t m = n + dx + (int64_t)dd.nnx * (dy + (int64_t)dd.nny * dz);
+    acc += (T)tof(st[o * dd.n + n]) * (x[m] - xn);
+  }
+  return acc;
+}
+template <>
+__device__ __forceinline__ double apply_row<double, double>(const double* __restrict__ st,
+                                                            const double* __restrict__ x, const LevelDims& dd,
+                                                            int64_t n, int i, int j, int k) {
+  const double xn = x[n];
+  double acc = st[13 * dd.n + n] * xn;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    if (o == 13) continue;
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
+    const int64_t m = n + dx + (int64_t)dd.nnx * (dy + (int64_t)dd.nny * dz);
+    acc += st[o * dd.n + n] * (x[m] - xn);
+  }
+  return acc;
+}
+
+// One Chebyshev step (step index `step` of the recurrence), x_out = x + d.
+template <typename TS, typename T>
+__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const double* __restrict__ lam,
+                                              double ratio, int step, int first) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = hl.h[blockIdx.y];
+  if (n >= dd.n) return;
+  if (!P.mask[h][n]) return;
+  int i, j, k;
+  node_ijk(dd, n, i, j, k);
+  const double lm = lam[h];
+  const double alpha = lm / ratio, beta = lm;
+  const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  const double sigma = theta / delta;
+  T res = P.b[h][n];
+  if (!first) res -= apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
+  const T z = P.dinv[h][n] * res;
+  T dn;
+  if (step == 0) {
+    dn = z * (T)(1.0 / theta);
+  } else {
+    double rho = 1.0 / sigma, rho_new = rho;
+    for (int s = 1; s <= step; ++s) {
+      rho = rho_new;
+      rho_new = 1.0 / (2.0 * sigma - rho);
+    }
+    dn = (T)(rho_new * rho) * P.d[h][n] + (T)(2.0 * rho_new / delta) * z;
+  }
+  P.d[h][n] = dn;
+  P.xo[h][n] = (first ? (T)0 : P.x[h][n]) + dn;
+}
+
+template <typename TS, typename T>
+__global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = hl.h[blockIdx.y];
+  if (n >= dd.n) return;
+  if (!P.mask[h][n]) return;   // level-0 phi_s hierarchies share r: never write masked-out nodes
+  int i, j, k;
+  node_ijk(dd, n, i, j, k);
+  P.r[h][n] = P.b[h][n] - apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
+}
+
+template <typename T>
+__global__ void k_restrict(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const T> fr,
+                           Ptr4<const uint8_t> fm, Ptr4<T> cb, HList hl) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = hl.h[blockIdx.y];
+  if (C >= cd.n) return;
+  int I, J, K;
+  node_ijk(cd, C, I, J, K);
+  T acc = 0;
+  for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
+    for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
+      for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
+        const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
+        if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+        const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
+        if (!fm.p[h][f]) continue;
+        const T w = (T)((cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0));
+        acc += w * fr.p[h][f];
+      }
+  cb.p[h][C] = acc;
+}
+
+template <typename T>
+__global__ void k_prolong(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const T> cx_,
+                          Ptr4<const uint8_t> fm, Ptr4<T> fx, HList hl) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = hl.h[blockIdx.y];
+  if (f >= fd.n) return;
+  if (!fm.p[h][f]) return;
+  int i, j, k;
+  node_ijk(fd, f, i, j, k);
+  int px[2], py[2], pz[2];
+  double wx[2], wy[2], wz[2];
+  const int nx_ = parents(i, cx, px, wx), ny_ = parents(j, cy, py, wy), nz_ = parents(k, cz, pz, wz);
+  T acc = 0;
+  for (int c3 = 0; c3 < nz_; ++c3)
+    for (int c2 = 0; c2 < ny_; ++c2)
+      for (int c1 = 0; c1 < nx_; ++c1)
+        acc += (T)(wx[c1] * wy[c2] * wz[c3]) *
+               cx_.p[h][px[c1] + (int64_t)cd.nnx * (py[c2] + (int64_t)cd.nny * pz[c3])];
+  fx.p[h][f] += acc;
+}
+
+template <typename T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ inv, Ptr4<const T> b, Ptr4<const uint8_t> mask,
+                               Ptr4<T> x, HList hl) {
+  const int h = hl.h[blockIdx.y];
+  const double* A = inv + (size_t)h * n * n;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int cidx = 0; cidx < n; ++cidx) acc += A[(size_t)r * n + cidx] * (double)b.p[h][cidx];
+    if (mask.p[h][r]) x.p[h][r] = (T)acc;   // masked-out rows are never read (and may be shared)
+  }
+}
+
+size_t tsize(int precision, int level) {
+  if (precision == 0) return sizeof(double);
+  if (precision == 2 && level > 0) return sizeof(__nv_bfloat16);
+  return sizeof(float);
+}
+
+template <typename T>
+HList make_hl(const int* hs, int nhs) {
+  HList l{};
+  for (int i = 0; i < kNH; ++i) l.h[i] = i < nhs ? hs[i] : hs[0];
+  return l;
+}
+
+LevelDims dims(const MGLevel& L) { return LevelDims{L.nnx, L.nny, L.nnz, L.n}; }
+
+template <typename TS, typename T>
+LvlPtrs<TS, T> ptrs(const MGLevel& L) {
+  LvlPtrs<TS, T> P;
+  for (int h = 0; h < kNH; ++h) {
+    P.st[h] = (const TS*)L.st[h];
+    P.dinv[h] = (const T*)L.dinv[h];
+    P.mask[h] = L.mask[h];
+    P.x[h] = (const T*)L.x[h];
+    P.xo[h] = (T*)L.x2[h];
+    P.b[h] = (const T*)L.b[h];
+    P.r[h] = (T*)L.r[h];
+    P.d[h] = (T*)L.d[h];
+  }
+  return P;
+}
+
+void swap_x(MGLevel& L, const int* hs, int nhs) {
+  bool done[kNH] = {false, false, false, false};
+  for (int t = 0; t < nhs; ++t) {
+    int h = hs[t];
+    // level-0 hierarchies 0/1 alias one buffer pair: swap it once
+    if (L.x[h] == L.x[h ^ 1] && h < 2) {
+      if (done[0]) continue;
+      done[0] = done[1] = true;
+      std::swap(L.x[0], L.x2[0]);
+      L.x[1] = L.x[0];
+      L.x2[1] = L.x2[0];
+      continue;
+    }
+    if (done[h]) continue;
+    done[h] = true;
+    std::swap(L.x[h], L.x2[h]);
+  }
+}
+
+template <typename TS0, typename TS, typename T>
+p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
+  const int L = c->nlev;
+  const int deg = c->prm.cheb_degree;
+  const double ratio = c->prm.cheb_ratio;
+  HList hl = make_hl<T>(hs, nhs);
+  for (int l = 0; l < L - 1; ++l) {
+    MGLevel& A = c->lev[l];
+    MGLevel& B = c->lev[l + 1];
+    const dim3 grid(nblocks(A.n), nhs);
+    for (int s = 0; s < deg; ++s) {
+      if (l == 0) k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, A.lam, ratio, s, s == 0);
+      else k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, A.lam, ratio, s, s == 0);
+      swap_x(A, hs, nhs);
+    }
+    if (l == 0) k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl);
+    else k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl);
+    Ptr4<const T> fr;
+    Ptr4<const uint8_t> fm;
+    Ptr4<T> cb;
+    for (int h = 0; h < kNH; ++h) { fr.p[h] = (const T*)A.r[h]; fm.p[h] = A.mask[h]; cb.p[h] = (T*)B.b[h]; }
+    k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fr, fm, cb, hl);
+  }
+  {
+    MGLevel& C = c->lev[L - 1];
+    Ptr4<const T> b;
+    Ptr4<const uint8_t> m;
+    Ptr4<T> x;
+    for (int h = 0; h < kNH; ++h) { b.p[h] = (const T*)C.b[h]; m.p[h] = C.mask[h]; x.p[h] = (T*)C.x[h]; }
+    k_coarse_solve<T><<<dim3(std::max(1, (int)((C.n + 127) / 128)), nhs), 128, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    MGLevel& A = c->lev[l];
+    MGLevel& B = c->lev[l + 1];
+    Ptr4<const T> cxp;
+    Ptr4<const uint8_t> fm;
+    Ptr4<T> fx;
+    for (int h = 0; h < kNH; ++h) { cxp.p[h] = (const T*)B.x[h]; fm.p[h] = A.mask[h]; fx.p[h] = (T*)A.x[h]; }
+    const dim3 grid(nblocks(A.n), nhs);
+    k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, cxp, fm, fx, hl);
+    for (int s = 0; s < deg; ++s) {
+      if (l == 0) k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, A.lam, ratio, s, 0);
+      else k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, A.lam, ratio, s, 0);
+      swap_x(A, hs, nhs);
+    }
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- planning
+p4d_status mg_plan(p4d_ctx* c) {
+  const int prec = c->prm.precision;
+  const size_t tv = prec == 0 ? sizeof(double) : sizeof(float);
+  int nnx = c->g.nnx, nny = c->g.nny, nnz = c->g.nnz;
+  int L = 0;
+  while (true) {
+    MGLevel& lv = c->lev[L];
+    lv.nnx = nnx; lv.nny = nny; lv.nnz = nnz;
+    lv.n = (int64_t)nnx * nny * nnz;
+    const int cx = ((nnx - 1) % 2 == 0) && (nnx - 1) >= 2;
+    const int cy = ((nny - 1) % 2 == 0) && (nny - 1) >= 2;
+    const int cz = ((nnz - 1) % 2 == 0) && (nnz - 1) >= 2;
+    ++L;
+    if (lv.n <= c->prm.coarse_max || !(cx || cy || cz) || L >= kMaxLevels) break;
+    lv.cx = cx; lv.cy = cy; lv.cz = cz;
+    nnx = cx ? (nnx - 1) / 2 + 1 : nnx;
+    nny = cy ? (nny - 1) / 2 + 1 : nny;
+    nnz = cz ? (nnz - 1) / 2 + 1 : nnz;
+  }
+  c->nlev = L;
+  if (c->lev[L - 1].n > 4096) return P4D_ERR_INVALID_ARG;   // coarsest level too large for a dense inverse
+  for (int l = 0; l < L; ++l) {
+    MGLevel& lv = c->lev[l];
+    const int64_t n = lv.n;
+    const size_t ts = tsize(prec, l);
+    P4D_TRYS(dalloc_t(c, &lv.lam, kNH));
+    for (int h = 0; h < kNH; ++h) P4D_TRYS(dalloc_t(c, &lv.mask[h], n));
+    if (l == 0) {
+      // fields: phi_s (hierarchies 0,1 share), phi_e (2), c_e (3)
+      void *st[3], *di[3], *x[3], *x2[3], *b[3], *r[3], *d[3];
+      for (int f = 0; f < 3; ++f) {
+        P4D_TRYS(dalloc(c, &st[f], ts * 27 * n));
+        P4D_TRYS(dalloc(c, &di[f], tv * n));
+        P4D_TRYS(dalloc(c, &x[f], tv * n));
+        P4D_TRYS(dalloc(c, &x2[f], tv * n));
+        P4D_TRYS(dalloc(c, &b[f], tv * n));
+        P4D_TRYS(dalloc(c, &r[f], tv * n));
+        P4D_TRYS(dalloc(c, &d[f], tv * n));
+        P4D_TRY(cudaMemset(x[f], 0, tv * n));
+        P4D_TRY(cudaMemset(x2[f], 0, tv * n));
+        P4D_TRY(cudaMemset(b[f], 0, tv * n));
+        P4D_TRY(cudaMemset(d[f], 0, tv * n));
+      }
+      const int fh[kNH] = {0, 0, 1, 2};
+      for (int h = 0; h < kNH; ++h) {
+        lv.st[h] = st[fh[h]]; lv.dinv[h] = di[fh[h]]; lv.x[h] = x[fh[h]]; lv.x2[h] = x2[fh[h]];
+        lv.b[h] = b[fh[h]]; lv.r[h] = r[fh[h]]; lv.d[h] = d[fh[h]];
+      }
+      k_mask0<<<nblocks(n), kBlock, 0, c->stream>>>(n, c->label, lv.mask[0], lv.mask[1], lv.mask[2], lv.mask[3]);
+    } else {
+      P4D_TRYS(dalloc_t(c, &lv.Ffix, (size_t)kNH * 27 * n));
+      P4D_TRYS(dalloc_t(c, &lv.Vvar, (size_t)kNH * 27 * n));
+      for (int h = 0; h < kNH; ++h) {
+        P4D_TRYS(dalloc(c, &lv.st[h], ts * 27 * n));
+        P4D_TRYS(dalloc(c, &lv.dinv[h], tv * n));
+        P4D_TRYS(dalloc(c, &lv.x[h], tv * n));
+        P4D_TRYS(dalloc(c, &lv.x2[h], tv * n));
+        P4D_TRYS(dalloc(c, &lv.b[h], tv * n));
+        P4D_TRYS(dalloc(c, &lv.r[h], tv * n));
+        P4D_TRYS(dalloc(c, &lv.d[h], tv * n));
+        P4D_TRY(cudaMemset(lv.x[h], 0, tv * n));
+        P4D_TRY(cudaMemset(lv.x2[h], 0, tv * n));
+        P4D_TRY(cudaMemset(lv.d[h], 0, tv * n));
+      }
+      MGLevel& fl = c->lev[l - 1];
+      Ptr4<const uint8_t> fm;
+      Ptr4<uint8_t> cm;
+      for (int h = 0; h < kNH; ++h) { fm.p[h] = fl.mask[h]; cm.p[h] = lv.mask[h]; }
+      k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.cx, fl.cy, fl.cz, fm, cm);
+    }
+    if (l == L - 1) P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
+  }
+  // level-0 particle work and variable row sums
+  P4D_TRYS(dalloc(c, &c->yc, (prec == 0 ? sizeof(double) : sizeof(float)) * (size_t)std::max<int64_t>(1, c->NE) * c->nc));
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+namespace {
+template <typename TS>
+__global__ void k_level0_offdiag(Grid g, const double* __restrict__ Jst, double s0, double s1, double s2, TS* st0,
+                                 TS* st1, TS* st2) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int64_t nn = g.nn;
+  TS* sts[3] = {st0, st1, st2};
+  const double sc[3] = {s0, s1, s2};
+  for (int f = 0; f < 3; ++f)
+    for (int o = 0; o < 27; ++o)
+      if (o != 13) sts[f][o * nn + n] = fromd<TS>(sc[f] * Jst[((size_t)f * 27 + o) * nn + n]);
+}
+}  // namespace
+
+p4d_status mg_setup_fixed(p4d_ctx* c) {
+  const int prec = c->prm.precision;
+  MGLevel& l0 = c->lev[0];
+  if (prec == 0)
+    k_level0_offdiag<double><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
+                                                                  (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3]);
+  else
+    k_level0_offdiag<float><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
+                                                                 (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3]);
+  const int64_t nn = c->g.nn;
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    MGLevel& A = c->lev[l];
+    MGLevel& B = c->lev[l + 1];
+    Ptr4<const double> fst, frs;
+    Ptr4<const uint8_t> fm, cm;
+    Ptr4<double> out;
+    const int fh[kNH] = {0, 0, 1, 2};
+    for (int h = 0; h < kNH; ++h) {
+      if (l == 0) {
+        fst.p[h] = c->Jst + (size_t)fh[h] * 27 * nn;
+        frs.p[h] = c->sfix + (size_t)fh[h] * nn;
+      } else {
+        fst.p[h] = A.Ffix + (size_t)h * 27 * A.n;
+        frs.p[h] = nullptr;
+      }
+      fm.p[h] = A.mask[h];
+      cm.p[h] = B.mask[h];
+      out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
+    }
+    k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 1);
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status mg_update(p4d_ctx* c) {
+  const int prec = c->prm.precision;
+  const int64_t nn = c->g.nn;
+  const double tau = (1.0 - c->prm.tplus) / c->prm.F;
+  const double* sf = c->scale_f;
+  const double sch[kNH] = {sf[0], sf[0], sf[1], sf[2]};
+  double* svar = c->tmp;   // [3][nn] scratch (Krylov scratch is idle during an update)
+  for (int l = 0; l < c->nlev; ++l) P4D_TRY(cudaMemsetAsync(c->lev[l].lam, 0, kNH * sizeof(double), c->stream));
+  MGLevel& l0 = c->lev[0];
+  if (prec == 0)
+    k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
+        c->g, tau, c->Jst, c->sfix, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
+        (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3], (double*)l0.dinv[0], (double*)l0.dinv[2],
+        (double*)l0.dinv[3], svar, l0.lam);
+  else
+    k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
+        c->g, tau, c->Jst, c->sfix, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
+        (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3], (float*)l0.dinv[0], (float*)l0.dinv[2],
+        (float*)l0.dinv[3], svar, l0.lam);
+  const int fh[kNH] = {0, 0, 1, 2};
+  for (int l = 1; l < c->nlev; ++l) {
+    MGLevel& A = c->lev[l - 1];
+    MGLevel& B = c->lev[l];
+    Ptr4<const uint8_t> fm, cm;
+    Ptr4<double> out;
+    for (int h = 0; h < kNH; ++h) { fm.p[h] = A.mask[h]; cm.p[h] = B.mask[h]; out.p[h] = B.Vvar + (size_t)h * 27 * B.n; }
+    if (l == 1) {
+      Ptr4<const double> s;
+      for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
+      k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, s, fm, cm, out);
+    } else {
+      Ptr4<const double> fst, frs;
+      for (int h = 0; h < kNH; ++h) { fst.p[h] = A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
+      k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 0);
+    }
+    Ptr4<const double> F, V;
+    Ptr4<const uint8_t> m;
+    for (int h = 0; h < kNH; ++h) {
+      F.p[h] = B.Ffix + (size_t)h * 27 * B.n;
+      V.p[h] = B.Vvar + (size_t)h * 27 * B.n;
+      m.p[h] = B.mask[h];
+    }
+    const dim3 grid(nblocks(B.n), kNH);
+    if (prec == 0) {
+      Ptr4<double> st, di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (double*)B.st[h]; di.p[h] = (double*)B.dinv[h]; }
+      k_level_combine<double, double><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    } else if (prec == 1) {
+      Ptr4<float> st, di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (float*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
+      k_level_combine<float, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    } else {
+      Ptr4<__nv_bfloat16> st;
+      Ptr4<float> di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (__nv_bfloat16*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
+      k_level_combine<__nv_bfloat16, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    }
+  }
+  // coarsest: dense scaled operator and its inverse
+  MGLevel& C = c->lev[c->nlev - 1];
+  if (c->nlev == 1) {
+    Ptr4<const uint8_t> m;
+    for (int h = 0; h < kNH; ++h) m.p[h] = C.mask[h];
+    double* mats = C.inv;
+    double* work = C.inv + (size_t)kNH * C.n * C.n;
+    k_dense0<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(c->g, c->Jst, c->sfix, svar, m, sf[0], sf[1], sf[2],
+                                                                 mats);
+    k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
+  } else {
+    Ptr4<const double> F, V;
+    for (int h = 0; h < kNH; ++h) {
+      F.p[h] = C.Ffix + (size_t)h * 27 * C.n;
+      V.p[h] = C.Vvar + (size_t)h * 27 * C.n;
+    }
+    double* mats = C.inv;
+    double* work = C.inv + (size_t)kNH * C.n * C.n;
+    k_dense<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
+    k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs) {
+  switch (c->prm.precision) {
+    case 0: return vcycle_t<double, double, double>(c, hs, nhs);
+    case 1: return vcycle_t<float, float, float>(c, hs, nhs);
+    default: return vcycle_t<float, __nv_bfloat16, float>(c, hs, nhs);
+  }
+}
+
+}  // namespace p4d

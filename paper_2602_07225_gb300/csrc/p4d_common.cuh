@@ -1,0 +1,202 @@
+// Internal declarations shared by the CUDA translation units of libp4d.
+//
+// Data layout in device memory (one handle = one cell):
+//   node arrays      [nn]            x fastest (node (i,j,k) -> i + nnx*(j + nny*k))
+//   element arrays   [nelem]
+//   stencils         [27][nn]        SoA by offset o = (dx+1) + 3(dy+1) + 9(dz+1)
+//   electrode nodes  [NE]            SoA per quantity, c_s vectors [NE][nc]
+//   Krylov basis     [m+1][len]      FP64
+// Multigrid stencils are kept in "difference form": slot 13 (the centre)
+// holds the row sum s_n, the other 26 slots the off-diagonal entries, so that
+// (A x)_n = sum_{o != 13} A_o (x_{n+o} - x_n) + s_n x_n.  The row sums carry
+// the reaction/Schur terms that anchor the near-constant modes of the
+// potential blocks; keeping them apart keeps those modes exact in FP32/BF16.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include "p4d.h"
+
+#define P4D_TRY(x)                                   \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return P4D_ERR_CUDA;      \
+  } while (0)
+
+#define P4D_TRYS(x)                                  \
+  do {                                               \
+    p4d_status s_ = (x);                             \
+    if (s_ != P4D_OK) return s_;                     \
+  } while (0)
+
+namespace p4d {
+
+constexpr int kMaxNc = 32;
+constexpr int kMaxLevels = 16;
+constexpr int kNH = 4;            // multigrid hierarchies: phi_s anode, phi_s cathode, phi_e, c_e
+constexpr int kBlock = 256;
+
+// device error flags (bits)
+enum : unsigned {
+  kFlagDomain = 1u,
+  kFlagNonfinite = 2u,
+};
+
+// Node label bits
+enum : uint8_t {
+  kLabAnode = 1,       // node of an anode element
+  kLabCathode = 2,     // node of a cathode element
+  kLabDirichlet = 4,   // node of a grounded face (z = 0, gamma_n)
+  kLabActive = 8,      // phi_s unknown (electrode node, not grounded)
+};
+
+// Small POD bundles passed to kernels by value.
+struct Grid {
+  int nnx, nny, nnz;
+  int64_t nn;
+};
+
+template <typename T>
+struct Ptr4 {
+  T* p[kNH];
+};
+
+struct MGLevel {
+  int nnx = 0, nny = 0, nnz = 0;
+  int64_t n = 0;
+  int cx = 0, cy = 0, cz = 0;          // coarsen flags towards the next level
+  // FP64 fixed (linearization independent) operator, difference form [kNH][27][n]
+  double* Ffix = nullptr;
+  // FP64 linearization-dependent part (levels >= 1), difference form [kNH][27][n]
+  double* Vvar = nullptr;
+  // stencil in storage precision [kNH][27][n] (level 0: hierarchies 0/1 alias field phi_s)
+  void* st[kNH] = {nullptr, nullptr, nullptr, nullptr};
+  void* dinv[kNH] = {};                // [n] in compute precision
+  uint8_t* mask[kNH] = {};             // [n]
+  void* x[kNH] = {};                   // [n] compute precision (level 0: 0/1 alias)
+  void* x2[kNH] = {};                  // double buffer
+  void* b[kNH] = {};
+  void* r[kNH] = {};
+  void* d[kNH] = {};
+  double* lam = nullptr;               // [kNH] Gershgorin bound of D^-1 A
+  // coarsest level only: dense inverse [kNH][n][n] FP64
+  double* inv = nullptr;
+};
+
+}  // namespace p4d
+
+struct p4d_ctx {
+  // sizes
+  int nx = 0, ny = 0, nz = 0;
+  p4d::Grid g{};
+  int64_t nelem = 0, NE = 0, ndof = 0;
+  int nc = 0;
+  p4d_params prm{};
+  cudaStream_t stream = nullptr;
+  bool linearized = false;
+  std::vector<int32_t> enodes_h;
+  double scale_f[3] = {1, 1, 1};       // multigrid per-field scaling (FP32 range)
+
+  // owned allocations (freed in destroy)
+  std::vector<void*> allocs;
+
+  // mesh (device)
+  double *hx = nullptr, *hy = nullptr, *hz = nullptr;
+  uint8_t* label = nullptr;            // [nn]
+  int32_t* eidx = nullptr;             // [nn] electrode index or -1
+  int32_t* enode = nullptr;            // [NE] node index
+  double* gpw = nullptr;               // [nn] Gamma_p lumped face weights
+  double* Mj = nullptr;                // [NE] lumped electrode volume
+  double* Aj = nullptr;                // [NE] 3 S_j / R_j
+  double* kapj = nullptr;              // [NE] D_s / R_s^2
+  double* betaj = nullptr;             // [NE] flux factor of eq. LR
+  uint8_t* etype = nullptr;            // [NE] 0 anode, 1 cathode
+  double* rref = nullptr;              // [3][nc] reference radial operator (R = D = 1): lo, di, up
+  double beta_ref = 0.0;               // surface flux factor for R = 1
+
+  // fixed FP64 stencils [4][27][nn]: 0 K_sigma (lifted), 1 K_kappa, 2 C = M_eps/dt + K_D, 3 M_eps/dt
+  double* Jst = nullptr;
+  double* sfix = nullptr;              // [3][nn] fixed multigrid row sums per field
+
+  // linearization
+  double* lnce = nullptr;              // [nn] ln c_e
+  double* lnce_r = nullptr;            // [nn] ln c_e at the state of a residual evaluation
+  double* rin = nullptr;               // [NE] i_n at the state of a residual evaluation
+  double* gdc = nullptr;               // [nn] gamma / c_e
+  double* in_ = nullptr;               // [NE] reaction current
+  double* ge = nullptr;                // [NE]
+  double* gc = nullptr;
+  double* gs = nullptr;
+  double* zj = nullptr;                // [NE] (T_j^-1)_NN
+  double* zeta = nullptr;              // [NE] 1 - z_j g_s M_j beta_j
+  double* tloc = nullptr;              // [NE] node-local coupling scalar of the last operator application
+  double* sqd = nullptr;               // [ndof] sqrt(diag J)
+  double* wf = nullptr;                // [4] per-field Krylov weights (device)
+  unsigned* flags = nullptr;           // device error flags
+  unsigned* flags_h = nullptr;         // pinned host mirror
+
+  // multigrid
+  int nlev = 0;
+  p4d::MGLevel lev[p4d::kMaxLevels];
+  void* yc = nullptr;                  // [NE][nc] particle solve work (compute precision)
+
+  // Krylov workspace
+  int mcap = 0;                        // allocated restart capacity
+  int64_t kry_len = 0;                 // allocated vector length
+  double* V = nullptr;                 // [mcap+1][len]
+  double* Z = nullptr;                 // [mcap][len]
+  double* w = nullptr;                 // [len]
+  double* r0 = nullptr;                // [ndof]
+  double* tmp = nullptr;               // [ndof]
+  double* bred = nullptr;              // [ndof] reduced right-hand side / scratch
+  double* part = nullptr;              // [nparts][kry dots] partial sums
+  double* hs = nullptr;                // device Hessenberg / Givens state
+  double* hs_h = nullptr;              // pinned host mirror of small scalars
+};
+
+// ---------------------------------------------------------------- helpers
+namespace p4d {
+
+p4d_status dalloc(p4d_ctx* c, void** p, size_t bytes);
+template <typename T>
+inline p4d_status dalloc_t(p4d_ctx* c, T** p, size_t count) {
+  return dalloc(c, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+
+// ---- assembly / linearization (assemble.cu)
+p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, const uint8_t* region);
+p4d_status linearize(p4d_ctx* c, const p4d_state* st);
+p4d_status residual(p4d_ctx* c, const p4d_state* st, double* r_out);
+p4d_status check_flags(p4d_ctx* c);
+
+// ---- operator application (jvp.cu)
+// y[i] = sc_out[i] * ((b ? b[i] : 0) +/- (J x)[i]); sign = -1 with b for residual form.
+p4d_status jvp_full(p4d_ctx* c, const double* x, double* y, int transpose, const double* b,
+                    bool scaled);
+p4d_status jvp_reduced(p4d_ctx* c, const double* x, double* y, int transpose, const double* b,
+                       bool scaled);
+
+// ---- particle elimination (particle.cu)
+p4d_status particle_solve64(p4d_ctx* c, const double* rc, double* yc, const double* tN, int transpose);
+p4d_status precond_full(p4d_ctx* c, const double* r, double* z, int transpose, bool scaled);
+p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose, bool scaled);
+
+// ---- multigrid (mg.cu)
+p4d_status mg_plan(p4d_ctx* c);
+p4d_status mg_setup_fixed(p4d_ctx* c);
+p4d_status mg_update(p4d_ctx* c);
+// run the V-cycles of the listed hierarchies on the level-0 right-hand sides already in place
+p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs);
+// level-0 rhs from an FP64 macro vector: b_h = scale * (r_f - corr)  (see mg.cu)
+p4d_status mg_load_rhs(p4d_ctx* c, const double* rm, const double* sinv_m, const int* hs, int nhs);
+p4d_status mg_store_out(p4d_ctx* c, const double* rm_unscaled_src, const double* sinv_m, double* zm,
+                        const int* fields, int nf);
+
+// ---- Krylov (krylov.cu)
+p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int transpose);
+
+}  // namespace p4d

@@ -1,0 +1,149 @@
+"""Thin Python binding over libp4d.so (argument marshalling only)."""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def default_params(**overrides):
+    """p4d_params with the library defaults, overridden by keyword."""
+    lib = N.load()
+    p = N.Params()
+    lib.p4d_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if k in ("ocp_n", "ocp_p"):
+            getattr(p, k)[0], getattr(p, k)[1] = float(v[0]), float(v[1])
+        elif k == "order":
+            for i in range(3):
+                p.order[i] = int(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+_PHYS_KEYS = ("F", "R", "T", "tplus", "brug", "De", "kappa", "sigma_n", "sigma_p", "k_n", "k_p", "cmax_n",
+              "cmax_p", "alpha", "ocp_n", "ocp_p", "dt", "i_app", "diffpot_sign")
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t
+
+
+class P4DSolver:
+    """One cell: mesh + parameters -> a libp4d handle.
+
+    case: dict with "mesh" (arrays as produced by ``p4d_inputs``) and
+    "params" (physical constants); solver options are keyword arguments
+    (precision, combine, order, restart, maxit, mode, cheb_degree,
+    coarse_max, cheb_ratio, rtol).
+    """
+
+    def __init__(self, case, device="cuda", stream=None, **opts):
+        self.lib = N.load()
+        m = case["mesh"]
+        phys = {k: case["params"][k] for k in _PHYS_KEYS if k in case["params"]}
+        self.params = default_params(**phys, **opts)
+        self._keep = []
+
+        def dp(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_double))
+
+        def up(a):
+            a = np.ascontiguousarray(a, dtype=np.uint8)
+            self._keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+        mesh = N.Mesh(nx=int(m["nx"]), ny=int(m["ny"]), nz=int(m["nz"]), hx=dp(m["hx"]), hy=dp(m["hy"]),
+                      hz=dp(m["hz"]), region=up(m["region"]), eps=dp(m["eps"]), eps_s=dp(m["eps_s"]),
+                      Rs=dp(m["Rs"]), Ds=dp(m["Ds"]), gamma_p=up(m["gamma_p"]), gamma_n=up(m["gamma_n"]),
+                      rgrid=dp(m["rgrid"]), nc=int(m["nc"]))
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = self.lib.p4d_setup(C.byref(mesh), C.byref(self.params), None, C.c_void_p(self.stream.cuda_stream),
+                                C.byref(h))
+        N.check(st, "p4d_setup")
+        self.h = h
+        nn, ne, nd, nc = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
+        N.check(self.lib.p4d_get_sizes(h, C.byref(nn), C.byref(ne), C.byref(nd), C.byref(nc)), "p4d_get_sizes")
+        self.nn, self.NE, self.ndof, self.nc = nn.value, ne.value, nd.value, nc.value
+        en = np.zeros(max(self.NE, 1), np.int32)
+        N.check(self.lib.p4d_electrode_nodes(h, en.ctypes.data_as(C.POINTER(C.c_int32))), "p4d_electrode_nodes")
+        self.enodes = en[: self.NE]
+
+    # ----------------------------------------------------------------- state
+    def state_tensors(self, st):
+        """Device tensors of a generator state (c_s rows of electrode nodes)."""
+        d = self.device
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float64), device=d)
+        return dict(phis=f(st["phis"]), phie=f(st["phie"]), ce=f(st["ce"]),
+                    cs=f(np.asarray(st["cs_node"])[self.enodes]), ce_prev=f(st["ce_prev"]),
+                    cs_prev=f(np.asarray(st["cs_prev_node"])[self.enodes]))
+
+    def _state(self, s):
+        for k in ("phis", "phie", "ce", "cs", "ce_prev", "cs_prev"):
+            _dev(s[k])
+        return N.State(phis=_ptr(s["phis"]), phie=_ptr(s["phie"]), ce=_ptr(s["ce"]), cs=_ptr(s["cs"]),
+                       ce_prev=_ptr(s["ce_prev"]), cs_prev=_ptr(s["cs_prev"]))
+
+    # ----------------------------------------------------------------- calls
+    def residual(self, s, out=None):
+        out = torch.empty(self.ndof, dtype=torch.float64, device=self.device) if out is None else _dev(out)
+        N.check(self.lib.p4d_residual(self.h, C.byref(self._state(s)), _ptr(out)), "p4d_residual")
+        return out
+
+    def jacobian_update(self, s):
+        N.check(self.lib.p4d_jacobian_update(self.h, C.byref(self._state(s))), "p4d_jacobian_update")
+
+    def jvp(self, x, transpose=False, out=None):
+        out = torch.empty_like(x) if out is None else out
+        N.check(self.lib.p4d_jvp(self.h, _ptr(_dev(x)), _ptr(_dev(out)), int(transpose)), "p4d_jvp")
+        return out
+
+    def precond(self, r, transpose=False, out=None):
+        out = torch.empty_like(r) if out is None else out
+        N.check(self.lib.p4d_precond_apply(self.h, _ptr(_dev(r)), _ptr(_dev(out)), int(transpose)),
+                "p4d_precond_apply")
+        return out
+
+    def set_options(self, **opts):
+        for k, v in opts.items():
+            if k == "order":
+                for i in range(3):
+                    self.params.order[i] = int(v[i])
+            else:
+                setattr(self.params, k, v)
+        N.check(self.lib.p4d_set_params(self.h, C.byref(self.params)), "p4d_set_params")
+
+    def solve(self, b, x=None, adjoint=False, check=True):
+        """FGMRES solve of J x = b (adjoint: J^T x = b); returns (x, info dict)."""
+        x = torch.zeros_like(b) if x is None else x
+        info = N.Info()
+        fn = self.lib.p4d_adjoint_solve if adjoint else self.lib.p4d_fgmres_solve
+        st = fn(self.h, _ptr(_dev(b)), _ptr(_dev(x)), C.byref(info))
+        if check and st not in (N.OK,):
+            raise N.P4DError(st, "p4d_fgmres_solve")
+        d = info.as_dict()
+        d["status"] = st
+        return x, d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.p4d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -274,3 +274,19 @@ def test_printed_parameters_and_dof_counts():
         assert 3 * (ex + 1) * (ey + 1) * (ez + 1) == pytest.approx(v["electrode_dofs"], rel=0.03)
         assert v["N_c"] * nelem == pytest.approx(v["particle_dofs"], rel=0.01)
         assert 3 * (ex + 1) * (ey + 1) * (ez + 1) + v["N_c"] * nelem == pytest.approx(v["total_dofs"], rel=0.01)
+
+
+@pytest.mark.parametrize("combine", ["additive", "multiplicative"])
+def test_preconditioner_transpose_is_adjoint(combine):
+    """<P^-1 x, y> = <x, P^-T y>: the V-cycles are symmetric and the
+    transposed block elimination is the exact adjoint."""
+    case = make_box_case(4, 4, (4, 2, 4), 30e-6, (40e-6, 15e-6, 40e-6), 4, 3)
+    d, st = _disc(case)
+    from oracle.blocks import BlockPrecond
+    P = BlockPrecond(d, d.jacobian(st), combine=combine, coarse_max=16)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(d.ndof)
+    y = rng.standard_normal(d.ndof)
+    a = P.apply(x) @ y
+    b = x @ P.apply_transpose(y)
+    assert abs(a - b) <= 1e-10 * (abs(a) + np.linalg.norm(P.apply(x)) * np.linalg.norm(y) * 1e-6)
