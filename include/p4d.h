@@ -186,6 +186,28 @@ p4d_status p4d_fgmres_solve(p4d_handle h, const double* b, double* x, p4d_info* 
    same conventions as p4d_fgmres_solve. */
 p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_info* info);
 
+/* Largest number of electrode nodes p4d_jvp_noalloc accepts (size of its
+   fixed scratch array: 2^20 doubles = 8 MiB per GPU that loads the library). */
+#define P4D_NOALLOC_MAX_NELEC (1 << 20)
+
+/* y = J x or J^T x like p4d_jvp, for callers that must not allocate device
+   memory at the time of the call: code running under CUDA stream capture,
+   where cudaMalloc would break the capture, or code whose device memory is
+   owned entirely by a framework's pool or a fixed arena.  The paper has no
+   counterpart; this is a deployment variant of p4d_jvp.  It calls no
+   cudaMalloc/cudaFree and no allocating library routine: the only scratch
+   the JVP needs (one coupling scalar per electrode node) lives in a fixed
+   device array of P4D_NOALLOC_MAX_NELEC doubles that every GPU loading the
+   library keeps until the process exits.  The first call on each device
+   looks up that array's device address (cudaGetSymbolAddress); make that
+   first call before any stream capture.  All calls share the one array, so
+   calls whose kernels overlap on the GPU (several streams or handles at
+   once) race; nothing in it needs to start at zero (each entry is written
+   before it is read within a call).  Returns INVALID_ARG when the handle has
+   more than P4D_NOALLOC_MAX_NELEC electrode nodes, when x == y or before a
+   p4d_jacobian_update; otherwise as p4d_jvp. */
+p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose);
+
 /* Human-readable name of a status. */
 const char* p4d_status_string(p4d_status s);
 

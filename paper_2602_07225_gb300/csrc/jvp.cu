@@ -11,6 +11,7 @@
 //
 // Output forms: y = sc .* (J x) or y = sc .* (b - J x), sc = w_f / sqrt(d) in
 // the scaled Krylov space, 1 otherwise.
+#include <mutex>
 #include "p4d_common.cuh"
 
 namespace p4d {
@@ -170,3 +171,62 @@ p4d_status jvp_reduced(p4d_ctx* c, const double* x, double* y, int transpose, co
 }
 
 }  // namespace p4d
+
+// ---------------------------------------------------------------------------
+// p4d_jvp_noalloc: the full-layout coupled JVP with its one piece of scratch
+// (the node-local coupling scalar per electrode node, written by the
+// macro-row kernel and read by the particle-row kernel) kept in a fixed
+// device array of this file instead of the handle's workspace.  Every GPU
+// that loads the library holds this array until the process exits.
+namespace p4d {
+
+static __device__ __align__(256) double g_noalloc_tloc[P4D_NOALLOC_MAX_NELEC];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_tloc on the current device, looked up once per
+// device with that device current (in host code the array's name is only a
+// stand-in for the device symbol, never a device address).
+p4d_status noalloc_scratch(double** out) {
+  int dev = -1;
+  P4D_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return P4D_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_tloc) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return P4D_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = static_cast<double*>(g_noalloc_ptr[dev]);
+  return P4D_OK;
+}
+
+}  // namespace
+}  // namespace p4d
+
+extern "C" p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose) {
+  using namespace p4d;
+  if (!h || !x || !y || x == y || !h->linearized) return P4D_ERR_INVALID_ARG;
+  if (h->NE > (int64_t)P4D_NOALLOC_MAX_NELEC) return P4D_ERR_INVALID_ARG;
+  double* tloc = nullptr;
+  P4D_TRYS(noalloc_scratch(&tloc));
+  JvpArgs a = make_args(h);
+  a.tloc = tloc;   // each entry read by the particle rows is written first by the macro rows
+  const int64_t nn = h->g.nn;
+  if (transpose) k_jvp_macro<true, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
+  else k_jvp_macro<false, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
+  if (h->NE > 0) {
+    const int64_t np = h->NE * h->nc;
+    if (transpose) k_jvp_particle<true><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
+    else k_jvp_particle<false><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
