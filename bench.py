@@ -148,15 +148,18 @@ def gpu_leg(args, rank, world, local):
     iters = 0
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lib = s.lib
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         barrier()
+        l0 = lib.p4d_launch_count()
         e0.record(stream)
         for _ in range(args.steps):
             x, info = step(s, st)
             iters += info["iters"]
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = lib.p4d_launch_count() - l0
         barrier()
     ms = e0.elapsed_time(e1)
     if world > 1:
@@ -198,7 +201,6 @@ def gpu_leg(args, rank, world, local):
 
     # ---- roofline: dominant kernel timed live (FP64 coupled JVP through the C ABI)
     roof = roofline_jvp(s, st, dev)
-    kern = kernel_breakdown(lambda: step(s, st))
 
     # ---- FP64 GPU path for the same step
     fp64 = None
@@ -221,34 +223,7 @@ def gpu_leg(args, rank, world, local):
         s64.close()
     return dict(ms_per_step=ms_per_step, solves_per_s=solves_per_s, iters_per_s=iters_per_s,
                 iters_per_solve=iters / args.steps, ndof=ndof, info=last_info, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h,
-                clocks=clk.summary(), roof=roof, fp64=fp64, kern=kern, nn=s.nn, NE=s.NE, nc=s.nc)
-
-
-def kernel_breakdown(step_fn):
-    """Kernels of one step, recorded by the CUDA activity tracer (one extra,
-    untimed step): launch count and device time per kernel name."""
-    import torch
-    from torch.profiler import profile, ProfilerActivity
-    torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        step_fn()
-        torch.cuda.synchronize()
-    agg = {}
-    for ev in prof.events():
-        if ev.device_type != torch.autograd.DeviceType.CUDA:
-            continue
-        name = ev.name
-        if "Memcpy" in name or "Memset" in name:
-            continue
-        a = agg.setdefault(name, [0, 0.0])
-        a[0] += 1
-        a[1] += ev.device_time_total if hasattr(ev, "device_time_total") else ev.cuda_time_total
-    total = sum(v[1] for v in agg.values())
-    rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
-    mine = sum(v[0] for k, v in agg.items() if "p4d" in k or k.startswith("void p4d") or "k_" in k)
-    return {"launches_per_step": mine, "all_launches_per_step": sum(v[0] for v in agg.values()),
-            "top": [{"kernel": k[:90], "launches": v[0], "us": round(v[1], 1),
-                     "share": round(v[1] / total, 4) if total else None} for k, v in rows[:12]]}
+                clocks=clk.summary(), roof=roof, fp64=fp64, launches=launches, nn=s.nn, NE=s.NE, nc=s.nc)
 
 
 def roofline_jvp(s, st, dev):
@@ -362,8 +337,7 @@ def main():
         "fp64_path": r["fp64"],
         "e2e": {"value": 1e3 / r["e2e_ms"], "unit": "solves/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
-        "gpu_launches": r["kern"]["launches_per_step"] * args.steps,
-        "kernels_per_step": r["kern"]["top"],
+        "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["roof"]["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": r["roof"]["gbs"] / peak, "traffic": None, "kernel": r["roof"]["kernel"],
                      "peak_source": src},

@@ -208,6 +208,10 @@ p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_inf
    p4d_jacobian_update; otherwise as p4d_jvp. */
 p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose);
 
+/* Number of CUDA kernels the library has launched in this process so far
+   (instrumentation for benchmarks; thread-safe, never reset). */
+long long p4d_launch_count(void);
+
 /* Human-readable name of a status. */
 const char* p4d_status_string(p4d_status s);
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "p4d_fgmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "p4d_adjoint_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "p4d_jvp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "p4d_launch_count": (C.c_longlong, []),
     "p4d_status_string": (C.c_char_p, [C.c_int]),
 }
 

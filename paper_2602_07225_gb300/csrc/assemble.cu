@@ -149,7 +149,7 @@ __global__ void k_linearize(int64_t NE, int nc, Kin kn, double dt, const int32_t
                             const double* __restrict__ betaj, const double* __restrict__ rref,
                             double* __restrict__ in_, double* __restrict__ ge, double* __restrict__ gc,
                             double* __restrict__ gs, double* __restrict__ zj, double* __restrict__ zeta,
-                            unsigned* flags) {
+                            double* __restrict__ ipiv, double* __restrict__ mult, unsigned* flags) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= NE) return;
   const int64_t n = enode[j];
@@ -162,46 +162,81 @@ __global__ void k_linearize(int64_t NE, int nc, Kin kn, double dt, const int32_t
   const double* lo = rref;
   const double* di = rref + nc;
   const double* up = rref + 2 * nc;
-  // scaled by 1/M: T/M = I/dt - kap Lref + e_N e_N^T beta g_s
-  double piv = 1.0 / dt - kap * di[0];
+  // LU of T/M = I/dt - kap Lref + e_N e_N^T beta g_s (unit lower L with
+  // multipliers mult_i, upper U with pivots piv_i): stored as 1/piv and mult
+  // so that every later FP64 particle solve is division free.
+  const double idt = 1.0 / dt;
+  double piv = idt - kap * di[0];
+  ipiv[j * nc] = 1.0 / piv;
+  mult[j * nc] = 0.0;
   for (int i = 1; i < nc; ++i) {
-    double dii = 1.0 / dt - kap * di[i];
+    double dii = idt - kap * di[i];
     if (i == nc - 1) dii += betaj[j] * d;
     const double l = -kap * lo[i];
     const double u = -kap * up[i - 1];
-    piv = dii - l * u / piv;
+    const double mi = l / piv;
+    piv = dii - mi * u;
+    mult[j * nc + i] = mi;
+    ipiv[j * nc + i] = 1.0 / piv;
   }
   const double z = 1.0 / (M * piv);
   zj[j] = z;
   zeta[j] = 1.0 - z * d * M * betaj[j];
 }
 
-// sqrt of the Jacobian diagonal per row (Krylov scaling).
-__global__ void k_diag(Grid g, int64_t NE, int nc, double tau, double dt, const double* __restrict__ Jst,
+// Jacobi scaling of the Krylov solve per row: sqrt(|J_ii|) and its inverse.
+// The square roots are taken in FP32 (FP64 square roots cost ~1 ms per
+// Newton step on this GPU); the scaling only defines the norm of the
+// residual and the preconditioner's input weighting, both of which are free
+// to be any positive diagonal, so a relative 1e-7 perturbation changes
+// nothing but that definition.
+__device__ __forceinline__ void put_scale(double d, double* sqd, double* rsqd, int64_t row) {
+  float a = (float)fabs(d);
+  if (!(a > 0.f) || !isfinite(a)) a = 1.f;
+  const float r = sqrtf(a);
+  sqd[row] = (double)r;
+  rsqd[row] = (double)(1.0f / r);
+}
+
+__global__ void k_diag(Grid g, int64_t NE, int nc, double tau, double idt, const double* __restrict__ Jst,
                        const uint8_t* __restrict__ label, const int32_t* __restrict__ eidx,
                        const double* __restrict__ Aj, const double* __restrict__ Mj,
                        const double* __restrict__ kapj, const double* __restrict__ betaj,
                        const double* __restrict__ rref, const double* __restrict__ ge,
-                       const double* __restrict__ gc, const double* __restrict__ gs, double* __restrict__ sqd) {
+                       const double* __restrict__ gc, const double* __restrict__ gs, double* __restrict__ sqd,
+                       double* __restrict__ rsqd) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
-  double d;
   if (t < nn) {
     const int64_t n = t;
     const int32_t e = eidx[n];
-    d = (label[n] & kLabActive) ? Jst[(0 * 27 + 13) * nn + n] + Aj[e] * ge[e] : 1.0;
-    sqd[n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
-    d = Jst[(1 * 27 + 13) * nn + n] + (e >= 0 ? Aj[e] * ge[e] : 0.0);
-    sqd[nn + n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
-    d = Jst[(2 * 27 + 13) * nn + n] - (e >= 0 ? tau * Aj[e] * gc[e] : 0.0);
-    sqd[2 * nn + n] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+    put_scale((label[n] & kLabActive) ? Jst[(0 * 27 + 13) * nn + n] + Aj[e] * ge[e] : 1.0, sqd, rsqd, n);
+    put_scale(Jst[(1 * 27 + 13) * nn + n] + (e >= 0 ? Aj[e] * ge[e] : 0.0), sqd, rsqd, nn + n);
+    put_scale(Jst[(2 * 27 + 13) * nn + n] - (e >= 0 ? tau * Aj[e] * gc[e] : 0.0), sqd, rsqd, 2 * nn + n);
   } else if (t < nn + NE * nc) {
     const int64_t q = t - nn;
     const int64_t e = q / nc;
     const int i = (int)(q % nc);
-    d = Mj[e] * (1.0 / dt - kapj[e] * rref[nc + i]);
+    double d = Mj[e] * (idt - kapj[e] * rref[nc + i]);
     if (i == nc - 1) d += Mj[e] * betaj[e] * gs[e];
-    sqd[3 * nn + q] = sqrt(fabs(d) > 0 ? fabs(d) : 1.0);
+    put_scale(d, sqd, rsqd, 3 * nn + q);
+  }
+}
+
+// Fixed off-diagonal sums of the level-0 multigrid operators (setup).
+__global__ void k_fixed_sums(Grid g, const double* __restrict__ Jst, const uint8_t* __restrict__ label,
+                             double* __restrict__ offsum, double* __restrict__ absoff) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nn = g.nn;
+  if (n >= nn) return;
+  for (int f = 0; f < 3; ++f) {
+    const double* st = Jst + (size_t)f * 27 * nn;
+    double s = 0.0, a = 0.0;
+    if (!(f == 0 && !(label[n] & kLabActive)))
+      for (int o = 0; o < 27; ++o)
+        if (o != 13) { s += st[o * nn + n]; a += fabs(st[o * nn + n]); }
+    offsum[f * nn + n] = s;
+    absoff[f * nn + n] = a;
   }
 }
 
@@ -284,7 +319,7 @@ __global__ void k_kinetics_only(int64_t NE, int nc, Kin kn, const int32_t* __res
 }
 
 // Particle rows: R_cs = M [(c - c_prev)/dt - kap Lref c] + e_N M beta i_n.
-__global__ void k_residual_particle(int64_t NE, int nc, double dt, const double* __restrict__ cs,
+__global__ void k_residual_particle(int64_t NE, int nc, double idt, const double* __restrict__ cs,
                                     const double* __restrict__ cs_prev, const double* __restrict__ Mj,
                                     const double* __restrict__ kapj, const double* __restrict__ betaj,
                                     const double* __restrict__ rref, const double* __restrict__ rin,
@@ -297,7 +332,7 @@ __global__ void k_residual_particle(int64_t NE, int nc, double dt, const double*
   double L = rref[nc + i] * c[i];
   if (i > 0) L += rref[i] * c[i - 1];
   if (i < nc - 1) L += rref[2 * nc + i] * c[i + 1];
-  double v = Mj[e] * ((c[i] - cs_prev[q]) / dt - kapj[e] * L);
+  double v = Mj[e] * ((c[i] - cs_prev[q]) * idt - kapj[e] * L);
   if (i == nc - 1) v += Mj[e] * betaj[e] * rin[e];
   r[q] = v;
 }
@@ -321,14 +356,17 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   P4D_TRYS(dalloc_t(c, &c->Jst, (size_t)4 * 27 * nn));
   P4D_TRYS(dalloc_t(c, &c->sfix, (size_t)3 * nn));
   Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt};
-  k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
+  ::p4d::count_launch(), k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
                                                        eps, eps_s, c->label, ph, c->Jst, c->sfix);
   P4D_TRY(cudaGetLastError());
+  P4D_TRYS(dalloc_t(c, &c->offsum, (size_t)3 * nn));
+  P4D_TRYS(dalloc_t(c, &c->absoff, (size_t)3 * nn));
+  ::p4d::count_launch(), k_fixed_sums<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->Jst, c->label, c->offsum, c->absoff);
   unsigned long long* mx = nullptr;
   P4D_TRYS(dalloc_t(c, &mx, 3));
   P4D_TRY(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), c->stream));
   for (int f = 0; f < 3; ++f)
-    k_maxdiag<<<4 * 152, kBlock, 0, c->stream>>>(c->Jst + (size_t)f * 27 * nn, nn, mx + f);
+    ::p4d::count_launch(), k_maxdiag<<<4 * 152, kBlock, 0, c->stream>>>(c->Jst + (size_t)f * 27 * nn, nn, mx + f);
   unsigned long long h[3];
   P4D_TRY(cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   P4D_TRY(cudaStreamSynchronize(c->stream));
@@ -346,15 +384,15 @@ p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
   const int nc = c->nc;
   Kin kn = make_kin(c->prm);
   P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
-  k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce, c->gdc, c->flags);
+  ::p4d::count_launch(), k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce, c->gdc, c->flags);
   if (NE > 0)
-    k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->prm.dt, c->enode, c->label, c->etype,
+    ::p4d::count_launch(), k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->prm.dt, c->enode, c->label, c->etype,
                                                         st->phis, st->phie, st->ce, st->cs, c->Mj, c->kapj,
                                                         c->betaj, c->rref, c->in_, c->ge, c->gc, c->gs, c->zj,
-                                                        c->zeta, c->flags);
-  k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, c->prm.dt, c->Jst, c->label,
+                                                        c->zeta, c->tfac, c->tfac + (size_t)NE * nc, c->flags);
+  ::p4d::count_launch(), k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, 1.0 / c->prm.dt, c->Jst, c->label,
                                                           c->eidx, c->Aj, c->Mj, c->kapj, c->betaj, c->rref,
-                                                          c->ge, c->gc, c->gs, c->sqd);
+                                                          c->ge, c->gc, c->gs, c->sqd, c->rsqd);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -364,15 +402,15 @@ p4d_status residual(p4d_ctx* c, const p4d_state* st, double* r) {
   const int nc = c->nc;
   Kin kn = make_kin(c->prm);
   P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
-  k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce_r, nullptr, c->flags);
+  ::p4d::count_launch(), k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce_r, nullptr, c->flags);
   if (NE > 0)
-    k_kinetics_only<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype, st->phis,
+    ::p4d::count_launch(), k_kinetics_only<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype, st->phis,
                                                             st->phie, st->ce, st->cs, c->rin, c->flags);
-  k_residual_macro<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, kn, c->Jst, c->label, c->eidx, c->Aj, c->gpw,
+  ::p4d::count_launch(), k_residual_macro<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, kn, c->Jst, c->label, c->eidx, c->Aj, c->gpw,
                                                              st->phis, st->phie, st->ce, st->ce_prev,
                                                              c->lnce_r, c->rin, r);
   if (NE > 0)
-    k_residual_particle<<<nblocks(NE * nc), kBlock, 0, c->stream>>>(NE, nc, c->prm.dt, st->cs, st->cs_prev, c->Mj,
+    ::p4d::count_launch(), k_residual_particle<<<nblocks(NE * nc), kBlock, 0, c->stream>>>(NE, nc, 1.0 / c->prm.dt, st->cs, st->cs_prev, c->Mj,
                                                                     c->kapj, c->betaj, c->rref, c->rin,
                                                                     r + 3 * nn);
   P4D_TRY(cudaGetLastError());

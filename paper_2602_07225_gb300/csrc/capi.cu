@@ -6,6 +6,8 @@
 // is (D/R^2) times it; the flux factor is beta_ref/R), uploads everything and
 // hands over to the device kernels for stencil assembly and the multigrid
 // hierarchy.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -14,6 +16,9 @@
 using namespace p4d;
 
 namespace p4d {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 p4d_status dalloc(p4d_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
@@ -206,7 +211,12 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->zj, NE));
   P4D_TRYS(dalloc_t(c, &c->zeta, NE));
   P4D_TRYS(dalloc_t(c, &c->tloc, NE));
+  P4D_TRYS(dalloc_t(c, &c->tfac, (size_t)2 * std::max<int64_t>(1, NE) * nc));
   P4D_TRYS(dalloc_t(c, &c->sqd, c->ndof));
+  P4D_TRYS(dalloc_t(c, &c->rsqd, c->ndof));
+  P4D_TRYS(dalloc_t(c, &c->iwf, 4));
+  P4D_TRYS(dalloc_t(c, &c->ujvp, nn));
+  P4D_TRY(cudaMallocHost(&c->lam_pin, sizeof(double) * kMaxLevels * kNH));
   P4D_TRYS(dalloc_t(c, &c->wf, 4));
   P4D_TRYS(dalloc_t(c, &c->flags, 1));
   P4D_TRY(cudaMallocHost(&c->flags_h, sizeof(unsigned)));
@@ -237,6 +247,7 @@ void free_ctx(p4d_ctx* c) {
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   if (c->flags_h) cudaFreeHost(c->flags_h);
+  if (c->lam_pin) cudaFreeHost(c->lam_pin);
   if (c->hs_h) cudaFreeHost(c->hs_h);
   delete c;
 }
@@ -328,6 +339,7 @@ p4d_status p4d_jacobian_update(p4d_handle h, const p4d_state* st) {
   P4D_TRYS(linearize(h, st));
   P4D_TRYS(mg_update(h));
   P4D_TRYS(check_flags(h));
+  P4D_TRYS(mg_fetch_lam(h));
   h->linearized = true;
   return P4D_OK;
 }
@@ -355,6 +367,8 @@ p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_inf
   if (!h->linearized) return P4D_ERR_INVALID_ARG;
   return fgmres(h, g, lam, info, 1);
 }
+
+long long p4d_launch_count(void) { return p4d::g_launches.load(std::memory_order_relaxed); }
 
 const char* p4d_status_string(p4d_status s) {
   switch (s) {

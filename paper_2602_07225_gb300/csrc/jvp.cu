@@ -21,17 +21,27 @@ struct JvpArgs {
   Grid g;
   int64_t NE;
   int nc;
-  double tau, dt;
+  double tau, dt, idt;
   const double* Jst;
   const uint8_t* label;
   const int32_t* eidx;
   const double *Aj, *Mj, *betaj, *kapj, *rref;
-  const double *ge, *gc, *gs, *zeta, *gdc, *sqd, *wf;
+  const double *ge, *gc, *gs, *zeta, *gdc, *rsqd, *wf;
   double* tloc;
+  const double* u;     // optional precombined phi_e + gamma/c_e * c_e of the input (non-transposed)
 };
 
 __device__ __forceinline__ double outscale(const JvpArgs& a, bool scaled, int f, int64_t row) {
-  return scaled ? a.wf[f] / a.sqd[row] : 1.0;
+  return scaled ? a.wf[f] * a.rsqd[row] : 1.0;
+}
+
+// u = x_phie + (gamma / c_e) x_ce: the input of the K_kappa stencil in the
+// phi_e rows, formed once per node instead of once per stencil neighbour.
+__global__ void k_jvp_combine(int64_t nn, const double* __restrict__ x, const double* __restrict__ gdc,
+                              double* __restrict__ u) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  u[n] = fma(gdc[n], x[2 * nn + n], x[nn + n]);
 }
 
 // Macro rows.  reduced: Schur operator on [phi_s | phi_e | c_e] only.
@@ -51,7 +61,7 @@ __global__ void __launch_bounds__(128) k_jvp_macro(JvpArgs a, const double* __re
   const double* Ks = a.Jst;
   const double* Kk = a.Jst + 27 * nn;
   const double* Cc = a.Jst + 2 * 27 * nn;
-  double ys = 0.0, ye = 0.0, yc = 0.0, yk = 0.0;
+  double ys = 0.0, ye = 0.0, yc = 0.0;
   const bool act = a.label[n] & kLabActive;
 #pragma unroll
   for (int o = 0; o < 27; ++o) {
@@ -62,15 +72,11 @@ __global__ void __launch_bounds__(128) k_jvp_macro(JvpArgs a, const double* __re
     const int64_t so = o * nn + n;
     if (act) ys += Ks[so] * xs[m];
     const double kk_ = Kk[so];
-    if (!TRANS) {
-      ye += kk_ * (xe[m] + a.gdc[m] * xc[m]);
-    } else {
-      ye += kk_ * xe[m];
-      yk += kk_ * xe[m];
-    }
+    if (!TRANS) ye += kk_ * (a.u ? a.u[m] : fma(a.gdc[m], xc[m], xe[m]));
+    else ye += kk_ * xe[m];
     yc += Cc[so] * xc[m];
   }
-  if (TRANS) yc += a.gdc[n] * yk;
+  if (TRANS) yc += a.gdc[n] * ye;   // (K_kappa diag(gamma/c_e))^T = diag(gamma/c_e) K_kappa
   if (!act) ys = xs[n];
   const int32_t e = a.eidx[n];
   if (e >= 0) {
@@ -128,7 +134,7 @@ __global__ void k_jvp_particle(JvpArgs a, const double* __restrict__ x, const do
     if (i > 0) L += up[i - 1] * xc[i - 1];
     if (i < nc - 1) L += lo[i + 1] * xc[i + 1];
   }
-  double v = a.Mj[e] * (xc[i] / a.dt - a.kapj[e] * L);
+  double v = a.Mj[e] * (xc[i] * a.idt - a.kapj[e] * L);
   if (i == nc - 1) v += (TRANS ? a.gs[e] : a.Mj[e] * a.betaj[e]) * a.tloc[e];
   if (b) v = b[3 * nn + q] - v;
   y[3 * nn + q] = outscale(a, scaled, 3, 3 * nn + q) * v;
@@ -137,11 +143,12 @@ __global__ void k_jvp_particle(JvpArgs a, const double* __restrict__ x, const do
 JvpArgs make_args(p4d_ctx* c) {
   JvpArgs a;
   a.g = c->g; a.NE = c->NE; a.nc = c->nc;
-  a.tau = (1.0 - c->prm.tplus) / c->prm.F; a.dt = c->prm.dt;
+  a.tau = (1.0 - c->prm.tplus) / c->prm.F; a.dt = c->prm.dt; a.idt = 1.0 / c->prm.dt;
   a.Jst = c->Jst; a.label = c->label; a.eidx = c->eidx;
   a.Aj = c->Aj; a.Mj = c->Mj; a.betaj = c->betaj; a.kapj = c->kapj; a.rref = c->rref;
-  a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.gdc = c->gdc; a.sqd = c->sqd; a.wf = c->wf;
+  a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.gdc = c->gdc; a.rsqd = c->rsqd; a.wf = c->wf;
   a.tloc = c->tloc;
+  a.u = nullptr;
   return a;
 }
 
@@ -150,12 +157,16 @@ JvpArgs make_args(p4d_ctx* c) {
 p4d_status jvp_full(p4d_ctx* c, const double* x, double* y, int transpose, const double* b, bool scaled) {
   JvpArgs a = make_args(c);
   const int64_t nn = c->g.nn;
-  if (transpose) k_jvp_macro<true, false><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
-  else k_jvp_macro<false, false><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
+  if (!transpose) {
+    ::p4d::count_launch(), k_jvp_combine<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, x, c->gdc, c->ujvp);
+    a.u = c->ujvp;
+  }
+  if (transpose) ::p4d::count_launch(), k_jvp_macro<true, false><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
+  else ::p4d::count_launch(), k_jvp_macro<false, false><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
   if (c->NE > 0) {
     const int64_t np = c->NE * c->nc;
-    if (transpose) k_jvp_particle<true><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
-    else k_jvp_particle<false><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
+    if (transpose) ::p4d::count_launch(), k_jvp_particle<true><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
+    else ::p4d::count_launch(), k_jvp_particle<false><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -164,8 +175,12 @@ p4d_status jvp_full(p4d_ctx* c, const double* x, double* y, int transpose, const
 p4d_status jvp_reduced(p4d_ctx* c, const double* x, double* y, int transpose, const double* b, bool scaled) {
   JvpArgs a = make_args(c);
   const int64_t nn = c->g.nn;
-  if (transpose) k_jvp_macro<true, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
-  else k_jvp_macro<false, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
+  if (!transpose) {
+    ::p4d::count_launch(), k_jvp_combine<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, x, c->gdc, c->ujvp);
+    a.u = c->ujvp;
+  }
+  if (transpose) ::p4d::count_launch(), k_jvp_macro<true, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
+  else ::p4d::count_launch(), k_jvp_macro<false, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -220,12 +235,12 @@ extern "C" p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, 
   JvpArgs a = make_args(h);
   a.tloc = tloc;   // each entry read by the particle rows is written first by the macro rows
   const int64_t nn = h->g.nn;
-  if (transpose) k_jvp_macro<true, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
-  else k_jvp_macro<false, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
+  if (transpose) ::p4d::count_launch(), k_jvp_macro<true, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
+  else ::p4d::count_launch(), k_jvp_macro<false, false><<<nblocks(nn, 128), 128, 0, h->stream>>>(a, x, nullptr, y, false);
   if (h->NE > 0) {
     const int64_t np = h->NE * h->nc;
-    if (transpose) k_jvp_particle<true><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
-    else k_jvp_particle<false><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
+    if (transpose) ::p4d::count_launch(), k_jvp_particle<true><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
+    else ::p4d::count_launch(), k_jvp_particle<false><<<nblocks(np), kBlock, 0, h->stream>>>(a, x, nullptr, y, false);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;

@@ -3,9 +3,11 @@
 // directions are stored unscaled (z_k = P^-1 (s^-1 v_k)), so that
 // x = x0 + sum_k y_k z_k and the operator is applied as s.(J z_k).
 //
-// Orthogonalisation: classical Gram-Schmidt with one full reorthogonalisation
-// ("twice is enough"), each pass a fused multi-dot over the basis with a
-// fixed-shape two-stage reduction (deterministic order).  The Hessenberg
+// Orthogonalisation: classical Gram-Schmidt; a second pass runs only when the
+// first cancelled more than half of the vector ("twice is enough" with the
+// Daniel-Gragg-Kaufman-Stewart test, decided on the device).  Each pass is a
+// register-blocked multi-dot over the basis with a fixed-shape two-stage
+// reduction (deterministic order).  The Hessenberg
 // column, Givens rotations and residual estimate are updated on the device by
 // one thread; the host reads one scalar per iteration.
 #include <cmath>
@@ -18,61 +20,84 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;   // reduction grid: a multiple of the SM count
 constexpr int kRedThreads = 256;
 
-// partial[blk][i] = sum over the block's elements of V[i][n] * w[n] (i < kp1);
-// if with_ww, partial[blk][kp1] = sum w[n]^2.
+// Multi-dot, register blocked: each thread keeps one accumulator per dot of
+// a group of up to kDotGroup dots over all of its elements, so the warp and
+// block reductions run once per dot and launch instead of once per element
+// chunk (FP64 adds are as scarce as FP64 FMAs on this GPU).
+// partial[blk][g0 + i] = sum over the block's elements of V[g0 + i][n] * w[n];
+// with_ww: partial[blk][kp1] = sum w[n]^2 (computed with the first group).
+constexpr int kDotGroup = 16;
+
 __global__ void __launch_bounds__(kRedThreads) k_mdot(const double* __restrict__ V, int64_t ldv, int kp1,
                                                       const double* __restrict__ w, int64_t len, int with_ww,
-                                                      double* __restrict__ partial, int pstride) {
-  __shared__ double red[kRedThreads / 32][130];
+                                                      double* __restrict__ partial, int pstride,
+                                                      const double* __restrict__ flag) {
+  if (flag && *flag == 0.0) return;   // conditional pass not needed
+  __shared__ double red[kRedThreads / 32][kDotGroup + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nd = kp1 + (with_ww ? 1 : 0);
-  for (int i = threadIdx.x; i < (kRedThreads / 32) * 130; i += blockDim.x) (&red[0][0])[i] = 0.0;
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) * 4; base < len; base += stride) {
-    double wv[4];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int g0 = 0; g0 < kp1 || (g0 == 0 && with_ww); g0 += kDotGroup) {
+    const int ng = min(kDotGroup, kp1 - g0);
+    const bool ww = with_ww && g0 == 0;
+    double acc[kDotGroup + 1];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t n = base + threadIdx.x + (int64_t)q * blockDim.x;
-      wv[q] = n < len ? w[n] : 0.0;
+    for (int i = 0; i <= kDotGroup; ++i) acc[i] = 0.0;
+    for (int64_t n = n0; n < len; n += stride) {
+      const double wn = w[n];
+#pragma unroll
+      for (int i = 0; i < kDotGroup; ++i)
+        if (i < ng) acc[i] = fma(V[(int64_t)(g0 + i) * ldv + n], wn, acc[i]);
+      if (ww) acc[kDotGroup] = fma(wn, wn, acc[kDotGroup]);
     }
-    for (int i = 0; i < nd; ++i) {
-      double acc = 0.0;
-      if (i < kp1) {
-        const double* v = V + (int64_t)i * ldv;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t n = base + threadIdx.x + (int64_t)q * blockDim.x;
-          if (n < len) acc += v[n] * wv[q];
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc += wv[q] * wv[q];
+    for (int i = 0; i <= kDotGroup; ++i) {
+      if (i < ng || (i == kDotGroup && ww)) {
+        double a = acc[i];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) red[warp][i] = a;
       }
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) red[warp][i] += acc;
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    double s = 0.0;
-    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[wv][i];
-    partial[(int64_t)blockIdx.x * pstride + i] = s;
+    __syncthreads();
+    if (threadIdx.x <= kDotGroup) {
+      const int i = threadIdx.x;
+      if (i < ng || (i == kDotGroup && ww)) {
+        double sum = 0.0;
+        for (int wv = 0; wv < kRedThreads / 32; ++wv) sum += red[wv][i];
+        partial[(int64_t)blockIdx.x * pstride + (i < kDotGroup ? g0 + i : kp1)] = sum;
+      }
+    }
+    __syncthreads();
+    if (kp1 == 0) break;
   }
 }
 
+// out[i] = sum over blocks of partial[b][i]: one block per dot, strided
+// per-thread sums and a shared-memory tree (fixed order: deterministic).
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int pstride, int nd,
-                                  double* __restrict__ out) {
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * pstride + i];
-    out[i] = s;
+                                  double* __restrict__ out, const double* __restrict__ flag, int zero_if_skipped) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
+  if (i >= nd) return;
+  if (flag && *flag == 0.0) {
+    if (zero_if_skipped && threadIdx.x == 0) out[i] = 0.0;
+    return;
   }
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(int64_t)b * pstride + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = red[0];
 }
 
 // w[n] -= sum_i h[i] V[i][n]   (h on the device)
 __global__ void k_maxpy(const double* __restrict__ V, int64_t ldv, int kp1, const double* __restrict__ h,
-                        double* __restrict__ w, int64_t len, double sign) {
+                        double* __restrict__ w, int64_t len, double sign, const double* __restrict__ flag) {
+  if (flag && *flag == 0.0) return;
   __shared__ double hs[130];
   for (int i = threadIdx.x; i < kp1; i += blockDim.x) hs[i] = sign * h[i];
   __syncthreads();
@@ -93,13 +118,13 @@ __global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, in
 }
 
 // Per-field squared norms of (b / sqrt(d)) over the 4 fields (c_s optional).
-__global__ void k_field_norms(const double* __restrict__ b, const double* __restrict__ sqd, int64_t nn, int64_t len,
+__global__ void k_field_norms(const double* __restrict__ b, const double* __restrict__ rsqd, int64_t nn, int64_t len,
                               double* __restrict__ partial) {
   __shared__ double red[4][kRedThreads / 32];
   double acc[4] = {0, 0, 0, 0};
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
     const int f = n < 3 * nn ? (int)(n / nn) : 3;
-    const double v = b[n] / sqd[n];
+    const double v = b[n] * rsqd[n];
     acc[f] += v * v;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -116,13 +141,15 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
   }
 }
 
-__global__ void k_weights(const double* __restrict__ partial, int nblk, double* __restrict__ wf, double* bn2) {
+__global__ void k_weights(const double* __restrict__ partial, int nblk, double* __restrict__ wf,
+                          double* __restrict__ iwf, double* bn2) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
   for (int f = 0; f < 4; ++f) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partial[b * 4 + f];
     wf[f] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    iwf[f] = s > 0.0 ? sqrt(s) : 1.0;
     bn2[f] = s;
     tot += s > 0.0 ? 1.0 : 0.0;
   }
@@ -230,6 +257,19 @@ __global__ void k_givens(double* hs, HLay L, int k) {
   hs[L.misc + 2 * m + 4] = status;
 }
 
+// Reorthogonalise only when the first Gram-Schmidt pass cancelled more than
+// half of the vector (||w_after|| < 0.7 ||w_before||, Daniel-Gragg-Kaufman-
+// Stewart); count the passes in misc+2m+7.
+__global__ void k_reorth_flag(double* hs, HLay L, int k) {
+  if (threadIdx.x != 0) return;
+  double* misc = hs + L.misc;
+  const double before = misc[k + 1];
+  const double after = misc[2 * L.m + 2];
+  const double f = (after < 0.49 * before) ? 1.0 : 0.0;
+  misc[2 * L.m + 6] = f;
+  misc[2 * L.m + 7] += f;
+}
+
 __global__ void k_backsolve(double* hs, HLay L, int kk) {
   if (threadIdx.x != 0) return;
   const int m = L.m;
@@ -298,15 +338,19 @@ __global__ void k_surface_coupling(int64_t NE, double tau, const int32_t* __rest
 struct Reducer {
   p4d_ctx* c;
   int nblk(int64_t len) const {
-    const int64_t want = (len + (int64_t)kRedThreads * 4 - 1) / ((int64_t)kRedThreads * 4);
+    const int64_t want = (len + (int64_t)kRedThreads * 8 - 1) / ((int64_t)kRedThreads * 8);
     return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, want));
   }
   // out[0..kp1) = V^T w, out[kp1] = w.w (optional)
-  void mdot(const double* V, int64_t ldv, int kp1, const double* w, int64_t len, bool ww, double* out) {
+  // flag (device, optional): the pass runs only if *flag != 0; otherwise out
+  // is zeroed (zero_if_skipped) or left unchanged
+  void mdot(const double* V, int64_t ldv, int kp1, const double* w, int64_t len, bool ww, double* out,
+            const double* flag = nullptr, int zero_if_skipped = 0) {
     const int nb = nblk(len);
     const int ps = 132;
-    k_mdot<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, kp1, w, len, ww ? 1 : 0, c->part, ps);
-    k_reduce_partials<<<1, 256, 0, c->stream>>>(c->part, nb, ps, kp1 + (ww ? 1 : 0), out);
+    ::p4d::count_launch(), k_mdot<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, kp1, w, len, ww ? 1 : 0, c->part, ps, flag);
+    ::p4d::count_launch(), k_reduce_partials<<<kp1 + (ww ? 1 : 0), 256, 0, c->stream>>>(c->part, nb, ps, kp1 + (ww ? 1 : 0), out, flag,
+                                                                  zero_if_skipped);
   }
 };
 
@@ -330,22 +374,22 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
   // per-field weights from the full right-hand side
   {
     const int nb = kRedBlocks;
-    k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->sqd, nn, c->ndof, c->part);
-    k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->wf, hs + L.misc + 2 * L.m + 8);
+    ::p4d::count_launch(), k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->rsqd, nn, c->ndof, c->part);
+    ::p4d::count_launch(), k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->wf, c->iwf, hs + L.misc + 2 * L.m + 8);
   }
   const double* bk = b;            // Krylov right-hand side (unscaled)
   if (!full) {
     // b_m' = b_m - A_mc T^-1 b_c
     P4D_TRYS(particle_solve64(c, b + 3 * nn, c->tmp + 3 * nn, nullptr, trans));
-    k_condense<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->nc, tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj,
+    ::p4d::count_launch(), k_condense<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->nc, tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj,
                                                       c->ge, c->gc, c->gs, b, c->tmp + 3 * nn, c->bred, trans);
     bk = c->bred;
   }
   // ||s.b_k|| = sqrt(sum_f w_f^2 ||(b_k / sqrt(d))_f||^2)
   double bnorm = 0.0;
   {
-    k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(bk, c->sqd, nn, len, c->part);
-    k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
+    ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(bk, c->rsqd, nn, len, c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
     P4D_TRY(cudaMemcpyAsync(c->hs_h, hs + L.misc + 2 * L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
     P4D_TRY(cudaStreamSynchronize(c->stream));
     const double* bn2 = c->hs_h;        // full-b field norms^2 (weights)
@@ -356,7 +400,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     }
     bnorm = std::sqrt(bnorm);
   }
-  int iters = 0, restarts = 0, reorth = 0;
+  int iters = 0, restarts = 0;
   p4d_status st = P4D_ERR_NOT_CONVERGED;
   double est = 1.0;
   if (bnorm == 0.0) {
@@ -365,14 +409,15 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     est = 0.0;
   }
   double* misc = hs + L.misc;
+  P4D_TRY(cudaMemsetAsync(misc + 2 * L.m + 7, 0, sizeof(double), c->stream));
   while (st == P4D_ERR_NOT_CONVERGED && iters < c->prm.maxit) {
     ++restarts;
     // V0 = s.(b_k - A x)
     if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
     else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
     R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
-    k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, 0);
-    k_scale<<<gb, kBlock, 0, c->stream>>>(c->V, c->V, len, misc + 2 * L.m + 5, 1);
+    ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, 0);
+    ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(c->V, c->V, len, misc + 2 * L.m + 5, 1);
     P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     P4D_TRY(cudaStreamSynchronize(c->stream));
     const double beta = c->hs_h[0];
@@ -388,16 +433,18 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       else P4D_TRYS(precond_macro(c, vk, zk, trans, true));
       if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
       else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
-      // CGS, twice
-      R.mdot(c->V, len, k + 1, w, len, false, misc);
-      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc, w, len, 1.0);
-      R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1);
-      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0);
-      ++reorth;
-      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2);
-      k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
+      // classical Gram-Schmidt, second pass only when needed
+      const double* flag = misc + 2 * L.m + 6;
+      R.mdot(c->V, len, k + 1, w, len, true, misc);                 // h1, ||w||^2 before
+      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc, w, len, 1.0, nullptr);
+      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2);            // ||w||^2 after
+      ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(hs, L, k);
+      R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
+      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag);
+      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2, flag, 0);   // ||w||^2 after the second pass
+      ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
       // v_{k+1} = w / h_{k+1,k}
-      k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
+      ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
       P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       P4D_TRY(cudaStreamSynchronize(c->stream));
       ++iters;
@@ -409,9 +456,9 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       if (stt == 1.0) { st = P4D_OK; break; }
     }
     if (kk > 0) {
-      k_backsolve<<<1, 1, 0, c->stream>>>(hs, L, kk);
+      ::p4d::count_launch(), k_backsolve<<<1, 1, 0, c->stream>>>(hs, L, kk);
       // x += Z y  (k_maxpy computes w -= sum h_i V_i; use sign -1)
-      k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->Z, len, kk, hs + L.y, x, len, -1.0);
+      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->Z, len, kk, hs + L.y, x, len, -1.0, nullptr);
     }
     if (st == P4D_ERR_NONFINITE) break;
     if (st == P4D_OK) {
@@ -428,16 +475,16 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
   }
   if (!full) {
     // x_c = T^-1 (b_c - A_cm x_m)
-    k_surface_coupling<<<nblocks(std::max<int64_t>(1, c->NE)), kBlock, 0, c->stream>>>(
+    ::p4d::count_launch(), k_surface_coupling<<<nblocks(std::max<int64_t>(1, c->NE)), kBlock, 0, c->stream>>>(
         c->NE, tau, c->enode, nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, x, c->tloc, trans);
     P4D_TRYS(particle_solve64(c, b + 3 * nn, x + 3 * nn, c->tloc, trans));
   }
   // final true residual of the full system in the scaled norm
   P4D_TRYS(jvp_full(c, x, c->r0, trans, b, true));
-  k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
-  k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, misc + 2 * L.m + 24);
+  ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
+  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, misc + 2 * L.m + 24);
   P4D_TRY(cudaEventRecord(ev1, c->stream));
-  P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 8, sizeof(double) * 24, cudaMemcpyDeviceToHost, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 7, sizeof(double) * 25, cudaMemcpyDeviceToHost, c->stream));
   P4D_TRY(cudaStreamSynchronize(c->stream));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
@@ -448,9 +495,9 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     info->iters = iters;
     info->restarts = restarts;
     info->status = st;
-    info->reorth = reorth;
-    const double* bn2 = c->hs_h;          // field norms^2 of b/sqd (weights: 1/sqrt)
-    const double* rr = c->hs_h + 16;      // field norms^2 of s.(b - Jx)
+    info->reorth = (int)c->hs_h[0];
+    const double* bn2 = c->hs_h + 1;      // field norms^2 of b/sqd (weights: 1/sqrt)
+    const double* rr = c->hs_h + 17;      // field norms^2 of s.(b - Jx)
     double tot_r = 0.0, tot_b = 0.0;
     for (int f = 0; f < 4; ++f) {
       info->rel_res_block[f] = bn2[f] > 0 ? std::sqrt(rr[f]) : std::sqrt(rr[f]);

@@ -27,8 +27,10 @@ template <> __device__ __forceinline__ float fromd<float>(double v) { return (fl
 template <> __device__ __forceinline__ __nv_bfloat16 fromd<__nv_bfloat16>(double v) {
   return __float2bfloat16((float)v);
 }
-template <typename T> __device__ __forceinline__ float tof(T v) { return (float)v; }
-template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+// stencil entry -> compute precision (identity for float/double, widen bf16)
+template <typename T> __device__ __forceinline__ T tof(T v) { return v; }
+__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 
 struct LevelDims {
   int nnx, nny, nnz;
@@ -206,9 +208,28 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// Block-wide maximum of a non-negative value, one atomic per block (all
+// threads of the block must call it).
+__device__ __forceinline__ void block_max_to(double* addr, double v) {
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (blockDim.x + 31) / 32 ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0 && v > 0.0) atomic_max_pos(addr, v);
+  }
+}
+
 // Level 0: variable row sums, storage stencil slot 13, inverse diagonal, lam.
+// The fixed off-diagonal sums come from setup; only node-local arithmetic
+// remains (the reciprocal and the Gershgorin ratio in the compute precision).
 template <typename TS, typename T>
-__global__ void k_level0_update(Grid g, double tau, const double* __restrict__ Jst, const double* __restrict__ sfix,
+__global__ void k_level0_update(Grid g, double tau, const double* __restrict__ sfix,
+                                const double* __restrict__ offsum, const double* __restrict__ absoff,
                                 const uint8_t* __restrict__ label, const int32_t* __restrict__ eidx,
                                 const double* __restrict__ Aj, const double* __restrict__ ge,
                                 const double* __restrict__ gc, const double* __restrict__ zeta, double s0,
@@ -216,45 +237,41 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ J
                                 double* __restrict__ svar, double* lam) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
-  if (n >= nn) return;
-  const int32_t e = eidx[n];
-  const uint8_t l = label[n];
-  const bool act = l & kLabActive;
-  double sv[3] = {0.0, 0.0, 0.0};
-  if (e >= 0) {
-    const double zA = zeta[e] * Aj[e];
-    if (act) sv[0] = zA * ge[e];
-    sv[1] = zA * ge[e];
-    sv[2] = -tau * zA * gc[e];
-  }
-  TS* sts[3] = {st0, st1, st2};
-  T* dis[3] = {di0, di1, di2};
-  const double sc[3] = {s0, s1, s2};
-  for (int f = 0; f < 3; ++f) {
-    const double* st = Jst + (size_t)f * 27 * nn;
-    const double s = sfix[f * nn + n] + sv[f];
-    double diag = s, absoff = 0.0;
-    if (f == 0 && !act) {
-      diag = 1.0;
-    } else {
-      for (int o = 0; o < 27; ++o)
-        if (o != 13) {
-          diag -= st[o * nn + n];
-          absoff += fabs(st[o * nn + n]);
-        }
+  double gl[kNH] = {0.0, 0.0, 0.0, 0.0};
+  if (n < nn) {
+    const int32_t e = eidx[n];
+    const uint8_t l = label[n];
+    const bool act = l & kLabActive;
+    double sv[3] = {0.0, 0.0, 0.0};
+    if (e >= 0) {
+      const double zA = zeta[e] * Aj[e];
+      if (act) sv[0] = zA * ge[e];
+      sv[1] = zA * ge[e];
+      sv[2] = -tau * zA * gc[e];
     }
-    svar[f * nn + n] = sv[f];
-    sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
-    if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);   // keep the smoother finite on a degenerate row
-    dis[f][n] = fromd<T>(1.0 / (sc[f] * diag));
-    const double gl = (absoff + fabs(diag)) / diag;
-    int h = f + 1;
-    if (f == 0) {
-      if (!act) continue;
-      h = (l & kLabAnode) ? 0 : 1;
+    TS* sts[3] = {st0, st1, st2};
+    T* dis[3] = {di0, di1, di2};
+    const double sc[3] = {s0, s1, s2};
+    for (int f = 0; f < 3; ++f) {
+      const double s = sfix[f * nn + n] + sv[f];
+      double diag = (f == 0 && !act) ? 1.0 : s - offsum[f * nn + n];
+      const double ab = absoff[f * nn + n];
+      if (!(diag > 0.0)) diag = fmax(ab, 1e-300);   // keep the smoother finite on a degenerate row
+      svar[f * nn + n] = sv[f];
+      sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
+      const T dsc = (T)(sc[f] * diag);
+      dis[f][n] = (T)1 / dsc;
+      int h = f + 1;
+      if (f == 0) {
+        if (!act) continue;
+        h = (l & kLabAnode) ? 0 : 1;
+      }
+      // Gershgorin ratio in FP64: the Chebyshev interval must not depend on
+      // the preconditioner precision
+      gl[h] = (ab + diag) / diag;
     }
-    atomic_max_pos(lam + h, gl);
   }
+  for (int h = 0; h < kNH; ++h) block_max_to(lam + h, gl[h]);
 }
 
 // Level >= 1: A = F + V into storage precision, inverse diagonal and lam.
@@ -264,21 +281,24 @@ __global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const do
                                 double sc3, double* lam) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
-  if (n >= d.n) return;
-  const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
-  const double* f = F.p[h];
-  const double* v = V.p[h];
-  double diag = 0.0, absoff = 0.0, s = 0.0;
-  for (int o = 0; o < 27; ++o) {
-    const double a = f[o * d.n + n] + v[o * d.n + n];
-    st.p[h][o * d.n + n] = fromd<TS>(sc * a);
-    if (o == 13) s = a;
-    else { diag -= a; absoff += fabs(a); }
+  double gl = 0.0;
+  if (n < d.n) {
+    const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
+    const double* f = F.p[h];
+    const double* v = V.p[h];
+    double diag = 0.0, absoff = 0.0, s = 0.0;
+    for (int o = 0; o < 27; ++o) {
+      const double a = f[o * d.n + n] + v[o * d.n + n];
+      st.p[h][o * d.n + n] = fromd<TS>(sc * a);
+      if (o == 13) s = a;
+      else { diag -= a; absoff += fabs(a); }
+    }
+    diag += s;
+    if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
+    dinv.p[h][n] = fromd<T>(1.0 / (sc * diag));
+    if (mask.p[h][n]) gl = (absoff + fabs(diag)) / diag;
   }
-  diag += s;
-  if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
-  dinv.p[h][n] = fromd<T>(1.0 / (sc * diag));
-  if (mask.p[h][n]) atomic_max_pos(lam + h, (absoff + fabs(diag)) / diag);
+  block_max_to(lam + h, gl);
 }
 
 // Dense scaled coarsest operator [n][n] (row major) from difference form.
@@ -400,80 +420,81 @@ struct LvlPtrs {
   T* d[kNH];
 };
 
+// (A x)_n in difference form.  Interior nodes (all 26 neighbours present)
+// take an unchecked path with constant offsets; boundary nodes check each
+// neighbour.  Indices are 32-bit (every level has fewer than 2^31/27 nodes).
 template <typename TS, typename T>
 __device__ __forceinline__ T apply_row(const TS* __restrict__ st, const T* __restrict__ x, const LevelDims& dd,
-                                       int64_t n, int i, int j, int k) {
+                                       int n, int i, int j, int k) {
+  const int N = (int)dd.n;
+  const int sx = 1, sy = dd.nnx, sz = dd.nnx * dd.nny;
   const T xn = x[n];
-  T acc = (T)tof(st[13 * dd.n + n]) * xn;
+  T acc = (T)tof(st[13 * N + n]) * xn;
+  if (i > 0 && j > 0 && k > 0 && i < dd.nnx - 1 && j < dd.nny - 1 && k < dd.nnz - 1) {
 #pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    if (o == 13) continue;
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-    const int ii = i + dx, jj = j + dy, kk = k + dz;
-    if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
-    const int64_t m = n + dx + (int64_t)dd.nnx * (dy + (int64_t)dd.nny * dz);
-    acc += (T)tof(st[o * dd.n + n]) * (x[m] - xn);
-  }
-  return acc;
-}
-template <>
-__device__ __forceinline__ double apply_row<double, double>(const double* __restrict__ st,
-                                                            const double* __restrict__ x, const LevelDims& dd,
-                                                            int64_t n, int i, int j, int k) {
-  const double xn = x[n];
-  double acc = st[13 * dd.n + n] * xn;
+    for (int o = 0; o < 27; ++o) {
+      if (o == 13) continue;
+      const int m = n + (o % 3 - 1) * sx + ((o / 3) % 3 - 1) * sy + (o / 9 - 1) * sz;
+      acc += (T)tof(st[o * N + n]) * (x[m] - xn);
+    }
+  } else {
 #pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    if (o == 13) continue;
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-    const int ii = i + dx, jj = j + dy, kk = k + dz;
-    if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
-    const int64_t m = n + dx + (int64_t)dd.nnx * (dy + (int64_t)dd.nny * dz);
-    acc += st[o * dd.n + n] * (x[m] - xn);
+    for (int o = 0; o < 27; ++o) {
+      if (o == 13) continue;
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int ii = i + dx, jj = j + dy, kk = k + dz;
+      if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
+      const int m = n + dx * sx + dy * sy + dz * sz;
+      acc += (T)tof(st[o * N + n]) * (x[m] - xn);
+    }
   }
   return acc;
 }
 
-// One Chebyshev step (step index `step` of the recurrence), x_out = x + d.
+__device__ __forceinline__ void node_ijk32(const LevelDims& d, int n, int& i, int& j, int& k) {
+  const int sxy = d.nnx * d.nny;
+  k = n / sxy;
+  const int r = n - k * sxy;
+  j = r / d.nnx;
+  i = r - j * d.nnx;
+}
+
+// Chebyshev coefficients of one step for up to four hierarchies (computed on
+// the host from the Gershgorin bounds): step 0: d = c0 z; later steps:
+// d = ca d + cb z, with z = D^-1 (b - A x).
+struct ChebCoef {
+  double c0[kNH], ca[kNH], cb[kNH];
+};
+
+// One Chebyshev step, x_out = x + d.
 template <typename TS, typename T>
-__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const double* __restrict__ lam,
-                                              double ratio, int step, int first) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int h = hl.h[blockIdx.y];
-  if (n >= dd.n) return;
+__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, ChebCoef cc, int step,
+                                              int first) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int hi = blockIdx.y;
+  const int h = hl.h[hi];
+  if (n >= (int)dd.n) return;
   if (!P.mask[h][n]) return;
   int i, j, k;
-  node_ijk(dd, n, i, j, k);
-  const double lm = lam[h];
-  const double alpha = lm / ratio, beta = lm;
-  const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
-  const double sigma = theta / delta;
+  node_ijk32(dd, n, i, j, k);
   T res = P.b[h][n];
   if (!first) res -= apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
   const T z = P.dinv[h][n] * res;
   T dn;
-  if (step == 0) {
-    dn = z * (T)(1.0 / theta);
-  } else {
-    double rho = 1.0 / sigma, rho_new = rho;
-    for (int s = 1; s <= step; ++s) {
-      rho = rho_new;
-      rho_new = 1.0 / (2.0 * sigma - rho);
-    }
-    dn = (T)(rho_new * rho) * P.d[h][n] + (T)(2.0 * rho_new / delta) * z;
-  }
+  if (step == 0) dn = (T)cc.c0[hi] * z;
+  else dn = (T)cc.ca[hi] * P.d[h][n] + (T)cc.cb[hi] * z;
   P.d[h][n] = dn;
   P.xo[h][n] = (first ? (T)0 : P.x[h][n]) + dn;
 }
 
 template <typename TS, typename T>
 __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int h = hl.h[blockIdx.y];
-  if (n >= dd.n) return;
+  if (n >= (int)dd.n) return;
   if (!P.mask[h][n]) return;   // level-0 phi_s hierarchies share r: never write masked-out nodes
   int i, j, k;
-  node_ijk(dd, n, i, j, k);
+  node_ijk32(dd, n, i, j, k);
   P.r[h][n] = P.b[h][n] - apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
 }
 
@@ -493,7 +514,7 @@ __global__ void k_restrict(LevelDims fd, LevelDims cd, int cx, int cy, int cz, P
         if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
         const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
         if (!fm.p[h][f]) continue;
-        const T w = (T)((cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0));
+        const T w = (tx == 0 ? (T)1 : (T)0.5) * (ty == 0 ? (T)1 : (T)0.5) * (tz == 0 ? (T)1 : (T)0.5);
         acc += w * fr.p[h][f];
       }
   cb.p[h][C] = acc;
@@ -508,16 +529,16 @@ __global__ void k_prolong(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Pt
   if (!fm.p[h][f]) return;
   int i, j, k;
   node_ijk(fd, f, i, j, k);
-  int px[2], py[2], pz[2];
-  double wx[2], wy[2], wz[2];
-  const int nx_ = parents(i, cx, px, wx), ny_ = parents(j, cy, py, wy), nz_ = parents(k, cz, pz, wz);
+  // parents along each axis: one (even index or not coarsened, weight 1) or two (odd, 1/2 each)
+  const int px0 = cx ? (i >> 1) : i, py0 = cy ? (j >> 1) : j, pz0 = cz ? (k >> 1) : k;
+  const int nx_ = (cx && (i & 1)) ? 2 : 1, ny_ = (cy && (j & 1)) ? 2 : 1, nz_ = (cz && (k & 1)) ? 2 : 1;
+  const T w = (nx_ == 2 ? (T)0.5 : (T)1) * (ny_ == 2 ? (T)0.5 : (T)1) * (nz_ == 2 ? (T)0.5 : (T)1);
   T acc = 0;
   for (int c3 = 0; c3 < nz_; ++c3)
     for (int c2 = 0; c2 < ny_; ++c2)
       for (int c1 = 0; c1 < nx_; ++c1)
-        acc += (T)(wx[c1] * wy[c2] * wz[c3]) *
-               cx_.p[h][px[c1] + (int64_t)cd.nnx * (py[c2] + (int64_t)cd.nny * pz[c3])];
-  fx.p[h][f] += acc;
+        acc += cx_.p[h][(px0 + c1) + (int64_t)cd.nnx * ((py0 + c2) + (int64_t)cd.nny * (pz0 + c3))];
+  fx.p[h][f] += w * acc;
 }
 
 template <typename T>
@@ -582,28 +603,48 @@ void swap_x(MGLevel& L, const int* hs, int nhs) {
   }
 }
 
+ChebCoef cheb_coef(const p4d_ctx* c, int level, const int* hs, int nhs, int step) {
+  ChebCoef cc{};
+  const double ratio = c->prm.cheb_ratio;
+  for (int t = 0; t < nhs && t < kNH; ++t) {
+    const double lm = c->lam_h[level][hs[t]] > 0 ? c->lam_h[level][hs[t]] : 1.0;
+    const double alpha = lm / ratio, beta = lm;
+    const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma, rho_new = rho;
+    for (int s = 1; s <= step; ++s) {
+      rho = rho_new;
+      rho_new = 1.0 / (2.0 * sigma - rho);
+    }
+    cc.c0[t] = 1.0 / theta;
+    cc.ca[t] = rho_new * rho;
+    cc.cb[t] = 2.0 * rho_new / delta;
+  }
+  return cc;
+}
+
 template <typename TS0, typename TS, typename T>
 p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   const int L = c->nlev;
   const int deg = c->prm.cheb_degree;
-  const double ratio = c->prm.cheb_ratio;
   HList hl = make_hl<T>(hs, nhs);
   for (int l = 0; l < L - 1; ++l) {
     MGLevel& A = c->lev[l];
     MGLevel& B = c->lev[l + 1];
     const dim3 grid(nblocks(A.n), nhs);
     for (int s = 0; s < deg; ++s) {
-      if (l == 0) k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, A.lam, ratio, s, s == 0);
-      else k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, A.lam, ratio, s, s == 0);
+      const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, s == 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, s == 0);
       swap_x(A, hs, nhs);
     }
-    if (l == 0) k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl);
-    else k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl);
+    if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl);
+    else ::p4d::count_launch(), k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl);
     Ptr4<const T> fr;
     Ptr4<const uint8_t> fm;
     Ptr4<T> cb;
     for (int h = 0; h < kNH; ++h) { fr.p[h] = (const T*)A.r[h]; fm.p[h] = A.mask[h]; cb.p[h] = (T*)B.b[h]; }
-    k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fr, fm, cb, hl);
+    ::p4d::count_launch(), k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fr, fm, cb, hl);
   }
   {
     MGLevel& C = c->lev[L - 1];
@@ -611,7 +652,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> m;
     Ptr4<T> x;
     for (int h = 0; h < kNH; ++h) { b.p[h] = (const T*)C.b[h]; m.p[h] = C.mask[h]; x.p[h] = (T*)C.x[h]; }
-    k_coarse_solve<T><<<dim3(std::max(1, (int)((C.n + 127) / 128)), nhs), 128, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
+    ::p4d::count_launch(), k_coarse_solve<T><<<dim3(std::max(1, (int)((C.n + 127) / 128)), nhs), 128, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
   }
   for (int l = L - 2; l >= 0; --l) {
     MGLevel& A = c->lev[l];
@@ -621,10 +662,11 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<T> fx;
     for (int h = 0; h < kNH; ++h) { cxp.p[h] = (const T*)B.x[h]; fm.p[h] = A.mask[h]; fx.p[h] = (T*)A.x[h]; }
     const dim3 grid(nblocks(A.n), nhs);
-    k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, cxp, fm, fx, hl);
+    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
-      if (l == 0) k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, A.lam, ratio, s, 0);
-      else k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, A.lam, ratio, s, 0);
+      const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, 0);
       swap_x(A, hs, nhs);
     }
   }
@@ -683,7 +725,7 @@ p4d_status mg_plan(p4d_ctx* c) {
         lv.st[h] = st[fh[h]]; lv.dinv[h] = di[fh[h]]; lv.x[h] = x[fh[h]]; lv.x2[h] = x2[fh[h]];
         lv.b[h] = b[fh[h]]; lv.r[h] = r[fh[h]]; lv.d[h] = d[fh[h]];
       }
-      k_mask0<<<nblocks(n), kBlock, 0, c->stream>>>(n, c->label, lv.mask[0], lv.mask[1], lv.mask[2], lv.mask[3]);
+      ::p4d::count_launch(), k_mask0<<<nblocks(n), kBlock, 0, c->stream>>>(n, c->label, lv.mask[0], lv.mask[1], lv.mask[2], lv.mask[3]);
     } else {
       P4D_TRYS(dalloc_t(c, &lv.Ffix, (size_t)kNH * 27 * n));
       P4D_TRYS(dalloc_t(c, &lv.Vvar, (size_t)kNH * 27 * n));
@@ -703,7 +745,7 @@ p4d_status mg_plan(p4d_ctx* c) {
       Ptr4<const uint8_t> fm;
       Ptr4<uint8_t> cm;
       for (int h = 0; h < kNH; ++h) { fm.p[h] = fl.mask[h]; cm.p[h] = lv.mask[h]; }
-      k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.cx, fl.cy, fl.cz, fm, cm);
+      ::p4d::count_launch(), k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.cx, fl.cy, fl.cz, fm, cm);
     }
     if (l == L - 1) P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
   }
@@ -732,10 +774,10 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
   const int prec = c->prm.precision;
   MGLevel& l0 = c->lev[0];
   if (prec == 0)
-    k_level0_offdiag<double><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
+    ::p4d::count_launch(), k_level0_offdiag<double><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
                                                                   (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3]);
   else
-    k_level0_offdiag<float><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
+    ::p4d::count_launch(), k_level0_offdiag<float><<<nblocks(l0.n), kBlock, 0, c->stream>>>(c->g, c->Jst, c->scale_f[0], c->scale_f[1], c->scale_f[2],
                                                                  (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3]);
   const int64_t nn = c->g.nn;
   for (int l = 0; l + 1 < c->nlev; ++l) {
@@ -757,7 +799,7 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
       cm.p[h] = B.mask[h];
       out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
     }
-    k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 1);
+    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 1);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -773,13 +815,13 @@ p4d_status mg_update(p4d_ctx* c) {
   for (int l = 0; l < c->nlev; ++l) P4D_TRY(cudaMemsetAsync(c->lev[l].lam, 0, kNH * sizeof(double), c->stream));
   MGLevel& l0 = c->lev[0];
   if (prec == 0)
-    k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
-        c->g, tau, c->Jst, c->sfix, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
+    ::p4d::count_launch(), k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
+        c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3], (double*)l0.dinv[0], (double*)l0.dinv[2],
         (double*)l0.dinv[3], svar, l0.lam);
   else
-    k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
-        c->g, tau, c->Jst, c->sfix, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
+    ::p4d::count_launch(), k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
+        c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3], (float*)l0.dinv[0], (float*)l0.dinv[2],
         (float*)l0.dinv[3], svar, l0.lam);
   const int fh[kNH] = {0, 0, 1, 2};
@@ -792,11 +834,11 @@ p4d_status mg_update(p4d_ctx* c) {
     if (l == 1) {
       Ptr4<const double> s;
       for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, s, fm, cm, out);
+      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, s, fm, cm, out);
     } else {
       Ptr4<const double> fst, frs;
       for (int h = 0; h < kNH; ++h) { fst.p[h] = A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
-      k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 0);
+      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 0);
     }
     Ptr4<const double> F, V;
     Ptr4<const uint8_t> m;
@@ -809,16 +851,16 @@ p4d_status mg_update(p4d_ctx* c) {
     if (prec == 0) {
       Ptr4<double> st, di;
       for (int h = 0; h < kNH; ++h) { st.p[h] = (double*)B.st[h]; di.p[h] = (double*)B.dinv[h]; }
-      k_level_combine<double, double><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+      ::p4d::count_launch(), k_level_combine<double, double><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
     } else if (prec == 1) {
       Ptr4<float> st, di;
       for (int h = 0; h < kNH; ++h) { st.p[h] = (float*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
-      k_level_combine<float, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+      ::p4d::count_launch(), k_level_combine<float, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
     } else {
       Ptr4<__nv_bfloat16> st;
       Ptr4<float> di;
       for (int h = 0; h < kNH; ++h) { st.p[h] = (__nv_bfloat16*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
-      k_level_combine<__nv_bfloat16, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+      ::p4d::count_launch(), k_level_combine<__nv_bfloat16, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
     }
   }
   // coarsest: dense scaled operator and its inverse
@@ -828,9 +870,9 @@ p4d_status mg_update(p4d_ctx* c) {
     for (int h = 0; h < kNH; ++h) m.p[h] = C.mask[h];
     double* mats = C.inv;
     double* work = C.inv + (size_t)kNH * C.n * C.n;
-    k_dense0<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(c->g, c->Jst, c->sfix, svar, m, sf[0], sf[1], sf[2],
+    ::p4d::count_launch(), k_dense0<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(c->g, c->Jst, c->sfix, svar, m, sf[0], sf[1], sf[2],
                                                                  mats);
-    k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
+    ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
   } else {
     Ptr4<const double> F, V;
     for (int h = 0; h < kNH; ++h) {
@@ -839,10 +881,20 @@ p4d_status mg_update(p4d_ctx* c) {
     }
     double* mats = C.inv;
     double* work = C.inv + (size_t)kNH * C.n * C.n;
-    k_dense<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
-    k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
+    ::p4d::count_launch(), k_dense<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
+    ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
   }
   P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status mg_fetch_lam(p4d_ctx* c) {
+  for (int l = 0; l < c->nlev; ++l)
+    P4D_TRY(cudaMemcpyAsync(c->lam_pin + l * kNH, c->lev[l].lam, kNH * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  for (int l = 0; l < c->nlev; ++l)
+    for (int h = 0; h < kNH; ++h) c->lam_h[l][h] = c->lam_pin[l * kNH + h];
   return P4D_OK;
 }
 

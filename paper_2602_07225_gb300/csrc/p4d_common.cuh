@@ -119,6 +119,8 @@ struct p4d_ctx {
   // fixed FP64 stencils [4][27][nn]: 0 K_sigma (lifted), 1 K_kappa, 2 C = M_eps/dt + K_D, 3 M_eps/dt
   double* Jst = nullptr;
   double* sfix = nullptr;              // [3][nn] fixed multigrid row sums per field
+  double* offsum = nullptr;            // [3][nn] sum of the fixed off-diagonal entries per field
+  double* absoff = nullptr;            // [3][nn] sum of their absolute values
 
   // linearization
   double* lnce = nullptr;              // [nn] ln c_e
@@ -131,8 +133,12 @@ struct p4d_ctx {
   double* gs = nullptr;
   double* zj = nullptr;                // [NE] (T_j^-1)_NN
   double* zeta = nullptr;              // [NE] 1 - z_j g_s M_j beta_j
+  double* tfac = nullptr;              // [2][NE][nc] LU of T_j/M_j: 1/pivot, multiplier
   double* tloc = nullptr;              // [NE] node-local coupling scalar of the last operator application
-  double* sqd = nullptr;               // [ndof] sqrt(diag J)
+  double* ujvp = nullptr;              // [nn] phi_e + gamma/c_e * c_e combination of a JVP input
+  double* sqd = nullptr;               // [ndof] sqrt(|diag J|)
+  double* rsqd = nullptr;              // [ndof] 1 / sqrt(|diag J|)
+  double* iwf = nullptr;               // [4] 1 / w_f
   double* wf = nullptr;                // [4] per-field Krylov weights (device)
   unsigned* flags = nullptr;           // device error flags
   unsigned* flags_h = nullptr;         // pinned host mirror
@@ -140,6 +146,8 @@ struct p4d_ctx {
   // multigrid
   int nlev = 0;
   p4d::MGLevel lev[p4d::kMaxLevels];
+  double lam_h[p4d::kMaxLevels][p4d::kNH] = {};   // Gershgorin bounds (host copy, per Newton update)
+  double* lam_pin = nullptr;           // pinned staging for lam
   void* yc = nullptr;                  // [NE][nc] particle solve work (compute precision)
 
   // Krylov workspace
@@ -167,6 +175,10 @@ inline p4d_status dalloc_t(p4d_ctx* c, T** p, size_t count) {
 
 inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
+// Process-wide count of kernel launches issued by the library (every launch
+// site is written "count_launch(), kernel<<<...>>>(...)").
+void count_launch();
+
 // ---- assembly / linearization (assemble.cu)
 p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, const uint8_t* region);
 p4d_status linearize(p4d_ctx* c, const p4d_state* st);
@@ -189,6 +201,7 @@ p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose
 p4d_status mg_plan(p4d_ctx* c);
 p4d_status mg_setup_fixed(p4d_ctx* c);
 p4d_status mg_update(p4d_ctx* c);
+p4d_status mg_fetch_lam(p4d_ctx* c);
 // run the V-cycles of the listed hierarchies on the level-0 right-hand sides already in place
 p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs);
 // level-0 rhs from an FP64 macro vector: b_h = scale * (r_f - corr)  (see mg.cu)

@@ -20,17 +20,17 @@ struct PcArgs {
   Grid g;
   int64_t NE;
   int nc;
-  double tau, dt;
+  double tau, dt, idt;
   const uint8_t* label;
   const int32_t* eidx;
   const int32_t* enode;
   const double *Aj, *Mj, *betaj, *kapj, *rref;
-  const double *ge, *gc, *gs, *zeta, *sqd, *wf;
+  const double *ge, *gc, *gs, *zeta, *sqd, *iwf;
   double sc[3];
 };
 
 __device__ __forceinline__ double insc(const PcArgs& a, bool scaled, int f, int64_t row) {
-  return scaled ? a.sqd[row] / a.wf[f] : 1.0;
+  return scaled ? a.sqd[row] * a.iwf[f] : 1.0;
 }
 
 // Thomas on T/M (or its transpose) for one particle; rhs in-place in x[0..nc).
@@ -38,7 +38,7 @@ template <typename T, bool TRANS>
 __device__ __forceinline__ void particle_thomas(const PcArgs& a, int64_t e, T* x) {
   const int nc = a.nc;
   const T kap = (T)a.kapj[e];
-  const T idt = (T)(1.0 / a.dt);
+  const T idt = (T)a.idt;
   const double* lo = a.rref;
   const double* di = a.rref + nc;
   const double* up = a.rref + 2 * nc;
@@ -162,10 +162,10 @@ __global__ void k_part_bwd(PcArgs a, const T* __restrict__ yc, const double* __r
 PcArgs make_pc(p4d_ctx* c) {
   PcArgs a;
   a.g = c->g; a.NE = c->NE; a.nc = c->nc;
-  a.tau = (1.0 - c->prm.tplus) / c->prm.F; a.dt = c->prm.dt;
+  a.tau = (1.0 - c->prm.tplus) / c->prm.F; a.dt = c->prm.dt; a.idt = 1.0 / c->prm.dt;
   a.label = c->label; a.eidx = c->eidx; a.enode = c->enode;
   a.Aj = c->Aj; a.Mj = c->Mj; a.betaj = c->betaj; a.kapj = c->kapj; a.rref = c->rref;
-  a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.sqd = c->sqd; a.wf = c->wf;
+  a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.sqd = c->sqd; a.iwf = c->iwf;
   for (int f = 0; f < 3; ++f) a.sc[f] = c->scale_f[f];
   return a;
 }
@@ -179,33 +179,33 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
   const int64_t nn = c->g.nn;
   T* yc = (T*)c->yc;
   if (FULL && c->NE > 0)
-    k_part_fwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, r, yc, scaled);
+    ::p4d::count_launch(), k_part_fwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, r, yc, scaled);
   MGLevel& l0 = c->lev[0];
   T* b[3] = {(T*)l0.b[0], (T*)l0.b[2], (T*)l0.b[3]};
   if (c->prm.combine == 0) {
-    k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 7, 0, scaled, b[0], b[1], b[2]);
+    ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 7, 0, scaled, b[0], b[1], b[2]);
     const int hs[4] = {0, 1, 2, 3};
     P4D_TRYS(mg_vcycle(c, hs, 4));
-    k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 7, (const T*)l0.x[0], (const T*)l0.x[2],
+    ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 7, (const T*)l0.x[0], (const T*)l0.x[2],
                                                       (const T*)l0.x[3], z);
   } else {
     int done = 0;
     for (int t = 0; t < 3; ++t) {
       const int f = TRANS ? c->prm.order[2 - t] : c->prm.order[t];
-      k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 1 << f, done, scaled, b[0], b[1],
+      ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 1 << f, done, scaled, b[0], b[1],
                                                                    b[2]);
       int hs[2];
       int nh = 0;
       for (int q = 0; q < 2; ++q)
         if (kHOfField[f][q] >= 0) hs[nh++] = kHOfField[f][q];
       P4D_TRYS(mg_vcycle(c, hs, nh));
-      k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 1 << f, (const T*)l0.x[0], (const T*)l0.x[2],
+      ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 1 << f, (const T*)l0.x[0], (const T*)l0.x[2],
                                                         (const T*)l0.x[3], z);
       done |= 1 << f;
     }
   }
   if (FULL && c->NE > 0)
-    k_part_bwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, yc, z, z + 3 * nn);
+    ::p4d::count_launch(), k_part_bwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, yc, z, z + 3 * nn);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -217,18 +217,56 @@ p4d_status apply_dispatch(p4d_ctx* c, const double* r, double* z, int transpose,
   return transpose ? apply_t<float, true, FULL>(c, r, z, scaled) : apply_t<float, false, FULL>(c, r, z, scaled);
 }
 
-// FP64 particle solve y = T^-1 (rc - e_N tN) (tN optional) for the reduced mode.
+// FP64 particle solve y = T^-1 (rc - e_N tN) (tN optional) for the reduced
+// mode's condensation and back substitution, with the LU factors of T/M
+// stored at the linearization (no divisions: FP64 divides run at 1/58 of the
+// FP32 rate on this GPU).  T/M = L U; transposed: T^T/M = U^T L^T.
 template <bool TRANS>
-__global__ void k_part64(PcArgs a, const double* __restrict__ rc, double* __restrict__ yc, const double* __restrict__ tN) {
+__global__ void k_part64(PcArgs a, const double* __restrict__ ipiv, const double* __restrict__ mult,
+                         const double* __restrict__ rc, double* __restrict__ yc, const double* __restrict__ tN) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= a.NE) return;
   const int nc = a.nc;
-  double x[kMaxNc];
   const double iM = 1.0 / a.Mj[e];
-  for (int i = 0; i < nc; ++i) x[i] = rc[e * nc + i] * iM;
-  if (tN) x[nc - 1] -= tN[e] * iM;
-  particle_thomas<double, TRANS>(a, e, x);
-  for (int i = 0; i < nc; ++i) yc[e * nc + i] = x[i];
+  const double kap = a.kapj[e];
+  const double* up = a.rref + 2 * nc;
+  const double* ip = ipiv + e * nc;
+  const double* ml = mult + e * nc;
+  const double* r = rc + e * nc;
+  double* y = yc + e * nc;
+  const double tl = tN ? tN[e] : 0.0;
+  if (!TRANS) {
+    // L z = r/M (forward), U y = z (backward); z kept in y
+    double zp = r[0] * iM;
+    y[0] = zp;
+    for (int i = 1; i < nc; ++i) {
+      double ri = r[i];
+      if (i == nc - 1) ri -= tl;
+      zp = fma(-ml[i], zp, ri * iM);
+      y[i] = zp;
+    }
+    double yn = y[nc - 1] * ip[nc - 1];
+    y[nc - 1] = yn;
+    for (int i = nc - 2; i >= 0; --i) {
+      yn = (y[i] + kap * up[i] * yn) * ip[i];   // U_{i,i+1} = -kap up_i
+      y[i] = yn;
+    }
+  } else {
+    // U^T z = r/M (forward), L^T y = z (backward)
+    double zp = r[0] * iM * ip[0];
+    y[0] = zp;
+    for (int i = 1; i < nc; ++i) {
+      double ri = r[i];
+      if (i == nc - 1) ri -= tl;
+      zp = (ri * iM + kap * up[i - 1] * zp) * ip[i];
+      y[i] = zp;
+    }
+    double yn = y[nc - 1];
+    for (int i = nc - 2; i >= 0; --i) {
+      yn = fma(-ml[i + 1], yn, y[i]);
+      y[i] = yn;
+    }
+  }
 }
 
 }  // namespace
@@ -244,8 +282,10 @@ p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose
 p4d_status particle_solve64(p4d_ctx* c, const double* rc, double* yc, const double* tN, int transpose) {
   if (c->NE == 0) return P4D_OK;
   PcArgs a = make_pc(c);
-  if (transpose) k_part64<true><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, rc, yc, tN);
-  else k_part64<false><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, rc, yc, tN);
+  const double* ip = c->tfac;
+  const double* ml = c->tfac + (size_t)c->NE * c->nc;
+  if (transpose) ::p4d::count_launch(), k_part64<true><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
+  else ::p4d::count_launch(), k_part64<false><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
