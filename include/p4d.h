@@ -84,6 +84,11 @@ typedef struct {
   const uint8_t* gamma_n;          /* [nx*ny] 1 = face (i,j) of the z = 0 boundary is grounded */
   const double* rgrid;             /* [nc] radial nodes / R_s, rgrid[0] = 0, rgrid[nc-1] = 1, increasing */
   int32_t nc;                      /* radial nodes per particle, 3 <= nc <= 32 */
+  const double* sigma_e;           /* optional [nelem] bulk solid conductivity per element (S/m);
+                                      NULL: sigma_n / sigma_p by region.  sigma_eff = eps_s^b sigma */
+  const double* Ds_e;              /* optional [nelem] solid diffusivity per element; when given, the
+                                      particle of an electrode node uses the volume-weighted mean over
+                                      its electrode elements and Ds is ignored */
 } p4d_mesh;
 
 /* Physics and solver options. */
@@ -207,6 +212,42 @@ p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_inf
    more than P4D_NOALLOC_MAX_NELEC electrode nodes, when x == y or before a
    p4d_jacobian_update; otherwise as p4d_jvp. */
 p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose);
+
+/* Newton's method for one backward-Euler step (paper section 4: the
+   monolithic residual R = [R_phis; R_phie; R_ce; R_cs] = 0, every linear
+   system solved by p4d_fgmres_solve).  phis, phie, ce, cs [device, updated
+   in place] hold the initial guess and receive the solution; ce_prev,
+   cs_prev [device] are the previous time level.  The residual is measured
+   in the Jacobi-scaled norm ||D^-1/2 R|| (D = diag J at the initial
+   guess); backtracking halves the step (at most 8 times) until that norm
+   decreases.  Converged when ||D^-1/2 R|| <= rtol ||D^-1/2 R_0|| or when the
+   full Newton step is below 1e-10 of the state in every field (the
+   residual has a rounding floor); NOT_CONVERGED after maxit iterations.
+   iters and info (last linear solve) may be NULL.  Returns OK,
+   NOT_CONVERGED, DOMAIN or a linear-solve failure.  Leaves the handle
+   linearized at the last accepted iterate but one. */
+p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce, double* cs,
+                            const double* ce_prev, const double* cs_prev, double rtol, int32_t maxit,
+                            int32_t* iters, p4d_info* info);
+
+/* Weights q of the terminal voltage V = q . u (full layout, [device] ndof
+   doubles): the mean of phi_s over the applied-current face Gamma_p
+   (bilinear face weights; phi_s = 0 on the grounded face). */
+p4d_status p4d_voltage_weights(p4d_handle h, double* q);
+
+/* Accumulate g_p += -lam^T dR/dp at `state` (the residual of one
+   backward-Euler step, paper section 4) for the per-element parameters
+   p = sigma (bulk solid conductivity), D_s (solid diffusivity, through the
+   volume-weighted node means) and eps (porosity, through kappa_eff,
+   D_e,eff and the electrolyte mass); eps_s is held fixed.  lam [device,
+   ndof]; g_sigma, g_Ds, g_eps [device, nelem], each may be NULL. */
+p4d_status p4d_param_grad(p4d_handle h, const p4d_state* state, const double* lam, double* g_sigma,
+                          double* g_Ds, double* g_eps);
+
+/* Adjoint coupling to the previous time level: out = -(dR_n/du_{n-1})^T lam
+   (only the c_e mass and the particle accumulation terms depend on the
+   previous state), [device] ndof doubles. */
+p4d_status p4d_adjoint_prev(p4d_handle h, const double* lam, double* out);
 
 /* Number of CUDA kernels the library has launched in this process so far
    (instrumentation for benchmarks; thread-safe, never reset). */

@@ -155,7 +155,13 @@ class Disc:
         self.M = Mn[self.enodes]
         self.S = Sn[self.enodes]
         self.Rs = np.asarray(mesh["Rs"], float)[self.enodes]
-        self.Ds = np.asarray(mesh["Ds"], float)[self.enodes]
+        if mesh.get("Ds_e") is not None:
+            # particle diffusivity = volume-weighted mean of the node's electrode elements
+            Dn = np.zeros(self.nn)
+            np.add.at(Dn, conn[el].ravel(), np.repeat(np.asarray(mesh["Ds_e"], float)[el] * self.vol[el] / 8.0, 8))
+            self.Ds = Dn[self.enodes] / self.M
+        else:
+            self.Ds = np.asarray(mesh["Ds"], float)[self.enodes]
         self.A = 3.0 * self.S / self.Rs
         p = self.p
         an = self.etype == 0
@@ -165,7 +171,11 @@ class Disc:
         self.u1 = np.where(an, p["ocp_n"][1], p["ocp_p"][1])
         b = p["brug"]
         sig_reg = np.where(an_el, p["sigma_n"], np.where(ca_el, p["sigma_p"], 0.0))
+        if mesh.get("sigma_e") is not None:
+            sig_reg = np.where(el, np.asarray(mesh["sigma_e"], float), 0.0)
+        self.sig_bulk = sig_reg
         self.sig = np.where(el, eps_s ** b * sig_reg, 0.0)
+        self.eps_s_e = eps_s
         self.kap = eps ** b * p["kappa"]
         self.Deff = eps ** b * p["De"]
         self.eps = eps

@@ -30,7 +30,7 @@ class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("hx", _dp), ("hy", _dp), ("hz", _dp), ("region", _u8p), ("eps", _dp), ("eps_s", _dp),
                 ("Rs", _dp), ("Ds", _dp), ("gamma_p", _u8p), ("gamma_n", _u8p), ("rgrid", _dp),
-                ("nc", C.c_int32)]
+                ("nc", C.c_int32), ("sigma_e", _dp), ("Ds_e", _dp)]
 
 
 class Params(C.Structure):
@@ -76,6 +76,11 @@ SIGNATURES = {
     "p4d_fgmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "p4d_adjoint_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "p4d_jvp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "p4d_newton_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(Info)]),
+    "p4d_voltage_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "p4d_param_grad": (C.c_int, [C.c_void_p, C.POINTER(State), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p4d_adjoint_prev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "p4d_launch_count": (C.c_longlong, []),
     "p4d_status_string": (C.c_char_p, [C.c_int]),
 }

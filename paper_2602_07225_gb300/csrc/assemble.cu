@@ -24,8 +24,9 @@ struct Phys {
 __global__ void k_assemble(Grid g, int nx, int ny, int nz, const double* __restrict__ hx,
                            const double* __restrict__ hy, const double* __restrict__ hz,
                            const uint8_t* __restrict__ region, const double* __restrict__ eps,
-                           const double* __restrict__ eps_s, const uint8_t* __restrict__ label, Phys ph,
-                           double* __restrict__ Jst, double* __restrict__ sfix) {
+                           const double* __restrict__ eps_s, const double* __restrict__ sig_e,
+                           const uint8_t* __restrict__ label, Phys ph, double* __restrict__ Jst,
+                           double* __restrict__ sfix) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int i = (int)(n % g.nnx);
@@ -45,7 +46,7 @@ __global__ void k_assemble(Grid g, int nx, int ny, int nz, const double* __restr
         const double a = hx[ei], b = hy[ej], cz = hz[ek];
         const double vol = a * b * cz;
         const uint8_t r = region[e];
-        const double sig = (r == 0 || r == 2) ? pow(eps_s[e], ph.brug) * (r == 0 ? ph.sigma_n : ph.sigma_p) : 0.0;
+        const double sig = (r == 0 || r == 2) ? pow(eps_s[e], ph.brug) * sig_e[e] : 0.0;
         const double epb = pow(eps[e], ph.brug);
         const double kap = epb * ph.kappa;
         const double Dd = epb * ph.De;
@@ -357,7 +358,7 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   P4D_TRYS(dalloc_t(c, &c->sfix, (size_t)3 * nn));
   Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt};
   ::p4d::count_launch(), k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
-                                                       eps, eps_s, c->label, ph, c->Jst, c->sfix);
+                                                       eps, eps_s, c->sig_e, c->label, ph, c->Jst, c->sfix);
   P4D_TRY(cudaGetLastError());
   P4D_TRYS(dalloc_t(c, &c->offsum, (size_t)3 * nn));
   P4D_TRYS(dalloc_t(c, &c->absoff, (size_t)3 * nn));

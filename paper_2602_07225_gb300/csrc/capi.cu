@@ -140,7 +140,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   c->ndof = 3 * nn + NE * nc;
 
   // ---- per electrode node: lumped volumes, particle constants
-  std::vector<double> Mn(nn, 0.0), Sn(nn, 0.0);
+  std::vector<double> Mn(nn, 0.0), Sn(nn, 0.0), Dn(nn, 0.0);
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -152,23 +152,33 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
           const int64_t n = node(i + (l & 1), j + ((l >> 1) & 1), k + ((l >> 2) & 1));
           Mn[n] += v8;
           Sn[n] += m->eps_s[e] * v8;
+          if (m->Ds_e) Dn[n] += m->Ds_e[e] * v8;
         }
       }
   std::vector<double> rref(3 * nc);
   double beta_ref = 0.0;
   radial_reference(m->rgrid, nc, prm->F, rref.data(), rref.data() + nc, rref.data() + 2 * nc, &beta_ref);
   c->beta_ref = beta_ref;
-  std::vector<double> Mj(NE), Aj(NE), kapj(NE), betaj(NE);
+  std::vector<double> Mj(NE), Aj(NE), kapj(NE), betaj(NE), Rj(NE);
   std::vector<uint8_t> et(NE);
   for (int64_t e = 0; e < NE; ++e) {
     const int64_t n = c->enodes_h[e];
-    const double R = m->Rs[n], D = m->Ds[n];
+    // D_s of the particle: the node value, or the volume-weighted mean of
+    // the per-element values over the node's electrode elements
+    const double R = m->Rs[n], D = m->Ds_e ? Dn[n] / Mn[n] : m->Ds[n];
+    Rj[e] = R;
     if (!(R > 0) || !(D > 0)) return P4D_ERR_INVALID_ARG;
     Mj[e] = Mn[n];
     Aj[e] = 3.0 * Sn[n] / R;
     kapj[e] = D / (R * R);
     betaj[e] = beta_ref / R;
     et[e] = (lab[n] & kLabAnode) ? 0 : 1;
+  }
+  // ---- per-element bulk solid conductivity
+  std::vector<double> sige(nelem, 0.0);
+  for (int64_t e = 0; e < nelem; ++e) {
+    const uint8_t r = m->region[e];
+    if (r == 0 || r == 2) sige[e] = m->sigma_e ? m->sigma_e[e] : (r == 0 ? prm->sigma_n : prm->sigma_p);
   }
   // ---- Gamma_p face weights (bilinear face integral of N_j)
   std::vector<double> gpw(nn, 0.0);
@@ -193,11 +203,14 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(upload(c, &c->betaj, betaj.data(), NE));
   P4D_TRYS(upload(c, &c->etype, et.data(), NE));
   P4D_TRYS(upload(c, &c->rref, rref.data(), 3 * nc));
-  uint8_t* reg_d = nullptr;
-  double *eps_d = nullptr, *epss_d = nullptr;
-  P4D_TRYS(upload(c, &reg_d, m->region, nelem));
-  P4D_TRYS(upload(c, &eps_d, m->eps, nelem));
-  P4D_TRYS(upload(c, &epss_d, m->eps_s, nelem));
+  P4D_TRYS(upload(c, &c->Rj, Rj.data(), NE));
+  P4D_TRYS(upload(c, &c->region, m->region, nelem));
+  P4D_TRYS(upload(c, &c->eps_e, m->eps, nelem));
+  P4D_TRYS(upload(c, &c->epss_e, m->eps_s, nelem));
+  P4D_TRYS(upload(c, &c->sig_e, sige.data(), nelem));
+  double gp_area = 0.0;
+  for (int64_t n = 0; n < nn; ++n) gp_area += gpw[n];
+  c->gp_area = gp_area;
 
   // ---- linearization workspace
   P4D_TRYS(dalloc_t(c, &c->lnce, nn));
@@ -222,7 +235,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRY(cudaMallocHost(&c->flags_h, sizeof(unsigned)));
   P4D_TRY(cudaMemset(c->flags, 0, sizeof(unsigned)));
 
-  P4D_TRYS(assemble_fixed(c, eps_d, epss_d, reg_d));
+  P4D_TRYS(assemble_fixed(c, c->eps_e, c->epss_e, c->region));
   P4D_TRYS(mg_plan(c));
   P4D_TRYS(mg_setup_fixed(c));
 
@@ -233,6 +246,8 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->Z, (size_t)c->mcap * c->kry_len));
   P4D_TRYS(dalloc_t(c, &c->w, c->kry_len));
   P4D_TRYS(dalloc_t(c, &c->r0, c->ndof));
+  P4D_TRYS(dalloc_t(c, &c->nwork, (size_t)5 * c->ndof));
+  P4D_TRYS(dalloc_t(c, &c->nrm4, 4));
   P4D_TRYS(dalloc_t(c, &c->tmp, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->bred, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->part, (size_t)1024 * 136));

@@ -144,14 +144,23 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
 __global__ void k_weights(const double* __restrict__ partial, int nblk, double* __restrict__ wf,
                           double* __restrict__ iwf, double* bn2) {
   if (threadIdx.x != 0) return;
-  double tot = 0.0;
+  // w_f = 1 / max(||b~_f||, 1e-2 ||b~||): fields balanced, but a field whose
+  // right-hand side is rounding noise is boosted at most 100-fold
+  double s4[4], all = 0.0;
   for (int f = 0; f < 4; ++f) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partial[b * 4 + f];
+    s4[f] = s;
+    all += s;
+  }
+  const double floor2 = 1e-4 * all;
+  double tot = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    const double s = fmax(s4[f], floor2);
     wf[f] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
     iwf[f] = s > 0.0 ? sqrt(s) : 1.0;
     bn2[f] = s;
-    tot += s > 0.0 ? 1.0 : 0.0;
+    tot += s > 0.0 ? s4[f] / s : 0.0;
   }
   bn2[4] = tot;
 }
@@ -498,11 +507,11 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     info->reorth = (int)c->hs_h[0];
     const double* bn2 = c->hs_h + 1;      // field norms^2 of b/sqd (weights: 1/sqrt)
     const double* rr = c->hs_h + 17;      // field norms^2 of s.(b - Jx)
-    double tot_r = 0.0, tot_b = 0.0;
+    double tot_r = 0.0;
+    const double tot_b = bn2[4];          // ||s.b||^2
     for (int f = 0; f < 4; ++f) {
-      info->rel_res_block[f] = bn2[f] > 0 ? std::sqrt(rr[f]) : std::sqrt(rr[f]);
+      info->rel_res_block[f] = std::sqrt(rr[f]);   // relative to the field's (floored) rhs norm
       tot_r += rr[f];
-      tot_b += bn2[f] > 0 ? 1.0 : 0.0;
     }
     info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
     info->ms_total = ms;

@@ -115,6 +115,14 @@ struct p4d_ctx {
   uint8_t* etype = nullptr;            // [NE] 0 anode, 1 cathode
   double* rref = nullptr;              // [3][nc] reference radial operator (R = D = 1): lo, di, up
   double beta_ref = 0.0;               // surface flux factor for R = 1
+  uint8_t* region = nullptr;           // [nelem]
+  double* eps_e = nullptr;             // [nelem] porosity
+  double* epss_e = nullptr;            // [nelem] active-material fraction
+  double* sig_e = nullptr;             // [nelem] bulk solid conductivity (region constants if not given)
+  double* Rj = nullptr;                // [NE] particle radius
+  double* nwork = nullptr;             // [4][ndof] Newton work (residual, step, trial state, trial residual)
+  double gp_area = 0.0;                // area of Gamma_p
+  double* nrm4 = nullptr;              // [4] device scratch for Newton field norms
 
   // fixed FP64 stencils [4][27][nn]: 0 K_sigma (lifted), 1 K_kappa, 2 C = M_eps/dt + K_D, 3 M_eps/dt
   double* Jst = nullptr;

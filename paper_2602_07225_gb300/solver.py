@@ -66,7 +66,9 @@ class P4DSolver:
         mesh = N.Mesh(nx=int(m["nx"]), ny=int(m["ny"]), nz=int(m["nz"]), hx=dp(m["hx"]), hy=dp(m["hy"]),
                       hz=dp(m["hz"]), region=up(m["region"]), eps=dp(m["eps"]), eps_s=dp(m["eps_s"]),
                       Rs=dp(m["Rs"]), Ds=dp(m["Ds"]), gamma_p=up(m["gamma_p"]), gamma_n=up(m["gamma_n"]),
-                      rgrid=dp(m["rgrid"]), nc=int(m["nc"]))
+                      rgrid=dp(m["rgrid"]), nc=int(m["nc"]),
+                      sigma_e=dp(m["sigma_e"]) if m.get("sigma_e") is not None else None,
+                      Ds_e=dp(m["Ds_e"]) if m.get("Ds_e") is not None else None)
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()
@@ -74,6 +76,7 @@ class P4DSolver:
                                 C.byref(h))
         N.check(st, "p4d_setup")
         self.h = h
+        self._nelem = int(m["nx"]) * int(m["ny"]) * int(m["nz"])
         nn, ne, nd, nc = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
         N.check(self.lib.p4d_get_sizes(h, C.byref(nn), C.byref(ne), C.byref(nd), C.byref(nc)), "p4d_get_sizes")
         self.nn, self.NE, self.ndof, self.nc = nn.value, ne.value, nd.value, nc.value
@@ -136,6 +139,31 @@ class P4DSolver:
         d = info.as_dict()
         d["status"] = st
         return x, d
+
+    def newton(self, s, rtol=1e-10, maxit=20):
+        """Newton solve of one backward-Euler step in place on s["phis"],
+        s["phie"], s["ce"], s["cs"] (previous level s["ce_prev"], s["cs_prev"])."""
+        it = C.c_int32()
+        info = N.Info()
+        st = self.lib.p4d_newton_solve(self.h, _ptr(_dev(s["phis"])), _ptr(_dev(s["phie"])), _ptr(_dev(s["ce"])),
+                                       _ptr(_dev(s["cs"])), _ptr(_dev(s["ce_prev"])), _ptr(_dev(s["cs_prev"])),
+                                       float(rtol), int(maxit), C.byref(it), C.byref(info))
+        N.check(st, "p4d_newton_solve")
+        return it.value, info.as_dict()
+
+    def voltage_weights(self):
+        q = torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        N.check(self.lib.p4d_voltage_weights(self.h, _ptr(q)), "p4d_voltage_weights")
+        return q
+
+    def param_grad(self, s, lam, g_sigma, g_Ds, g_eps):
+        N.check(self.lib.p4d_param_grad(self.h, C.byref(self._state(s)), _ptr(_dev(lam)), _ptr(_dev(g_sigma)),
+                                        _ptr(_dev(g_Ds)), _ptr(_dev(g_eps))), "p4d_param_grad")
+
+    def adjoint_prev(self, lam, out=None):
+        out = torch.empty_like(lam) if out is None else out
+        N.check(self.lib.p4d_adjoint_prev(self.h, _ptr(_dev(lam)), _ptr(_dev(out))), "p4d_adjoint_prev")
+        return out
 
     def close(self):
         if getattr(self, "h", None):
