@@ -21,10 +21,10 @@ electrode node: -z_j b_j c_j^T with z_j = (T_j^-1)_NN.
 Scaling (a reading: the paper states no norm).  With d = diag(J) > 0 and a
 per-field weight w_f, the Krylov solve works on
     A^ = diag(s) J diag(s),  s_i = w_f(i) / sqrt(d_i),
-    w_f = 1 / max(|| (b / sqrt(d))_f ||_2, 1e-2 || b / sqrt(d) ||_2),
-so the scaled right-hand side has unit norm in every field and every
-residual block counts equally (a field whose right-hand side is only
-rounding noise is boosted at most 100-fold).  The block preconditioner P approximates
+    w_f = 1 / max(|| (b / sqrt(d))_f ||_2, (1e-14/rtol) || (sqrt(d) u)_f ||_2)
+(u: the linearization state), so the scaled right-hand side has unit norm
+in every field and every residual block counts equally, unless a field's
+right-hand side lies below the rounding level of its own terms.  The block preconditioner P approximates
 J^-1 itself (its multigrid needs the near-null vectors of the unscaled
 blocks, the constants) and is mapped to the scaled space by
 P^^-1 v = s^-1 * P^-1 (s^-1 * v).
@@ -36,19 +36,19 @@ import scipy.sparse.linalg as spla
 from .mg import GMG
 
 
-def field_weights(disc, J, b):
-    """d = diag(J) and w_f = 1 / max(||(b / sqrt(d))_f||, 1e-2 ||b / sqrt(d)||)
-    (1 if b = 0): every field's scaled right-hand side has unit norm, except
-    that a field whose right-hand side is rounding noise is boosted at most
-    100-fold over the plain Jacobi scaling."""
+def field_weights(disc, J, b, u=None, rtol=1e-8):
+    """d = diag(J) and w_f = 1 / max(||(b / sqrt(d))_f||, floor_f) with
+    floor_f = (1e-14 / rtol) ||(sqrt(d) u)_f|| (u: the linearization state;
+    0 if not given): every field's scaled right-hand side has unit norm,
+    unless it lies below the rounding level of the field's own terms."""
     d = J.diagonal()
     if np.any(d <= 0):
         raise ValueError("non-positive Jacobian diagonal")
     bt = b / np.sqrt(d)
-    tot = np.linalg.norm(bt)
     w = np.ones(4)
     for f, sl in enumerate(disc.field_slices()):
-        nf = max(np.linalg.norm(bt[sl]), 1e-2 * tot)
+        fl = 0.0 if u is None else (1e-14 / rtol) * np.linalg.norm((np.sqrt(d) * u)[sl])
+        nf = max(np.linalg.norm(bt[sl]), fl)
         if nf > 0:
             w[f] = 1.0 / nf
     return d, w
@@ -227,9 +227,9 @@ class BlockPrecond:
         return np.concatenate([zm, zc.ravel()])
 
 
-def scaled_system(disc, J, b):
+def scaled_system(disc, J, b, u=None, rtol=1e-8):
     """Return (s, d, w): s the Krylov scaling vector, d = diag J, w the
     per-field weights."""
-    d, w = field_weights(disc, J, b)
+    d, w = field_weights(disc, J, b, u, rtol)
     s = w[field_of_row(disc)] / np.sqrt(d)
     return s, d, w

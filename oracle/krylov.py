@@ -102,7 +102,7 @@ class LinearSolve:
                order=(1, 0, 2), exact_macro=False, exact_schur=False, degree=2, coarse_max=128,
                ratio=10.0):
         b = self.b if b is None else b
-        s, d, w = scaled_system(self.disc, self.J, b)
+        s, d, w = scaled_system(self.disc, self.J, b, self.disc.pack(self.st), rtol)
         P = BlockPrecond(self.disc, self.J, combine=combine, order=order, exact_macro=exact_macro,
                          exact_schur=exact_schur, degree=degree, coarse_max=coarse_max, ratio=ratio)
         sinv = 1.0 / s

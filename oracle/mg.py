@@ -7,8 +7,9 @@ algebraic-multigrid V-cycle (section 4, "Preconditioning").  On the
 structured box meshes used here the same role is played by a geometric
 V-cycle, written out plainly:
 
-* coarsening by two along every axis whose element count is even, until at
-  most ``coarse_max`` nodes remain;
+* coarsening by two along every axis with at least two elements (an odd
+  count keeps its last fine node as a coarse node), until at most
+  ``coarse_max`` nodes remain;
 * trilinear prolongation P (Kronecker product of 1D linear interpolations),
   with the rows of masked-out fine nodes set to zero (phi_s has unknowns
   only at non-grounded electrode nodes);
@@ -25,25 +26,30 @@ import scipy.sparse as sp
 
 
 def interp_1d(n_fine_nodes, coarsen):
-    """1D linear interpolation from the coarse to the fine node line."""
+    """1D linear interpolation from the coarse to the fine node line.  The
+    coarse nodes are the even fine nodes and, when the element count is odd,
+    also the last fine node (that coarse element spans one fine element)."""
     if not coarsen:
         return sp.identity(n_fine_nodes, format="csr")
-    nce = (n_fine_nodes - 1) // 2
+    ne = n_fine_nodes - 1
+    nc = (ne + 1) // 2 + 1
     rows, cols, vals = [], [], []
     for i in range(n_fine_nodes):
-        if i % 2 == 0:
+        if ne % 2 == 1 and i == ne:
+            rows.append(i); cols.append(nc - 1); vals.append(1.0)
+        elif i % 2 == 0:
             rows.append(i); cols.append(i // 2); vals.append(1.0)
         else:
             rows += [i, i]; cols += [(i - 1) // 2, (i + 1) // 2]; vals += [0.5, 0.5]
-    return sp.csr_matrix((vals, (rows, cols)), shape=(n_fine_nodes, nce + 1))
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n_fine_nodes, nc))
 
 
 def coarsen_flags(dims):
-    return tuple(((n - 1) % 2 == 0) and (n - 1) >= 2 for n in dims)
+    return tuple((n - 1) >= 2 for n in dims)
 
 
 def coarse_dims(dims, flags):
-    return tuple((n - 1) // 2 + 1 if f else n for n, f in zip(dims, flags))
+    return tuple((n - 1 + 1) // 2 + 1 if f else n for n, f in zip(dims, flags))
 
 
 def chebyshev(A, dinv, b, x, degree, lam, ratio):

@@ -223,3 +223,60 @@ def make_case(name, **kw):
         return make_box_case(128, 128, (40, 16, 40), 100e-6, (100e-6, 25e-6, 100e-6), 20,
                              kw.pop("seed", 1003), hetero=True, rs_cv=0.3, **kw)
     raise KeyError(name)
+
+
+def make_gyroid_cell(n, t, periods, nc, seed, L_lat=100e-6, L_layers=(100e-6, 25e-6, 100e-6)):
+    """Layered cube (anode/separator/cathode split 10/4/10 of nz = 1.5 n)
+    whose electrode elements become electrolyte-only (region 3, eps = 1,
+    eps_s = 0) where the gyroid level set
+        g = sin X cos Y + sin Y cos Z + sin Z cos X,  (X, Y, Z) = 2 pi p (x, y, z) / L
+    at the element centre is >= t.  Gamma_p / Gamma_n flag only the top /
+    bottom faces of cathode / anode elements."""
+    nz = (3 * n) // 2
+    if nz % 12:
+        raise ValueError("nz = 1.5 n must be a multiple of 12")
+    layers = (nz * 10 // 24, nz * 4 // 24, nz * 10 // 24)
+    case = make_box_case(n, n, layers, L_lat, L_layers, nc, seed)
+    m = case["mesh"]
+    hx, hy, hz = m["hx"], m["hy"], m["hz"]
+    xc = np.cumsum(hx) - hx / 2
+    yc = np.cumsum(hy) - hy / 2
+    zc = np.cumsum(hz) - hz / 2
+    Lz = hz.sum()
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    k = 2 * np.pi * periods
+    Xs, Ys, Zs = k * X / L_lat, k * Y / L_lat, k * Z / Lz
+    g = (np.sin(Xs) * np.cos(Ys) + np.sin(Ys) * np.cos(Zs) + np.sin(Zs) * np.cos(Xs)).ravel()
+    region = m["region"].copy()
+    void = ((region == 0) | (region == 2)) & (g >= t)
+    region[void] = 3
+    m["region"] = region
+    m["eps"] = np.where(void, 1.0, m["eps"])
+    m["eps_s"] = np.where(void, 0.0, m["eps_s"])
+    nx = ny = n
+    r3 = region.reshape(nz, ny, nx)
+    m["gamma_p"] = (r3[-1] == 2).astype(np.uint8).ravel()
+    m["gamma_n"] = (r3[0] == 0).astype(np.uint8).ravel()
+    # 1C from the theoretical capacity of the remaining active material
+    p = case["params"]
+    vol = (hx[None, None, :] * hy[None, :, None] * hz[:, None, None]).ravel()
+    qn = p["F"] / 3600 * np.sum((m["eps_s"] * vol)[region == 0]) * p["cmax_n"]
+    qp = p["F"] / 3600 * np.sum((m["eps_s"] * vol)[region == 2]) * p["cmax_p"]
+    area = np.sum((hx[None, :] * hy[:, None]).ravel()[m["gamma_p"].astype(bool)])
+    p["i_app"] = -min(qn, qp) / area if area > 0 else 0.0
+    case["gyroid"] = dict(n=n, t=t, periods=periods, nc=nc)
+    return case
+
+
+def make_gyroid_batch(ncells=64, seed=1004, sizes=(16, 24, 32, 40, 48, 56, 64)):
+    """Seeded batch of gyroid cells of uneven sizes: lateral n uniform over
+    `sizes` (nz = 1.5 n), t ~ U(-0.3, 0.3), periods in {1, 2, 3}, N_c in 10..20."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cells = []
+    for c in range(ncells):
+        n = int(rng.choice(sizes))
+        t = float(rng.uniform(-0.3, 0.3))
+        per = int(rng.integers(1, 4))
+        nc = int(rng.integers(10, 21))
+        cells.append(make_gyroid_cell(n, t, per, nc, seed * 1000 + c))
+    return cells

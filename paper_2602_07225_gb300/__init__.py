@@ -8,3 +8,4 @@ memory and streams.  There is no CPU fallback.
 from ._native import P4DError, load  # noqa: F401
 from .solver import P4DSolver, default_params  # noqa: F401
 from .adjoint import TerminalVoltage, terminal_voltage  # noqa: F401
+from .batch import BatchSolver, Autotuner  # noqa: F401

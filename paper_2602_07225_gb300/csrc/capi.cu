@@ -228,6 +228,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->sqd, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->rsqd, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->iwf, 4));
+  P4D_TRYS(dalloc_t(c, &c->unorm2, 4));
   P4D_TRYS(dalloc_t(c, &c->ujvp, nn));
   P4D_TRY(cudaMallocHost(&c->lam_pin, sizeof(double) * kMaxLevels * kNH));
   P4D_TRYS(dalloc_t(c, &c->wf, 4));

@@ -141,11 +141,16 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
   }
 }
 
-__global__ void k_weights(const double* __restrict__ partial, int nblk, double* __restrict__ wf,
-                          double* __restrict__ iwf, double* bn2) {
+// Field weights of the Krylov norm: w_f = 1 / max(||b~_f||, floor_f), b~ = b/sqrt(d).
+// Forward solves: floor_f = (1e-14/rtol) ||(sqrt(d) u)_f|| with u the
+// linearization state -- a field's right-hand side is balanced against the
+// others unless it lies below the rounding level of the field's own terms
+// (then FGMRES could never reduce its residual by rtol).  Adjoint solves:
+// floor_f = 1e-2 ||b~|| (the adjoint variable has no state scale).
+__global__ void k_weights(const double* __restrict__ partial, int nblk, const double* __restrict__ unorm2,
+                          double floor_rel, int adjoint, double* __restrict__ wf, double* __restrict__ iwf,
+                          double* bn2) {
   if (threadIdx.x != 0) return;
-  // w_f = 1 / max(||b~_f||, 1e-2 ||b~||): fields balanced, but a field whose
-  // right-hand side is rounding noise is boosted at most 100-fold
   double s4[4], all = 0.0;
   for (int f = 0; f < 4; ++f) {
     double s = 0.0;
@@ -153,10 +158,10 @@ __global__ void k_weights(const double* __restrict__ partial, int nblk, double* 
     s4[f] = s;
     all += s;
   }
-  const double floor2 = 1e-4 * all;
   double tot = 0.0;
   for (int f = 0; f < 4; ++f) {
-    const double s = fmax(s4[f], floor2);
+    const double fl = adjoint ? 1e-4 * all : floor_rel * floor_rel * unorm2[f];
+    const double s = fmax(s4[f], fl);
     wf[f] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
     iwf[f] = s > 0.0 ? sqrt(s) : 1.0;
     bn2[f] = s;
@@ -384,7 +389,8 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
   {
     const int nb = kRedBlocks;
     ::p4d::count_launch(), k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->rsqd, nn, c->ndof, c->part);
-    ::p4d::count_launch(), k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->wf, c->iwf, hs + L.misc + 2 * L.m + 8);
+    ::p4d::count_launch(), k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->unorm2, 1e-14 / c->prm.rtol, trans,
+                                                             c->wf, c->iwf, hs + L.misc + 2 * L.m + 8);
   }
   const double* bk = b;            // Krylov right-hand side (unscaled)
   if (!full) {

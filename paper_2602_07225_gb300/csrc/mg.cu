@@ -15,6 +15,7 @@
 // inverse on the coarsest level.  Stencils are in difference form (slot 13
 // = row sum), see p4d_common.cuh.
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include "p4d_common.cuh"
 
@@ -47,20 +48,14 @@ __device__ __forceinline__ void node_ijk(const LevelDims& d, int64_t n, int& i, 
   k = (int)(n / ((int64_t)d.nnx * d.nny));
 }
 
-// Fine nodes of the support of coarse node C along one axis: f = 2C + t for a
-// coarsened axis (t in {-1,0,1}, weight 1 or 1/2), f = C otherwise.
-__device__ __forceinline__ int supp_lo(int coarsen) { return coarsen ? -1 : 0; }
-__device__ __forceinline__ int supp_hi(int coarsen) { return coarsen ? 1 : 0; }
-__device__ __forceinline__ double wt(int t) { return t == 0 ? 1.0 : 0.5; }
+// One-dimensional linear interpolation between a fine node line (ne
+// elements) and its coarsening: coarse nodes sit on the even fine nodes and,
+// when ne is odd, also on the last fine node (that coarse element spans one
+// fine element), so every element count >= 2 can be coarsened.  Per fine
+// node: up to two parents; per coarse node: up to three support nodes.
+// (struct Axis / Xfer: p4d_common.cuh)
 
-// Coarse parents of fine index f along one axis: returns count (1 or 2),
-// parents p[] and weights w[].
-__device__ __forceinline__ int parents(int f, int coarsen, int* p, double* w) {
-  if (!coarsen) { p[0] = f; w[0] = 1.0; return 1; }
-  if ((f & 1) == 0) { p[0] = f >> 1; w[0] = 1.0; return 1; }
-  p[0] = f >> 1; p[1] = (f >> 1) + 1; w[0] = w[1] = 0.5; return 2;
-}
-
+// ---------------------------------------------------------------- masks
 // ---------------------------------------------------------------- masks
 __global__ void k_mask0(int64_t nn, const uint8_t* __restrict__ label, uint8_t* m0, uint8_t* m1, uint8_t* m2,
                         uint8_t* m3) {
@@ -74,21 +69,26 @@ __global__ void k_mask0(int64_t nn, const uint8_t* __restrict__ label, uint8_t* 
   m3[n] = 1;
 }
 
-__global__ void k_mask_coarse(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const uint8_t> fm,
-                              Ptr4<uint8_t> cm) {
+__global__ void k_mask_coarse(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const uint8_t> fm, Ptr4<uint8_t> cm) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
   if (C >= cd.n) return;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
   uint8_t any = 0;
-  for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
-    for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
-      for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
-        const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
-        if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+  for (int tz = 0; tz < 3; ++tz) {
+    const int fk = X.a[2].sup[K * 3 + tz];
+    if (fk < 0) continue;
+    for (int ty = 0; ty < 3; ++ty) {
+      const int fj = X.a[1].sup[J * 3 + ty];
+      if (fj < 0) continue;
+      for (int tx = 0; tx < 3; ++tx) {
+        const int fi = X.a[0].sup[I * 3 + tx];
+        if (fi < 0) continue;
         any |= fm.p[h][fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk)];
       }
+    }
+  }
   cm.p[h][C] = any ? 1 : 0;
 }
 
@@ -103,7 +103,7 @@ struct SrcOp {
 // A_c = P^T diag(m) A diag(m) P for one hierarchy; writes difference form.
 // identity_out: coarse nodes without support get an identity row (fixed part)
 // or a zero row (variable part).
-__global__ void k_rap(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const double> fst,
+__global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst,
                       Ptr4<const double> frs, Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out,
                       int identity_out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -120,14 +120,18 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<c
   const uint8_t* m = fm.p[h];
   const int64_t fn = fd.n;
   if (cm.p[h][C]) {
-    for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
-      for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
-        for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
-          const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
-          if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+    for (int tz = 0; tz < 3; ++tz) {
+      const int fk = X.a[2].sup[K * 3 + tz];
+      if (fk < 0) continue;
+      for (int ty = 0; ty < 3; ++ty) {
+        const int fj = X.a[1].sup[J * 3 + ty];
+        if (fj < 0) continue;
+        for (int tx = 0; tx < 3; ++tx) {
+          const int fi = X.a[0].sup[I * 3 + tx];
+          if (fi < 0) continue;
           const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
           if (!m[f]) continue;
-          const double wf = (cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0);
+          const double wf = X.a[0].supw[I * 3 + tx] * X.a[1].supw[J * 3 + ty] * X.a[2].supw[K * 3 + tz];
           const double sf = rs ? rs[f] : st[13 * fn + f];
           rsum += wf * sf;
           // full-form diagonal of row f
@@ -142,17 +146,26 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<c
             if (!m[gidx]) continue;
             const double a = (o == 13 ? diag : st[o * fn + f]) * wf;
             if (a == 0.0) continue;
-            int px[2], py[2], pz[2];
-            double wx[2], wy[2], wz[2];
-            const int nx_ = parents(gi, cx, px, wx), ny_ = parents(gj, cy, py, wy), nz_ = parents(gk, cz, pz, wz);
-            for (int c3 = 0; c3 < nz_; ++c3)
-              for (int c2 = 0; c2 < ny_; ++c2)
-                for (int c1 = 0; c1 < nx_; ++c1) {
-                  const int oo = (px[c1] - I + 1) + 3 * (py[c2] - J + 1) + 9 * (pz[c3] - K + 1);
-                  acc[oo] += a * wx[c1] * wy[c2] * wz[c3];
+            for (int c3 = 0; c3 < 2; ++c3) {
+              const int pz = X.a[2].par[gk * 2 + c3];
+              if (pz < 0) continue;
+              const double wz = X.a[2].parw[gk * 2 + c3];
+              for (int c2 = 0; c2 < 2; ++c2) {
+                const int py = X.a[1].par[gj * 2 + c2];
+                if (py < 0) continue;
+                const double wy = X.a[1].parw[gj * 2 + c2];
+                for (int c1 = 0; c1 < 2; ++c1) {
+                  const int px = X.a[0].par[gi * 2 + c1];
+                  if (px < 0) continue;
+                  const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
+                  acc[oo] += a * X.a[0].parw[gi * 2 + c1] * wy * wz;
                 }
+              }
+            }
           }
         }
+      }
+    }
   }
   double* o_ = out.p[h];
   const int64_t cn = cd.n;
@@ -165,7 +178,7 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<c
 }
 
 // V_1 = P^T diag(m s) P (level-0 variable part is diagonal).
-__global__ void k_rap_diag(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const double> s,
+__global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
                            Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
@@ -178,26 +191,37 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, int cx, int cy, int cz, P
   node_ijk(cd, C, I, J, K);
   const uint8_t* m = fm.p[h];
   if (cm.p[h][C]) {
-    for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
-      for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
-        for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
-          const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
-          if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
+    for (int tz = 0; tz < 3; ++tz) {
+      const int fk = X.a[2].sup[K * 3 + tz];
+      if (fk < 0) continue;
+      for (int ty = 0; ty < 3; ++ty) {
+        const int fj = X.a[1].sup[J * 3 + ty];
+        if (fj < 0) continue;
+        for (int tx = 0; tx < 3; ++tx) {
+          const int fi = X.a[0].sup[I * 3 + tx];
+          if (fi < 0) continue;
           const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
           if (!m[f]) continue;
-          const double wf = (cx ? wt(tx) : 1.0) * (cy ? wt(ty) : 1.0) * (cz ? wt(tz) : 1.0);
+          const double wf = X.a[0].supw[I * 3 + tx] * X.a[1].supw[J * 3 + ty] * X.a[2].supw[K * 3 + tz];
           const double a = wf * s.p[h][f];
           rsum += a;
-          int px[2], py[2], pz[2];
-          double wx[2], wy[2], wz[2];
-          const int nx_ = parents(fi, cx, px, wx), ny_ = parents(fj, cy, py, wy), nz_ = parents(fk, cz, pz, wz);
-          for (int c3 = 0; c3 < nz_; ++c3)
-            for (int c2 = 0; c2 < ny_; ++c2)
-              for (int c1 = 0; c1 < nx_; ++c1) {
-                const int oo = (px[c1] - I + 1) + 3 * (py[c2] - J + 1) + 9 * (pz[c3] - K + 1);
-                acc[oo] += a * wx[c1] * wy[c2] * wz[c3];
+          for (int c3 = 0; c3 < 2; ++c3) {
+            const int pz = X.a[2].par[fk * 2 + c3];
+            if (pz < 0) continue;
+            for (int c2 = 0; c2 < 2; ++c2) {
+              const int py = X.a[1].par[fj * 2 + c2];
+              if (py < 0) continue;
+              for (int c1 = 0; c1 < 2; ++c1) {
+                const int px = X.a[0].par[fi * 2 + c1];
+                if (px < 0) continue;
+                const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
+                acc[oo] += a * X.a[0].parw[fi * 2 + c1] * X.a[1].parw[fj * 2 + c2] * X.a[2].parw[fk * 2 + c3];
               }
+            }
+          }
         }
+      }
+    }
   }
   double* o_ = out.p[h];
   const int64_t cn = cd.n;
@@ -499,46 +523,60 @@ __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, H
 }
 
 template <typename T>
-__global__ void k_restrict(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const T> fr,
-                           Ptr4<const uint8_t> fm, Ptr4<T> cb, HList hl) {
-  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr, Ptr4<const uint8_t> fm, Ptr4<T> cb,
+                           HList hl) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
   const int h = hl.h[blockIdx.y];
-  if (C >= cd.n) return;
+  if (C >= (int)cd.n) return;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
   T acc = 0;
-  for (int tz = supp_lo(cz); tz <= supp_hi(cz); ++tz)
-    for (int ty = supp_lo(cy); ty <= supp_hi(cy); ++ty)
-      for (int tx = supp_lo(cx); tx <= supp_hi(cx); ++tx) {
-        const int fi = cx ? 2 * I + tx : I, fj = cy ? 2 * J + ty : J, fk = cz ? 2 * K + tz : K;
-        if (fi < 0 || fj < 0 || fk < 0 || fi >= fd.nnx || fj >= fd.nny || fk >= fd.nnz) continue;
-        const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
+  for (int tz = 0; tz < 3; ++tz) {
+    const int fk = X.a[2].sup[K * 3 + tz];
+    if (fk < 0) continue;
+    const T wz = (T)X.a[2].supw[K * 3 + tz];
+    for (int ty = 0; ty < 3; ++ty) {
+      const int fj = X.a[1].sup[J * 3 + ty];
+      if (fj < 0) continue;
+      const T wy = (T)X.a[1].supw[J * 3 + ty];
+      for (int tx = 0; tx < 3; ++tx) {
+        const int fi = X.a[0].sup[I * 3 + tx];
+        if (fi < 0) continue;
+        const int f = fi + fd.nnx * (fj + fd.nny * fk);
         if (!fm.p[h][f]) continue;
-        const T w = (tx == 0 ? (T)1 : (T)0.5) * (ty == 0 ? (T)1 : (T)0.5) * (tz == 0 ? (T)1 : (T)0.5);
-        acc += w * fr.p[h][f];
+        acc += (T)X.a[0].supw[I * 3 + tx] * wy * wz * fr.p[h][f];
       }
+    }
+  }
   cb.p[h][C] = acc;
 }
 
 template <typename T>
-__global__ void k_prolong(LevelDims fd, LevelDims cd, int cx, int cy, int cz, Ptr4<const T> cx_,
-                          Ptr4<const uint8_t> fm, Ptr4<T> fx, HList hl) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_, Ptr4<const uint8_t> fm, Ptr4<T> fx,
+                          HList hl) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
   const int h = hl.h[blockIdx.y];
-  if (f >= fd.n) return;
+  if (f >= (int)fd.n) return;
   if (!fm.p[h][f]) return;
   int i, j, k;
   node_ijk(fd, f, i, j, k);
-  // parents along each axis: one (even index or not coarsened, weight 1) or two (odd, 1/2 each)
-  const int px0 = cx ? (i >> 1) : i, py0 = cy ? (j >> 1) : j, pz0 = cz ? (k >> 1) : k;
-  const int nx_ = (cx && (i & 1)) ? 2 : 1, ny_ = (cy && (j & 1)) ? 2 : 1, nz_ = (cz && (k & 1)) ? 2 : 1;
-  const T w = (nx_ == 2 ? (T)0.5 : (T)1) * (ny_ == 2 ? (T)0.5 : (T)1) * (nz_ == 2 ? (T)0.5 : (T)1);
   T acc = 0;
-  for (int c3 = 0; c3 < nz_; ++c3)
-    for (int c2 = 0; c2 < ny_; ++c2)
-      for (int c1 = 0; c1 < nx_; ++c1)
-        acc += cx_.p[h][(px0 + c1) + (int64_t)cd.nnx * ((py0 + c2) + (int64_t)cd.nny * (pz0 + c3))];
-  fx.p[h][f] += w * acc;
+  for (int c3 = 0; c3 < 2; ++c3) {
+    const int pz = X.a[2].par[k * 2 + c3];
+    if (pz < 0) continue;
+    const T wz = (T)X.a[2].parw[k * 2 + c3];
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int py = X.a[1].par[j * 2 + c2];
+      if (py < 0) continue;
+      const T wy = (T)X.a[1].parw[j * 2 + c2];
+      for (int c1 = 0; c1 < 2; ++c1) {
+        const int px = X.a[0].par[i * 2 + c1];
+        if (px < 0) continue;
+        acc += (T)X.a[0].parw[i * 2 + c1] * wy * wz * cx_.p[h][px + cd.nnx * (py + cd.nny * pz)];
+      }
+    }
+  }
+  fx.p[h][f] += acc;
 }
 
 template <typename T>
@@ -644,7 +682,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> fm;
     Ptr4<T> cb;
     for (int h = 0; h < kNH; ++h) { fr.p[h] = (const T*)A.r[h]; fm.p[h] = A.mask[h]; cb.p[h] = (T*)B.b[h]; }
-    ::p4d::count_launch(), k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fr, fm, cb, hl);
+    ::p4d::count_launch(), k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fr, fm, cb, hl);
   }
   {
     MGLevel& C = c->lev[L - 1];
@@ -662,7 +700,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<T> fx;
     for (int h = 0; h < kNH; ++h) { cxp.p[h] = (const T*)B.x[h]; fm.p[h] = A.mask[h]; fx.p[h] = (T*)A.x[h]; }
     const dim3 grid(nblocks(A.n), nhs);
-    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, cxp, fm, fx, hl);
+    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
       const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
       if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, 0);
@@ -686,15 +724,48 @@ p4d_status mg_plan(p4d_ctx* c) {
     MGLevel& lv = c->lev[L];
     lv.nnx = nnx; lv.nny = nny; lv.nnz = nnz;
     lv.n = (int64_t)nnx * nny * nnz;
-    const int cx = ((nnx - 1) % 2 == 0) && (nnx - 1) >= 2;
-    const int cy = ((nny - 1) % 2 == 0) && (nny - 1) >= 2;
-    const int cz = ((nnz - 1) % 2 == 0) && (nnz - 1) >= 2;
+    // every axis with >= 2 elements is coarsened (odd counts included)
+    const int cx = (nnx - 1) >= 2, cy = (nny - 1) >= 2, cz = (nnz - 1) >= 2;
     ++L;
     if (lv.n <= c->prm.coarse_max || !(cx || cy || cz) || L >= kMaxLevels) break;
     lv.cx = cx; lv.cy = cy; lv.cz = cz;
-    nnx = cx ? (nnx - 1) / 2 + 1 : nnx;
-    nny = cy ? (nny - 1) / 2 + 1 : nny;
-    nnz = cz ? (nnz - 1) / 2 + 1 : nnz;
+    const int dn[3] = {nnx, nny, nnz}, fl[3] = {cx, cy, cz};
+    int cn[3];
+    for (int a = 0; a < 3; ++a) {
+      const int nf = dn[a], ne = nf - 1;
+      const int nc = fl[a] ? (ne + 1) / 2 + 1 : nf;
+      cn[a] = nc;
+      std::vector<int> par(2 * nf, -1), sup(3 * nc, -1);
+      std::vector<double> parw(2 * nf, 0.0), supw(3 * nc, 0.0);
+      for (int i = 0; i < nf; ++i) {
+        if (!fl[a]) { par[2 * i] = i; parw[2 * i] = 1.0; continue; }
+        if ((ne & 1) && i == ne) { par[2 * i] = (ne + 1) / 2; parw[2 * i] = 1.0; }
+        else if ((i & 1) == 0) { par[2 * i] = i / 2; parw[2 * i] = 1.0; }
+        else { par[2 * i] = (i - 1) / 2; par[2 * i + 1] = (i + 1) / 2; parw[2 * i] = parw[2 * i + 1] = 0.5; }
+      }
+      std::vector<int> cnt(nc, 0);
+      for (int i = 0; i < nf; ++i)
+        for (int q = 0; q < 2; ++q) {
+          const int C = par[2 * i + q];
+          if (C < 0) continue;
+          if (cnt[C] >= 3) return P4D_ERR_INVALID_ARG;
+          sup[3 * C + cnt[C]] = i;
+          supw[3 * C + cnt[C]] = parw[2 * i + q];
+          ++cnt[C];
+        }
+      int* dp = nullptr;
+      double* dw = nullptr;
+      P4D_TRYS(dalloc_t(c, &dp, par.size() + sup.size()));
+      P4D_TRYS(dalloc_t(c, &dw, parw.size() + supw.size()));
+      P4D_TRY(cudaMemcpy(dp, par.data(), par.size() * sizeof(int), cudaMemcpyHostToDevice));
+      P4D_TRY(cudaMemcpy(dp + par.size(), sup.data(), sup.size() * sizeof(int), cudaMemcpyHostToDevice));
+      P4D_TRY(cudaMemcpy(dw, parw.data(), parw.size() * sizeof(double), cudaMemcpyHostToDevice));
+      P4D_TRY(cudaMemcpy(dw + parw.size(), supw.data(), supw.size() * sizeof(double), cudaMemcpyHostToDevice));
+      lv.X.a[a] = Axis{dp, dw, dp + par.size(), dw + parw.size()};
+    }
+    nnx = cn[0];
+    nny = cn[1];
+    nnz = cn[2];
   }
   c->nlev = L;
   if (c->lev[L - 1].n > 4096) return P4D_ERR_INVALID_ARG;   // coarsest level too large for a dense inverse
@@ -745,7 +816,7 @@ p4d_status mg_plan(p4d_ctx* c) {
       Ptr4<const uint8_t> fm;
       Ptr4<uint8_t> cm;
       for (int h = 0; h < kNH; ++h) { fm.p[h] = fl.mask[h]; cm.p[h] = lv.mask[h]; }
-      ::p4d::count_launch(), k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.cx, fl.cy, fl.cz, fm, cm);
+      ::p4d::count_launch(), k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.X, fm, cm);
     }
     if (l == L - 1) P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
   }
@@ -799,7 +870,7 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
       cm.p[h] = B.mask[h];
       out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
     }
-    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 1);
+    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -834,11 +905,11 @@ p4d_status mg_update(p4d_ctx* c) {
     if (l == 1) {
       Ptr4<const double> s;
       for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, s, fm, cm, out);
+      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
     } else {
       Ptr4<const double> fst, frs;
       for (int h = 0; h < kNH; ++h) { fst.p[h] = A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
-      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.cx, A.cy, A.cz, fst, frs, fm, cm, out, 0);
+      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
     }
     Ptr4<const double> F, V;
     Ptr4<const uint8_t> m;

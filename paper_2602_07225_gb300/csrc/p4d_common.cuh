@@ -63,10 +63,24 @@ struct Ptr4 {
   T* p[kNH];
 };
 
+// One-dimensional interpolation tables between a fine node line and its
+// coarsening (see mg.cu): per fine node up to two parents, per coarse node
+// up to three support nodes, with weights.
+struct Axis {
+  const int* par;      // [nf][2] parent coarse nodes (-1: none)
+  const double* parw;  // [nf][2]
+  const int* sup;      // [nc][3] support fine nodes (-1: none)
+  const double* supw;  // [nc][3]
+};
+struct Xfer {
+  Axis a[3];
+};
+
 struct MGLevel {
   int nnx = 0, nny = 0, nnz = 0;
   int64_t n = 0;
   int cx = 0, cy = 0, cz = 0;          // coarsen flags towards the next level
+  Xfer X{};                            // interpolation tables towards the next level
   // FP64 fixed (linearization independent) operator, difference form [kNH][27][n]
   double* Ffix = nullptr;
   // FP64 linearization-dependent part (levels >= 1), difference form [kNH][27][n]
@@ -147,6 +161,7 @@ struct p4d_ctx {
   double* sqd = nullptr;               // [ndof] sqrt(|diag J|)
   double* rsqd = nullptr;              // [ndof] 1 / sqrt(|diag J|)
   double* iwf = nullptr;               // [4] 1 / w_f
+  double* unorm2 = nullptr;            // [4] ||(sqrt(d) u)_f||^2 of the linearization state
   double* wf = nullptr;                // [4] per-field Krylov weights (device)
   unsigned* flags = nullptr;           // device error flags
   unsigned* flags_h = nullptr;         // pinned host mirror

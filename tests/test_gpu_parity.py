@@ -16,6 +16,7 @@ CASES = {
     "odd": lambda: make_box_case(6, 4, (4, 2, 4), 30e-6, (40e-6, 15e-6, 40e-6), 5, 77),
     "hetero": lambda: make_box_case(8, 8, (6, 4, 6), 60e-6, (60e-6, 25e-6, 60e-6), 6, 1234, hetero=True,
                                     rs_cv=0.3),
+    "oddcoarse": lambda: make_box_case(11, 9, (7, 3, 7), 40e-6, (45e-6, 20e-6, 45e-6), 5, 99),
 }
 
 
@@ -78,7 +79,7 @@ def test_jvp_parity(name, transpose):
     assert _field_rel(d, y, y_ref) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "odd"])
+@pytest.mark.parametrize("name", ["tiny", "cube8", "odd", "oddcoarse"])
 @pytest.mark.parametrize("combine", ["additive", "multiplicative"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_precond_fp64_matches_oracle_algorithm(name, combine, transpose):
@@ -118,6 +119,11 @@ def test_adjointness_on_gpu(name):
         assert abs(a - b) <= 1e-12 * scale, (op.__name__, a, b)
 
 
+# solution error per unit of scaled residual: ~1-2 for the layered cubes,
+# ~25 for meshes whose coarse grids keep half-width last elements
+AMPLIFICATION = {"oddcoarse": 25.0}
+
+
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fgmres_fp64_matches_direct(name, mode):
@@ -129,7 +135,7 @@ def test_fgmres_fp64_matches_direct(name, mode):
     err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
     assert info["status"] == 0, info
     assert info["rel_res"] <= 2e-10, info
-    assert err <= 1e-9, (err, info)
+    assert err <= 1e-9 * AMPLIFICATION.get(name, 1.0), (err, info)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -143,7 +149,7 @@ def test_fgmres_mixed_matches_direct(name, precision, combine):
     x_ref = LinearSolve(d, ref).direct()
     err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
     assert info["status"] == 0, info
-    assert err <= 1e-7, (err, info)
+    assert err <= 1e-7 * AMPLIFICATION.get(name, 1.0), (err, info)
 
 
 def test_iteration_counts_match_oracle():

@@ -232,12 +232,17 @@ def test_fgmres_matches_direct(combine):
     assert its < 60
 
 
+@pytest.mark.parametrize("odd", [False, True])
 @pytest.mark.parametrize("block,limit", [(1, 0.25), (2, 0.25), ("phis_anode", 0.3), ("phis_cathode", 0.3)])
-def test_multigrid_convergence_factor(block, limit):
+def test_multigrid_convergence_factor(block, limit, odd):
     """V(2,2) Chebyshev multigrid as a stationary iteration: textbook
     convergence factors on the electrolyte blocks (Q1 Laplacian plus mass or
-    reaction) and on each electrode's masked phi_s block."""
-    case = make_box_case(16, 16, (6, 4, 6), 100e-6, (40e-6, 25e-6, 40e-6), 3, 1, state="initial")
+    reaction) and on each electrode's masked phi_s block; also with odd
+    element counts (coarse grids keeping the last fine node)."""
+    if odd:
+        case = make_box_case(15, 13, (7, 3, 7), 100e-6, (45e-6, 20e-6, 45e-6), 3, 1, state="initial")
+    else:
+        case = make_box_case(16, 16, (6, 4, 6), 100e-6, (40e-6, 25e-6, 40e-6), 3, 1, state="initial")
     d, st = _disc(case)
     J = d.jacobian(st)
     nn = d.nn
@@ -258,7 +263,9 @@ def test_multigrid_convergence_factor(block, limit):
     for _ in range(10):
         x = x + mg.vcycle(-(A @ x))
     rho = (np.linalg.norm(x) / e0) ** 0.1
-    assert rho < limit, rho
+    # odd element counts leave one coarse element of half width per axis and
+    # level, which costs a few hundredths in the factor
+    assert rho < limit + (0.05 if odd else 0.0), rho
 
 
 def test_printed_parameters_and_dof_counts():
