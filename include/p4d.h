@@ -111,6 +111,8 @@ typedef struct {
   int32_t coarse_max;   /* coarsen while a level has more than this many nodes (>= 8) */
   double cheb_ratio;    /* Chebyshev interval [lam/ratio, lam] on D^-1 A */
   double rtol;          /* relative residual target of FGMRES in the scaled norm */
+  int32_t profile;      /* 1: time phases and kernel classes of each solve with CUDA events
+                           (fields ms_* / n_* of p4d_info); 0: off */
 } p4d_params;
 
 /* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */
@@ -128,6 +130,13 @@ typedef struct {
   double rel_res;         /* final ||s.(b - J x)|| / ||s.b|| (true residual, scaled norm) */
   double rel_res_block[4];/* the same restricted to phi_s, phi_e, c_e, c_s rows */
   double ms_total;        /* device time of the solve (CUDA events) */
+  /* filled when p4d_params.profile = 1 (device time, CUDA events on the handle's stream): */
+  double ms_precond;      /* preconditioner applications */
+  double ms_jvp;          /* operator applications inside the Krylov loop */
+  double ms_ortho;        /* Gram-Schmidt passes, norms and Givens updates */
+  double ms_smooth0;      /* level-0 Chebyshev steps that apply the stencil (all hierarchies) */
+  int32_t n_smooth0;      /* number of those launches */
+  int32_t n_jvp;          /* number of operator applications timed in ms_jvp */
 } p4d_info;
 
 /* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,

@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("combine", C.c_int32), ("order", C.c_int32 * 3),
                 ("restart", C.c_int32), ("maxit", C.c_int32), ("mode", C.c_int32),
                 ("cheb_degree", C.c_int32), ("coarse_max", C.c_int32), ("cheb_ratio", C.c_double),
-                ("rtol", C.c_double)]
+                ("rtol", C.c_double), ("profile", C.c_int32)]
 
 
 class State(C.Structure):
@@ -53,11 +53,15 @@ class State(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32), ("reorth", C.c_int32),
-                ("rel_res", C.c_double), ("rel_res_block", C.c_double * 4), ("ms_total", C.c_double)]
+                ("rel_res", C.c_double), ("rel_res_block", C.c_double * 4), ("ms_total", C.c_double),
+                ("ms_precond", C.c_double), ("ms_jvp", C.c_double), ("ms_ortho", C.c_double),
+                ("ms_smooth0", C.c_double), ("n_smooth0", C.c_int32), ("n_jvp", C.c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, restarts=self.restarts, status=self.status, reorth=self.reorth,
-                    rel_res=self.rel_res, rel_res_block=list(self.rel_res_block), ms_total=self.ms_total)
+                    rel_res=self.rel_res, rel_res_block=list(self.rel_res_block), ms_total=self.ms_total,
+                    ms_precond=self.ms_precond, ms_jvp=self.ms_jvp, ms_ortho=self.ms_ortho,
+                    ms_smooth0=self.ms_smooth0, n_smooth0=self.n_smooth0, n_jvp=self.n_jvp)
 
 
 # name -> (restype, argtypes); every symbol declared in include/p4d.h

@@ -32,6 +32,34 @@ p4d_status dalloc(p4d_ctx* c, void** p, size_t bytes) {
   return P4D_OK;
 }
 
+void prof_mark(p4d_ctx* c, int cls) {
+  if (!c->prm.profile) return;
+  auto& P = c->prof;
+  if (P.used[cls] >= P.ev[cls].size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+    P.ev[cls].push_back(e);
+  }
+  cudaEventRecord(P.ev[cls][P.used[cls]++], c->stream);
+}
+
+double prof_sum(p4d_ctx* c, int cls, int* count) {
+  auto& P = c->prof;
+  double ms = 0.0;
+  int n = 0;
+  for (size_t i = 0; i + 1 < P.used[cls]; i += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, P.ev[cls][i], P.ev[cls][i + 1]) == cudaSuccess) { ms += t; ++n; }
+    else cudaGetLastError();
+  }
+  if (count) *count = n;
+  return ms;
+}
+
+void prof_reset(p4d_ctx* c) {
+  for (int k = 0; k < 4; ++k) c->prof.used[k] = 0;
+}
+
 p4d_status check_flags(p4d_ctx* c) {
   P4D_TRY(cudaMemcpyAsync(c->flags_h, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   P4D_TRY(cudaStreamSynchronize(c->stream));
@@ -261,6 +289,8 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
 void free_ctx(p4d_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  for (int k = 0; k < 4; ++k)
+    for (cudaEvent_t e : c->prof.ev[k]) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->flags_h) cudaFreeHost(c->flags_h);
   if (c->lam_pin) cudaFreeHost(c->lam_pin);
@@ -282,7 +312,7 @@ void p4d_params_default(p4d_params* p) {
   p->dt = 10.0; p->i_app = -40.2022; p->diffpot_sign = 1.0;
   p->precision = 1; p->combine = 0; p->order[0] = 1; p->order[1] = 0; p->order[2] = 2;
   p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
-  p->cheb_ratio = 10.0; p->rtol = 1e-8;
+  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,
@@ -334,6 +364,7 @@ p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out) {
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
   if (!h || !p || !valid_params(p)) return P4D_ERR_INVALID_ARG;
   if (p->precision != h->prm.precision || p->coarse_max != h->prm.coarse_max) return P4D_ERR_INVALID_ARG;
+  if (p->profile != 0 && p->profile != 1) return P4D_ERR_INVALID_ARG;
   if (p->restart > h->mcap) return P4D_ERR_INVALID_ARG;
   if (p->mode == 0 && h->kry_len < h->ndof) return P4D_ERR_INVALID_ARG;
   const bool relin = p->cheb_ratio != h->prm.cheb_ratio;

@@ -378,6 +378,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
   const HLay L = hlay(c->mcap);
   double* hs = c->hs;
   Reducer R{c};
+  prof_reset(c);
   cudaEvent_t ev0, ev1;
   P4D_TRY(cudaEventCreate(&ev0));
   P4D_TRY(cudaEventCreate(&ev1));
@@ -444,10 +445,15 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       double* vk = c->V + (int64_t)k * len;
       double* zk = c->Z + (int64_t)k * len;
       double* w = c->V + (int64_t)(k + 1) * len;
+      prof_mark(c, 0);
       if (full) P4D_TRYS(precond_full(c, vk, zk, trans, true));
       else P4D_TRYS(precond_macro(c, vk, zk, trans, true));
+      prof_mark(c, 0);
+      prof_mark(c, 1);
       if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
       else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
+      prof_mark(c, 1);
+      prof_mark(c, 2);
       // classical Gram-Schmidt, second pass only when needed
       const double* flag = misc + 2 * L.m + 6;
       R.mdot(c->V, len, k + 1, w, len, true, misc);                 // h1, ||w||^2 before
@@ -460,6 +466,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
       // v_{k+1} = w / h_{k+1,k}
       ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
+      prof_mark(c, 2);
       P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       P4D_TRY(cudaStreamSynchronize(c->stream));
       ++iters;
@@ -521,6 +528,15 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     }
     info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
     info->ms_total = ms;
+    if (c->prm.profile) {
+      int n = 0;
+      info->ms_precond = prof_sum(c, 0, nullptr);
+      info->ms_jvp = prof_sum(c, 1, &n);
+      info->n_jvp = n;
+      info->ms_ortho = prof_sum(c, 2, nullptr);
+      info->ms_smooth0 = prof_sum(c, 3, &n);
+      info->n_smooth0 = n;
+    }
   }
   return st;
 }

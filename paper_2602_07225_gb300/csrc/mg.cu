@@ -672,8 +672,10 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     const dim3 grid(nblocks(A.n), nhs);
     for (int s = 0; s < deg; ++s) {
       const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
+      if (l == 0 && s > 0) prof_mark(c, 3);
       if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, s == 0);
       else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, s == 0);
+      if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
     if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl);
@@ -703,8 +705,10 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
       const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
+      if (l == 0) prof_mark(c, 3);
       if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, 0);
       else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, 0);
+      if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
   }

@@ -185,6 +185,12 @@ struct p4d_ctx {
   double* part = nullptr;              // [nparts][kry dots] partial sums
   double* hs = nullptr;                // device Hessenberg / Givens state
   double* hs_h = nullptr;              // pinned host mirror of small scalars
+
+  // profiling (p4d_params.profile): event pairs per timed class, reused across solves
+  struct Prof {
+    std::vector<cudaEvent_t> ev[4];    // 0 precond, 1 jvp, 2 ortho, 3 level-0 stencil smoothing
+    size_t used[4] = {0, 0, 0, 0};
+  } prof;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -231,6 +237,12 @@ p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs);
 p4d_status mg_load_rhs(p4d_ctx* c, const double* rm, const double* sinv_m, const int* hs, int nhs);
 p4d_status mg_store_out(p4d_ctx* c, const double* rm_unscaled_src, const double* sinv_m, double* zm,
                         const int* fields, int nf);
+
+// ---- profiling: mark(c, cls, begin) records an event pair member when
+// p4d_params.profile is set; prof_sum(c, cls) sums the pairs (after a sync)
+void prof_mark(p4d_ctx* c, int cls);
+double prof_sum(p4d_ctx* c, int cls, int* count);
+void prof_reset(p4d_ctx* c);
 
 // ---- Krylov (krylov.cu)
 p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int transpose);
