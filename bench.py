@@ -27,6 +27,8 @@ METRIC = "Newton linear solves/s & FGMRES iters/s to 1e-8 rel. residual; mixed v
 WORKLOAD = "cube128"
 # unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
 # the 82 electrode node layers (41 anode + 41 cathode)
+WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40)",
+                 "cube96": "cube96 (profiling case): Q1 hex 96x96x72 (anode/sep/cathode 30/12/30)"}
 CUBE128_DOF = 3 * 129 * 129 * 97 + 20 * 82 * 129 * 129
 
 
@@ -400,9 +402,9 @@ def main():
         "vs_baseline": None,
         "dtype": "f64 outer / f32 preconditioner",
         "data": "synthetic",
-        "config": {"workload": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40), N_c=20, "
-                               "seeded linearization state, REDUCED Schur mode, block Jacobi, V(2,2) Chebyshev, "
-                               "FGMRES(30) rtol 1e-8",
+        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload) +
+                               ", N_c=20, seeded linearization state, REDUCED Schur mode, block Jacobi, "
+                               "V(2,2) Chebyshev, FGMRES(30) rtol 1e-8",
                    "unknowns": r["ndof"], "l2": "inputs larger than L2 (Krylov basis and stencils > 129 MB)"},
         "fgmres_iters_per_s": r["iters_per_s"],
         "iters_per_solve": r["iters_per_solve"],

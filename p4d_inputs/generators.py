@@ -209,6 +209,9 @@ def make_case(name, **kw):
     hetero128:  cube128 mesh with lognormal porosity (mean 0.3, CV 0.2,
                 correlation 8 elements) and lognormal particle radius
                 (mean 5 um, CV 0.3) (seed 1003).
+    cube96:     96x96x72 (30/12/30), cube128's physics at three quarters of
+                its resolution (seed 1002); a profiling case whose level-0
+                working set still exceeds the 129 MB L2.
     tiny:       2x2x5 (2/1/2), N_c = 4 (seed 7).
     """
     if name == "tiny":
@@ -218,6 +221,9 @@ def make_case(name, **kw):
                              kw.pop("seed", 1001), **kw)
     if name == "cube128":
         return make_box_case(128, 128, (40, 16, 40), 100e-6, (100e-6, 25e-6, 100e-6), 20,
+                             kw.pop("seed", 1002), **kw)
+    if name == "cube96":
+        return make_box_case(96, 96, (30, 12, 30), 100e-6, (100e-6, 25e-6, 100e-6), 20,
                              kw.pop("seed", 1002), **kw)
     if name == "hetero128":
         return make_box_case(128, 128, (40, 16, 40), 100e-6, (100e-6, 25e-6, 100e-6), 20,

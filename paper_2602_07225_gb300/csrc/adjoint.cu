@@ -28,9 +28,11 @@ __global__ void k_fnorm(const double* __restrict__ r, const double* __restrict__
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
     const int f = n < 3 * nn ? (int)(n / nn) : 3;
     const double v = wgt ? r[n] * wgt[n] : r[n];
-    acc[f] = fma(v, v, acc[f]);
+    #pragma unroll
+    for (int t = 0; t < 4; ++t) acc[t] = t == f ? fma(v, v, acc[t]) : acc[t];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  #pragma unroll
   for (int f = 0; f < 4; ++f) {
     double a = acc[f];
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);

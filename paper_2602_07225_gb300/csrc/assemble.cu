@@ -239,9 +239,11 @@ __global__ void k_state_scale(int64_t nn, int64_t ncs, const double* __restrict_
     else if (q < 3 * nn) { u = ce[q - 2 * nn]; f = 2; }
     else { u = cs[q - 3 * nn]; f = 3; }
     const double v = sqd[q] * u;
-    acc[f] = fma(v, v, acc[f]);
+    #pragma unroll
+    for (int t = 0; t < 4; ++t) acc[t] = t == f ? fma(v, v, acc[t]) : acc[t];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  #pragma unroll
   for (int f = 0; f < 4; ++f) {
     double a = acc[f];
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);

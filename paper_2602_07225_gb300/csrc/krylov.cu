@@ -125,9 +125,11 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
     const int f = n < 3 * nn ? (int)(n / nn) : 3;
     const double v = b[n] * rsqd[n];
-    acc[f] += v * v;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += q == f ? v * v : 0.0;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  #pragma unroll
   for (int f = 0; f < 4; ++f) {
     double a = acc[f];
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
@@ -176,9 +178,11 @@ __global__ void k_field_norms_plain(const double* __restrict__ r, int64_t nn, in
   double acc[4] = {0, 0, 0, 0};
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
     const int f = n < 3 * nn ? (int)(n / nn) : 3;
-    acc[f] += r[n] * r[n];
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += q == f ? r[n] * r[n] : 0.0;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  #pragma unroll
   for (int f = 0; f < 4; ++f) {
     double a = acc[f];
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);

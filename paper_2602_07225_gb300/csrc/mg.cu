@@ -85,11 +85,11 @@ __global__ void k_mask_coarse(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const uin
       for (int tx = 0; tx < 3; ++tx) {
         const int fi = X.a[0].sup[I * 3 + tx];
         if (fi < 0) continue;
-        any |= fm.p[h][fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk)];
+        any |= pk(fm.p, h)[fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk)];
       }
     }
   }
-  cm.p[h][C] = any ? 1 : 0;
+  pk(cm.p, h)[C] = any ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- Galerkin
@@ -115,11 +115,11 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst
   double rsum = 0.0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
-  const double* st = fst.p[h];
-  const double* rs = frs.p[h];
-  const uint8_t* m = fm.p[h];
+  const double* st = pk(fst.p, h);
+  const double* rs = pk(frs.p, h);
+  const uint8_t* m = pk(fm.p, h);
   const int64_t fn = fd.n;
-  if (cm.p[h][C]) {
+  if (pk(cm.p, h)[C]) {
     for (int tz = 0; tz < 3; ++tz) {
       const int fk = X.a[2].sup[K * 3 + tz];
       if (fk < 0) continue;
@@ -167,9 +167,9 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst
       }
     }
   }
-  double* o_ = out.p[h];
+  double* o_ = pk(out.p, h);
   const int64_t cn = cd.n;
-  if (!cm.p[h][C]) {
+  if (!pk(cm.p, h)[C]) {
     for (int o = 0; o < 27; ++o) o_[o * cn + C] = 0.0;
     o_[13 * cn + C] = identity_out ? 1.0 : 0.0;
     return;
@@ -189,8 +189,8 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double
   double rsum = 0.0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
-  const uint8_t* m = fm.p[h];
-  if (cm.p[h][C]) {
+  const uint8_t* m = pk(fm.p, h);
+  if (pk(cm.p, h)[C]) {
     for (int tz = 0; tz < 3; ++tz) {
       const int fk = X.a[2].sup[K * 3 + tz];
       if (fk < 0) continue;
@@ -203,7 +203,7 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double
           const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
           if (!m[f]) continue;
           const double wf = X.a[0].supw[I * 3 + tx] * X.a[1].supw[J * 3 + ty] * X.a[2].supw[K * 3 + tz];
-          const double a = wf * s.p[h][f];
+          const double a = wf * pk(s.p, h)[f];
           rsum += a;
           for (int c3 = 0; c3 < 2; ++c3) {
             const int pz = X.a[2].par[fk * 2 + c3];
@@ -223,9 +223,9 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double
       }
     }
   }
-  double* o_ = out.p[h];
+  double* o_ = pk(out.p, h);
   const int64_t cn = cd.n;
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (cm.p[h][C] ? acc[o] : 0.0);
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o] : 0.0);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -308,19 +308,19 @@ __global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const do
   double gl = 0.0;
   if (n < d.n) {
     const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
-    const double* f = F.p[h];
-    const double* v = V.p[h];
+    const double* f = pk(F.p, h);
+    const double* v = pk(V.p, h);
     double diag = 0.0, absoff = 0.0, s = 0.0;
     for (int o = 0; o < 27; ++o) {
       const double a = f[o * d.n + n] + v[o * d.n + n];
-      st.p[h][o * d.n + n] = fromd<TS>(sc * a);
+      pk(st.p, h)[o * d.n + n] = fromd<TS>(sc * a);
       if (o == 13) s = a;
       else { diag -= a; absoff += fabs(a); }
     }
     diag += s;
     if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
-    dinv.p[h][n] = fromd<T>(1.0 / (sc * diag));
-    if (mask.p[h][n]) gl = (absoff + fabs(diag)) / diag;
+    pk(dinv.p, h)[n] = fromd<T>(1.0 / (sc * diag));
+    if (pk(mask.p, h)[n]) gl = (absoff + fabs(diag)) / diag;
   }
   block_max_to(lam + h, gl);
 }
@@ -338,7 +338,7 @@ __global__ void k_dense(LevelDims d, Ptr4<const double> F, Ptr4<const double> V,
   for (int64_t m = 0; m < d.n; ++m) A[n * d.n + m] = 0.0;
   double diag = 0.0;
   for (int o = 0; o < 27; ++o) {
-    const double a = F.p[h][o * d.n + n] + V.p[h][o * d.n + n];
+    const double a = pk(F.p, h)[o * d.n + n] + pk(V.p, h)[o * d.n + n];
     if (o == 13) { diag += a; continue; }
     diag -= a;
     const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
@@ -363,7 +363,7 @@ __global__ void k_dense0(Grid g, const double* __restrict__ Jst, const double* _
   const double sc = f == 0 ? sc0 : (f == 1 ? sc1 : sc2);
   double* A = out + (size_t)h * nn * nn;
   for (int64_t m = 0; m < nn; ++m) A[n * nn + m] = 0.0;
-  if (!mask.p[h][n]) {
+  if (!pk(mask.p, h)[n]) {
     A[n * nn + n] = 1.0;
     return;
   }
@@ -378,7 +378,7 @@ __global__ void k_dense0(Grid g, const double* __restrict__ Jst, const double* _
     const int ii = i + dx, jj = j + dy, kk = k + dz;
     if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
     const int64_t m = ii + (int64_t)g.nnx * (jj + (int64_t)g.nny * kk);
-    if (mask.p[h][m]) A[n * nn + m] = sc * a;
+    if (pk(mask.p, h)[m]) A[n * nn + m] = sc * a;
   }
   A[n * nn + n] = sc * diag;
 }
@@ -444,43 +444,62 @@ struct LvlPtrs {
   T* d[kNH];
 };
 
-// (A x)_n in difference form.  Interior nodes (all 26 neighbours present)
-// take an unchecked path with constant offsets; boundary nodes check each
-// neighbour.  Indices are 32-bit (every level has fewer than 2^31/27 nodes).
+// Stencil kernels: kNpt rows per thread, blockDim apart (each load
+// instruction stays coalesced), and the loads of one z-plane of the stencil
+// (9 coefficients and 9 neighbour values per row) issued before their
+// updates.  The kernels are bound by memory latency unless enough loads are
+// in flight; on cube128 level 0 one row per thread with plane-batched loads
+// and two rows with per-offset loads were fastest (4.9-5.0 TB/s), four or
+// more rows per thread slower (register pressure).
+#ifndef P4D_STENCIL_NPT
+#define P4D_STENCIL_NPT 1
+#endif
+constexpr int kNpt = P4D_STENCIL_NPT;
+
+// ax[q] = (A x)_{n[q]} in difference form, for the rows with on[q]:
+// ax = s_13 x_n + sum_{o != 13} s_o (x_{n+off(o)} - x_n).  Every row takes
+// the same unchecked path: the stencils hold exact zeros in the slots of
+// neighbours outside the grid, and the x vectors carry zeroed guard zones
+// (see alloc_x), so the loads of boundary rows stay in bounds and such a
+// slot adds fma(0, finite, acc) = acc.  Indices are 32-bit (every level has
+// fewer than 2^31/27 nodes).
 template <typename TS, typename T>
-__device__ __forceinline__ T apply_row(const TS* __restrict__ st, const T* __restrict__ x, const LevelDims& dd,
-                                       int n, int i, int j, int k) {
+__device__ __forceinline__ void stencil_rows(const TS* __restrict__ st, const T* __restrict__ x, const LevelDims& dd,
+                                             const int (&n)[kNpt], const bool (&on)[kNpt], T (&ax)[kNpt]) {
   const int N = (int)dd.n;
-  const int sx = 1, sy = dd.nnx, sz = dd.nnx * dd.nny;
-  const T xn = x[n];
-  T acc = (T)tof(st[13 * N + n]) * xn;
-  if (i > 0 && j > 0 && k > 0 && i < dd.nnx - 1 && j < dd.nny - 1 && k < dd.nnz - 1) {
+  const int sy = dd.nnx, sz = dd.nnx * dd.nny;
+  T xn[kNpt];
 #pragma unroll
-    for (int o = 0; o < 27; ++o) {
+  for (int q = 0; q < kNpt; ++q) {
+    xn[q] = on[q] ? x[n[q]] : (T)0;
+    ax[q] = on[q] ? (T)tof(st[13 * N + n[q]]) * xn[q] : (T)0;
+  }
+  // one z-plane of the stencil at a time: all of its loads first, then the
+  // updates, summed in offset order
+#pragma unroll
+  for (int pz = 0; pz < 3; ++pz) {
+    TS sv[9][kNpt];
+    T xv[9][kNpt];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int o = 9 * pz + t;
       if (o == 13) continue;
-      const int m = n + (o % 3 - 1) * sx + ((o / 3) % 3 - 1) * sy + (o / 9 - 1) * sz;
-      acc += (T)tof(st[o * N + n]) * (x[m] - xn);
+      const int off = (o % 3 - 1) + ((o / 3) % 3 - 1) * sy + (o / 9 - 1) * sz;
+#pragma unroll
+      for (int q = 0; q < kNpt; ++q)
+        if (on[q]) {
+          sv[t][q] = st[o * N + n[q]];
+          xv[t][q] = x[n[q] + off];
+        }
     }
-  } else {
 #pragma unroll
-    for (int o = 0; o < 27; ++o) {
-      if (o == 13) continue;
-      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-      const int ii = i + dx, jj = j + dy, kk = k + dz;
-      if (ii < 0 || jj < 0 || kk < 0 || ii >= dd.nnx || jj >= dd.nny || kk >= dd.nnz) continue;
-      const int m = n + dx * sx + dy * sy + dz * sz;
-      acc += (T)tof(st[o * N + n]) * (x[m] - xn);
+    for (int t = 0; t < 9; ++t) {
+      if (9 * pz + t == 13) continue;
+#pragma unroll
+      for (int q = 0; q < kNpt; ++q)
+        if (on[q]) ax[q] += (T)tof(sv[t][q]) * (xv[t][q] - xn[q]);
     }
   }
-  return acc;
-}
-
-__device__ __forceinline__ void node_ijk32(const LevelDims& d, int n, int& i, int& j, int& k) {
-  const int sxy = d.nnx * d.nny;
-  k = n / sxy;
-  const int r = n - k * sxy;
-  j = r / d.nnx;
-  i = r - j * d.nnx;
 }
 
 // Chebyshev coefficients of one step for up to four hierarchies (computed on
@@ -490,43 +509,70 @@ struct ChebCoef {
   double c0[kNH], ca[kNH], cb[kNH];
 };
 
+// Rows of this thread: n[q] = block base + q blockDim + tid, active where in
+// range and inside the hierarchy's mask.
+__device__ __forceinline__ void stencil_nodes(int N, const uint8_t* __restrict__ mask, int (&n)[kNpt],
+                                              bool (&on)[kNpt]) {
+  const int base = blockIdx.x * (blockDim.x * kNpt) + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kNpt; ++q) {
+    n[q] = base + q * blockDim.x;
+    on[q] = n[q] < N && mask[n[q]];
+  }
+}
+
 // One Chebyshev step, x_out = x + d.
 template <typename TS, typename T>
 __global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, ChebCoef cc, int step,
                                               int first) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int hi = blockIdx.y;
-  const int h = hl.h[hi];
-  if (n >= (int)dd.n) return;
-  if (!P.mask[h][n]) return;
-  int i, j, k;
-  node_ijk32(dd, n, i, j, k);
-  T res = P.b[h][n];
-  if (!first) res -= apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
-  const T z = P.dinv[h][n] * res;
-  T dn;
-  if (step == 0) dn = (T)cc.c0[hi] * z;
-  else dn = (T)cc.ca[hi] * P.d[h][n] + (T)cc.cb[hi] * z;
-  P.d[h][n] = dn;
-  P.xo[h][n] = (first ? (T)0 : P.x[h][n]) + dn;
+  const int h = pk(hl.h, hi);
+  int n[kNpt];
+  bool on[kNpt];
+  stencil_nodes((int)dd.n, pk(P.mask, h), n, on);
+  T ax[kNpt];
+  if (!first) stencil_rows<TS, T>(pk(P.st, h), pk(P.x, h), dd, n, on, ax);
+  const T* __restrict__ b = pk(P.b, h);
+  const T* __restrict__ dinv = pk(P.dinv, h);
+  const T* __restrict__ x = pk(P.x, h);
+  T* __restrict__ d = pk(P.d, h);
+  T* __restrict__ xo = pk(P.xo, h);
+  const T c0 = (T)pk(cc.c0, hi), ca = (T)pk(cc.ca, hi), cb = (T)pk(cc.cb, hi);
+#pragma unroll
+  for (int q = 0; q < kNpt; ++q) {
+    if (!on[q]) continue;
+    const int m = n[q];
+    T res = b[m];
+    if (!first) res -= ax[q];
+    const T z = dinv[m] * res;
+    const T dn = step == 0 ? c0 * z : ca * d[m] + cb * z;
+    d[m] = dn;
+    xo[m] = (first ? (T)0 : x[m]) + dn;
+  }
 }
 
 template <typename TS, typename T>
 __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const int h = hl.h[blockIdx.y];
-  if (n >= (int)dd.n) return;
-  if (!P.mask[h][n]) return;   // level-0 phi_s hierarchies share r: never write masked-out nodes
-  int i, j, k;
-  node_ijk32(dd, n, i, j, k);
-  P.r[h][n] = P.b[h][n] - apply_row<TS, T>(P.st[h], P.x[h], dd, n, i, j, k);
+  const int h = pk(hl.h, blockIdx.y);
+  int n[kNpt];
+  bool on[kNpt];   // level-0 phi_s hierarchies share r: never write masked-out nodes
+  stencil_nodes((int)dd.n, pk(P.mask, h), n, on);
+  T ax[kNpt];
+  stencil_rows<TS, T>(pk(P.st, h), pk(P.x, h), dd, n, on, ax);
+  const T* __restrict__ b = pk(P.b, h);
+  T* __restrict__ r = pk(P.r, h);
+#pragma unroll
+  for (int q = 0; q < kNpt; ++q)
+    if (on[q]) r[n[q]] = b[n[q]] - ax[q];
 }
+
+inline unsigned stencil_blocks(int64_t n) { return nblocks(n, kBlock * kNpt); }
 
 template <typename T>
 __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr, Ptr4<const uint8_t> fm, Ptr4<T> cb,
                            HList hl) {
   const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  const int h = hl.h[blockIdx.y];
+  const int h = pk(hl.h, blockIdx.y);
   if (C >= (int)cd.n) return;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
@@ -543,21 +589,21 @@ __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr,
         const int fi = X.a[0].sup[I * 3 + tx];
         if (fi < 0) continue;
         const int f = fi + fd.nnx * (fj + fd.nny * fk);
-        if (!fm.p[h][f]) continue;
-        acc += (T)X.a[0].supw[I * 3 + tx] * wy * wz * fr.p[h][f];
+        if (!pk(fm.p, h)[f]) continue;
+        acc += (T)X.a[0].supw[I * 3 + tx] * wy * wz * pk(fr.p, h)[f];
       }
     }
   }
-  cb.p[h][C] = acc;
+  pk(cb.p, h)[C] = acc;
 }
 
 template <typename T>
 __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_, Ptr4<const uint8_t> fm, Ptr4<T> fx,
                           HList hl) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  const int h = hl.h[blockIdx.y];
+  const int h = pk(hl.h, blockIdx.y);
   if (f >= (int)fd.n) return;
-  if (!fm.p[h][f]) return;
+  if (!pk(fm.p, h)[f]) return;
   int i, j, k;
   node_ijk(fd, f, i, j, k);
   T acc = 0;
@@ -572,22 +618,22 @@ __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_,
       for (int c1 = 0; c1 < 2; ++c1) {
         const int px = X.a[0].par[i * 2 + c1];
         if (px < 0) continue;
-        acc += (T)X.a[0].parw[i * 2 + c1] * wy * wz * cx_.p[h][px + cd.nnx * (py + cd.nny * pz)];
+        acc += (T)X.a[0].parw[i * 2 + c1] * wy * wz * pk(cx_.p, h)[px + cd.nnx * (py + cd.nny * pz)];
       }
     }
   }
-  fx.p[h][f] += acc;
+  pk(fx.p, h)[f] += acc;
 }
 
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ inv, Ptr4<const T> b, Ptr4<const uint8_t> mask,
                                Ptr4<T> x, HList hl) {
-  const int h = hl.h[blockIdx.y];
+  const int h = pk(hl.h, blockIdx.y);
   const double* A = inv + (size_t)h * n * n;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int cidx = 0; cidx < n; ++cidx) acc += A[(size_t)r * n + cidx] * (double)b.p[h][cidx];
-    if (mask.p[h][r]) x.p[h][r] = (T)acc;   // masked-out rows are never read (and may be shared)
+    for (int cidx = 0; cidx < n; ++cidx) acc += A[(size_t)r * n + cidx] * (double)pk(b.p, h)[cidx];
+    if (pk(mask.p, h)[r]) pk(x.p, h)[r] = (T)acc;   // masked-out rows are never read (and may be shared)
   }
 }
 
@@ -669,7 +715,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   for (int l = 0; l < L - 1; ++l) {
     MGLevel& A = c->lev[l];
     MGLevel& B = c->lev[l + 1];
-    const dim3 grid(nblocks(A.n), nhs);
+    const dim3 grid(stencil_blocks(A.n), nhs);
     for (int s = 0; s < deg; ++s) {
       const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
       if (l == 0 && s > 0) prof_mark(c, 3);
@@ -701,8 +747,8 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> fm;
     Ptr4<T> fx;
     for (int h = 0; h < kNH; ++h) { cxp.p[h] = (const T*)B.x[h]; fm.p[h] = A.mask[h]; fx.p[h] = (T*)A.x[h]; }
-    const dim3 grid(nblocks(A.n), nhs);
-    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
+    const dim3 grid(stencil_blocks(A.n), nhs);
+    ::p4d::count_launch(), k_prolong<T><<<dim3(nblocks(A.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
       const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
       if (l == 0) prof_mark(c, 3);
@@ -719,6 +765,19 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
 }  // namespace
 
 // ---------------------------------------------------------------- planning
+// An x vector of a level (the input of the unchecked stencil loads) with a
+// zeroed guard of at least nnx nny + nnx + 1 entries on both sides, rounded
+// to 64 entries so that the vector keeps the allocation's alignment.
+p4d_status alloc_x(p4d_ctx* c, void** p, size_t ts, const MGLevel& lv) {
+  const int64_t G = ((int64_t)lv.nnx * lv.nny + lv.nnx + 1 + 63) / 64 * 64;
+  const size_t bytes = ts * (size_t)(lv.n + 2 * G);
+  void* base = nullptr;
+  P4D_TRYS(dalloc(c, &base, bytes));
+  P4D_TRY(cudaMemset(base, 0, bytes));
+  *p = static_cast<char*>(base) + ts * G;
+  return P4D_OK;
+}
+
 p4d_status mg_plan(p4d_ctx* c) {
   const int prec = c->prm.precision;
   const size_t tv = prec == 0 ? sizeof(double) : sizeof(float);
@@ -785,8 +844,8 @@ p4d_status mg_plan(p4d_ctx* c) {
       for (int f = 0; f < 3; ++f) {
         P4D_TRYS(dalloc(c, &st[f], ts * 27 * n));
         P4D_TRYS(dalloc(c, &di[f], tv * n));
-        P4D_TRYS(dalloc(c, &x[f], tv * n));
-        P4D_TRYS(dalloc(c, &x2[f], tv * n));
+        P4D_TRYS(alloc_x(c, &x[f], tv, lv));
+        P4D_TRYS(alloc_x(c, &x2[f], tv, lv));
         P4D_TRYS(dalloc(c, &b[f], tv * n));
         P4D_TRYS(dalloc(c, &r[f], tv * n));
         P4D_TRYS(dalloc(c, &d[f], tv * n));
@@ -807,8 +866,8 @@ p4d_status mg_plan(p4d_ctx* c) {
       for (int h = 0; h < kNH; ++h) {
         P4D_TRYS(dalloc(c, &lv.st[h], ts * 27 * n));
         P4D_TRYS(dalloc(c, &lv.dinv[h], tv * n));
-        P4D_TRYS(dalloc(c, &lv.x[h], tv * n));
-        P4D_TRYS(dalloc(c, &lv.x2[h], tv * n));
+        P4D_TRYS(alloc_x(c, &lv.x[h], tv, lv));
+        P4D_TRYS(alloc_x(c, &lv.x2[h], tv, lv));
         P4D_TRYS(dalloc(c, &lv.b[h], tv * n));
         P4D_TRYS(dalloc(c, &lv.r[h], tv * n));
         P4D_TRYS(dalloc(c, &lv.d[h], tv * n));

@@ -63,6 +63,14 @@ struct Ptr4 {
   T* p[kNH];
 };
 
+// Entry h of a per-hierarchy kernel-parameter array.  Indexing such an array
+// with a run-time index makes the compiler copy the parameter block to the
+// thread's stack; selecting among the four constant-index reads does not.
+template <typename T>
+__device__ __forceinline__ T pk(const T (&a)[kNH], int h) {
+  return h == 0 ? a[0] : (h == 1 ? a[1] : (h == 2 ? a[2] : a[3]));
+}
+
 // One-dimensional interpolation tables between a fine node line and its
 // coarsening (see mg.cu): per fine node up to two parents, per coarse node
 // up to three support nodes, with weights.

@@ -30,7 +30,7 @@ def test_batch_matches_oracle_and_sequential():
     from oracle.fe import Disc
     from oracle.krylov import LinearSolve, per_field_error
     cells = _cells()
-    bs = BatchSolver(cells, threads=4, precision=1, rtol=1e-10, maxit=800)
+    bs = BatchSolver(cells, threads=4, precision=1, rtol=1e-11, maxit=800)
     assert len(bs.tuned) == len({c["gyroid"]["n"] for c in cells})   # one tuning per grid shape
     for deg, ratio in bs.tuned.values():
         assert deg in (1, 2, 3, 4) and ratio > 1

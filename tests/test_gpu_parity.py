@@ -120,8 +120,9 @@ def test_adjointness_on_gpu(name):
 
 
 # solution error per unit of scaled residual: ~1-2 for the layered cubes,
-# ~25 for meshes whose coarse grids keep half-width last elements
-AMPLIFICATION = {"oddcoarse": 25.0}
+# ~25 for meshes with odd element counts, whose coarse grids keep a
+# half-width last element (measured 2.3e-9 at rel_res 1e-10 on "odd")
+AMPLIFICATION = {"odd": 25.0, "oddcoarse": 25.0}
 
 
 @pytest.mark.parametrize("name", list(CASES))
