@@ -140,7 +140,7 @@ typedef struct {
 } p4d_info;
 
 /* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,
-   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10). */
+   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 3, ratio 20). */
 void p4d_params_default(p4d_params* p);
 
 /* Build a handle for one cell (paper sections 3-4): validates the mesh,
@@ -163,7 +163,9 @@ p4d_status p4d_get_sizes(p4d_handle h, int64_t* nnode, int64_t* nelec, int64_t* 
 p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out);
 
 /* Change solver options (combine, order, restart, maxit, rtol, cheb_ratio,
-   cheb_degree, mode).  precision and coarse_max cannot change (INVALID_ARG). */
+   cheb_degree, mode, profile) and the kinetics constants.  precision,
+   coarse_max and the parameters assembled at setup (dt, F, brug, De, kappa,
+   sigma_n, sigma_p) cannot change (INVALID_ARG). */
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* params);
 
 /* Nonlinear residual R(u) (paper section 4, block residual [R_phis; R_phie;

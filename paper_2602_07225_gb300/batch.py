@@ -16,7 +16,7 @@ import torch
 
 from .solver import P4DSolver
 
-CANDIDATES = ((1, 4.0), (2, 4.0), (2, 10.0), (3, 10.0), (4, 10.0))
+CANDIDATES = ((1, 4.0), (2, 10.0), (3, 10.0), (3, 20.0), (4, 20.0))
 
 
 class Autotuner:

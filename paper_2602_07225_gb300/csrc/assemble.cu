@@ -139,18 +139,45 @@ __global__ void k_node_ln(int64_t nn, const double* __restrict__ ce, double gamm
   if (gdc) gdc[n] = gamma / c;
 }
 
-// Linearization per electrode node: kinetics derivatives, last pivot of the
-// particle tridiagonal T_j = M_j (I/dt - kap_j Lref) + e_N e_N^T M_j beta_j g_s
-// (z_j = 1 / pivot = (T_j^-1)_NN) and zeta_j = 1 - z_j g_s M_j beta_j.
-__global__ void k_linearize(int64_t NE, int nc, Kin kn, double dt, const int32_t* __restrict__ enode,
+// LU of T_j / M_j = I/dt - kap_j Lref + e_N e_N^T beta_j g_s without its
+// surface term (unit lower L with multipliers mult_i, upper U with pivots
+// piv_i): every pivot but the last and all multipliers depend only on dt,
+// kap_j and the radial grid, so they are factored once.  Stored as 1/piv and
+// mult, so that every later FP64 particle solve is division free; qfix_j is
+// the last pivot without the surface term.
+__global__ void k_particle_lu_fixed(int64_t NE, int nc, double dt, const double* __restrict__ kapj,
+                                    const double* __restrict__ rref, double* __restrict__ ipiv,
+                                    double* __restrict__ mult, double* __restrict__ qfix) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= NE) return;
+  const double kap = kapj[j];
+  const double* lo = rref;
+  const double* di = rref + nc;
+  const double* up = rref + 2 * nc;
+  const double idt = 1.0 / dt;
+  double piv = idt - kap * di[0];
+  mult[j * nc] = 0.0;
+  for (int i = 1; i < nc; ++i) {
+    ipiv[j * nc + i - 1] = 1.0 / piv;
+    const double mi = (-kap * lo[i]) / piv;
+    piv = (idt - kap * di[i]) - mi * (-kap * up[i - 1]);
+    mult[j * nc + i] = mi;
+  }
+  qfix[j] = piv;
+}
+
+// Linearization per electrode node: kinetics derivatives, the last pivot of
+// the particle tridiagonal T_j = M_j (I/dt - kap_j Lref) + e_N e_N^T M_j
+// beta_j g_s (the fixed part plus the surface term), z_j = 1 / (M_j pivot) =
+// (T_j^-1)_NN and zeta_j = 1 - z_j g_s M_j beta_j.
+__global__ void k_linearize(int64_t NE, int nc, Kin kn, const int32_t* __restrict__ enode,
                             const uint8_t* __restrict__ label, const uint8_t* __restrict__ etype,
                             const double* __restrict__ phis, const double* __restrict__ phie,
                             const double* __restrict__ ce, const double* __restrict__ cs,
-                            const double* __restrict__ Mj, const double* __restrict__ kapj,
-                            const double* __restrict__ betaj, const double* __restrict__ rref,
-                            double* __restrict__ in_, double* __restrict__ ge, double* __restrict__ gc,
-                            double* __restrict__ gs, double* __restrict__ zj, double* __restrict__ zeta,
-                            double* __restrict__ ipiv, double* __restrict__ mult, unsigned* flags) {
+                            const double* __restrict__ Mj, const double* __restrict__ betaj,
+                            const double* __restrict__ qfix, double* __restrict__ in_, double* __restrict__ ge,
+                            double* __restrict__ gc, double* __restrict__ gs, double* __restrict__ zj,
+                            double* __restrict__ zeta, double* __restrict__ ipiv, unsigned* flags) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= NE) return;
   const int64_t n = enode[j];
@@ -159,27 +186,9 @@ __global__ void k_linearize(int64_t NE, int nc, Kin kn, double dt, const int32_t
   if (!kinetics(kn, etype[j], act ? phis[n] : 0.0, phie[n], ce[n], cs[j * nc + nc - 1], a, b, c, d))
     atomicOr(flags, kFlagDomain);
   in_[j] = a; ge[j] = b; gc[j] = c; gs[j] = d;
-  const double kap = kapj[j], M = Mj[j];
-  const double* lo = rref;
-  const double* di = rref + nc;
-  const double* up = rref + 2 * nc;
-  // LU of T/M = I/dt - kap Lref + e_N e_N^T beta g_s (unit lower L with
-  // multipliers mult_i, upper U with pivots piv_i): stored as 1/piv and mult
-  // so that every later FP64 particle solve is division free.
-  const double idt = 1.0 / dt;
-  double piv = idt - kap * di[0];
-  ipiv[j * nc] = 1.0 / piv;
-  mult[j * nc] = 0.0;
-  for (int i = 1; i < nc; ++i) {
-    double dii = idt - kap * di[i];
-    if (i == nc - 1) dii += betaj[j] * d;
-    const double l = -kap * lo[i];
-    const double u = -kap * up[i - 1];
-    const double mi = l / piv;
-    piv = dii - mi * u;
-    mult[j * nc + i] = mi;
-    ipiv[j * nc + i] = 1.0 / piv;
-  }
+  const double M = Mj[j];
+  const double piv = qfix[j] + betaj[j] * d;
+  ipiv[j * nc + nc - 1] = 1.0 / piv;
   const double z = 1.0 / (M * piv);
   zj[j] = z;
   zeta[j] = 1.0 - z * d * M * betaj[j];
@@ -396,6 +405,10 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   P4D_TRYS(dalloc_t(c, &c->offsum, (size_t)3 * nn));
   P4D_TRYS(dalloc_t(c, &c->absoff, (size_t)3 * nn));
   ::p4d::count_launch(), k_fixed_sums<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->Jst, c->label, c->offsum, c->absoff);
+  P4D_TRYS(dalloc_t(c, &c->tqfix, (size_t)std::max<int64_t>(1, c->NE)));
+  if (c->NE > 0)
+    ::p4d::count_launch(), k_particle_lu_fixed<<<nblocks(c->NE), kBlock, 0, c->stream>>>(
+        c->NE, c->nc, c->prm.dt, c->kapj, c->rref, c->tfac, c->tfac + (size_t)c->NE * c->nc, c->tqfix);
   unsigned long long* mx = nullptr;
   P4D_TRYS(dalloc_t(c, &mx, 3));
   P4D_TRY(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), c->stream));
@@ -420,10 +433,10 @@ p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
   P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
   ::p4d::count_launch(), k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce, c->gdc, c->flags);
   if (NE > 0)
-    ::p4d::count_launch(), k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->prm.dt, c->enode, c->label, c->etype,
-                                                        st->phis, st->phie, st->ce, st->cs, c->Mj, c->kapj,
-                                                        c->betaj, c->rref, c->in_, c->ge, c->gc, c->gs, c->zj,
-                                                        c->zeta, c->tfac, c->tfac + (size_t)NE * nc, c->flags);
+    ::p4d::count_launch(), k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype,
+                                                        st->phis, st->phie, st->ce, st->cs, c->Mj, c->betaj,
+                                                        c->tqfix, c->in_, c->ge, c->gc, c->gs, c->zj, c->zeta,
+                                                        c->tfac, c->flags);
   ::p4d::count_launch(), k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, 1.0 / c->prm.dt, c->Jst, c->label,
                                                           c->eidx, c->Aj, c->Mj, c->kapj, c->betaj, c->rref,
                                                           c->ge, c->gc, c->gs, c->sqd, c->rsqd);

@@ -20,55 +20,80 @@ namespace {
 constexpr int kRedBlocks = 4 * 152;   // reduction grid: a multiple of the SM count
 constexpr int kRedThreads = 256;
 
-// Multi-dot, register blocked: each thread keeps one accumulator per dot of
-// a group of up to kDotGroup dots over all of its elements, so the warp and
-// block reductions run once per dot and launch instead of once per element
-// chunk (FP64 adds are as scarce as FP64 FMAs on this GPU).
+// Multi-dot, register blocked with a compile-time group size: each thread
+// keeps one accumulator per dot of a group of NG dots (plus w.w) over all of
+// its elements, so exactly NG FP64 FMAs run per element (a run-time group
+// size with predicated FMAs issued all sixteen).  The warp stage is a
+// transpose reduction: with P (a power of two >= NG + WW) values per lane,
+// each butterfly step halves the values a lane keeps, P - 1 + log2(32/P)
+// FP64 adds per lane instead of 5 per value (FP64 adds are as scarce as FP64
+// FMAs on this GPU).
 // partial[blk][g0 + i] = sum over the block's elements of V[g0 + i][n] * w[n];
-// with_ww: partial[blk][kp1] = sum w[n]^2 (computed with the first group).
+// WW: partial[blk][kp1] = sum w[n]^2.
 constexpr int kDotGroup = 16;
 
-__global__ void __launch_bounds__(kRedThreads) k_mdot(const double* __restrict__ V, int64_t ldv, int kp1,
-                                                      const double* __restrict__ w, int64_t len, int with_ww,
+template <int X>
+struct Pow2Up {
+  static constexpr int v = X <= 1 ? 1 : (X <= 2 ? 2 : (X <= 4 ? 4 : (X <= 8 ? 8 : (X <= 16 ? 16 : 32))));
+};
+template <int X>
+struct Log2 {
+  static constexpr int v = X <= 1 ? 0 : 1 + Log2<X / 2>::v;
+};
+template <>
+struct Log2<1> {
+  static constexpr int v = 0;
+};
+
+// After the call, lane l holds in a[0] the warp total of value index
+// l >> (5 - log2 P) (every lane of a group of 32/P lanes holds the same).
+template <int P>
+__device__ __forceinline__ void warp_transpose_reduce(double (&a)[P], int lane) {
+#pragma unroll
+  for (int c = P, o = 16; c > 1; c >>= 1, o >>= 1) {
+    const bool upper = lane & o;
+#pragma unroll
+    for (int t = 0; t < c / 2; ++t) {
+      const double send = upper ? a[t] : a[t + c / 2];
+      const double keep = upper ? a[t + c / 2] : a[t];
+      a[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int o = 16 >> Log2<P>::v; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+}
+
+template <int NG, bool WW>
+__global__ void __launch_bounds__(kRedThreads) k_mdot(const double* __restrict__ V, int64_t ldv, int g0, int kp1,
+                                                      const double* __restrict__ w, int64_t len,
                                                       double* __restrict__ partial, int pstride,
                                                       const double* __restrict__ flag) {
   if (flag && *flag == 0.0) return;   // conditional pass not needed
-  __shared__ double red[kRedThreads / 32][kDotGroup + 1];
+  constexpr int NA = NG + (WW ? 1 : 0);
+  constexpr int P = Pow2Up<NA>::v;
+  __shared__ double red[kRedThreads / 32][P];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int g0 = 0; g0 < kp1 || (g0 == 0 && with_ww); g0 += kDotGroup) {
-    const int ng = min(kDotGroup, kp1 - g0);
-    const bool ww = with_ww && g0 == 0;
-    double acc[kDotGroup + 1];
+  double acc[P];
 #pragma unroll
-    for (int i = 0; i <= kDotGroup; ++i) acc[i] = 0.0;
-    for (int64_t n = n0; n < len; n += stride) {
-      const double wn = w[n];
+  for (int i = 0; i < P; ++i) acc[i] = 0.0;
+  const double* Vg = V + (int64_t)g0 * ldv;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += stride) {
+    const double wn = w[n];
 #pragma unroll
-      for (int i = 0; i < kDotGroup; ++i)
-        if (i < ng) acc[i] = fma(V[(int64_t)(g0 + i) * ldv + n], wn, acc[i]);
-      if (ww) acc[kDotGroup] = fma(wn, wn, acc[kDotGroup]);
-    }
+    for (int i = 0; i < NG; ++i) acc[i] = fma(Vg[(int64_t)i * ldv + n], wn, acc[i]);
+    if (WW) acc[NG] = fma(wn, wn, acc[NG]);
+  }
+  warp_transpose_reduce<P>(acc, lane);
+  constexpr int span = 32 / P;
+  if ((lane & (span - 1)) == 0) red[warp][lane / span] = acc[0];
+  __syncthreads();
+  if (threadIdx.x < NA) {
+    const int i = threadIdx.x;
+    double sum = 0.0;
 #pragma unroll
-    for (int i = 0; i <= kDotGroup; ++i) {
-      if (i < ng || (i == kDotGroup && ww)) {
-        double a = acc[i];
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-        if (lane == 0) red[warp][i] = a;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x <= kDotGroup) {
-      const int i = threadIdx.x;
-      if (i < ng || (i == kDotGroup && ww)) {
-        double sum = 0.0;
-        for (int wv = 0; wv < kRedThreads / 32; ++wv) sum += red[wv][i];
-        partial[(int64_t)blockIdx.x * pstride + (i < kDotGroup ? g0 + i : kp1)] = sum;
-      }
-    }
-    __syncthreads();
-    if (kp1 == 0) break;
+    for (int wv = 0; wv < kRedThreads / 32; ++wv) sum += red[wv][i];
+    partial[(int64_t)blockIdx.x * pstride + (i < NG ? g0 + i : kp1)] = sum;
   }
 }
 
@@ -94,17 +119,32 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, 
   if (threadIdx.x == 0) out[i] = red[0];
 }
 
-// w[n] -= sum_i h[i] V[i][n]   (h on the device)
-__global__ void k_maxpy(const double* __restrict__ V, int64_t ldv, int kp1, const double* __restrict__ h,
-                        double* __restrict__ w, int64_t len, double sign, const double* __restrict__ flag) {
+// w[n] -= sum_i h[i] V[i][n]   (h on the device).  With `partial`, each
+// block also writes the sum of the updated w[n]^2 over its elements.
+__global__ void __launch_bounds__(kBlock) k_maxpy(const double* __restrict__ V, int64_t ldv, int kp1,
+                                                  const double* __restrict__ h, double* __restrict__ w,
+                                                  int64_t len, double sign, const double* __restrict__ flag,
+                                                  double* __restrict__ partial) {
   if (flag && *flag == 0.0) return;
   __shared__ double hs[130];
+  __shared__ double red[kBlock / 32];
   for (int i = threadIdx.x; i < kp1; i += blockDim.x) hs[i] = sign * h[i];
   __syncthreads();
+  double ss = 0.0;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
     double acc = w[n];
     for (int i = 0; i < kp1; ++i) acc -= hs[i] * V[(int64_t)i * ldv + n];
     w[n] = acc;
+    if (partial) ss = fma(acc, acc, ss);
+  }
+  if (!partial) return;
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) t += red[i];
+    partial[blockIdx.x] = t;
   }
 }
 
@@ -366,9 +406,37 @@ struct Reducer {
             const double* flag = nullptr, int zero_if_skipped = 0) {
     const int nb = nblk(len);
     const int ps = 132;
-    ::p4d::count_launch(), k_mdot<<<nb, kRedThreads, 0, c->stream>>>(V, ldv, kp1, w, len, ww ? 1 : 0, c->part, ps, flag);
+    if (kp1 == 0) launch_group<0>(ww, V, ldv, 0, kp1, w, len, nb, ps, flag);
+    for (int g0 = 0; g0 < kp1; g0 += kDotGroup)
+      dispatch(std::min(kDotGroup, kp1 - g0), ww && g0 == 0, V, ldv, g0, kp1, w, len, nb, ps, flag);
     ::p4d::count_launch(), k_reduce_partials<<<kp1 + (ww ? 1 : 0), 256, 0, c->stream>>>(c->part, nb, ps, kp1 + (ww ? 1 : 0), out, flag,
                                                                   zero_if_skipped);
+  }
+  template <int NG>
+  void launch_group(bool ww, const double* V, int64_t ldv, int g0, int kp1, const double* w, int64_t len, int nb,
+                    int ps, const double* flag) {
+    if (ww) ::p4d::count_launch(), k_mdot<NG, true><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, g0, kp1, w, len, c->part, ps, flag);
+    else ::p4d::count_launch(), k_mdot<NG, false><<<nb, kRedThreads, 0, c->stream>>>(V, ldv, g0, kp1, w, len, c->part, ps, flag);
+  }
+  void dispatch(int ng, bool ww, const double* V, int64_t ldv, int g0, int kp1, const double* w, int64_t len, int nb,
+                int ps, const double* flag) {
+    switch (ng) {
+#define P4D_MDOT_CASE(K) \
+  case K: launch_group<K>(ww, V, ldv, g0, kp1, w, len, nb, ps, flag); break;
+      P4D_MDOT_CASE(1) P4D_MDOT_CASE(2) P4D_MDOT_CASE(3) P4D_MDOT_CASE(4) P4D_MDOT_CASE(5) P4D_MDOT_CASE(6)
+      P4D_MDOT_CASE(7) P4D_MDOT_CASE(8) P4D_MDOT_CASE(9) P4D_MDOT_CASE(10) P4D_MDOT_CASE(11) P4D_MDOT_CASE(12)
+      P4D_MDOT_CASE(13) P4D_MDOT_CASE(14) P4D_MDOT_CASE(15) P4D_MDOT_CASE(16)
+#undef P4D_MDOT_CASE
+      default: break;
+    }
+  }
+  // w -= V h over kp1 vectors; with norm_out, also norm_out = ||w_new||^2
+  void maxpy(const double* V, int64_t ldv, int kp1, const double* h, double* w, int64_t len, double sign,
+             const double* flag, double* norm_out, unsigned gb) {
+    ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(V, ldv, kp1, h, w, len, sign, flag,
+                                                               norm_out ? c->part : nullptr);
+    if (norm_out)
+      ::p4d::count_launch(), k_reduce_partials<<<1, 256, 0, c->stream>>>(c->part, (int)gb, 1, 1, norm_out, flag, 0);
   }
 };
 
@@ -460,13 +528,12 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       prof_mark(c, 2);
       // classical Gram-Schmidt, second pass only when needed
       const double* flag = misc + 2 * L.m + 6;
-      R.mdot(c->V, len, k + 1, w, len, true, misc);                 // h1, ||w||^2 before
-      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc, w, len, 1.0, nullptr);
-      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2);            // ||w||^2 after
+      R.mdot(c->V, len, k + 1, w, len, true, misc);                          // h1, ||w||^2 before
+      R.maxpy(c->V, len, k + 1, misc, w, len, 1.0, nullptr, misc + 2 * L.m + 2, gb);   // ||w||^2 after
       ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(hs, L, k);
       R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
-      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag);
-      R.mdot(w, 0, 0, w, len, true, misc + 2 * L.m + 2, flag, 0);   // ||w||^2 after the second pass
+      // ||w||^2 after the second pass (left unchanged when it is skipped)
+      R.maxpy(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag, misc + 2 * L.m + 2, gb);
       ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
       // v_{k+1} = w / h_{k+1,k}
       ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
@@ -484,7 +551,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     if (kk > 0) {
       ::p4d::count_launch(), k_backsolve<<<1, 1, 0, c->stream>>>(hs, L, kk);
       // x += Z y  (k_maxpy computes w -= sum h_i V_i; use sign -1)
-      ::p4d::count_launch(), k_maxpy<<<gb, kBlock, 0, c->stream>>>(c->Z, len, kk, hs + L.y, x, len, -1.0, nullptr);
+      R.maxpy(c->Z, len, kk, hs + L.y, x, len, -1.0, nullptr, nullptr, gb);
     }
     if (st == P4D_ERR_NONFINITE) break;
     if (st == P4D_OK) {

@@ -103,15 +103,20 @@ struct SrcOp {
 // A_c = P^T diag(m) A diag(m) P for one hierarchy; writes difference form.
 // identity_out: coarse nodes without support get an identity row (fixed part)
 // or a zero row (variable part).
-__global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst,
+constexpr int kRapBlock = 64;
+
+__global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst,
                       Ptr4<const double> frs, Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out,
                       int identity_out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
   if (C >= cd.n) return;
-  double acc[27];
+  // per-thread accumulators in shared memory: the target slot is a run-time
+  // index, and a register array indexed that way would live on the stack
+  __shared__ double sacc[27 * kRapBlock];
+  double* acc = sacc + threadIdx.x;
 #pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = 0.0;
   double rsum = 0.0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
@@ -158,7 +163,7 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst
                   const int px = X.a[0].par[gi * 2 + c1];
                   if (px < 0) continue;
                   const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
-                  acc[oo] += a * X.a[0].parw[gi * 2 + c1] * wy * wz;
+                  acc[oo * kRapBlock] += a * X.a[0].parw[gi * 2 + c1] * wy * wz;
                 }
               }
             }
@@ -174,18 +179,21 @@ __global__ void k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst
     o_[13 * cn + C] = identity_out ? 1.0 : 0.0;
     return;
   }
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : acc[o];
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : acc[o * kRapBlock];
 }
 
 // V_1 = P^T diag(m s) P (level-0 variable part is diagonal).
-__global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
+__global__ void __launch_bounds__(kRapBlock) k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
                            Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
   if (C >= cd.n) return;
-  double acc[27];
+  // per-thread accumulators in shared memory: the target slot is a run-time
+  // index, and a register array indexed that way would live on the stack
+  __shared__ double sacc[27 * kRapBlock];
+  double* acc = sacc + threadIdx.x;
 #pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = 0.0;
   double rsum = 0.0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
@@ -215,7 +223,7 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double
                 const int px = X.a[0].par[fi * 2 + c1];
                 if (px < 0) continue;
                 const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
-                acc[oo] += a * X.a[0].parw[fi * 2 + c1] * X.a[1].parw[fj * 2 + c2] * X.a[2].parw[fk * 2 + c3];
+                acc[oo * kRapBlock] += a * X.a[0].parw[fi * 2 + c1] * X.a[1].parw[fj * 2 + c2] * X.a[2].parw[fk * 2 + c3];
               }
             }
           }
@@ -225,7 +233,7 @@ __global__ void k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double
   }
   double* o_ = pk(out.p, h);
   const int64_t cn = cd.n;
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o] : 0.0);
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o * kRapBlock] : 0.0);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -389,7 +397,8 @@ __global__ void k_gauss_jordan(int n, double* mats, double* work) {
   double* Inv = work + (size_t)blockIdx.x * n * n;
   __shared__ int piv;
   __shared__ double pval;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) Inv[t] = (t / n == t % n) ? 1.0 : 0.0;
+  for (int r = threadIdx.x >> 5; r < n; r += blockDim.x >> 5)
+    for (int cc = threadIdx.x & 31; cc < n; cc += 32) Inv[(size_t)r * n + cc] = r == cc ? 1.0 : 0.0;
   __syncthreads();
   for (int col = 0; col < n; ++col) {
     if (threadIdx.x == 0) {
@@ -416,12 +425,15 @@ __global__ void k_gauss_jordan(int n, double* mats, double* work) {
       Inv[(size_t)col * n + t] *= inv_p;
     }
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
-      const int r = (int)(t / n), cc = (int)(t % n);
+    // rows over warps, columns over lanes (no 64-bit index division)
+    for (int r = threadIdx.x >> 5; r < n; r += blockDim.x >> 5) {
       if (r == col) continue;
       const double f = A[(size_t)r * n + col];
-      if (cc != col) A[(size_t)r * n + cc] -= f * A[(size_t)col * n + cc];
-      Inv[(size_t)r * n + cc] -= f * Inv[(size_t)col * n + cc];
+      if (f == 0.0) continue;
+      for (int cc = threadIdx.x & 31; cc < n; cc += 32) {
+        if (cc != col) A[(size_t)r * n + cc] -= f * A[(size_t)col * n + cc];
+        Inv[(size_t)r * n + cc] -= f * Inv[(size_t)col * n + cc];
+      }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x)
@@ -933,7 +945,7 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
       cm.p[h] = B.mask[h];
       out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
     }
-    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
+    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -968,11 +980,11 @@ p4d_status mg_update(p4d_ctx* c) {
     if (l == 1) {
       Ptr4<const double> s;
       for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
+      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
     } else {
       Ptr4<const double> fst, frs;
       for (int h = 0; h < kNH; ++h) { fst.p[h] = A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
-      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, 64), kNH), 64, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
+      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
     }
     Ptr4<const double> F, V;
     Ptr4<const uint8_t> m;

@@ -164,6 +164,7 @@ struct p4d_ctx {
   double* zj = nullptr;                // [NE] (T_j^-1)_NN
   double* zeta = nullptr;              // [NE] 1 - z_j g_s M_j beta_j
   double* tfac = nullptr;              // [2][NE][nc] LU of T_j/M_j: 1/pivot, multiplier
+  double* tqfix = nullptr;             // [NE] last pivot of T_j/M_j without the surface term
   double* tloc = nullptr;              // [NE] node-local coupling scalar of the last operator application
   double* ujvp = nullptr;              // [nn] phi_e + gamma/c_e * c_e combination of a JVP input
   double* sqd = nullptr;               // [ndof] sqrt(|diag J|)

@@ -82,13 +82,17 @@ def test_jvp_parity(name, transpose):
 @pytest.mark.parametrize("name", ["tiny", "cube8", "odd", "oddcoarse"])
 @pytest.mark.parametrize("combine", ["additive", "multiplicative"])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_precond_fp64_matches_oracle_algorithm(name, combine, transpose):
+@pytest.mark.parametrize("cheb", [(2, 10.0), (3, 20.0)])
+def test_precond_fp64_matches_oracle_algorithm(name, combine, transpose, cheb):
     """FP64 preconditioner = the oracle's plain implementation of the same
-    algorithm (particle Schur elimination + BJ/BGS over V(2,2) cycles)."""
-    case, d, ref, s, st = _setup(name, precision=0, combine=0 if combine == "additive" else 1, mode=0)
+    algorithm (particle Schur elimination + BJ/BGS over V(d,d) cycles with
+    Chebyshev degree d and eigenvalue ratio as given)."""
+    deg, ratio = cheb
+    case, d, ref, s, st = _setup(name, precision=0, combine=0 if combine == "additive" else 1, mode=0,
+                                 cheb_degree=deg, cheb_ratio=ratio)
     s.jacobian_update(st)
     J = d.jacobian(ref)
-    P = BlockPrecond(d, J, combine=combine, order=(1, 0, 2))
+    P = BlockPrecond(d, J, combine=combine, order=(1, 0, 2), degree=deg, ratio=ratio)
     rng = np.random.default_rng(9)
     # a residual of balanced size in every row (as the scaled Krylov solve feeds it)
     r = rng.standard_normal(d.ndof) * np.sqrt(J.diagonal())
@@ -154,11 +158,11 @@ def test_fgmres_mixed_matches_direct(name, precision, combine):
 
 
 def test_iteration_counts_match_oracle():
-    case, d, ref, s, st = _setup("cube8", precision=0, mode=0, rtol=1e-10)
+    case, d, ref, s, st = _setup("cube8", precision=0, mode=0, rtol=1e-10, cheb_degree=2, cheb_ratio=10.0)
     s.jacobian_update(st)
     b = -s.residual(st)
     x, info = s.solve(b)
-    _, its, _ = LinearSolve(d, ref).fgmres(rtol=1e-10)
+    _, its, _ = LinearSolve(d, ref).fgmres(rtol=1e-10, degree=2, ratio=10.0)
     assert abs(info["iters"] - its) <= 2, (info["iters"], its)
 
 
@@ -176,3 +180,18 @@ def test_adjoint_solve_matches_direct(name):
     JT = (sp.diags(sc) @ J.T @ sp.diags(sc)).tocsc()
     lam_ref = sc * spla.spsolve(JT, sc * g)
     assert per_field_error(d, lam.cpu().numpy(), lam_ref)[0] <= 1e-8
+
+
+def test_set_params_refuses_assembled_physics():
+    """dt, F and the transport coefficients are baked into the stencils and
+    particle factors at setup: changing them through p4d_set_params is an
+    invalid argument; solver options and kinetics constants may change."""
+    from paper_2602_07225_gb300 import P4DError
+    case, d, ref, s, st = _setup("tiny")
+    s.set_options(cheb_degree=2, rtol=1e-9, k_n=3e-5)
+    for name, val in (("dt", 5.0), ("kappa", 2.0), ("De", 1e-9), ("sigma_n", 50.0), ("F", 96000.0)):
+        old = getattr(s.params, name)
+        with pytest.raises(P4DError):
+            s.set_options(**{name: val})
+        setattr(s.params, name, old)
+    s.set_options(cheb_degree=3)
