@@ -102,28 +102,63 @@ struct SrcOp {
 
 // A_c = P^T diag(m) A diag(m) P for one hierarchy; writes difference form.
 // identity_out: coarse nodes without support get an identity row (fixed part)
-// or a zero row (variable part).
+// or a zero row (variable part).  TV: the precision of input, accumulation
+// and output (FP64 for the fixed part and the FP64 preconditioner).
 constexpr int kRapBlock = 64;
 
-__global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> fst,
-                      Ptr4<const double> frs, Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out,
-                      int identity_out) {
+// acc[oo] += a * w(g -> D) over the (up to 8) coarse parents D of fine node
+// (gi, gj, gk), oo the slot of D in the coarse row of (I, J, K).
+template <typename TV>
+__device__ __forceinline__ void rap_scatter(const Xfer& X, int gi, int gj, int gk, int I, int J, int K, TV a,
+                                            TV* acc) {
+  const TV* pwx = parw_t<TV>(X.a[0]);
+  const TV* pwy = parw_t<TV>(X.a[1]);
+  const TV* pwz = parw_t<TV>(X.a[2]);
+  int oyz[4];
+  TV wyz[4];
+  int nyz = 0;
+  for (int c3 = 0; c3 < 2; ++c3) {
+    const int pz = X.a[2].par[gk * 2 + c3];
+    if (pz < 0) continue;
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int py = X.a[1].par[gj * 2 + c2];
+      if (py < 0) continue;
+      oyz[nyz] = 3 * (py - J + 1) + 9 * (pz - K + 1);
+      wyz[nyz] = pwy[gj * 2 + c2] * pwz[gk * 2 + c3];
+      ++nyz;
+    }
+  }
+  for (int c1 = 0; c1 < 2; ++c1) {
+    const int px = X.a[0].par[gi * 2 + c1];
+    if (px < 0) continue;
+    const TV t = a * pwx[gi * 2 + c1];
+    for (int q = 0; q < nyz; ++q) acc[(oyz[q] + px - I + 1) * kRapBlock] += t * wyz[q];
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const TV> fst,
+                                                   Ptr4<const TV> frs, Ptr4<const uint8_t> fm,
+                                                   Ptr4<const uint8_t> cm, Ptr4<TV> out, int identity_out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
   if (C >= cd.n) return;
   // per-thread accumulators in shared memory: the target slot is a run-time
   // index, and a register array indexed that way would live on the stack
-  __shared__ double sacc[27 * kRapBlock];
-  double* acc = sacc + threadIdx.x;
+  __shared__ TV sacc[27 * kRapBlock];
+  TV* acc = sacc + threadIdx.x;
 #pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = 0.0;
-  double rsum = 0.0;
+  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = (TV)0;
+  TV rsum = 0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
-  const double* st = pk(fst.p, h);
-  const double* rs = pk(frs.p, h);
+  const TV* st = pk(fst.p, h);
+  const TV* rs = pk(frs.p, h);
   const uint8_t* m = pk(fm.p, h);
   const int64_t fn = fd.n;
+  const TV* swx = supw_t<TV>(X.a[0]);
+  const TV* swy = supw_t<TV>(X.a[1]);
+  const TV* swz = supw_t<TV>(X.a[2]);
   if (pk(cm.p, h)[C]) {
     for (int tz = 0; tz < 3; ++tz) {
       const int fk = X.a[2].sup[K * 3 + tz];
@@ -131,16 +166,17 @@ __global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, X
       for (int ty = 0; ty < 3; ++ty) {
         const int fj = X.a[1].sup[J * 3 + ty];
         if (fj < 0) continue;
+        const TV wyz = swy[J * 3 + ty] * swz[K * 3 + tz];
         for (int tx = 0; tx < 3; ++tx) {
           const int fi = X.a[0].sup[I * 3 + tx];
           if (fi < 0) continue;
           const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
           if (!m[f]) continue;
-          const double wf = X.a[0].supw[I * 3 + tx] * X.a[1].supw[J * 3 + ty] * X.a[2].supw[K * 3 + tz];
-          const double sf = rs ? rs[f] : st[13 * fn + f];
+          const TV wf = swx[I * 3 + tx] * wyz;
+          const TV sf = rs ? rs[f] : st[13 * fn + f];
           rsum += wf * sf;
           // full-form diagonal of row f
-          double diag = sf;
+          TV diag = sf;
           for (int o = 0; o < 27; ++o)
             if (o != 13) diag -= st[o * fn + f];
           for (int o = 0; o < 27; ++o) {
@@ -149,55 +185,44 @@ __global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, X
             if (gi < 0 || gj < 0 || gk < 0 || gi >= fd.nnx || gj >= fd.nny || gk >= fd.nnz) continue;
             const int64_t gidx = gi + (int64_t)fd.nnx * (gj + (int64_t)fd.nny * gk);
             if (!m[gidx]) continue;
-            const double a = (o == 13 ? diag : st[o * fn + f]) * wf;
-            if (a == 0.0) continue;
-            for (int c3 = 0; c3 < 2; ++c3) {
-              const int pz = X.a[2].par[gk * 2 + c3];
-              if (pz < 0) continue;
-              const double wz = X.a[2].parw[gk * 2 + c3];
-              for (int c2 = 0; c2 < 2; ++c2) {
-                const int py = X.a[1].par[gj * 2 + c2];
-                if (py < 0) continue;
-                const double wy = X.a[1].parw[gj * 2 + c2];
-                for (int c1 = 0; c1 < 2; ++c1) {
-                  const int px = X.a[0].par[gi * 2 + c1];
-                  if (px < 0) continue;
-                  const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
-                  acc[oo * kRapBlock] += a * X.a[0].parw[gi * 2 + c1] * wy * wz;
-                }
-              }
-            }
+            const TV a = (o == 13 ? diag : st[o * fn + f]) * wf;
+            if (a == (TV)0) continue;
+            rap_scatter<TV>(X, gi, gj, gk, I, J, K, a, acc);
           }
         }
       }
     }
   }
-  double* o_ = pk(out.p, h);
+  TV* o_ = pk(out.p, h);
   const int64_t cn = cd.n;
   if (!pk(cm.p, h)[C]) {
-    for (int o = 0; o < 27; ++o) o_[o * cn + C] = 0.0;
-    o_[13 * cn + C] = identity_out ? 1.0 : 0.0;
+    for (int o = 0; o < 27; ++o) o_[o * cn + C] = (TV)0;
+    o_[13 * cn + C] = identity_out ? (TV)1 : (TV)0;
     return;
   }
   for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : acc[o * kRapBlock];
 }
 
-// V_1 = P^T diag(m s) P (level-0 variable part is diagonal).
+// V_1 = P^T diag(m s) P (level-0 variable part is diagonal), in precision TV.
+template <typename TV>
 __global__ void __launch_bounds__(kRapBlock) k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
-                           Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm, Ptr4<double> out) {
+                                                        Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm,
+                                                        Ptr4<TV> out) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
   if (C >= cd.n) return;
-  // per-thread accumulators in shared memory: the target slot is a run-time
-  // index, and a register array indexed that way would live on the stack
-  __shared__ double sacc[27 * kRapBlock];
-  double* acc = sacc + threadIdx.x;
+  __shared__ TV sacc[27 * kRapBlock];
+  TV* acc = sacc + threadIdx.x;
 #pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = 0.0;
-  double rsum = 0.0;
+  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = (TV)0;
+  TV rsum = 0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
   const uint8_t* m = pk(fm.p, h);
+  const double* sv = pk(s.p, h);
+  const TV* swx = supw_t<TV>(X.a[0]);
+  const TV* swy = supw_t<TV>(X.a[1]);
+  const TV* swz = supw_t<TV>(X.a[2]);
   if (pk(cm.p, h)[C]) {
     for (int tz = 0; tz < 3; ++tz) {
       const int fk = X.a[2].sup[K * 3 + tz];
@@ -205,35 +230,22 @@ __global__ void __launch_bounds__(kRapBlock) k_rap_diag(LevelDims fd, LevelDims 
       for (int ty = 0; ty < 3; ++ty) {
         const int fj = X.a[1].sup[J * 3 + ty];
         if (fj < 0) continue;
+        const TV wyz = swy[J * 3 + ty] * swz[K * 3 + tz];
         for (int tx = 0; tx < 3; ++tx) {
           const int fi = X.a[0].sup[I * 3 + tx];
           if (fi < 0) continue;
           const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
           if (!m[f]) continue;
-          const double wf = X.a[0].supw[I * 3 + tx] * X.a[1].supw[J * 3 + ty] * X.a[2].supw[K * 3 + tz];
-          const double a = wf * pk(s.p, h)[f];
+          const TV a = swx[I * 3 + tx] * wyz * (TV)sv[f];
           rsum += a;
-          for (int c3 = 0; c3 < 2; ++c3) {
-            const int pz = X.a[2].par[fk * 2 + c3];
-            if (pz < 0) continue;
-            for (int c2 = 0; c2 < 2; ++c2) {
-              const int py = X.a[1].par[fj * 2 + c2];
-              if (py < 0) continue;
-              for (int c1 = 0; c1 < 2; ++c1) {
-                const int px = X.a[0].par[fi * 2 + c1];
-                if (px < 0) continue;
-                const int oo = (px - I + 1) + 3 * (py - J + 1) + 9 * (pz - K + 1);
-                acc[oo * kRapBlock] += a * X.a[0].parw[fi * 2 + c1] * X.a[1].parw[fj * 2 + c2] * X.a[2].parw[fk * 2 + c3];
-              }
-            }
-          }
+          rap_scatter<TV>(X, fi, fj, fk, I, J, K, a, acc);
         }
       }
     }
   }
-  double* o_ = pk(out.p, h);
+  TV* o_ = pk(out.p, h);
   const int64_t cn = cd.n;
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o * kRapBlock] : 0.0);
+  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o * kRapBlock] : (TV)0);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -307,8 +319,8 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
 }
 
 // Level >= 1: A = F + V into storage precision, inverse diagonal and lam.
-template <typename TS, typename T>
-__global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const double> V, Ptr4<TS> st,
+template <typename TS, typename T, typename TV>
+__global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const TV> V, Ptr4<TS> st,
                                 Ptr4<T> dinv, Ptr4<const uint8_t> mask, double sc0, double sc1, double sc2,
                                 double sc3, double* lam) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -317,10 +329,10 @@ __global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const do
   if (n < d.n) {
     const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
     const double* f = pk(F.p, h);
-    const double* v = pk(V.p, h);
+    const TV* v = pk(V.p, h);
     double diag = 0.0, absoff = 0.0, s = 0.0;
     for (int o = 0; o < 27; ++o) {
-      const double a = f[o * d.n + n] + v[o * d.n + n];
+      const double a = f[o * d.n + n] + (double)v[o * d.n + n];
       pk(st.p, h)[o * d.n + n] = fromd<TS>(sc * a);
       if (o == 13) s = a;
       else { diag -= a; absoff += fabs(a); }
@@ -334,7 +346,8 @@ __global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const do
 }
 
 // Dense scaled coarsest operator [n][n] (row major) from difference form.
-__global__ void k_dense(LevelDims d, Ptr4<const double> F, Ptr4<const double> V, double sc0, double sc1,
+template <typename TV>
+__global__ void k_dense(LevelDims d, Ptr4<const double> F, Ptr4<const TV> V, double sc0, double sc1,
                         double sc2, double sc3, double* out) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int h = blockIdx.y;
@@ -346,7 +359,7 @@ __global__ void k_dense(LevelDims d, Ptr4<const double> F, Ptr4<const double> V,
   for (int64_t m = 0; m < d.n; ++m) A[n * d.n + m] = 0.0;
   double diag = 0.0;
   for (int o = 0; o < 27; ++o) {
-    const double a = pk(F.p, h)[o * d.n + n] + pk(V.p, h)[o * d.n + n];
+    const double a = pk(F.p, h)[o * d.n + n] + (double)pk(V.p, h)[o * d.n + n];
     if (o == 13) { diag += a; continue; }
     diag -= a;
     const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
@@ -836,7 +849,13 @@ p4d_status mg_plan(p4d_ctx* c) {
       P4D_TRY(cudaMemcpy(dp + par.size(), sup.data(), sup.size() * sizeof(int), cudaMemcpyHostToDevice));
       P4D_TRY(cudaMemcpy(dw, parw.data(), parw.size() * sizeof(double), cudaMemcpyHostToDevice));
       P4D_TRY(cudaMemcpy(dw + parw.size(), supw.data(), supw.size() * sizeof(double), cudaMemcpyHostToDevice));
-      lv.X.a[a] = Axis{dp, dw, dp + par.size(), dw + parw.size()};
+      std::vector<float> wf(parw.size() + supw.size());
+      for (size_t q = 0; q < parw.size(); ++q) wf[q] = (float)parw[q];
+      for (size_t q = 0; q < supw.size(); ++q) wf[parw.size() + q] = (float)supw[q];
+      float* dwf = nullptr;
+      P4D_TRYS(dalloc_t(c, &dwf, wf.size()));
+      P4D_TRY(cudaMemcpy(dwf, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+      lv.X.a[a] = Axis{dp, dw, dp + par.size(), dw + parw.size(), dwf, dwf + parw.size()};
     }
     nnx = cn[0];
     nny = cn[1];
@@ -874,7 +893,7 @@ p4d_status mg_plan(p4d_ctx* c) {
       ::p4d::count_launch(), k_mask0<<<nblocks(n), kBlock, 0, c->stream>>>(n, c->label, lv.mask[0], lv.mask[1], lv.mask[2], lv.mask[3]);
     } else {
       P4D_TRYS(dalloc_t(c, &lv.Ffix, (size_t)kNH * 27 * n));
-      P4D_TRYS(dalloc_t(c, &lv.Vvar, (size_t)kNH * 27 * n));
+      P4D_TRYS(dalloc(c, &lv.Vvar, (prec == 0 ? sizeof(double) : sizeof(float)) * (size_t)kNH * 27 * n));
       for (int h = 0; h < kNH; ++h) {
         P4D_TRYS(dalloc(c, &lv.st[h], ts * 27 * n));
         P4D_TRYS(dalloc(c, &lv.dinv[h], tv * n));
@@ -945,8 +964,78 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
       cm.p[h] = B.mask[h];
       out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
     }
-    ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
+    ::p4d::count_launch(), k_rap<double><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
   }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+// Variable part of levels >= 1 (Galerkin products in precision TV), the
+// stored level operators, and the coarsest dense inverse (FP64).
+template <typename TV>
+p4d_status mg_update_levels(p4d_ctx* c, const double* svar, const double* sch) {
+  const int prec = c->prm.precision;
+  const int64_t nn = c->g.nn;
+  const double* sf = c->scale_f;
+  const int fh[kNH] = {0, 0, 1, 2};
+  for (int l = 1; l < c->nlev; ++l) {
+    MGLevel& A = c->lev[l - 1];
+    MGLevel& B = c->lev[l];
+    Ptr4<const uint8_t> fm, cm;
+    Ptr4<TV> out;
+    for (int h = 0; h < kNH; ++h) { fm.p[h] = A.mask[h]; cm.p[h] = B.mask[h]; out.p[h] = (TV*)B.Vvar + (size_t)h * 27 * B.n; }
+    if (l == 1) {
+      Ptr4<const double> s;
+      for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
+      ::p4d::count_launch(), k_rap_diag<TV><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
+    } else {
+      Ptr4<const TV> fst, frs;
+      for (int h = 0; h < kNH; ++h) { fst.p[h] = (const TV*)A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
+      ::p4d::count_launch(), k_rap<TV><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
+    }
+    Ptr4<const double> F;
+    Ptr4<const TV> V;
+    Ptr4<const uint8_t> m;
+    for (int h = 0; h < kNH; ++h) {
+      F.p[h] = B.Ffix + (size_t)h * 27 * B.n;
+      V.p[h] = (const TV*)B.Vvar + (size_t)h * 27 * B.n;
+      m.p[h] = B.mask[h];
+    }
+    const dim3 grid(nblocks(B.n), kNH);
+    if (prec == 0) {
+      Ptr4<double> st, di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (double*)B.st[h]; di.p[h] = (double*)B.dinv[h]; }
+      ::p4d::count_launch(), k_level_combine<double, double, TV><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    } else if (prec == 1) {
+      Ptr4<float> st, di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (float*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
+      ::p4d::count_launch(), k_level_combine<float, float, TV><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    } else {
+      Ptr4<__nv_bfloat16> st;
+      Ptr4<float> di;
+      for (int h = 0; h < kNH; ++h) { st.p[h] = (__nv_bfloat16*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
+      ::p4d::count_launch(), k_level_combine<__nv_bfloat16, float, TV><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
+    }
+  }
+  // coarsest: dense scaled operator and its inverse
+  MGLevel& C = c->lev[c->nlev - 1];
+  double* mats = C.inv;
+  double* work = C.inv + (size_t)kNH * C.n * C.n;
+  if (c->nlev == 1) {
+    Ptr4<const uint8_t> m;
+    for (int h = 0; h < kNH; ++h) m.p[h] = C.mask[h];
+    ::p4d::count_launch(), k_dense0<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(c->g, c->Jst, c->sfix, svar, m, sf[0], sf[1], sf[2],
+                                                                 mats);
+  } else {
+    Ptr4<const double> F;
+    Ptr4<const TV> V;
+    for (int h = 0; h < kNH; ++h) {
+      F.p[h] = C.Ffix + (size_t)h * 27 * C.n;
+      V.p[h] = (const TV*)C.Vvar + (size_t)h * 27 * C.n;
+    }
+    ::p4d::count_launch(), k_dense<TV><<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
+  }
+  ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -970,66 +1059,8 @@ p4d_status mg_update(p4d_ctx* c) {
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3], (float*)l0.dinv[0], (float*)l0.dinv[2],
         (float*)l0.dinv[3], svar, l0.lam);
-  const int fh[kNH] = {0, 0, 1, 2};
-  for (int l = 1; l < c->nlev; ++l) {
-    MGLevel& A = c->lev[l - 1];
-    MGLevel& B = c->lev[l];
-    Ptr4<const uint8_t> fm, cm;
-    Ptr4<double> out;
-    for (int h = 0; h < kNH; ++h) { fm.p[h] = A.mask[h]; cm.p[h] = B.mask[h]; out.p[h] = B.Vvar + (size_t)h * 27 * B.n; }
-    if (l == 1) {
-      Ptr4<const double> s;
-      for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      ::p4d::count_launch(), k_rap_diag<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
-    } else {
-      Ptr4<const double> fst, frs;
-      for (int h = 0; h < kNH; ++h) { fst.p[h] = A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
-      ::p4d::count_launch(), k_rap<<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
-    }
-    Ptr4<const double> F, V;
-    Ptr4<const uint8_t> m;
-    for (int h = 0; h < kNH; ++h) {
-      F.p[h] = B.Ffix + (size_t)h * 27 * B.n;
-      V.p[h] = B.Vvar + (size_t)h * 27 * B.n;
-      m.p[h] = B.mask[h];
-    }
-    const dim3 grid(nblocks(B.n), kNH);
-    if (prec == 0) {
-      Ptr4<double> st, di;
-      for (int h = 0; h < kNH; ++h) { st.p[h] = (double*)B.st[h]; di.p[h] = (double*)B.dinv[h]; }
-      ::p4d::count_launch(), k_level_combine<double, double><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
-    } else if (prec == 1) {
-      Ptr4<float> st, di;
-      for (int h = 0; h < kNH; ++h) { st.p[h] = (float*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
-      ::p4d::count_launch(), k_level_combine<float, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
-    } else {
-      Ptr4<__nv_bfloat16> st;
-      Ptr4<float> di;
-      for (int h = 0; h < kNH; ++h) { st.p[h] = (__nv_bfloat16*)B.st[h]; di.p[h] = (float*)B.dinv[h]; }
-      ::p4d::count_launch(), k_level_combine<__nv_bfloat16, float><<<grid, kBlock, 0, c->stream>>>(dims(B), F, V, st, di, m, sch[0], sch[1], sch[2], sch[3], B.lam);
-    }
-  }
-  // coarsest: dense scaled operator and its inverse
-  MGLevel& C = c->lev[c->nlev - 1];
-  if (c->nlev == 1) {
-    Ptr4<const uint8_t> m;
-    for (int h = 0; h < kNH; ++h) m.p[h] = C.mask[h];
-    double* mats = C.inv;
-    double* work = C.inv + (size_t)kNH * C.n * C.n;
-    ::p4d::count_launch(), k_dense0<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(c->g, c->Jst, c->sfix, svar, m, sf[0], sf[1], sf[2],
-                                                                 mats);
-    ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
-  } else {
-    Ptr4<const double> F, V;
-    for (int h = 0; h < kNH; ++h) {
-      F.p[h] = C.Ffix + (size_t)h * 27 * C.n;
-      V.p[h] = C.Vvar + (size_t)h * 27 * C.n;
-    }
-    double* mats = C.inv;
-    double* work = C.inv + (size_t)kNH * C.n * C.n;
-    ::p4d::count_launch(), k_dense<<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
-    ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
-  }
+  if (prec == 0) P4D_TRYS(mg_update_levels<double>(c, svar, sch));
+  else P4D_TRYS(mg_update_levels<float>(c, svar, sch));
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }

@@ -79,7 +79,17 @@ struct Axis {
   const double* parw;  // [nf][2]
   const int* sup;      // [nc][3] support fine nodes (-1: none)
   const double* supw;  // [nc][3]
+  const float* parwf;  // FP32 copies of parw and supw (the weights are exact in FP32)
+  const float* supwf;
 };
+
+// Interpolation weight tables in the precision T of a computation.
+template <typename T> __device__ __forceinline__ const T* parw_t(const Axis& a);
+template <typename T> __device__ __forceinline__ const T* supw_t(const Axis& a);
+template <> __device__ __forceinline__ const double* parw_t<double>(const Axis& a) { return a.parw; }
+template <> __device__ __forceinline__ const float* parw_t<float>(const Axis& a) { return a.parwf; }
+template <> __device__ __forceinline__ const double* supw_t<double>(const Axis& a) { return a.supw; }
+template <> __device__ __forceinline__ const float* supw_t<float>(const Axis& a) { return a.supwf; }
 struct Xfer {
   Axis a[3];
 };
@@ -91,8 +101,9 @@ struct MGLevel {
   Xfer X{};                            // interpolation tables towards the next level
   // FP64 fixed (linearization independent) operator, difference form [kNH][27][n]
   double* Ffix = nullptr;
-  // FP64 linearization-dependent part (levels >= 1), difference form [kNH][27][n]
-  double* Vvar = nullptr;
+  // linearization-dependent part (levels >= 1), difference form [kNH][27][n]:
+  // FP64 for the FP64 preconditioner, FP32 otherwise
+  void* Vvar = nullptr;
   // stencil in storage precision [kNH][27][n] (level 0: hierarchies 0/1 alias field phi_s)
   void* st[kNH] = {nullptr, nullptr, nullptr, nullptr};
   void* dinv[kNH] = {};                // [n] in compute precision
