@@ -149,7 +149,8 @@ void p4d_params_default(p4d_params* p);
    Q1 stiffness/mass stencils, plans the multigrid hierarchy and allocates
    all workspace.  If state != NULL the Jacobian is linearized at it (as
    p4d_jacobian_update).  stream: a cudaStream_t or NULL.
-   Errors: INVALID_ARG (sizes, options, anode/cathode contact), OOM, CUDA. */
+   Errors: INVALID_ARG (sizes, options, anode/cathode contact; kernels use
+   32-bit indices, so 27 N_n and N_E N_c must stay below 2^31), OOM, CUDA. */
 p4d_status p4d_setup(const p4d_mesh* mesh, const p4d_params* params, const p4d_state* state,
                      void* stream, p4d_handle* out);
 

@@ -173,7 +173,7 @@ __global__ void k_adjoint_prev(Grid g, int64_t NE, int nc, double idt, const dou
     out[2 * nn + n] = acc;
   } else if (q < nn + NE * nc) {
     const int64_t p = q - nn;
-    out[3 * nn + p] = Mj[p / nc] * idt * lam[3 * nn + p];
+    out[3 * nn + p] = Mj[(uint32_t)p / (uint32_t)nc] * idt * lam[3 * nn + p];
   }
 }
 

@@ -143,11 +143,12 @@ __global__ void k_node_ln(int64_t nn, const double* __restrict__ ce, double gamm
 // surface term (unit lower L with multipliers mult_i, upper U with pivots
 // piv_i): every pivot but the last and all multipliers depend only on dt,
 // kap_j and the radial grid, so they are factored once.  Stored as 1/piv and
-// mult, so that every later FP64 particle solve is division free; qfix_j is
-// the last pivot without the surface term.
+// mult, radial-major ([nc][NE]: coalesced over nodes), so that every later
+// FP64 particle solve is division free; qfix_j is the last pivot without the
+// surface term.
 __global__ void k_particle_lu_fixed(int64_t NE, int nc, double dt, const double* __restrict__ kapj,
                                     const double* __restrict__ rref, double* __restrict__ ipiv,
-                                    double* __restrict__ mult, double* __restrict__ qfix) {
+                                    double* __restrict__ mult, double* __restrict__ qfix, float* __restrict__ f32) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= NE) return;
   const double kap = kapj[j];
@@ -156,14 +157,19 @@ __global__ void k_particle_lu_fixed(int64_t NE, int nc, double dt, const double*
   const double* up = rref + 2 * nc;
   const double idt = 1.0 / dt;
   double piv = idt - kap * di[0];
-  mult[j * nc] = 0.0;
+  mult[j] = 0.0;
   for (int i = 1; i < nc; ++i) {
-    ipiv[j * nc + i - 1] = 1.0 / piv;
+    ipiv[(i - 1) * NE + j] = 1.0 / piv;
     const double mi = (-kap * lo[i]) / piv;
     piv = (idt - kap * di[i]) - mi * (-kap * up[i - 1]);
-    mult[j * nc + i] = mi;
+    mult[i * NE + j] = mi;
   }
   qfix[j] = piv;
+  if (f32)   // FP32 copies: [nc][NE] 1/pivot, then [nc][NE] multipliers
+    for (int i = 0; i < nc; ++i) {
+      f32[i * NE + j] = (float)ipiv[i * NE + j];
+      f32[(nc + i) * NE + j] = (float)mult[i * NE + j];
+    }
 }
 
 // Linearization per electrode node: kinetics derivatives, the last pivot of
@@ -177,7 +183,8 @@ __global__ void k_linearize(int64_t NE, int nc, Kin kn, const int32_t* __restric
                             const double* __restrict__ Mj, const double* __restrict__ betaj,
                             const double* __restrict__ qfix, double* __restrict__ in_, double* __restrict__ ge,
                             double* __restrict__ gc, double* __restrict__ gs, double* __restrict__ zj,
-                            double* __restrict__ zeta, double* __restrict__ ipiv, unsigned* flags) {
+                            double* __restrict__ zeta, double* __restrict__ ipiv, float* __restrict__ ipiv32,
+                            unsigned* flags) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= NE) return;
   const int64_t n = enode[j];
@@ -188,7 +195,8 @@ __global__ void k_linearize(int64_t NE, int nc, Kin kn, const int32_t* __restric
   in_[j] = a; ge[j] = b; gc[j] = c; gs[j] = d;
   const double M = Mj[j];
   const double piv = qfix[j] + betaj[j] * d;
-  ipiv[j * nc + nc - 1] = 1.0 / piv;
+  ipiv[(nc - 1) * NE + j] = 1.0 / piv;
+  if (ipiv32) ipiv32[(nc - 1) * NE + j] = (float)(1.0 / piv);
   const double z = 1.0 / (M * piv);
   zj[j] = z;
   zeta[j] = 1.0 - z * d * M * betaj[j];
@@ -225,8 +233,8 @@ __global__ void k_diag(Grid g, int64_t NE, int nc, double tau, double idt, const
     put_scale(Jst[(2 * 27 + 13) * nn + n] - (e >= 0 ? tau * Aj[e] * gc[e] : 0.0), sqd, rsqd, 2 * nn + n);
   } else if (t < nn + NE * nc) {
     const int64_t q = t - nn;
-    const int64_t e = q / nc;
-    const int i = (int)(q % nc);
+    const int64_t e = (uint32_t)q / (uint32_t)nc;   // NE nc < 2^31 (checked at setup)
+    const int i = (int)(q - e * nc);
     double d = Mj[e] * (idt - kapj[e] * rref[nc + i]);
     if (i == nc - 1) d += Mj[e] * betaj[e] * gs[e];
     put_scale(d, sqd, rsqd, 3 * nn + q);
@@ -369,8 +377,8 @@ __global__ void k_residual_particle(int64_t NE, int nc, double idt, const double
                                     double* __restrict__ r) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= NE * nc) return;
-  const int64_t e = q / nc;
-  const int i = (int)(q % nc);
+  const int64_t e = (uint32_t)q / (uint32_t)nc;   // NE nc < 2^31 (checked at setup)
+  const int i = (int)(q - e * nc);
   const double* c = cs + e * nc;
   double L = rref[nc + i] * c[i];
   if (i > 0) L += rref[i] * c[i - 1];
@@ -408,7 +416,7 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   P4D_TRYS(dalloc_t(c, &c->tqfix, (size_t)std::max<int64_t>(1, c->NE)));
   if (c->NE > 0)
     ::p4d::count_launch(), k_particle_lu_fixed<<<nblocks(c->NE), kBlock, 0, c->stream>>>(
-        c->NE, c->nc, c->prm.dt, c->kapj, c->rref, c->tfac, c->tfac + (size_t)c->NE * c->nc, c->tqfix);
+        c->NE, c->nc, c->prm.dt, c->kapj, c->rref, c->tfac, c->tfac + (size_t)c->NE * c->nc, c->tqfix, c->tfac32);
   unsigned long long* mx = nullptr;
   P4D_TRYS(dalloc_t(c, &mx, 3));
   P4D_TRY(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), c->stream));
@@ -436,7 +444,7 @@ p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
     ::p4d::count_launch(), k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype,
                                                         st->phis, st->phie, st->ce, st->cs, c->Mj, c->betaj,
                                                         c->tqfix, c->in_, c->ge, c->gc, c->gs, c->zj, c->zeta,
-                                                        c->tfac, c->flags);
+                                                        c->tfac, c->tfac32, c->flags);
   ::p4d::count_launch(), k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, 1.0 / c->prm.dt, c->Jst, c->label,
                                                           c->eidx, c->Aj, c->Mj, c->kapj, c->betaj, c->rref,
                                                           c->ge, c->gc, c->gs, c->sqd, c->rsqd);

@@ -164,6 +164,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
     }
   }
   const int64_t NE = (int64_t)c->enodes_h.size();
+  if (NE * nc >= (int64_t(1) << 31) || 27 * nn >= (int64_t(1) << 31)) return P4D_ERR_INVALID_ARG;   // 32-bit kernel indices
   c->NE = NE;
   c->ndof = 3 * nn + NE * nc;
 
@@ -226,6 +227,11 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(upload(c, &c->enode, c->enodes_h.data(), NE));
   P4D_TRYS(upload(c, &c->gpw, gpw.data(), nn));
   P4D_TRYS(upload(c, &c->Mj, Mj.data(), NE));
+  {
+    std::vector<double> iM(NE);
+    for (int64_t e = 0; e < NE; ++e) iM[e] = 1.0 / Mj[e];
+    P4D_TRYS(upload(c, &c->iMj, iM.data(), NE));
+  }
   P4D_TRYS(upload(c, &c->Aj, Aj.data(), NE));
   P4D_TRYS(upload(c, &c->kapj, kapj.data(), NE));
   P4D_TRYS(upload(c, &c->betaj, betaj.data(), NE));
@@ -253,6 +259,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->zeta, NE));
   P4D_TRYS(dalloc_t(c, &c->tloc, NE));
   P4D_TRYS(dalloc_t(c, &c->tfac, (size_t)2 * std::max<int64_t>(1, NE) * nc));
+  if (prm->precision != 0) P4D_TRYS(dalloc_t(c, &c->tfac32, (size_t)2 * std::max<int64_t>(1, NE) * nc));
   P4D_TRYS(dalloc_t(c, &c->sqd, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->rsqd, c->ndof));
   P4D_TRYS(dalloc_t(c, &c->iwf, 4));

@@ -119,8 +119,8 @@ __global__ void k_jvp_particle(JvpArgs a, const double* __restrict__ x, const do
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int nc = a.nc;
   if (q >= a.NE * nc) return;
-  const int64_t e = q / nc;
-  const int i = (int)(q % nc);
+  const int64_t e = (uint32_t)q / (uint32_t)nc;   // NE nc < 2^31 (checked at setup)
+  const int i = (int)(q - e * nc);
   const int64_t nn = a.g.nn;
   const double* xc = x + 3 * nn + e * nc;
   const double* lo = a.rref;

@@ -142,6 +142,7 @@ struct p4d_ctx {
   int32_t* enode = nullptr;            // [NE] node index
   double* gpw = nullptr;               // [nn] Gamma_p lumped face weights
   double* Mj = nullptr;                // [NE] lumped electrode volume
+  double* iMj = nullptr;               // [NE] 1 / Mj
   double* Aj = nullptr;                // [NE] 3 S_j / R_j
   double* kapj = nullptr;              // [NE] D_s / R_s^2
   double* betaj = nullptr;             // [NE] flux factor of eq. LR
@@ -174,8 +175,9 @@ struct p4d_ctx {
   double* gs = nullptr;
   double* zj = nullptr;                // [NE] (T_j^-1)_NN
   double* zeta = nullptr;              // [NE] 1 - z_j g_s M_j beta_j
-  double* tfac = nullptr;              // [2][NE][nc] LU of T_j/M_j: 1/pivot, multiplier
+  double* tfac = nullptr;              // [2][nc][NE] LU of T_j/M_j: 1/pivot, multiplier
   double* tqfix = nullptr;             // [NE] last pivot of T_j/M_j without the surface term
+  float* tfac32 = nullptr;             // FP32 copy of tfac (FP32 preconditioners)
   double* tloc = nullptr;              // [NE] node-local coupling scalar of the last operator application
   double* ujvp = nullptr;              // [nn] phi_e + gamma/c_e * c_e combination of a JVP input
   double* sqd = nullptr;               // [ndof] sqrt(|diag J|)

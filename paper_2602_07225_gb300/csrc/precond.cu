@@ -24,7 +24,7 @@ struct PcArgs {
   const uint8_t* label;
   const int32_t* eidx;
   const int32_t* enode;
-  const double *Aj, *Mj, *betaj, *kapj, *rref;
+  const double *Aj, *Mj, *iMj, *betaj, *kapj, *rref;
   const double *ge, *gc, *gs, *zeta, *sqd, *iwf;
   double sc[3];
 };
@@ -33,46 +33,74 @@ __device__ __forceinline__ double insc(const PcArgs& a, bool scaled, int f, int6
   return scaled ? a.sqd[row] * a.iwf[f] : 1.0;
 }
 
-// Thomas on T/M (or its transpose) for one particle; rhs in-place in x[0..nc).
+constexpr int kPartBlock = 128;   // nodes per block of the staged particle kernels
+
+// LU factors of T_j / M_j in precision T, radial-major ([nc][NE]): 1/pivot
+// and multiplier (unit lower L, upper U with U_{i,i+1} = -kap_j up_i).
+template <typename T>
+struct PartLU {
+  const T* ip;
+  const T* ml;
+};
+
+// In-place solve of (T_j/M_j) y = x (TRANS: its transpose) for one particle
+// with the stored factors, x[i] at x[i] (stride 1), factor entry i of node
+// e at f[i * NE + e].  Division free.
 template <typename T, bool TRANS>
-__device__ __forceinline__ void particle_thomas(const PcArgs& a, int64_t e, T* x) {
-  const int nc = a.nc;
-  const T kap = (T)a.kapj[e];
-  const T idt = (T)a.idt;
-  const double* lo = a.rref;
-  const double* di = a.rref + nc;
-  const double* up = a.rref + 2 * nc;
-  T cp[kMaxNc];
-  T dg = idt - kap * (T)di[0];
-  T u0 = TRANS ? -kap * (T)lo[1] : -kap * (T)up[0];
-  cp[0] = u0 / dg;
-  x[0] = x[0] / dg;
-  for (int i = 1; i < nc; ++i) {
-    T dii = idt - kap * (T)di[i];
-    if (i == nc - 1) dii += (T)(a.betaj[e] * a.gs[e]);
-    const T l = TRANS ? -kap * (T)up[i - 1] : -kap * (T)lo[i];
-    const T den = dii - l * cp[i - 1];
-    if (i < nc - 1) cp[i] = (TRANS ? -kap * (T)lo[i + 1] : -kap * (T)up[i]) / den;
-    x[i] = (x[i] - l * x[i - 1]) / den;
+__device__ __forceinline__ void particle_lu_solve(const PartLU<T>& F, int64_t NE, int64_t e, int nc, T kap,
+                                                  const double* __restrict__ up, T* x) {
+  const T* ip = F.ip + e;
+  const T* ml = F.ml + e;
+  if (!TRANS) {
+    T zp = x[0];
+    for (int i = 1; i < nc; ++i) {
+      zp = x[i] - ml[i * NE] * zp;
+      x[i] = zp;
+    }
+    T yn = x[nc - 1] * ip[(nc - 1) * NE];
+    x[nc - 1] = yn;
+    for (int i = nc - 2; i >= 0; --i) {
+      yn = (x[i] + kap * (T)up[i] * yn) * ip[i * NE];
+      x[i] = yn;
+    }
+  } else {
+    T zp = x[0] * ip[0];
+    x[0] = zp;
+    for (int i = 1; i < nc; ++i) {
+      zp = (x[i] + kap * (T)up[i - 1] * zp) * ip[i * NE];
+      x[i] = zp;
+    }
+    T yn = x[nc - 1];
+    for (int i = nc - 2; i >= 0; --i) {
+      yn = x[i] - ml[(i + 1) * NE] * yn;
+      x[i] = yn;
+    }
   }
-  for (int i = nc - 2; i >= 0; --i) x[i] -= cp[i] * x[i + 1];
 }
 
-// Step 1 + condensation coefficient: y_c = T^-1 (s^-1 r_c) stored in yc.
+// Step 1 + condensation coefficient: y_c = T^-1 (s^-1 r_c), written to yc
+// radial-major ([nc][NE], internal).  The block's node-major slab of r goes
+// through shared memory (rows padded to an odd stride).
 template <typename T, bool TRANS>
-__global__ void k_part_fwd(PcArgs a, const double* __restrict__ r, T* __restrict__ yc, bool scaled) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.NE) return;
-  const int nc = a.nc;
-  const int64_t nn = a.g.nn;
-  T x[kMaxNc];
-  const double iM = 1.0 / a.Mj[e];
-  for (int i = 0; i < nc; ++i) {
-    const int64_t row = 3 * nn + e * nc + i;
-    x[i] = (T)(r[row] * insc(a, scaled, 3, row) * iM);
-  }
-  particle_thomas<T, TRANS>(a, e, x);
-  for (int i = 0; i < nc; ++i) yc[e * nc + i] = x[i];
+__global__ void __launch_bounds__(kPartBlock) k_part_fwd(PcArgs a, PartLU<T> F, const double* __restrict__ r,
+                                                         T* __restrict__ yc, bool scaled) {
+  __shared__ T sl[kPartBlock * (kMaxNc + 1)];
+  const int nc = a.nc, ld = nc | 1;
+  const int64_t NE = a.NE, nn = a.g.nn;
+  const int64_t e0 = (int64_t)blockIdx.x * kPartBlock;
+  const int nb = NE - e0 < kPartBlock ? (int)(NE - e0) : kPartBlock;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < nb; q += kPartBlock / 32)
+    if (lane < nc) {
+      const int64_t row = 3 * nn + (e0 + q) * nc + lane;
+      sl[q * ld + lane] = (T)(r[row] * insc(a, scaled, 3, row) * a.iMj[e0 + q]);
+    }
+  __syncthreads();
+  if (threadIdx.x >= nb) return;
+  const int64_t e = e0 + threadIdx.x;
+  T* x = sl + threadIdx.x * ld;
+  particle_lu_solve<T, TRANS>(F, NE, e, nc, (T)a.kapj[e], a.rref + 2 * nc, x);
+  for (int i = 0; i < nc; ++i) yc[i * NE + e] = x[i];
 }
 
 // Local vectors at electrode node e: u = (A act, -A, -tau A, M beta),
@@ -101,7 +129,7 @@ __global__ void k_load(PcArgs a, const double* __restrict__ r, const T* __restri
   double yN = 0.0, coup = 0.0;
   if (e >= 0) {
     local_uv(a, e, act, u, v);
-    if (FULL) yN = (double)yc[(int64_t)e * a.nc + a.nc - 1];
+    if (FULL) yN = (double)yc[(int64_t)(a.nc - 1) * a.NE + e];
     if (done) {
       for (int g = 0; g < 3; ++g)
         if (done & (1 << g)) coup += (TRANS ? u[g] : v[g]) * zm[g * nn + n];
@@ -139,24 +167,54 @@ __global__ void k_store(Grid g, const uint8_t* __restrict__ label, int fmask, co
   }
 }
 
-// z_c = y_c - T^-1 (A_cm z_m): A_cm z_m is nonzero only in the surface row.
+// z_c = y_c - T^-1 (A_cm z_m): A_cm z_m is nonzero only in the surface row,
+// so T^-1 A_cm z_m = t w with w = T^-1 e_N / M (one backward recurrence
+// with the stored factors).  z_c (node-major) is written through shared
+// memory for coalesced stores.
 template <typename T, bool TRANS>
-__global__ void k_part_bwd(PcArgs a, const T* __restrict__ yc, const double* __restrict__ z, double* __restrict__ zc) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.NE) return;
-  const int nc = a.nc;
-  const int64_t nn = a.g.nn;
-  const int64_t n = a.enode[e];
-  const bool act = a.label[n] & kLabActive;
-  double u[4], v[4];
-  local_uv(a, e, act, u, v);
-  double t = 0.0;
-  for (int f = 0; f < 3; ++f) t += (TRANS ? u[f] * v[3] : u[3] * v[f]) * z[f * nn + n];
-  T w[kMaxNc];
-  for (int i = 0; i < nc; ++i) w[i] = (T)0;
-  w[nc - 1] = (T)(1.0 / a.Mj[e]);
-  particle_thomas<T, TRANS>(a, e, w);
-  for (int i = 0; i < nc; ++i) zc[e * nc + i] = (double)yc[e * nc + i] - t * (double)w[i];
+__global__ void __launch_bounds__(kPartBlock) k_part_bwd(PcArgs a, PartLU<T> F, const T* __restrict__ yc,
+                                                         const double* __restrict__ z, double* __restrict__ zc) {
+  __shared__ double sl[kPartBlock * (kMaxNc + 1)];
+  const int nc = a.nc, ld = nc | 1;
+  const int64_t NE = a.NE, nn = a.g.nn;
+  const int64_t e0 = (int64_t)blockIdx.x * kPartBlock;
+  const int nb = NE - e0 < kPartBlock ? (int)(NE - e0) : kPartBlock;
+  if (threadIdx.x < nb) {
+    const int64_t e = e0 + threadIdx.x;
+    const int64_t n = a.enode[e];
+    const bool act = a.label[n] & kLabActive;
+    double u[4], v[4];
+    local_uv(a, e, act, u, v);
+    double t = 0.0;
+    for (int f = 0; f < 3; ++f) t += (TRANS ? u[f] * v[3] : u[3] * v[f]) * z[f * nn + n];
+    const T kap = (T)a.kapj[e];
+    const double* up = a.rref + 2 * nc;
+    const T* ip = F.ip + e;
+    const T* ml = F.ml + e;
+    double* out = sl + threadIdx.x * ld;
+    const T iM = (T)a.iMj[e];
+    if (!TRANS) {
+      // L z' = e_N / M gives z' = e_N / M; U w = z'
+      T w = iM * ip[(nc - 1) * NE];
+      out[nc - 1] = (double)yc[(nc - 1) * NE + e] - t * (double)w;
+      for (int i = nc - 2; i >= 0; --i) {
+        w = kap * (T)up[i] * w * ip[i * NE];
+        out[i] = (double)yc[i * NE + e] - t * (double)w;
+      }
+    } else {
+      // U^T z' = e_N / M gives z' = e_N ip_N / M; L^T w = z'
+      T w = iM * ip[(nc - 1) * NE];
+      out[nc - 1] = (double)yc[(nc - 1) * NE + e] - t * (double)w;
+      for (int i = nc - 2; i >= 0; --i) {
+        w = -ml[(i + 1) * NE] * w;
+        out[i] = (double)yc[i * NE + e] - t * (double)w;
+      }
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < nb; q += kPartBlock / 32)
+    if (lane < nc) zc[(e0 + q) * nc + lane] = sl[q * ld + lane];
 }
 
 PcArgs make_pc(p4d_ctx* c) {
@@ -164,7 +222,7 @@ PcArgs make_pc(p4d_ctx* c) {
   a.g = c->g; a.NE = c->NE; a.nc = c->nc;
   a.tau = (1.0 - c->prm.tplus) / c->prm.F; a.dt = c->prm.dt; a.idt = 1.0 / c->prm.dt;
   a.label = c->label; a.eidx = c->eidx; a.enode = c->enode;
-  a.Aj = c->Aj; a.Mj = c->Mj; a.betaj = c->betaj; a.kapj = c->kapj; a.rref = c->rref;
+  a.Aj = c->Aj; a.Mj = c->Mj; a.iMj = c->iMj; a.betaj = c->betaj; a.kapj = c->kapj; a.rref = c->rref;
   a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.sqd = c->sqd; a.iwf = c->iwf;
   for (int f = 0; f < 3; ++f) a.sc[f] = c->scale_f[f];
   return a;
@@ -178,8 +236,12 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
   PcArgs a = make_pc(c);
   const int64_t nn = c->g.nn;
   T* yc = (T*)c->yc;
+  PartLU<T> F;
+  const T* fac = sizeof(T) == sizeof(double) ? (const T*)c->tfac : (const T*)c->tfac32;
+  F.ip = fac;
+  F.ml = fac + (size_t)c->NE * c->nc;
   if (FULL && c->NE > 0)
-    ::p4d::count_launch(), k_part_fwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, r, yc, scaled);
+    ::p4d::count_launch(), k_part_fwd<T, TRANS><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, F, r, yc, scaled);
   MGLevel& l0 = c->lev[0];
   T* b[3] = {(T*)l0.b[0], (T*)l0.b[2], (T*)l0.b[3]};
   if (c->prm.combine == 0) {
@@ -205,7 +267,7 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
     }
   }
   if (FULL && c->NE > 0)
-    ::p4d::count_launch(), k_part_bwd<T, TRANS><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, yc, z, z + 3 * nn);
+    ::p4d::count_launch(), k_part_bwd<T, TRANS><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, F, yc, z, z + 3 * nn);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -222,51 +284,66 @@ p4d_status apply_dispatch(p4d_ctx* c, const double* r, double* z, int transpose,
 // stored at the linearization (no divisions: FP64 divides run at 1/58 of the
 // FP32 rate on this GPU).  T/M = L U; transposed: T^T/M = U^T L^T.
 template <bool TRANS>
-__global__ void k_part64(PcArgs a, const double* __restrict__ ipiv, const double* __restrict__ mult,
-                         const double* __restrict__ rc, double* __restrict__ yc, const double* __restrict__ tN) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.NE) return;
-  const int nc = a.nc;
-  const double iM = 1.0 / a.Mj[e];
-  const double kap = a.kapj[e];
-  const double* up = a.rref + 2 * nc;
-  const double* ip = ipiv + e * nc;
-  const double* ml = mult + e * nc;
-  const double* r = rc + e * nc;
-  double* y = yc + e * nc;
-  const double tl = tN ? tN[e] : 0.0;
-  if (!TRANS) {
-    // L z = r/M (forward), U y = z (backward); z kept in y
-    double zp = r[0] * iM;
-    y[0] = zp;
-    for (int i = 1; i < nc; ++i) {
-      double ri = r[i];
-      if (i == nc - 1) ri -= tl;
-      zp = fma(-ml[i], zp, ri * iM);
-      y[i] = zp;
-    }
-    double yn = y[nc - 1] * ip[nc - 1];
-    y[nc - 1] = yn;
-    for (int i = nc - 2; i >= 0; --i) {
-      yn = (y[i] + kap * up[i] * yn) * ip[i];   // U_{i,i+1} = -kap up_i
-      y[i] = yn;
-    }
-  } else {
-    // U^T z = r/M (forward), L^T y = z (backward)
-    double zp = r[0] * iM * ip[0];
-    y[0] = zp;
-    for (int i = 1; i < nc; ++i) {
-      double ri = r[i];
-      if (i == nc - 1) ri -= tl;
-      zp = (ri * iM + kap * up[i - 1] * zp) * ip[i];
-      y[i] = zp;
-    }
-    double yn = y[nc - 1];
-    for (int i = nc - 2; i >= 0; --i) {
-      yn = fma(-ml[i + 1], yn, y[i]);
-      y[i] = yn;
+__global__ void __launch_bounds__(kPartBlock) k_part64(PcArgs a, const double* __restrict__ ipiv,
+                                                       const double* __restrict__ mult,
+                                                       const double* __restrict__ rc, double* __restrict__ yc,
+                                                       const double* __restrict__ tN) {
+  // the block's node-major slab of r (contiguous) goes through shared memory,
+  // node rows padded to an odd stride; each thread solves its node in place
+  __shared__ double sl[kPartBlock * (kMaxNc + 1)];
+  const int nc = a.nc, ld = nc | 1;
+  const int64_t NE = a.NE;
+  const int64_t e0 = (int64_t)blockIdx.x * kPartBlock;
+  const int nb = NE - e0 < kPartBlock ? (int)(NE - e0) : kPartBlock;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < nb; q += kPartBlock / 32)
+    if (lane < nc) sl[q * ld + lane] = rc[(e0 + q) * nc + lane];
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    const int64_t e = e0 + threadIdx.x;
+    double* y = sl + threadIdx.x * ld;
+    const double iM = a.iMj[e];
+    const double kap = a.kapj[e];
+    const double* up = a.rref + 2 * nc;
+    const double* ip = ipiv + e;     // ip[i * NE]
+    const double* ml = mult + e;
+    const double tl = tN ? tN[e] : 0.0;
+    if (!TRANS) {
+      // L z = r/M (forward), U y = z (backward); z kept in y
+      double zp = y[0] * iM;
+      y[0] = zp;
+      for (int i = 1; i < nc; ++i) {
+        double ri = y[i];
+        if (i == nc - 1) ri -= tl;
+        zp = fma(-ml[i * NE], zp, ri * iM);
+        y[i] = zp;
+      }
+      double yn = y[nc - 1] * ip[(nc - 1) * NE];
+      y[nc - 1] = yn;
+      for (int i = nc - 2; i >= 0; --i) {
+        yn = (y[i] + kap * up[i] * yn) * ip[i * NE];   // U_{i,i+1} = -kap up_i
+        y[i] = yn;
+      }
+    } else {
+      // U^T z = r/M (forward), L^T y = z (backward)
+      double zp = y[0] * iM * ip[0];
+      y[0] = zp;
+      for (int i = 1; i < nc; ++i) {
+        double ri = y[i];
+        if (i == nc - 1) ri -= tl;
+        zp = (ri * iM + kap * up[i - 1] * zp) * ip[i * NE];
+        y[i] = zp;
+      }
+      double yn = y[nc - 1];
+      for (int i = nc - 2; i >= 0; --i) {
+        yn = fma(-ml[(i + 1) * NE], yn, y[i]);
+        y[i] = yn;
+      }
     }
   }
+  __syncthreads();
+  for (int q = warp; q < nb; q += kPartBlock / 32)
+    if (lane < nc) yc[(e0 + q) * nc + lane] = sl[q * ld + lane];
 }
 
 }  // namespace
@@ -284,8 +361,8 @@ p4d_status particle_solve64(p4d_ctx* c, const double* rc, double* yc, const doub
   PcArgs a = make_pc(c);
   const double* ip = c->tfac;
   const double* ml = c->tfac + (size_t)c->NE * c->nc;
-  if (transpose) ::p4d::count_launch(), k_part64<true><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
-  else ::p4d::count_launch(), k_part64<false><<<nblocks(c->NE, 128), 128, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
+  if (transpose) ::p4d::count_launch(), k_part64<true><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
+  else ::p4d::count_launch(), k_part64<false><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, ip, ml, rc, yc, tN);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
