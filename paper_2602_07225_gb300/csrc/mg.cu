@@ -104,13 +104,19 @@ struct SrcOp {
 // identity_out: coarse nodes without support get an identity row (fixed part)
 // or a zero row (variable part).  TV: the precision of input, accumulation
 // and output (FP64 for the fixed part and the FP64 preconditioner).
-constexpr int kRapBlock = 64;
+//
+// One warp per coarse node, lane t < 27 owning fine support node t: each
+// lane scatters its row's products into its own column of 27 accumulators
+// in shared memory, then lane o sums slot o over the 27 columns in a fixed
+// order (deterministic, no atomics).
+constexpr int kRapWarps = 4;     // coarse nodes per block
+constexpr int kRapLd = 28;       // accumulator column stride (27 lanes, padded)
 
-// acc[oo] += a * w(g -> D) over the (up to 8) coarse parents D of fine node
-// (gi, gj, gk), oo the slot of D in the coarse row of (I, J, K).
+// acc[stride * oo] += a * w(g -> D) over the (up to 8) coarse parents D of
+// fine node (gi, gj, gk), oo the slot of D in the coarse row of (I, J, K).
 template <typename TV>
 __device__ __forceinline__ void rap_scatter(const Xfer& X, int gi, int gj, int gk, int I, int J, int K, TV a,
-                                            TV* acc) {
+                                            TV* acc, int stride) {
   const TV* pwx = parw_t<TV>(X.a[0]);
   const TV* pwy = parw_t<TV>(X.a[1]);
   const TV* pwz = parw_t<TV>(X.a[2]);
@@ -132,120 +138,118 @@ __device__ __forceinline__ void rap_scatter(const Xfer& X, int gi, int gj, int g
     const int px = X.a[0].par[gi * 2 + c1];
     if (px < 0) continue;
     const TV t = a * pwx[gi * 2 + c1];
-    for (int q = 0; q < nyz; ++q) acc[(oyz[q] + px - I + 1) * kRapBlock] += t * wyz[q];
+    for (int q = 0; q < nyz; ++q) acc[(oyz[q] + px - I + 1) * stride] += t * wyz[q];
   }
 }
 
+// Fine support node of lane t (t < 27) of coarse node (I, J, K): index f and
+// weight, or false when absent or masked out.
 template <typename TV>
-__global__ void __launch_bounds__(kRapBlock) k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const TV> fst,
-                                                   Ptr4<const TV> frs, Ptr4<const uint8_t> fm,
-                                                   Ptr4<const uint8_t> cm, Ptr4<TV> out, int identity_out) {
-  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ bool rap_support(const LevelDims& fd, const Xfer& X, const uint8_t* m, int I, int J, int K,
+                                            int t, int& fi, int& fj, int& fk, int64_t& f, TV& wf) {
+  const int tx = t % 3, ty = (t / 3) % 3, tz = t / 9;
+  fi = X.a[0].sup[I * 3 + tx];
+  fj = X.a[1].sup[J * 3 + ty];
+  fk = X.a[2].sup[K * 3 + tz];
+  if (fi < 0 || fj < 0 || fk < 0) return false;
+  f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
+  if (!m[f]) return false;
+  wf = supw_t<TV>(X.a[0])[I * 3 + tx] * (supw_t<TV>(X.a[1])[J * 3 + ty] * supw_t<TV>(X.a[2])[K * 3 + tz]);
+  return true;
+}
+
+// Slot totals of one warp's accumulator block and the row sum: lane o < 27
+// writes slot o of coarse node C.
+template <typename TV>
+__device__ __forceinline__ void rap_finish(const TV* my, TV rs_lane, bool cin, int identity_out, int lane,
+                                           TV* o_, int64_t cn, int64_t C) {
+  TV rsum = rs_lane;
+  for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+  if (lane >= 27) return;
+  TV v;
+  if (!cin) {
+    v = (lane == 13 && identity_out) ? (TV)1 : (TV)0;
+  } else if (lane == 13) {
+    v = rsum;
+  } else {
+    v = 0;
+    for (int l = 0; l < 27; ++l) v += my[lane * kRapLd + l];
+  }
+  o_[lane * cn + C] = v;
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(32 * kRapWarps) k_rap(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const TV> fst,
+                                                        Ptr4<const TV> frs, Ptr4<const uint8_t> fm,
+                                                        Ptr4<const uint8_t> cm, Ptr4<TV> out, int identity_out) {
+  __shared__ TV part[kRapWarps][27 * kRapLd];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t C = (int64_t)blockIdx.x * kRapWarps + warp;
   const int h = blockIdx.y;
-  if (C >= cd.n) return;
-  // per-thread accumulators in shared memory: the target slot is a run-time
-  // index, and a register array indexed that way would live on the stack
-  __shared__ TV sacc[27 * kRapBlock];
-  TV* acc = sacc + threadIdx.x;
-#pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = (TV)0;
-  TV rsum = 0;
+  if (C >= cd.n) return;   // per warp
+  TV* my = part[warp];
+  if (lane < 27)
+    for (int o = 0; o < 27; ++o) my[o * kRapLd + lane] = (TV)0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
+  const bool cin = pk(cm.p, h)[C];
   const TV* st = pk(fst.p, h);
   const TV* rs = pk(frs.p, h);
-  const uint8_t* m = pk(fm.p, h);
   const int64_t fn = fd.n;
-  const TV* swx = supw_t<TV>(X.a[0]);
-  const TV* swy = supw_t<TV>(X.a[1]);
-  const TV* swz = supw_t<TV>(X.a[2]);
-  if (pk(cm.p, h)[C]) {
-    for (int tz = 0; tz < 3; ++tz) {
-      const int fk = X.a[2].sup[K * 3 + tz];
-      if (fk < 0) continue;
-      for (int ty = 0; ty < 3; ++ty) {
-        const int fj = X.a[1].sup[J * 3 + ty];
-        if (fj < 0) continue;
-        const TV wyz = swy[J * 3 + ty] * swz[K * 3 + tz];
-        for (int tx = 0; tx < 3; ++tx) {
-          const int fi = X.a[0].sup[I * 3 + tx];
-          if (fi < 0) continue;
-          const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
-          if (!m[f]) continue;
-          const TV wf = swx[I * 3 + tx] * wyz;
-          const TV sf = rs ? rs[f] : st[13 * fn + f];
-          rsum += wf * sf;
-          // full-form diagonal of row f
-          TV diag = sf;
-          for (int o = 0; o < 27; ++o)
-            if (o != 13) diag -= st[o * fn + f];
-          for (int o = 0; o < 27; ++o) {
-            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-            const int gi = fi + dx, gj = fj + dy, gk = fk + dz;
-            if (gi < 0 || gj < 0 || gk < 0 || gi >= fd.nnx || gj >= fd.nny || gk >= fd.nnz) continue;
-            const int64_t gidx = gi + (int64_t)fd.nnx * (gj + (int64_t)fd.nny * gk);
-            if (!m[gidx]) continue;
-            const TV a = (o == 13 ? diag : st[o * fn + f]) * wf;
-            if (a == (TV)0) continue;
-            rap_scatter<TV>(X, gi, gj, gk, I, J, K, a, acc);
-          }
-        }
-      }
+  TV rs_l = 0;
+  int fi, fj, fk;
+  int64_t f;
+  TV wf;
+  if (cin && lane < 27 && rap_support<TV>(fd, X, pk(fm.p, h), I, J, K, lane, fi, fj, fk, f, wf)) {
+    const uint8_t* m = pk(fm.p, h);
+    const TV sf = rs ? rs[f] : st[13 * fn + f];
+    rs_l = wf * sf;
+    // full-form diagonal of row f
+    TV diag = sf;
+    for (int o = 0; o < 27; ++o)
+      if (o != 13) diag -= st[o * fn + f];
+    for (int o = 0; o < 27; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int gi = fi + dx, gj = fj + dy, gk = fk + dz;
+      if (gi < 0 || gj < 0 || gk < 0 || gi >= fd.nnx || gj >= fd.nny || gk >= fd.nnz) continue;
+      const int64_t gidx = gi + (int64_t)fd.nnx * (gj + (int64_t)fd.nny * gk);
+      if (!m[gidx]) continue;
+      const TV a = (o == 13 ? diag : st[o * fn + f]) * wf;
+      if (a == (TV)0) continue;
+      rap_scatter<TV>(X, gi, gj, gk, I, J, K, a, my + lane, kRapLd);
     }
   }
-  TV* o_ = pk(out.p, h);
-  const int64_t cn = cd.n;
-  if (!pk(cm.p, h)[C]) {
-    for (int o = 0; o < 27; ++o) o_[o * cn + C] = (TV)0;
-    o_[13 * cn + C] = identity_out ? (TV)1 : (TV)0;
-    return;
-  }
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : acc[o * kRapBlock];
+  __syncwarp();
+  rap_finish<TV>(my, rs_l, cin, identity_out, lane, pk(out.p, h), cd.n, C);
 }
 
 // V_1 = P^T diag(m s) P (level-0 variable part is diagonal), in precision TV.
 template <typename TV>
-__global__ void __launch_bounds__(kRapBlock) k_rap_diag(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
-                                                        Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm,
-                                                        Ptr4<TV> out) {
-  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kRapWarps) k_rap_diag(LevelDims fd, LevelDims cd, Xfer X,
+                                                             Ptr4<const double> s, Ptr4<const uint8_t> fm,
+                                                             Ptr4<const uint8_t> cm, Ptr4<TV> out) {
+  __shared__ TV part[kRapWarps][27 * kRapLd];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t C = (int64_t)blockIdx.x * kRapWarps + warp;
   const int h = blockIdx.y;
-  if (C >= cd.n) return;
-  __shared__ TV sacc[27 * kRapBlock];
-  TV* acc = sacc + threadIdx.x;
-#pragma unroll
-  for (int o = 0; o < 27; ++o) acc[o * kRapBlock] = (TV)0;
-  TV rsum = 0;
+  if (C >= cd.n) return;   // per warp
+  TV* my = part[warp];
+  if (lane < 27)
+    for (int o = 0; o < 27; ++o) my[o * kRapLd + lane] = (TV)0;
   int I, J, K;
   node_ijk(cd, C, I, J, K);
-  const uint8_t* m = pk(fm.p, h);
-  const double* sv = pk(s.p, h);
-  const TV* swx = supw_t<TV>(X.a[0]);
-  const TV* swy = supw_t<TV>(X.a[1]);
-  const TV* swz = supw_t<TV>(X.a[2]);
-  if (pk(cm.p, h)[C]) {
-    for (int tz = 0; tz < 3; ++tz) {
-      const int fk = X.a[2].sup[K * 3 + tz];
-      if (fk < 0) continue;
-      for (int ty = 0; ty < 3; ++ty) {
-        const int fj = X.a[1].sup[J * 3 + ty];
-        if (fj < 0) continue;
-        const TV wyz = swy[J * 3 + ty] * swz[K * 3 + tz];
-        for (int tx = 0; tx < 3; ++tx) {
-          const int fi = X.a[0].sup[I * 3 + tx];
-          if (fi < 0) continue;
-          const int64_t f = fi + (int64_t)fd.nnx * (fj + (int64_t)fd.nny * fk);
-          if (!m[f]) continue;
-          const TV a = swx[I * 3 + tx] * wyz * (TV)sv[f];
-          rsum += a;
-          rap_scatter<TV>(X, fi, fj, fk, I, J, K, a, acc);
-        }
-      }
-    }
+  const bool cin = pk(cm.p, h)[C];
+  TV rs_l = 0;
+  int fi, fj, fk;
+  int64_t f;
+  TV wf;
+  if (cin && lane < 27 && rap_support<TV>(fd, X, pk(fm.p, h), I, J, K, lane, fi, fj, fk, f, wf)) {
+    const TV a = wf * (TV)pk(s.p, h)[f];
+    rs_l = a;
+    rap_scatter<TV>(X, fi, fj, fk, I, J, K, a, my + lane, kRapLd);
   }
-  TV* o_ = pk(out.p, h);
-  const int64_t cn = cd.n;
-  for (int o = 0; o < 27; ++o) o_[o * cn + C] = (o == 13) ? rsum : (pk(cm.p, h)[C] ? acc[o * kRapBlock] : (TV)0);
+  __syncwarp();
+  rap_finish<TV>(my, rs_l, cin, 0, lane, pk(out.p, h), cd.n, C);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -405,6 +409,106 @@ __global__ void k_dense0(Grid g, const double* __restrict__ Jst, const double* _
 }
 
 // In-place Gauss-Jordan inversion with partial pivoting, one block per matrix.
+// Coarsest-level inverse, n <= kLuMax: LU with partial pivoting of each
+// hierarchy's matrix in one block (row-major, in place in lu; perm[i] = the
+// original row now at row i), then the columns of the inverse, one warp
+// each, by forward and backward substitution.  FP64 throughout.
+constexpr int kLuMax = 256;
+
+__global__ void __launch_bounds__(256) k_lu_factor(int n, const double* __restrict__ mats, double* __restrict__ lu,
+                                                   int* __restrict__ perm) {
+  const double* A0 = mats + (size_t)blockIdx.x * n * n;
+  double* A = lu + (size_t)blockIdx.x * n * n;
+  int* P = perm + (size_t)blockIdx.x * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int piv;
+  __shared__ double inv_d;
+  for (int r = warp; r < n; r += nw)
+    for (int cc = lane; cc < n; cc += 32) A[(size_t)r * n + cc] = A0[(size_t)r * n + cc];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) P[r] = r;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int idx = k;
+      for (int r = k + lane; r < n; r += 32) {
+        const double v = fabs(A[(size_t)r * n + k]);
+        if (v > best) { best = v; idx = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+      }
+      if (lane == 0) {
+        piv = idx;
+        const double d = A[(size_t)idx * n + k];
+        inv_d = d != 0.0 ? 1.0 / d : 0.0;
+      }
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k) {
+      for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
+        const double t = A[(size_t)k * n + cc];
+        A[(size_t)k * n + cc] = A[(size_t)p * n + cc];
+        A[(size_t)p * n + cc] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = P[k];
+        P[k] = P[p];
+        P[p] = t;
+      }
+    }
+    __syncthreads();
+    const double id = inv_d;
+    for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) A[(size_t)r * n + k] *= id;
+    __syncthreads();
+    for (int r = k + 1 + warp; r < n; r += nw) {
+      const double l = A[(size_t)r * n + k];
+      if (l == 0.0) continue;
+      for (int cc = k + 1 + lane; cc < n; cc += 32) A[(size_t)r * n + cc] -= l * A[(size_t)k * n + cc];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(128) k_lu_inverse(int n, const double* __restrict__ lu, const int* __restrict__ perm,
+                                                    double* __restrict__ inv) {
+  __shared__ double xs[4][kLuMax];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 4 + warp;
+  if (j >= n) return;   // per warp
+  const double* A = lu + (size_t)blockIdx.y * n * n;
+  const int* P = perm + (size_t)blockIdx.y * n;
+  double* x = xs[warp];
+  // x = P e_j, then L y = x (unit lower), then U x = y
+  for (int i = lane; i < n; i += 32) x[i] = P[i] == j ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k = 0; k < n - 1; ++k) {
+    const double xk = x[k];
+    __syncwarp();
+    if (xk != 0.0)
+      for (int i = k + 1 + lane; i < n; i += 32) x[i] -= A[(size_t)i * n + k] * xk;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double xk = 0.0;
+    if (lane == 0) {
+      const double d = A[(size_t)k * n + k];
+      xk = d != 0.0 ? x[k] / d : 0.0;
+      x[k] = xk;
+    }
+    xk = __shfl_sync(0xffffffffu, xk, 0);
+    __syncwarp();
+    if (xk != 0.0)
+      for (int i = lane; i < k; i += 32) x[i] -= A[(size_t)i * n + k] * xk;
+    __syncwarp();
+  }
+  double* Inv = inv + (size_t)blockIdx.y * n * n;
+  for (int i = lane; i < n; i += 32) Inv[(size_t)i * n + j] = x[i];
+}
+
 __global__ void k_gauss_jordan(int n, double* mats, double* work) {
   double* A = mats + (size_t)blockIdx.x * n * n;
   double* Inv = work + (size_t)blockIdx.x * n * n;
@@ -912,7 +1016,10 @@ p4d_status mg_plan(p4d_ctx* c) {
       for (int h = 0; h < kNH; ++h) { fm.p[h] = fl.mask[h]; cm.p[h] = lv.mask[h]; }
       ::p4d::count_launch(), k_mask_coarse<<<dim3(nblocks(n), kNH), kBlock, 0, c->stream>>>(dims(fl), dims(lv), fl.X, fm, cm);
     }
-    if (l == L - 1) P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
+    if (l == L - 1) {
+      P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
+      P4D_TRYS(dalloc_t(c, &lv.perm, (size_t)kNH * n));
+    }
   }
   // level-0 particle work and variable row sums
   P4D_TRYS(dalloc(c, &c->yc, (prec == 0 ? sizeof(double) : sizeof(float)) * (size_t)std::max<int64_t>(1, c->NE) * c->nc));
@@ -964,7 +1071,21 @@ p4d_status mg_setup_fixed(p4d_ctx* c) {
       cm.p[h] = B.mask[h];
       out.p[h] = B.Ffix + (size_t)h * 27 * B.n;
     }
-    ::p4d::count_launch(), k_rap<double><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
+    ::p4d::count_launch(), k_rap<double><<<dim3(nblocks(B.n, kRapWarps), kNH), 32 * kRapWarps, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 1);
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+// Inverse of the coarsest dense matrices in mats (overwritten with it);
+// work: scratch of the same size.
+p4d_status coarse_inverse(p4d_ctx* c, MGLevel& C, double* mats, double* work) {
+  const int n = (int)C.n;
+  if (n <= kLuMax) {
+    ::p4d::count_launch(), k_lu_factor<<<kNH, 256, 0, c->stream>>>(n, mats, work, C.perm);
+    ::p4d::count_launch(), k_lu_inverse<<<dim3((n + 3) / 4, kNH), 128, 0, c->stream>>>(n, work, C.perm, mats);
+  } else {
+    ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>(n, mats, work);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -987,11 +1108,11 @@ p4d_status mg_update_levels(p4d_ctx* c, const double* svar, const double* sch) {
     if (l == 1) {
       Ptr4<const double> s;
       for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      ::p4d::count_launch(), k_rap_diag<TV><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
+      ::p4d::count_launch(), k_rap_diag<TV><<<dim3(nblocks(B.n, kRapWarps), kNH), 32 * kRapWarps, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
     } else {
       Ptr4<const TV> fst, frs;
       for (int h = 0; h < kNH; ++h) { fst.p[h] = (const TV*)A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
-      ::p4d::count_launch(), k_rap<TV><<<dim3(nblocks(B.n, kRapBlock), kNH), kRapBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
+      ::p4d::count_launch(), k_rap<TV><<<dim3(nblocks(B.n, kRapWarps), kNH), 32 * kRapWarps, 0, c->stream>>>(dims(A), dims(B), A.X, fst, frs, fm, cm, out, 0);
     }
     Ptr4<const double> F;
     Ptr4<const TV> V;
@@ -1035,7 +1156,7 @@ p4d_status mg_update_levels(p4d_ctx* c, const double* svar, const double* sch) {
     }
     ::p4d::count_launch(), k_dense<TV><<<dim3(nblocks(C.n), kNH), kBlock, 0, c->stream>>>(dims(C), F, V, sch[0], sch[1], sch[2], sch[3], mats);
   }
-  ::p4d::count_launch(), k_gauss_jordan<<<kNH, 256, 0, c->stream>>>((int)C.n, mats, work);
+  P4D_TRYS(coarse_inverse(c, C, mats, work));
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }

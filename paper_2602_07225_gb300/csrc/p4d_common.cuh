@@ -114,8 +114,9 @@ struct MGLevel {
   void* r[kNH] = {};
   void* d[kNH] = {};
   double* lam = nullptr;               // [kNH] Gershgorin bound of D^-1 A
-  // coarsest level only: dense inverse [kNH][n][n] FP64
+  // coarsest level only: dense inverse [kNH][n][n] FP64 (+ scratch), LU row permutation
   double* inv = nullptr;
+  int* perm = nullptr;
 };
 
 }  // namespace p4d
