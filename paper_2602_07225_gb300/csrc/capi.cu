@@ -18,7 +18,13 @@ using namespace p4d;
 namespace p4d {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long* t_capture = nullptr;
+void count_launch() {
+  if (t_capture) ++*t_capture;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void capture_counter(long long* counter) { t_capture = counter; }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 p4d_status dalloc(p4d_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
@@ -266,6 +272,11 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->unorm2, 4));
   P4D_TRYS(dalloc_t(c, &c->ujvp, nn));
   P4D_TRY(cudaMallocHost(&c->lam_pin, sizeof(double) * kMaxLevels * kNH));
+  P4D_TRY(cudaMallocHost(&c->cheb_pin, sizeof(double) * kMaxLevels * kMaxDeg * 3 * kNH));
+  P4D_TRYS(dalloc_t(c, &c->cheb_dev, (size_t)kMaxLevels * kMaxDeg * 3 * kNH));
+  P4D_TRYS(dalloc_t(c, &c->kdev, 1));
+  P4D_TRY(cudaMemset(c->kdev, 0, sizeof(int)));
+  P4D_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   P4D_TRYS(dalloc_t(c, &c->wf, 4));
   P4D_TRYS(dalloc_t(c, &c->flags, 1));
   P4D_TRY(cudaMallocHost(&c->flags_h, sizeof(unsigned)));
@@ -298,6 +309,9 @@ void free_ctx(p4d_ctx* c) {
   cudaDeviceSynchronize();
   for (int k = 0; k < 4; ++k)
     for (cudaEvent_t e : c->prof.ev[k]) cudaEventDestroy(e);
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->cheb_pin) cudaFreeHost(c->cheb_pin);
   for (void* p : c->allocs) cudaFree(p);
   if (c->flags_h) cudaFreeHost(c->flags_h);
   if (c->lam_pin) cudaFreeHost(c->lam_pin);
@@ -380,9 +394,10 @@ p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
       p->sigma_n != o.sigma_n || p->sigma_p != o.sigma_p)
     return P4D_ERR_INVALID_ARG;
   if (p->mode == 0 && h->kry_len < h->ndof) return P4D_ERR_INVALID_ARG;
-  const bool relin = p->cheb_ratio != h->prm.cheb_ratio;
+  const bool recoef = p->cheb_ratio != h->prm.cheb_ratio || p->cheb_degree != h->prm.cheb_degree;
   h->prm = *p;
-  (void)relin;
+  drop_graphs(h);
+  if (recoef && h->linearized) return cheb_upload(h);
   return P4D_OK;
 }
 

@@ -267,8 +267,9 @@ HLay hlay(int m) {
 //   misc+2m+4              : status (0 ok, 1 breakdown, 2 nonfinite)
 //   misc+2m+5              : beta (initial residual norm)
 
-__global__ void k_init_cycle(double* hs, HLay L, int64_t unused) {
+__global__ void k_init_cycle(double* hs, HLay L, int* kdev) {
   if (threadIdx.x != 0) return;
+  *kdev = 0;   // Krylov column of the next preconditioner application
   const double* nrm2 = hs + L.misc + 2 * L.m + 2;
   const double beta = sqrt(*nrm2);
   for (int i = 0; i <= L.m; ++i) hs[L.g + i] = 0.0;
@@ -278,8 +279,9 @@ __global__ void k_init_cycle(double* hs, HLay L, int64_t unused) {
 }
 
 // Column k: h = h1 + h2, h_{k+1,k} = ||w||, previous rotations, new rotation.
-__global__ void k_givens(double* hs, HLay L, int k) {
+__global__ void k_givens(double* hs, HLay L, int k, int* kdev) {
   if (threadIdx.x != 0) return;
+  *kdev = k + 1;
   const int m = L.m;
   double* H = hs + L.H;
   double* cs = hs + L.cs;
@@ -504,7 +506,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
     else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
     R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
-    ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, 0);
+    ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, c->kdev);
     ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(c->V, c->V, len, misc + 2 * L.m + 5, 1);
     P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     P4D_TRY(cudaStreamSynchronize(c->stream));
@@ -514,12 +516,10 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     if (beta <= c->prm.rtol * bnorm) { st = P4D_OK; break; }
     int kk = 0;
     for (int k = 0; k < m && iters < c->prm.maxit; ++k) {
-      double* vk = c->V + (int64_t)k * len;
       double* zk = c->Z + (int64_t)k * len;
       double* w = c->V + (int64_t)(k + 1) * len;
       prof_mark(c, 0);
-      if (full) P4D_TRYS(precond_full(c, vk, zk, trans, true));
-      else P4D_TRYS(precond_macro(c, vk, zk, trans, true));
+      P4D_TRYS(precond_column(c, trans));   // z_k = P^-1 (s^-1 v_k), k read from c->kdev
       prof_mark(c, 0);
       prof_mark(c, 1);
       if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
@@ -534,7 +534,7 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
       R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
       // ||w||^2 after the second pass (left unchanged when it is skipped)
       R.maxpy(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag, misc + 2 * L.m + 2, gb);
-      ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k);
+      ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k, c->kdev);
       // v_{k+1} = w / h_{k+1,k}
       ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
       prof_mark(c, 2);

@@ -631,12 +631,13 @@ __device__ __forceinline__ void stencil_rows(const TS* __restrict__ st, const T*
   }
 }
 
-// Chebyshev coefficients of one step for up to four hierarchies (computed on
-// the host from the Gershgorin bounds): step 0: d = c0 z; later steps:
-// d = ca d + cb z, with z = D^-1 (b - A x).
-struct ChebCoef {
-  double c0[kNH], ca[kNH], cb[kNH];
-};
+// Chebyshev coefficients, on the device (so that captured graphs stay valid
+// across linearizations): for level l, step s and hierarchy h,
+// tab[((l kMaxDeg + s) 3 + j) kNH + h], j = 0: c0, 1: ca, 2: cb.  Step 0:
+// d = c0 z; later steps: d = ca d + cb z, with z = D^-1 (b - A x).
+__device__ __forceinline__ double cheb_at(const double* tab, int level, int step, int j, int h) {
+  return tab[((level * kMaxDeg + step) * 3 + j) * kNH + h];
+}
 
 // Rows of this thread: n[q] = block base + q blockDim + tid, active where in
 // range and inside the hierarchy's mask.
@@ -652,8 +653,8 @@ __device__ __forceinline__ void stencil_nodes(int N, const uint8_t* __restrict__
 
 // One Chebyshev step, x_out = x + d.
 template <typename TS, typename T>
-__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, ChebCoef cc, int step,
-                                              int first) {
+__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const double* __restrict__ ctab,
+                                              int level, int step, int first) {
   const int hi = blockIdx.y;
   const int h = pk(hl.h, hi);
   int n[kNpt];
@@ -666,7 +667,8 @@ __global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HL
   const T* __restrict__ x = pk(P.x, h);
   T* __restrict__ d = pk(P.d, h);
   T* __restrict__ xo = pk(P.xo, h);
-  const T c0 = (T)pk(cc.c0, hi), ca = (T)pk(cc.ca, hi), cb = (T)pk(cc.cb, hi);
+  const T c0 = (T)cheb_at(ctab, level, step, 0, h), ca = (T)cheb_at(ctab, level, step, 1, h),
+          cb = (T)cheb_at(ctab, level, step, 2, h);
 #pragma unroll
   for (int q = 0; q < kNpt; ++q) {
     if (!on[q]) continue;
@@ -816,25 +818,6 @@ void swap_x(MGLevel& L, const int* hs, int nhs) {
   }
 }
 
-ChebCoef cheb_coef(const p4d_ctx* c, int level, const int* hs, int nhs, int step) {
-  ChebCoef cc{};
-  const double ratio = c->prm.cheb_ratio;
-  for (int t = 0; t < nhs && t < kNH; ++t) {
-    const double lm = c->lam_h[level][hs[t]] > 0 ? c->lam_h[level][hs[t]] : 1.0;
-    const double alpha = lm / ratio, beta = lm;
-    const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
-    const double sigma = theta / delta;
-    double rho = 1.0 / sigma, rho_new = rho;
-    for (int s = 1; s <= step; ++s) {
-      rho = rho_new;
-      rho_new = 1.0 / (2.0 * sigma - rho);
-    }
-    cc.c0[t] = 1.0 / theta;
-    cc.ca[t] = rho_new * rho;
-    cc.cb[t] = 2.0 * rho_new / delta;
-  }
-  return cc;
-}
 
 template <typename TS0, typename TS, typename T>
 p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
@@ -846,10 +829,9 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     MGLevel& B = c->lev[l + 1];
     const dim3 grid(stencil_blocks(A.n), nhs);
     for (int s = 0; s < deg; ++s) {
-      const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
       if (l == 0 && s > 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, s == 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, s == 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, c->cheb_dev, l, s, s == 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, c->cheb_dev, l, s, s == 0);
       if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
@@ -879,10 +861,9 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     const dim3 grid(stencil_blocks(A.n), nhs);
     ::p4d::count_launch(), k_prolong<T><<<dim3(nblocks(A.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
-      const ChebCoef cc = cheb_coef(c, l, hs, nhs, s);
       if (l == 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cc, s, 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cc, s, 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, c->cheb_dev, l, s, 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, c->cheb_dev, l, s, 0);
       if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
@@ -1193,6 +1174,35 @@ p4d_status mg_fetch_lam(p4d_ctx* c) {
   P4D_TRY(cudaStreamSynchronize(c->stream));
   for (int l = 0; l < c->nlev; ++l)
     for (int h = 0; h < kNH; ++h) c->lam_h[l][h] = c->lam_pin[l * kNH + h];
+  return cheb_upload(c);
+}
+
+// Chebyshev(degree d) coefficients on [lam/ratio, lam] of D^-1 A for every
+// level, step and hierarchy (three-term recurrence of the shifted Chebyshev
+// polynomials), copied to the device table.
+p4d_status cheb_upload(p4d_ctx* c) {
+  const double ratio = c->prm.cheb_ratio;
+  double* t = c->cheb_pin;
+  P4D_TRY(cudaStreamSynchronize(c->stream));   // the previous copy from t has completed
+  for (int l = 0; l < c->nlev; ++l)
+    for (int h = 0; h < kNH; ++h) {
+      const double lm = c->lam_h[l][h] > 0 ? c->lam_h[l][h] : 1.0;
+      const double alpha = lm / ratio, beta = lm;
+      const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+      const double sigma = theta / delta;
+      double rho = 1.0 / sigma, rho_new = rho;
+      for (int st = 0; st < c->prm.cheb_degree && st < kMaxDeg; ++st) {
+        if (st > 0) {
+          rho = rho_new;
+          rho_new = 1.0 / (2.0 * sigma - rho);
+        }
+        t[((l * kMaxDeg + st) * 3 + 0) * kNH + h] = 1.0 / theta;
+        t[((l * kMaxDeg + st) * 3 + 1) * kNH + h] = rho_new * rho;
+        t[((l * kMaxDeg + st) * 3 + 2) * kNH + h] = 2.0 * rho_new / delta;
+      }
+    }
+  P4D_TRY(cudaMemcpyAsync(c->cheb_dev, t, sizeof(double) * kMaxLevels * kMaxDeg * 3 * kNH, cudaMemcpyHostToDevice,
+                          c->stream));
   return P4D_OK;
 }
 

@@ -34,6 +34,7 @@
 namespace p4d {
 
 constexpr int kMaxNc = 32;
+constexpr int kMaxDeg = 16;        // Chebyshev degree limit
 constexpr int kMaxLevels = 16;
 constexpr int kNH = 4;            // multigrid hierarchies: phi_s anode, phi_s cathode, phi_e, c_e
 constexpr int kBlock = 256;
@@ -214,6 +215,18 @@ struct p4d_ctx {
     std::vector<cudaEvent_t> ev[4];    // 0 precond, 1 jvp, 2 ortho, 3 level-0 stencil smoothing
     size_t used[4] = {0, 0, 0, 0};
   } prof;
+
+  // CUDA graphs of the preconditioner applied to Krylov column k (k read on
+  // the device from kdev), [transpose][full layout]; captured on cap_stream
+  // at first use and dropped whenever the options change.
+  struct PcGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;             // kernel nodes (added to the launch counter per launch)
+  } pcg[2][2];
+  cudaStream_t cap_stream = nullptr;
+  int* kdev = nullptr;                 // current Krylov column (device)
+  double* cheb_dev = nullptr;          // Chebyshev coefficients [kMaxLevels][kMaxDeg][3][kNH]
+  double* cheb_pin = nullptr;          // pinned staging of cheb_dev
 };
 
 // ---------------------------------------------------------------- helpers
@@ -230,6 +243,18 @@ inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 
 // Process-wide count of kernel launches issued by the library (every launch
 // site is written "count_launch(), kernel<<<...>>>(...)").
 void count_launch();
+// While a thread captures a graph its launches are counted into *counter
+// (the graph's kernel nodes) instead of the global launch counter.
+void capture_counter(long long* counter);
+void count_launches(long long n);
+
+// A device vector chosen at run time: base + stride * (*k) (k == NULL: base).
+struct VRef {
+  double* base;
+  int64_t stride;
+  const int* k;
+  __device__ __forceinline__ double* get() const { return k ? base + stride * (int64_t)(*k) : base; }
+};
 
 // ---- assembly / linearization (assemble.cu)
 p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, const uint8_t* region);
@@ -248,6 +273,11 @@ p4d_status jvp_reduced(p4d_ctx* c, const double* x, double* y, int transpose, co
 p4d_status particle_solve64(p4d_ctx* c, const double* rc, double* yc, const double* tN, int transpose);
 p4d_status precond_full(p4d_ctx* c, const double* r, double* z, int transpose, bool scaled);
 p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose, bool scaled);
+// Preconditioner applied to Krylov column *kdev of V into column *kdev of Z
+// (scaled space), through a CUDA graph unless profiling.
+p4d_status precond_column(p4d_ctx* c, int transpose);
+void drop_graphs(p4d_ctx* c);
+p4d_status cheb_upload(p4d_ctx* c);
 
 // ---- multigrid (mg.cu)
 p4d_status mg_plan(p4d_ctx* c);

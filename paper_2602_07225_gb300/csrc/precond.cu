@@ -82,9 +82,10 @@ __device__ __forceinline__ void particle_lu_solve(const PartLU<T>& F, int64_t NE
 // radial-major ([nc][NE], internal).  The block's node-major slab of r goes
 // through shared memory (rows padded to an odd stride).
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(kPartBlock) k_part_fwd(PcArgs a, PartLU<T> F, const double* __restrict__ r,
-                                                         T* __restrict__ yc, bool scaled) {
+__global__ void __launch_bounds__(kPartBlock) k_part_fwd(PcArgs a, PartLU<T> F, VRef rref_, T* __restrict__ yc,
+                                                         bool scaled) {
   __shared__ T sl[kPartBlock * (kMaxNc + 1)];
+  const double* __restrict__ r = rref_.get();
   const int nc = a.nc, ld = nc | 1;
   const int64_t NE = a.NE, nn = a.g.nn;
   const int64_t e0 = (int64_t)blockIdx.x * kPartBlock;
@@ -117,9 +118,11 @@ __device__ __forceinline__ void local_uv(const PcArgs& a, int64_t e, bool act, d
 // in `done` (bits, their z already written to zm).  phi_s rows without an
 // unknown are identity rows: z = r directly.
 template <typename T, bool TRANS, bool FULL>
-__global__ void k_load(PcArgs a, const double* __restrict__ r, const T* __restrict__ yc,
-                       const double* __restrict__ zm, double* __restrict__ zout, int fmask, int done, bool scaled,
+__global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref_, int fmask, int done, bool scaled,
                        T* b0, T* b1, T* b2) {
+  const double* __restrict__ r = rref_.get();
+  const double* zm = zref_.get();
+  double* zout = zref_.get();
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = a.g.nn;
   if (n >= nn) return;
@@ -155,7 +158,8 @@ __global__ void k_load(PcArgs a, const double* __restrict__ r, const T* __restri
 
 template <typename T>
 __global__ void k_store(Grid g, const uint8_t* __restrict__ label, int fmask, const T* __restrict__ x0,
-                        const T* __restrict__ x1, const T* __restrict__ x2, double* __restrict__ zm) {
+                        const T* __restrict__ x1, const T* __restrict__ x2, VRef zref_) {
+  double* __restrict__ zm = zref_.get();
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
   if (n >= nn) return;
@@ -173,8 +177,10 @@ __global__ void k_store(Grid g, const uint8_t* __restrict__ label, int fmask, co
 // memory for coalesced stores.
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(kPartBlock) k_part_bwd(PcArgs a, PartLU<T> F, const T* __restrict__ yc,
-                                                         const double* __restrict__ z, double* __restrict__ zc) {
+                                                         VRef zref_) {
   __shared__ double sl[kPartBlock * (kMaxNc + 1)];
+  const double* __restrict__ z = zref_.get();
+  double* __restrict__ zc = zref_.get() + 3 * a.g.nn;
   const int nc = a.nc, ld = nc | 1;
   const int64_t NE = a.NE, nn = a.g.nn;
   const int64_t e0 = (int64_t)blockIdx.x * kPartBlock;
@@ -232,7 +238,7 @@ PcArgs make_pc(p4d_ctx* c) {
 const int kHOfField[3][2] = {{0, 1}, {2, -1}, {3, -1}};
 
 template <typename T, bool TRANS, bool FULL>
-p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
+p4d_status apply_t(p4d_ctx* c, VRef r, VRef z, bool scaled) {
   PcArgs a = make_pc(c);
   const int64_t nn = c->g.nn;
   T* yc = (T*)c->yc;
@@ -245,7 +251,7 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
   MGLevel& l0 = c->lev[0];
   T* b[3] = {(T*)l0.b[0], (T*)l0.b[2], (T*)l0.b[3]};
   if (c->prm.combine == 0) {
-    ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 7, 0, scaled, b[0], b[1], b[2]);
+    ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 7, 0, scaled, b[0], b[1], b[2]);
     const int hs[4] = {0, 1, 2, 3};
     P4D_TRYS(mg_vcycle(c, hs, 4));
     ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 7, (const T*)l0.x[0], (const T*)l0.x[2],
@@ -254,7 +260,7 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
     int done = 0;
     for (int t = 0; t < 3; ++t) {
       const int f = TRANS ? c->prm.order[2 - t] : c->prm.order[t];
-      ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, z, 1 << f, done, scaled, b[0], b[1],
+      ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 1 << f, done, scaled, b[0], b[1],
                                                                    b[2]);
       int hs[2];
       int nh = 0;
@@ -267,13 +273,13 @@ p4d_status apply_t(p4d_ctx* c, const double* r, double* z, bool scaled) {
     }
   }
   if (FULL && c->NE > 0)
-    ::p4d::count_launch(), k_part_bwd<T, TRANS><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, F, yc, z, z + 3 * nn);
+    ::p4d::count_launch(), k_part_bwd<T, TRANS><<<nblocks(c->NE, kPartBlock), kPartBlock, 0, c->stream>>>(a, F, yc, z);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
 
 template <bool FULL>
-p4d_status apply_dispatch(p4d_ctx* c, const double* r, double* z, int transpose, bool scaled) {
+p4d_status apply_dispatch(p4d_ctx* c, VRef r, VRef z, int transpose, bool scaled) {
   if (c->prm.precision == 0)
     return transpose ? apply_t<double, true, FULL>(c, r, z, scaled) : apply_t<double, false, FULL>(c, r, z, scaled);
   return transpose ? apply_t<float, true, FULL>(c, r, z, scaled) : apply_t<float, false, FULL>(c, r, z, scaled);
@@ -349,11 +355,63 @@ __global__ void __launch_bounds__(kPartBlock) k_part64(PcArgs a, const double* _
 }  // namespace
 
 p4d_status precond_full(p4d_ctx* c, const double* r, double* z, int transpose, bool scaled) {
-  return apply_dispatch<true>(c, r, z, transpose, scaled);
+  return apply_dispatch<true>(c, VRef{const_cast<double*>(r), 0, nullptr}, VRef{z, 0, nullptr}, transpose, scaled);
 }
 
 p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose, bool scaled) {
-  return apply_dispatch<false>(c, rm, zm, transpose, scaled);
+  return apply_dispatch<false>(c, VRef{const_cast<double*>(rm), 0, nullptr}, VRef{zm, 0, nullptr}, transpose, scaled);
+}
+
+void drop_graphs(p4d_ctx* c) {
+  for (auto& row : c->pcg)
+    for (auto& g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      g.kernels = 0;
+    }
+}
+
+// The preconditioner of FGMRES iteration k: z_k = P^-1 (s^-1 v_k).  Every
+// kernel of one application reads k from c->kdev, so one captured graph per
+// (transpose, layout) serves every column; the Chebyshev coefficients are
+// read from the device table, so the graph survives linearization updates.
+// The multigrid ping-pong buffers return to their start after each V-cycle
+// (2 d swaps per level), so the captured pointers stay those in use.
+p4d_status precond_column(p4d_ctx* c, int transpose) {
+  const bool full = c->prm.mode == 0;
+  const int64_t len = full ? c->ndof : 3 * c->g.nn;
+  const VRef r{c->V, len, c->kdev}, z{c->Z, len, c->kdev};
+  auto apply = [&]() {
+    return full ? apply_dispatch<true>(c, r, z, transpose, true) : apply_dispatch<false>(c, r, z, transpose, true);
+  };
+  if (c->prm.profile) return apply();   // per-kernel events cannot sit inside a graph
+  p4d_ctx::PcGraph& g = c->pcg[transpose ? 1 : 0][full ? 1 : 0];
+  if (!g.exec) {
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    long long kernels = 0;
+    capture_counter(&kernels);
+    cudaGraph_t graph = nullptr;
+    p4d_status st = P4D_OK;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = P4D_ERR_CUDA;
+    if (st == P4D_OK) {
+      st = apply();
+      if (cudaStreamEndCapture(c->cap_stream, &graph) != cudaSuccess && st == P4D_OK) st = P4D_ERR_CUDA;
+    }
+    capture_counter(nullptr);
+    c->stream = user;
+    if (st == P4D_OK && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) st = P4D_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (st != P4D_OK) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      return st;
+    }
+    g.kernels = kernels;
+  }
+  count_launches(g.kernels);
+  P4D_TRY(cudaGraphLaunch(g.exec, c->stream));
+  return P4D_OK;
 }
 
 p4d_status particle_solve64(p4d_ctx* c, const double* rc, double* yc, const double* tN, int transpose) {
