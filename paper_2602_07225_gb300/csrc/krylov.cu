@@ -442,6 +442,19 @@ struct Reducer {
   }
 };
 
+// Runs Arnoldi step k of FGMRES through its captured graph (captured on
+// first use, per transpose and layout; dropped when the options change).
+template <typename F>
+p4d_status launch_step_graph(p4d_ctx* c, int trans, int k, F&& body) {
+  auto& vec = c->itg[trans ? 1 : 0][c->prm.mode == 0 ? 1 : 0];
+  if ((int)vec.size() <= k) vec.resize(k + 1);
+  p4d_ctx::PcGraph& g = vec[k];
+  if (!g.exec) P4D_TRYS(capture_graph(c, g, body));
+  count_launches(g.kernels);
+  P4D_TRY(cudaGraphLaunch(g.exec, c->stream));
+  return P4D_OK;
+}
+
 }  // namespace
 
 p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
@@ -516,29 +529,35 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
     if (beta <= c->prm.rtol * bnorm) { st = P4D_OK; break; }
     int kk = 0;
     for (int k = 0; k < m && iters < c->prm.maxit; ++k) {
-      double* zk = c->Z + (int64_t)k * len;
-      double* w = c->V + (int64_t)(k + 1) * len;
-      prof_mark(c, 0);
-      P4D_TRYS(precond_column(c, trans));   // z_k = P^-1 (s^-1 v_k), k read from c->kdev
-      prof_mark(c, 0);
-      prof_mark(c, 1);
-      if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
-      else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
-      prof_mark(c, 1);
-      prof_mark(c, 2);
-      // classical Gram-Schmidt, second pass only when needed
-      const double* flag = misc + 2 * L.m + 6;
-      R.mdot(c->V, len, k + 1, w, len, true, misc);                          // h1, ||w||^2 before
-      R.maxpy(c->V, len, k + 1, misc, w, len, 1.0, nullptr, misc + 2 * L.m + 2, gb);   // ||w||^2 after
-      ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(hs, L, k);
-      R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
-      // ||w||^2 after the second pass (left unchanged when it is skipped)
-      R.maxpy(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag, misc + 2 * L.m + 2, gb);
-      ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k, c->kdev);
-      // v_{k+1} = w / h_{k+1,k}
-      ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
-      prof_mark(c, 2);
-      P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      // one Arnoldi step: z_k = P^-1 (s^-1 v_k), w = s.J z_k, CGS (second
+      // pass only when needed), Givens, v_{k+1} = w / h_{k+1,k}, and the
+      // residual estimate and status copied to the host
+      auto step = [&](bool graph_precond) -> p4d_status {
+        double* zk = c->Z + (int64_t)k * len;
+        double* w = c->V + (int64_t)(k + 1) * len;
+        prof_mark(c, 0);
+        P4D_TRYS(precond_column(c, trans, graph_precond));   // k read from c->kdev
+        prof_mark(c, 0);
+        prof_mark(c, 1);
+        if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
+        else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
+        prof_mark(c, 1);
+        prof_mark(c, 2);
+        const double* flag = misc + 2 * L.m + 6;
+        R.mdot(c->V, len, k + 1, w, len, true, misc);                          // h1, ||w||^2 before
+        R.maxpy(c->V, len, k + 1, misc, w, len, 1.0, nullptr, misc + 2 * L.m + 2, gb);   // ||w||^2 after
+        ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(hs, L, k);
+        R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
+        // ||w||^2 after the second pass (left unchanged when it is skipped)
+        R.maxpy(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag, misc + 2 * L.m + 2, gb);
+        ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k, c->kdev);
+        ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
+        prof_mark(c, 2);
+        P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        return P4D_OK;
+      };
+      if (c->prm.profile) P4D_TRYS(step(true));
+      else P4D_TRYS(launch_step_graph(c, trans, k, [&]() { return step(false); }));
       P4D_TRY(cudaStreamSynchronize(c->stream));
       ++iters;
       kk = k + 1;

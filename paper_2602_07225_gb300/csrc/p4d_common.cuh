@@ -223,6 +223,7 @@ struct p4d_ctx {
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;             // kernel nodes (added to the launch counter per launch)
   } pcg[2][2];
+  std::vector<PcGraph> itg[2][2];      // Arnoldi step k of FGMRES, [transpose][full][k]
   cudaStream_t cap_stream = nullptr;
   int* kdev = nullptr;                 // current Krylov column (device)
   double* cheb_dev = nullptr;          // Chebyshev coefficients [kMaxLevels][kMaxDeg][3][kNH]
@@ -275,7 +276,35 @@ p4d_status precond_full(p4d_ctx* c, const double* r, double* z, int transpose, b
 p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose, bool scaled);
 // Preconditioner applied to Krylov column *kdev of V into column *kdev of Z
 // (scaled space), through a CUDA graph unless profiling.
-p4d_status precond_column(p4d_ctx* c, int transpose);
+p4d_status precond_column(p4d_ctx* c, int transpose, bool use_graph);
+
+// Captures what body() launches on c->stream into g (on c->cap_stream,
+// thread-local capture mode; launches are counted as g's kernel nodes).
+template <typename F>
+p4d_status capture_graph(p4d_ctx* c, p4d_ctx::PcGraph& g, F&& body) {
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  long long kernels = 0;
+  capture_counter(&kernels);
+  cudaGraph_t graph = nullptr;
+  p4d_status st = P4D_OK;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = P4D_ERR_CUDA;
+  if (st == P4D_OK) {
+    st = body();
+    if (cudaStreamEndCapture(c->cap_stream, &graph) != cudaSuccess && st == P4D_OK) st = P4D_ERR_CUDA;
+  }
+  capture_counter(nullptr);
+  c->stream = user;
+  if (st == P4D_OK && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) st = P4D_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    g.exec = nullptr;
+    return st;
+  }
+  g.kernels = kernels;
+  return P4D_OK;
+}
 void drop_graphs(p4d_ctx* c);
 p4d_status cheb_upload(p4d_ctx* c);
 

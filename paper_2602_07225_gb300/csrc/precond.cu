@@ -363,11 +363,17 @@ p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose
 }
 
 void drop_graphs(p4d_ctx* c) {
+  auto drop = [](p4d_ctx::PcGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.kernels = 0;
+  };
   for (auto& row : c->pcg)
-    for (auto& g : row) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      g.exec = nullptr;
-      g.kernels = 0;
+    for (auto& g : row) drop(g);
+  for (auto& row : c->itg)
+    for (auto& v : row) {
+      for (auto& g : v) drop(g);
+      v.clear();
     }
 }
 
@@ -377,38 +383,16 @@ void drop_graphs(p4d_ctx* c) {
 // read from the device table, so the graph survives linearization updates.
 // The multigrid ping-pong buffers return to their start after each V-cycle
 // (2 d swaps per level), so the captured pointers stay those in use.
-p4d_status precond_column(p4d_ctx* c, int transpose) {
+p4d_status precond_column(p4d_ctx* c, int transpose, bool use_graph) {
   const bool full = c->prm.mode == 0;
   const int64_t len = full ? c->ndof : 3 * c->g.nn;
   const VRef r{c->V, len, c->kdev}, z{c->Z, len, c->kdev};
   auto apply = [&]() {
     return full ? apply_dispatch<true>(c, r, z, transpose, true) : apply_dispatch<false>(c, r, z, transpose, true);
   };
-  if (c->prm.profile) return apply();   // per-kernel events cannot sit inside a graph
+  if (c->prm.profile || !use_graph) return apply();   // per-kernel events cannot sit inside a graph
   p4d_ctx::PcGraph& g = c->pcg[transpose ? 1 : 0][full ? 1 : 0];
-  if (!g.exec) {
-    cudaStream_t user = c->stream;
-    c->stream = c->cap_stream;
-    long long kernels = 0;
-    capture_counter(&kernels);
-    cudaGraph_t graph = nullptr;
-    p4d_status st = P4D_OK;
-    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = P4D_ERR_CUDA;
-    if (st == P4D_OK) {
-      st = apply();
-      if (cudaStreamEndCapture(c->cap_stream, &graph) != cudaSuccess && st == P4D_OK) st = P4D_ERR_CUDA;
-    }
-    capture_counter(nullptr);
-    c->stream = user;
-    if (st == P4D_OK && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) st = P4D_ERR_CUDA;
-    if (graph) cudaGraphDestroy(graph);
-    if (st != P4D_OK) {
-      cudaGetLastError();
-      g.exec = nullptr;
-      return st;
-    }
-    g.kernels = kernels;
-  }
+  if (!g.exec) P4D_TRYS(capture_graph(c, g, apply));
   count_launches(g.kernels);
   P4D_TRY(cudaGraphLaunch(g.exec, c->stream));
   return P4D_OK;

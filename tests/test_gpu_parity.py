@@ -195,3 +195,24 @@ def test_set_params_refuses_assembled_physics():
             s.set_options(**{name: val})
         setattr(s.params, name, old)
     s.set_options(cheb_degree=3)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_graph_and_direct_paths_agree(mode, adjoint):
+    """The captured CUDA graphs (preconditioner, Arnoldi steps) launch the same
+    kernels in the same order as the direct path taken when profiling: the
+    solutions are bit-identical, also after an option change drops the
+    graphs and they are captured again."""
+    case, d, ref, s, st = _setup("cube8", precision=1, mode=mode, rtol=1e-10, maxit=400)
+    s.jacobian_update(st)
+    b = -s.residual(st)
+    for deg in (3, 2):
+        s.set_options(cheb_degree=deg, profile=0)
+        x_graph, i1 = s.solve(b, adjoint=adjoint)
+        x_graph2, _ = s.solve(b, adjoint=adjoint)
+        s.set_options(profile=1)
+        x_direct, i2 = s.solve(b, adjoint=adjoint)
+        assert i1["iters"] == i2["iters"]
+        assert torch.equal(x_graph, x_direct)
+        assert torch.equal(x_graph, x_graph2)
