@@ -27,6 +27,10 @@ METRIC = "Newton linear solves/s & FGMRES iters/s to 1e-8 rel. residual; mixed v
 WORKLOAD = "cube128"
 # unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
 # the 82 electrode node layers (41 anode + 41 cathode)
+# DRAM bytes per algorithmic byte of the level-0 Chebyshev step, from the ncu
+# capture in profiles/k_cheb_level0_cube96.md (257,057,792 / 259,039,179)
+TRAFFIC_PER_ALG_BYTE = 257057792 / 259039179
+FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (3, 20.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms
 WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40)",
                  "cube96": "cube96 (profiling case): Q1 hex 96x96x72 (anode/sep/cathode 30/12/30)"}
@@ -248,10 +252,18 @@ def roofline_smooth(s, st, case, step):
     n_act = s.NE - (int(m["nx"]) + 1) * (int(m["ny"]) + 1)   # grounded z = 0 face is anode (cube)
     bytes_ = 133 * (n_act + 2 * s.nn)
     ms = info["ms_smooth0"] / max(1, info["n_smooth0"])
+    # reduced FP64 JVP of the same solve (k_jvp_combine + k_jvp_macro): FP64
+    # FMAs per launch = 27 per active phi_s node (K_sigma) + 2 x 27 per node
+    # (K_kappa, C) + 1 per node (u = x_phie + gamma/c_e x_ce) + 10 per
+    # electrode node (Schur coupling)
+    fma = 27 * n_act + 55 * s.nn + 10 * s.NE
+    jvp_ms = info["ms_jvp"] / max(1, info["n_jvp"])
     return {"kernel": "k_cheb level 0 (FP32 27-point stencil smoothing, 4 hierarchies)", "ms": ms,
             "bytes": bytes_, "gbs": bytes_ / (ms * 1e-3) / 1e9, "launches": info["n_smooth0"],
             "phases_ms": {"precond": info["ms_precond"], "jvp": info["ms_jvp"], "ortho": info["ms_ortho"],
-                          "total": info["ms_total"]}}
+                          "total": info["ms_total"]},
+            "jvp": {"ms": jvp_ms, "flops": 2 * fma, "tflops": 2 * fma / (jvp_ms * 1e-3) / 1e12,
+                    "launches": info["n_jvp"]}}
 
 
 def roofline_jvp(s, st, dev):
@@ -418,10 +430,19 @@ def main():
                 "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["roof"]["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": r["roof"]["gbs"] / peak, "traffic": None, "kernel": r["roof"]["kernel"],
-                     "peak_source": src, "ms_per_launch": r["roof"]["ms"], "bytes_per_launch": r["roof"]["bytes"]},
+                     "frac": r["roof"]["gbs"] / peak,
+                     "traffic": TRAFFIC_PER_ALG_BYTE * r["roof"]["bytes"] if args.workload in ("cube128", "cube96")
+                     else None,
+                     "traffic_source": "ncu dram__bytes_read+write of the level-0 k_cheb on cube96 "
+                                       "(0.992 x algorithmic), scaled by rows processed",
+                     "kernel": r["roof"]["kernel"], "peak_source": src, "ms_per_launch": r["roof"]["ms"],
+                     "bytes_per_launch": r["roof"]["bytes"]},
         "solve_phases_ms": r["roof"]["phases_ms"],
-        "roofline_fp64_jvp": {"bound": "fp64 alu", "achieved_gbs": r["roof_jvp"]["gbs"],
+        "roofline_fp64": {"kernel": "k_jvp_combine + k_jvp_macro (reduced FP64 JVP inside FGMRES)", "bound": "alu",
+                          "achieved": r["roof"]["jvp"]["tflops"], "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                          "frac": r["roof"]["jvp"]["tflops"] / FP64_TFLOPS, "ms_per_launch": r["roof"]["jvp"]["ms"],
+                          "peak_source": "GB300 nominal FP64 (non-tensor) 1.25 TFLOP/s; an FMA loop measured 1.20"},
+        "roofline_fp64_jvp_full": {"bound": "fp64 alu", "achieved_gbs": r["roof_jvp"]["gbs"],
                               "hbm_frac": r["roof_jvp"]["gbs"] / peak, "ms_per_launch": r["roof_jvp"]["ms"],
                               "note": "FP64 FMA rate 1.20 TFLOP/s measured (58x below FP32)"},
         "cpu_baseline": cpu,

@@ -272,8 +272,9 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(dalloc_t(c, &c->unorm2, 4));
   P4D_TRYS(dalloc_t(c, &c->ujvp, nn));
   P4D_TRY(cudaMallocHost(&c->lam_pin, sizeof(double) * kMaxLevels * kNH));
-  P4D_TRY(cudaMallocHost(&c->cheb_pin, sizeof(double) * kMaxLevels * kMaxDeg * 3 * kNH));
+  P4D_TRY(cudaMallocHost(&c->cheb_pin, 2 * sizeof(double) * kMaxLevels * kMaxDeg * 3 * kNH));
   P4D_TRYS(dalloc_t(c, &c->cheb_dev, (size_t)kMaxLevels * kMaxDeg * 3 * kNH));
+  P4D_TRYS(dalloc_t(c, &c->cheb_dev32, (size_t)kMaxLevels * kMaxDeg * 3 * kNH));
   P4D_TRYS(dalloc_t(c, &c->kdev, 1));
   P4D_TRY(cudaMemset(c->kdev, 0, sizeof(int)));
   P4D_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));

@@ -635,7 +635,8 @@ __device__ __forceinline__ void stencil_rows(const TS* __restrict__ st, const T*
 // across linearizations): for level l, step s and hierarchy h,
 // tab[((l kMaxDeg + s) 3 + j) kNH + h], j = 0: c0, 1: ca, 2: cb.  Step 0:
 // d = c0 z; later steps: d = ca d + cb z, with z = D^-1 (b - A x).
-__device__ __forceinline__ double cheb_at(const double* tab, int level, int step, int j, int h) {
+template <typename T>
+__device__ __forceinline__ T cheb_at(const T* tab, int level, int step, int j, int h) {
   return tab[((level * kMaxDeg + step) * 3 + j) * kNH + h];
 }
 
@@ -653,7 +654,7 @@ __device__ __forceinline__ void stencil_nodes(int N, const uint8_t* __restrict__
 
 // One Chebyshev step, x_out = x + d.
 template <typename TS, typename T>
-__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const double* __restrict__ ctab,
+__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const T* __restrict__ ctab,
                                               int level, int step, int first) {
   const int hi = blockIdx.y;
   const int h = pk(hl.h, hi);
@@ -667,8 +668,8 @@ __global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HL
   const T* __restrict__ x = pk(P.x, h);
   T* __restrict__ d = pk(P.d, h);
   T* __restrict__ xo = pk(P.xo, h);
-  const T c0 = (T)cheb_at(ctab, level, step, 0, h), ca = (T)cheb_at(ctab, level, step, 1, h),
-          cb = (T)cheb_at(ctab, level, step, 2, h);
+  const T c0 = cheb_at(ctab, level, step, 0, h), ca = cheb_at(ctab, level, step, 1, h),
+          cb = cheb_at(ctab, level, step, 2, h);
 #pragma unroll
   for (int q = 0; q < kNpt; ++q) {
     if (!on[q]) continue;
@@ -819,6 +820,11 @@ void swap_x(MGLevel& L, const int* hs, int nhs) {
 }
 
 
+// The Chebyshev coefficient table in the smoother's precision.
+template <typename T> const T* cheb_tab(const p4d_ctx* c);
+template <> const double* cheb_tab<double>(const p4d_ctx* c) { return c->cheb_dev; }
+template <> const float* cheb_tab<float>(const p4d_ctx* c) { return c->cheb_dev32; }
+
 template <typename TS0, typename TS, typename T>
 p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   const int L = c->nlev;
@@ -830,8 +836,8 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     const dim3 grid(stencil_blocks(A.n), nhs);
     for (int s = 0; s < deg; ++s) {
       if (l == 0 && s > 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, c->cheb_dev, l, s, s == 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, c->cheb_dev, l, s, s == 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cheb_tab<T>(c), l, s, s == 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cheb_tab<T>(c), l, s, s == 0);
       if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
@@ -862,8 +868,8 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     ::p4d::count_launch(), k_prolong<T><<<dim3(nblocks(A.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
       if (l == 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, c->cheb_dev, l, s, 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, c->cheb_dev, l, s, 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cheb_tab<T>(c), l, s, 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cheb_tab<T>(c), l, s, 0);
       if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
@@ -1201,8 +1207,11 @@ p4d_status cheb_upload(p4d_ctx* c) {
         t[((l * kMaxDeg + st) * 3 + 2) * kNH + h] = 2.0 * rho_new / delta;
       }
     }
-  P4D_TRY(cudaMemcpyAsync(c->cheb_dev, t, sizeof(double) * kMaxLevels * kMaxDeg * 3 * kNH, cudaMemcpyHostToDevice,
-                          c->stream));
+  const size_t ne = (size_t)kMaxLevels * kMaxDeg * 3 * kNH;
+  float* t32 = reinterpret_cast<float*>(t + ne);   // FP32 copy for the FP32 smoothers
+  for (size_t q = 0; q < ne; ++q) t32[q] = (float)t[q];
+  P4D_TRY(cudaMemcpyAsync(c->cheb_dev, t, sizeof(double) * ne, cudaMemcpyHostToDevice, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->cheb_dev32, t32, sizeof(float) * ne, cudaMemcpyHostToDevice, c->stream));
   return P4D_OK;
 }
 

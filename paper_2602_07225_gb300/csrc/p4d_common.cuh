@@ -227,7 +227,8 @@ struct p4d_ctx {
   cudaStream_t cap_stream = nullptr;
   int* kdev = nullptr;                 // current Krylov column (device)
   double* cheb_dev = nullptr;          // Chebyshev coefficients [kMaxLevels][kMaxDeg][3][kNH]
-  double* cheb_pin = nullptr;          // pinned staging of cheb_dev
+  float* cheb_dev32 = nullptr;         // the same in FP32
+  double* cheb_pin = nullptr;          // pinned staging of cheb_dev and cheb_dev32
 };
 
 // ---------------------------------------------------------------- helpers
