@@ -89,6 +89,11 @@ typedef struct {
   const double* Ds_e;              /* optional [nelem] solid diffusivity per element; when given, the
                                       particle of an electrode node uses the volume-weighted mean over
                                       its electrode elements and Ds is ignored */
+  double shell_sigma_t_p;          /* current-collector foil on the z = Lz face as a thin shell: surface
+                                      conductance sigma_foil * thickness (S), 0 = none.  Adds the 2D Q1
+                                      stiffness of the face to the phi_s rows between active nodes (a
+                                      stand-in for the collector layers of the paper's jelly roll, section 5) */
+  double shell_sigma_t_n;          /* the same on the z = 0 face (anode foil) */
 } p4d_mesh;
 
 /* Physics and solver options. */

@@ -32,7 +32,15 @@ the design notes of the repository):
   carry identity rows, and their phi_s values are lifted to zero wherever
   another row reads them;
 * a = 3 eps_s / R_s (matches the tables: 1.5e5 = 3*0.5/1e-5,
-  1.8e5 = 3*0.6/1e-5).
+  1.8e5 = 3*0.6/1e-5);
+* current collectors (optional, the jelly-roll slab): a thin conducting
+  foil on the z = Lz face (cathode) and on the z = 0 face (anode), each a
+  surface conductance sigma_t = sigma_foil * thickness (S) entering the
+  phi_s rows as the 2D Q1 stiffness of the face (bilinear quads, 2x2 Gauss,
+  exact), only between active phi_s nodes like the bulk term; the applied
+  current enters through the faces flagged in gamma_p and the grounded
+  (Dirichlet) nodes are those of the faces flagged in gamma_n (tab strips).
+  The paper meshes its collectors as layers; the shell replaces them.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -195,6 +203,14 @@ class Disc:
         self.act = np.zeros(self.nn, bool)
         self.act[self.enodes] = True
         self.act[self.dirichlet] = False
+        # thin collector shells on the z = Lz (cathode) and z = 0 (anode) faces
+        self.shell = []
+        for key, kk in (("shell_sigma_t_p", nz), ("shell_sigma_t_n", 0)):
+            st_ = float(mesh.get(key, 0.0) or 0.0)
+            if st_ > 0.0:
+                fconn = np.stack([(fi + (l & 1)) + self.nnx * ((fj + ((l >> 1) & 1)) + self.nny * kk)
+                                  for l in range(4)], axis=1)
+                self.shell.append((st_, fconn, hx[fi], hy[fj]))
         self.nc = int(mesh["nc"])
         self.r = self.Rs[:, None] * np.asarray(mesh["rgrid"], float)[None, :]
         self.lo, self.di, self.up, self.beta = radial_operator(self.r, self.Ds, p["F"])
@@ -230,6 +246,17 @@ class Disc:
         for d in range(3):
             out += (self.vol / self.h[:, d] ** 2)[:, None] * (ue @ KREF[d])
         return out
+
+    @staticmethod
+    def _shell_ke(sig_t, a, b):
+        """2D Q1 stiffness of one face quad a x b times sig_t, local nodes
+        l = x + 2 y: sig_t [(b/a) K1 (x) M1 + (a/b) M1 (x) K1] with
+        K1 = [[1,-1],[-1,1]], M1 = [[1/3,1/6],[1/6,1/3]]."""
+        K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+        M1 = np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
+        kx = np.kron(M1, K1)   # x fastest: index l = x + 2 y -> kron(Y, X)
+        ky = np.kron(K1, M1)
+        return sig_t * ((b / a)[:, None, None] * kx[None] + (a / b)[:, None, None] * ky[None])
 
     def _scatter(self, vals):
         return np.bincount(self.conn.ravel(), weights=vals.ravel(), minlength=self.nn)
@@ -271,6 +298,10 @@ class Disc:
             raise DomainError("c_e <= 0")
         # electronic charge (eq. phis-weak)
         R_s = self._scatter(self.sig[:, None] * self._lap(phis_l[self.conn]))
+        for sig_t, fconn, a, b in self.shell:
+            Ke = self._shell_ke(sig_t, a, b)
+            R_s += np.bincount(fconn.ravel(), weights=np.einsum("fij,fj->fi", Ke, phis_l[fconn]).ravel(),
+                               minlength=self.nn)
         # ionic charge (eq. phie-weak); diffusion potential through the Q1
         # interpolant of ln c_e
         R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn])
@@ -321,6 +352,12 @@ class Disc:
         # phi_s - phi_s (active rows and columns only)
         keep = self.el[:, None, None] & self.act[R8] & self.act[C8]
         add(R8[keep], C8[keep], (self.sig[:, None, None] * Ke)[keep])
+        for sig_t, fconn, a, b in self.shell:
+            Kf = self._shell_ke(sig_t, a, b)
+            R4 = np.broadcast_to(fconn[:, :, None], Kf.shape)
+            C4 = np.broadcast_to(fconn[:, None, :], Kf.shape)
+            kf = self.act[R4] & self.act[C4]
+            add(R4[kf], C4[kf], Kf[kf])
         # phi_e - phi_e
         add(nn + R8, nn + C8, self.kap[:, None, None] * Ke)
         # phi_e - c_e: derivative of the diffusion-potential term, K_kappa diag(gamma / c_e)

@@ -16,7 +16,6 @@ PARAMS_DEFAULT = dict(
     ocp_n=(0.229016, -0.067279), ocp_p=(4.948384, -1.535617),
     dt=10.0, i_app=-40.2022,
     diffpot_sign=1.0,
-    shell_sigma_t_p=0.0, shell_sigma_t_n=0.0,
 )
 
 CASES = ("tiny", "cube8", "cube128", "hetero128")
@@ -104,8 +103,9 @@ def make_box_case(nx, ny, nz_layers, L_lat, L_layers, nc, seed, *, params=None,
     n_an, n_sep, n_ca = nz_layers
     L_an, L_sep, L_ca = L_layers
     nz = n_an + n_sep + n_ca
-    hx = np.full(nx, L_lat / nx)
-    hy = np.full(ny, L_lat / ny)
+    Lx, Ly = (L_lat, L_lat) if np.isscalar(L_lat) else L_lat
+    hx = np.full(nx, Lx / nx)
+    hy = np.full(ny, Ly / ny)
     hz, reg_z = _layers(n_an, n_sep, n_ca, L_an, L_sep, L_ca)
     nelem = nx * ny * nz
     region = np.repeat(reg_z, nx * ny).astype(np.uint8)
@@ -123,7 +123,7 @@ def make_box_case(nx, ny, nz_layers, L_lat, L_layers, nc, seed, *, params=None,
     gamma_p = np.ones(nx * ny, np.uint8)
     gamma_n = np.ones(nx * ny, np.uint8)
     if "i_app" not in (params or {}):
-        p["i_app"] = theoretical_iapp(L_lat, L_lat, L_an, L_ca, eps_s[0], eps_s[1],
+        p["i_app"] = theoretical_iapp(Lx, Ly, L_an, L_ca, eps_s[0], eps_s[1],
                                       p["cmax_n"], p["cmax_p"], p["F"])
     an, ca = _node_types(nx, ny, nz, region)
     (c0n, c1n), (c0p, c1p) = p["ocp_n"], p["ocp_p"]
@@ -193,6 +193,28 @@ def _hetero_fields(nx, ny, nz, hx, hy, hz, region, rng, corr=8, mean=0.3, cv=0.2
     eps_b = np.where(region == 0, 0.1, np.where(region == 2, 0.2, 0.0))
     eps_s = np.where((region == 0) | (region == 2), 1.0 - eps - eps_b, 0.0)
     return eps, eps_s
+
+
+def make_slab_case(nx=2048, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=64, crate=2.0,
+                   h_lat=100e-6 / 128, L_layers=(100e-6, 25e-6, 100e-6), shell=(565.0, 596.0),
+                   state="initial"):
+    """Flattened jelly-roll-like slab: nx x ny elements of h_lat x h_lat
+    laterally, anode/separator/cathode layers in z.  Both current-collector
+    foils are thin shells over the whole z = Lz (cathode, aluminium
+    3.77e7 S/m x 15 um = 565 S) and z = 0 (anode, copper 5.96e7 S/m x 10 um =
+    596 S) faces; the tabs are the strips of the first `tab` element columns
+    along x: gamma_p (applied current) and gamma_n (grounded) flag only
+    them.  i_app is the C-rate current of the whole slab (theoretical
+    capacity) spread over the tab area."""
+    case = make_box_case(nx, ny, layers, (nx * h_lat, ny * h_lat), L_layers, nc, seed, state=state)
+    m, p = case["mesh"], case["params"]
+    col = np.arange(nx * ny) % nx
+    m["gamma_p"] = (col < tab).astype(np.uint8)
+    m["gamma_n"] = (col < tab).astype(np.uint8)
+    m["shell_sigma_t_p"], m["shell_sigma_t_n"] = float(shell[0]), float(shell[1])
+    p["i_app"] = crate * theoretical_iapp(nx * h_lat, ny * h_lat, L_layers[0], L_layers[2], 0.6, 0.5,
+                                          p["cmax_n"], p["cmax_p"], p["F"]) * nx / tab
+    return case
 
 
 def make_tiny_case(nx=2, ny=2, layers=(2, 1, 2), nc=4, seed=7, **kw):

@@ -30,7 +30,8 @@ class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("hx", _dp), ("hy", _dp), ("hz", _dp), ("region", _u8p), ("eps", _dp), ("eps_s", _dp),
                 ("Rs", _dp), ("Ds", _dp), ("gamma_p", _u8p), ("gamma_n", _u8p), ("rgrid", _dp),
-                ("nc", C.c_int32), ("sigma_e", _dp), ("Ds_e", _dp)]
+                ("nc", C.c_int32), ("sigma_e", _dp), ("Ds_e", _dp), ("shell_sigma_t_p", C.c_double),
+                ("shell_sigma_t_n", C.c_double)]
 
 
 class Params(C.Structure):

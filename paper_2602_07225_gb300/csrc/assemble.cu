@@ -19,6 +19,7 @@ namespace {
 
 struct Phys {
   double brug, sigma_n, sigma_p, kappa, De, dt;
+  double shell_p, shell_n;   // collector-foil surface conductances of the z = Lz / z = 0 faces (S)
 };
 
 __global__ void k_assemble(Grid g, int nx, int ny, int nz, const double* __restrict__ hx,
@@ -73,6 +74,30 @@ __global__ void k_assemble(Grid g, int nx, int ny, int nz, const double* __restr
               mlump += mcoef * mf;
             }
       }
+  // collector foil of a boundary face as a thin shell: the 2D Q1 stiffness of
+  // the face quads a x b around the node, sig_t [(b/a) k_x m_y + (a/b) m_x k_y]
+  // (k = +1 same / -1 other node along the axis, m = 1/3 same / 1/6 other)
+  const double sht = k == nz ? ph.shell_p : (k == 0 ? ph.shell_n : 0.0);
+  if (sht > 0.0 && act) {
+    for (int q = 0; q < 2; ++q)
+      for (int p = 0; p < 2; ++p) {
+        const int ei = i - 1 + p, ej = j - 1 + q;
+        if (ei < 0 || ej < 0 || ei >= nx || ej >= ny) continue;
+        const double a = hx[ei], b = hy[ej];
+        const int an = 1 - p, bn = 1 - q;
+        for (int bb = 0; bb < 2; ++bb)
+          for (int aa = 0; aa < 2; ++aa) {
+            const int dx = p - 1 + aa, dy = q - 1 + bb;
+            const int o = (dx + 1) + 3 * (dy + 1) + 9;
+            const double kx = aa == an ? 1.0 : -1.0, mx = aa == an ? 1.0 / 3.0 : 1.0 / 6.0;
+            const double ky = bb == bn ? 1.0 : -1.0, my = bb == bn ? 1.0 / 3.0 : 1.0 / 6.0;
+            const double v = sht * (b / a * kx * my + a / b * mx * ky);
+            const int64_t nb = n + dx + (int64_t)g.nnx * dy;
+            if (label[nb] & kLabActive) Ks[o] += v;
+            else sdrop -= v;
+          }
+      }
+  }
   const int64_t nn = g.nn;
 #pragma unroll
   for (int o = 0; o < 27; ++o) {
@@ -406,7 +431,7 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   const int64_t nn = c->g.nn;
   P4D_TRYS(dalloc_t(c, &c->Jst, (size_t)4 * 27 * nn));
   P4D_TRYS(dalloc_t(c, &c->sfix, (size_t)3 * nn));
-  Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt};
+  Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt, c->shell_p, c->shell_n};
   ::p4d::count_launch(), k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
                                                        eps, eps_s, c->sig_e, c->label, ph, c->Jst, c->sfix);
   P4D_TRY(cudaGetLastError());

@@ -141,6 +141,11 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   c->nelem = nelem;
   c->nc = nc;
   c->prm = *prm;
+  if (!(m->shell_sigma_t_p >= 0.0) || !(m->shell_sigma_t_n >= 0.0) || !std::isfinite(m->shell_sigma_t_p) ||
+      !std::isfinite(m->shell_sigma_t_n))
+    return P4D_ERR_INVALID_ARG;
+  c->shell_p = m->shell_sigma_t_p;
+  c->shell_n = m->shell_sigma_t_n;
 
   // ---- node classification (host)
   std::vector<uint8_t> lab(nn, 0);

@@ -133,6 +133,7 @@ struct p4d_ctx {
   bool linearized = false;
   std::vector<int32_t> enodes_h;
   double scale_f[3] = {1, 1, 1};       // multigrid per-field scaling (FP32 range)
+  double shell_p = 0.0, shell_n = 0.0; // collector-foil surface conductances on z = Lz / z = 0 (S)
 
   // owned allocations (freed in destroy)
   std::vector<void*> allocs;

@@ -68,7 +68,9 @@ class P4DSolver:
                       Rs=dp(m["Rs"]), Ds=dp(m["Ds"]), gamma_p=up(m["gamma_p"]), gamma_n=up(m["gamma_n"]),
                       rgrid=dp(m["rgrid"]), nc=int(m["nc"]),
                       sigma_e=dp(m["sigma_e"]) if m.get("sigma_e") is not None else None,
-                      Ds_e=dp(m["Ds_e"]) if m.get("Ds_e") is not None else None)
+                      Ds_e=dp(m["Ds_e"]) if m.get("Ds_e") is not None else None,
+                      shell_sigma_t_p=float(m.get("shell_sigma_t_p", 0.0) or 0.0),
+                      shell_sigma_t_n=float(m.get("shell_sigma_t_n", 0.0) or 0.0))
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()

@@ -30,10 +30,24 @@ def _disc(case):
     return d, d.state_from_case(case["state"])
 
 
-@pytest.mark.parametrize("name", ["tiny", "tiny_void"])
+def _tiny_tab_shell(nc=4):
+    """4x2 lateral tiny box with tab strips (first element column) on both
+    faces and collector shells on both."""
+    case = make_case("tiny", nx=4, ny=2, nc=nc)
+    m = case["mesh"]
+    col = np.arange(4 * 2) % 4
+    m["gamma_p"] = (col < 1).astype(np.uint8)
+    m["gamma_n"] = (col < 1).astype(np.uint8)
+    m["shell_sigma_t_p"], m["shell_sigma_t_n"] = 3.0, 5.0
+    return case
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_void", "tiny_tab_shell"])
 def test_jacobian_matches_central_differences(name):
     if name == "tiny":
         case = make_case("tiny")
+    elif name == "tiny_tab_shell":
+        case = _tiny_tab_shell()
     else:
         case = make_case("tiny", nc=3)
         # make one electrolyte-only element inside the cathode layer and vary eps
@@ -106,6 +120,54 @@ def test_charge_balance_and_lithium_conservation():
     assert lith[1] == pytest.approx(-I / p["F"] * dt, rel=1e-8)
     assert lith[0] == pytest.approx(I / p["F"] * dt, rel=1e-8)
     assert I < 0 and lith[1] > 0          # discharge: lithium enters the cathode
+
+
+def test_collector_shell_energy_and_patch():
+    """The shell adds sig_t times the 2D Q1 face stiffness to the phi_s rows:
+    for phi = x (resp. y) over the all-active z = Lz face, phi^T dJ phi equals
+    sig_t |grad phi|^2 times the face area (exact for bilinear elements), and
+    a linear phi leaves the rows of interior face nodes at zero (patch test);
+    on non-square faces a swapped b/a <-> a/b fails both."""
+    base = make_box_case(5, 3, (2, 1, 2), (50e-6, 18e-6), (20e-6, 10e-6, 20e-6), 3, 4, state="initial")
+    d0, st = _disc(base)
+    m = dict(base["mesh"])
+    m["shell_sigma_t_p"] = 7.0
+    d1 = Disc(m, base["params"])
+    dJ = (d1.jacobian(st) - d0.jacobian(st)).tocsr()[:d0.nn, :d0.nn]
+    hx, hy = np.asarray(m["hx"]), np.asarray(m["hy"])
+    X = np.concatenate([[0.0], np.cumsum(hx)])
+    Y = np.concatenate([[0.0], np.cumsum(hy)])
+    kk, jj, ii = np.indices((d0.nnz, d0.nny, d0.nnx))
+    top = kk.ravel() == d0.nz
+    Lx, Ly = X[-1], Y[-1]
+    for coord, grad2 in ((X[ii.ravel()], 1.0), (Y[jj.ravel()], 1.0)):
+        phi = np.where(top, coord, 0.0)
+        assert phi @ (dJ @ phi) == pytest.approx(7.0 * grad2 * Lx * Ly, rel=1e-12)
+        r = dJ @ phi
+        inner = top & (ii.ravel() > 0) & (ii.ravel() < d0.nx) & (jj.ravel() > 0) & (jj.ravel() < d0.ny)
+        assert np.max(np.abs(r[inner])) <= 1e-12 * np.max(np.abs(r))
+    assert abs(dJ[~top][:, ~top]).sum() == 0.0      # only face rows and columns change
+
+
+def test_tab_charge_balance():
+    """With the applied current and the ground on tab strips and the current
+    spread by collector shells, a converged step still balances charge: the
+    cathode reaction current equals i_app times the tab area."""
+    from p4d_inputs import make_slab_case
+    case = make_slab_case(nx=8, ny=2, layers=(3, 2, 3), nc=5, tab=2, crate=1.0, h_lat=8e-6,
+                          L_layers=(30e-6, 15e-6, 30e-6))
+    d, st = _disc(case)
+    st1, hist = time_step(d, st, rtol=1e-13)
+    phis_l = np.where(d.act, st1["phis"], 0.0)
+    i_n, *_ = d.kinetics(phis_l, st1["phie"], st1["ce"], st1["cs"][:, -1])
+    tab_area = 2 * 2 * 8e-6 * 8e-6
+    assert d.gpw.sum() == pytest.approx(tab_area, rel=1e-14)
+    I = case["params"]["i_app"] * tab_area
+    ca = d.etype == 1
+    assert np.sum(d.A[ca] * i_n[ca]) == pytest.approx(I, rel=1e-9)
+    assert np.sum(d.A[~ca] * i_n[~ca]) == pytest.approx(-I, rel=1e-9)
+    # the grounded nodes are exactly the tab's bottom nodes
+    assert d.dirichlet.sum() == 3 * 3
 
 
 def _p2d_residual(z_h, region, p, nc, R, D, u, prev, eps_e=0.3, eps_s=(0.6, 0.5)):
