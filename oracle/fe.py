@@ -297,10 +297,17 @@ class Disc:
         if np.any(ce <= 0):
             raise DomainError("c_e <= 0")
         # electronic charge (eq. phis-weak)
-        R_s = self._scatter(self.sig[:, None] * self._lap(phis_l[self.conn]))
+        # element matrices have zero row sums, so each element (and face) acts
+        # on its values shifted by their mean: the same sums without the
+        # rounding of large products of nearly equal potentials (collector
+        # shells carry conductances ~1e7 times the bulk ones)
+        pe = phis_l[self.conn]
+        R_s = self._scatter(self.sig[:, None] * self._lap(pe - pe.mean(axis=1, keepdims=True)))
         for sig_t, fconn, a, b in self.shell:
             Ke = self._shell_ke(sig_t, a, b)
-            R_s += np.bincount(fconn.ravel(), weights=np.einsum("fij,fj->fi", Ke, phis_l[fconn]).ravel(),
+            pf = phis_l[fconn]
+            R_s += np.bincount(fconn.ravel(),
+                               weights=np.einsum("fij,fj->fi", Ke, pf - pf.mean(axis=1, keepdims=True)).ravel(),
                                minlength=self.nn)
         # ionic charge (eq. phie-weak); diffusion potential through the Q1
         # interpolant of ln c_e

@@ -196,16 +196,18 @@ def _hetero_fields(nx, ny, nz, hx, hy, hz, region, rng, corr=8, mean=0.3, cv=0.2
 
 
 def make_slab_case(nx=2048, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=64, crate=2.0,
-                   h_lat=100e-6 / 128, L_layers=(100e-6, 25e-6, 100e-6), shell=(565.0, 596.0),
+                   h_lat=100e-6 / 128, L_layers=(100e-6, 25e-6, 100e-6), shell=(0.0, 0.0),
                    state="initial"):
     """Flattened jelly-roll-like slab: nx x ny elements of h_lat x h_lat
-    laterally, anode/separator/cathode layers in z.  Both current-collector
-    foils are thin shells over the whole z = Lz (cathode, aluminium
-    3.77e7 S/m x 15 um = 565 S) and z = 0 (anode, copper 5.96e7 S/m x 10 um =
-    596 S) faces; the tabs are the strips of the first `tab` element columns
-    along x: gamma_p (applied current) and gamma_n (grounded) flag only
-    them.  i_app is the C-rate current of the whole slab (theoretical
-    capacity) spread over the tab area."""
+    laterally, anode/separator/cathode layers in z.  The tabs are the
+    strips of the first `tab` element columns along x: gamma_p (applied
+    current, z = Lz) and gamma_n (grounded, z = 0) flag only them, so the
+    current runs along the electrodes to the tabs.  i_app is the C-rate
+    current of the whole slab (theoretical capacity) spread over the tab
+    area.  shell = (cathode, anode) collector-foil surface conductances in S
+    (0: none); real foils (aluminium 3.77e7 S/m x 15 um = 565 S, copper
+    5.96e7 S/m x 10 um = 596 S) are ~1e8 times the bulk conductance of a
+    sub-micron element."""
     case = make_box_case(nx, ny, layers, (nx * h_lat, ny * h_lat), L_layers, nc, seed, state=state)
     m, p = case["mesh"], case["params"]
     col = np.arange(nx * ny) % nx

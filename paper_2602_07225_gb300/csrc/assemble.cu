@@ -338,7 +338,7 @@ __global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
                                  const double* __restrict__ phis, const double* __restrict__ phie,
                                  const double* __restrict__ ce, const double* __restrict__ ce_prev,
                                  const double* __restrict__ lnce, const double* __restrict__ rin,
-                                 double* __restrict__ r) {
+                                 const double* __restrict__ sfix, double* __restrict__ r) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
   if (n >= nn) return;
@@ -348,11 +348,25 @@ __global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
   const int32_t e = eidx[n];
   const double ain = e >= 0 ? Aj[e] * rin[e] : 0.0;
   const bool act = label[n] & kLabActive;
-  // phi_s: lifted stencil (entries to inactive nodes are zero)
+  // phi_s: lifted stencil (entries to inactive nodes are zero) in difference
+  // form, sum_{m != n} K_nm (phi_m - phi_n) + s_n phi_n with s_n the row sum
+  // of the lifted stencil (exactly 0 where no coupling was dropped): the
+  // collector-shell rows couple nodes whose potentials agree to microvolts
+  // through conductances ~1e7 times the bulk ones, and the standard form
+  // would leave rounding of those large products in the residual
   if (act) {
-    const double s = stencil_apply(Jst + 0 * 27 * nn, nn, g, n, i, j, k, [&](int64_t m) {
-      return (label[m] & kLabActive) ? phis[m] : 0.0;
-    });
+    const double* Ks = Jst;
+    const double pn = phis[n];
+    double s = sfix[n] * pn;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      if (o == 13) continue;
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int ii = i + dx, jj = j + dy, kk = k + dz;
+      if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
+      const int64_t m = n + dx + (int64_t)g.nnx * (dy + (int64_t)g.nny * dz);
+      if (label[m] & kLabActive) s += Ks[o * nn + n] * (phis[m] - pn);
+    }
     r[n] = s + ain - kn.i_app * gpw[n];
   } else {
     r[n] = phis[n];
@@ -491,7 +505,7 @@ p4d_status residual(p4d_ctx* c, const p4d_state* st, double* r) {
                                                             st->phie, st->ce, st->cs, c->rin, c->flags);
   ::p4d::count_launch(), k_residual_macro<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, kn, c->Jst, c->label, c->eidx, c->Aj, c->gpw,
                                                              st->phis, st->phie, st->ce, st->ce_prev,
-                                                             c->lnce_r, c->rin, r);
+                                                             c->lnce_r, c->rin, c->sfix, r);
   if (NE > 0)
     ::p4d::count_launch(), k_residual_particle<<<nblocks(NE * nc), kBlock, 0, c->stream>>>(NE, nc, 1.0 / c->prm.dt, st->cs, st->cs_prev, c->Mj,
                                                                     c->kapj, c->betaj, c->rref, c->rin,

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from p4d_inputs import make_case, make_box_case
+from p4d_inputs import make_case, make_box_case, make_slab_case
 from oracle.fe import Disc
 from oracle.krylov import LinearSolve, per_field_error
 from oracle.blocks import BlockPrecond
@@ -17,6 +17,8 @@ CASES = {
     "hetero": lambda: make_box_case(8, 8, (6, 4, 6), 60e-6, (60e-6, 25e-6, 60e-6), 6, 1234, hetero=True,
                                     rs_cv=0.3),
     "oddcoarse": lambda: make_box_case(11, 9, (7, 3, 7), 40e-6, (45e-6, 20e-6, 45e-6), 5, 99),
+    "tabshell": lambda: make_slab_case(nx=12, ny=3, layers=(3, 2, 3), nc=5, seed=55, tab=3, crate=1.0, h_lat=8e-6,
+                                       L_layers=(30e-6, 15e-6, 30e-6), shell=(2e-4, 3e-4), state="seeded"),
 }
 
 
@@ -79,7 +81,7 @@ def test_jvp_parity(name, transpose):
     assert _field_rel(d, y, y_ref) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "odd", "oddcoarse"])
+@pytest.mark.parametrize("name", ["tiny", "cube8", "odd", "oddcoarse", "tabshell"])
 @pytest.mark.parametrize("combine", ["additive", "multiplicative"])
 @pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("cheb", [(2, 10.0), (3, 20.0)])
