@@ -28,8 +28,8 @@ WORKLOAD = "cube128"
 # unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
 # the 82 electrode node layers (41 anode + 41 cathode)
 # DRAM bytes per algorithmic byte of the level-0 Chebyshev step, from the ncu
-# capture in profiles/k_cheb_level0_cube96.md (257,057,792 / 259,039,179)
-TRAFFIC_PER_ALG_BYTE = 257057792 / 259039179
+# capture in profiles/k_cheb_level0_cube96.md (255,476,864 / 259,039,179)
+TRAFFIC_PER_ALG_BYTE = 255476864 / 259039179
 FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (3, 20.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms
 WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40)",
@@ -663,7 +663,7 @@ def main():
                      "traffic": TRAFFIC_PER_ALG_BYTE * r["roof"]["bytes"] if args.workload in ("cube128", "cube96")
                      else None,
                      "traffic_source": "ncu dram__bytes_read+write of the level-0 k_cheb on cube96 "
-                                       "(0.992 x algorithmic), scaled by rows processed",
+                                       "(0.986 x algorithmic), scaled by rows processed",
                      "kernel": r["roof"]["kernel"], "peak_source": src, "ms_per_launch": r["roof"]["ms"],
                      "bytes_per_launch": r["roof"]["bytes"]},
         "solve_phases_ms": r["roof"]["phases_ms"],
