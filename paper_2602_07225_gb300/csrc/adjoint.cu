@@ -26,10 +26,9 @@ __global__ void k_fnorm(const double* __restrict__ r, const double* __restrict__
   __shared__ double red[4][kBlock / 32];
   double acc[4] = {0, 0, 0, 0};
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = n < 3 * nn ? (int)(n / nn) : 3;
+    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
     const double v = wgt ? r[n] * wgt[n] : r[n];
-    #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[t] = t == f ? fma(v, v, acc[t]) : acc[t];
+    acc_field(acc, f, v);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   #pragma unroll

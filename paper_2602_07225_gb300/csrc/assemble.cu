@@ -281,8 +281,7 @@ __global__ void k_state_scale(int64_t nn, int64_t ncs, const double* __restrict_
     else if (q < 3 * nn) { u = ce[q - 2 * nn]; f = 2; }
     else { u = cs[q - 3 * nn]; f = 3; }
     const double v = sqd[q] * u;
-    #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[t] = t == f ? fma(v, v, acc[t]) : acc[t];
+    acc_field(acc, f, v);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   #pragma unroll

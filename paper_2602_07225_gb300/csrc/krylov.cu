@@ -163,10 +163,9 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
   __shared__ double red[4][kRedThreads / 32];
   double acc[4] = {0, 0, 0, 0};
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = n < 3 * nn ? (int)(n / nn) : 3;
+    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
     const double v = b[n] * rsqd[n];
-    #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += q == f ? v * v : 0.0;
+    acc_field(acc, f, v);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   #pragma unroll
@@ -217,9 +216,8 @@ __global__ void k_field_norms_plain(const double* __restrict__ r, int64_t nn, in
   __shared__ double red[4][kRedThreads / 32];
   double acc[4] = {0, 0, 0, 0};
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = n < 3 * nn ? (int)(n / nn) : 3;
-    #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += q == f ? r[n] * r[n] : 0.0;
+    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
+    acc_field(acc, f, r[n]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   #pragma unroll

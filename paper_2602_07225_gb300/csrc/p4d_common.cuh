@@ -246,6 +246,19 @@ inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 
 // Process-wide count of kernel launches issued by the library (every launch
 // site is written "count_launch(), kernel<<<...>>>(...)").
 void count_launch();
+
+// acc[f] += v^2 for a field index f known only at run time: one FP64 FMA
+// (a select over the four accumulators would issue four) and no run-time
+// index into the register array.
+__device__ __forceinline__ void acc_field(double (&acc)[4], int f, double v) {
+  switch (f) {
+    case 0: acc[0] = fma(v, v, acc[0]); break;
+    case 1: acc[1] = fma(v, v, acc[1]); break;
+    case 2: acc[2] = fma(v, v, acc[2]); break;
+    default: acc[3] = fma(v, v, acc[3]); break;
+  }
+}
+
 // While a thread captures a graph its launches are counted into *counter
 // (the graph's kernel nodes) instead of the global launch counter.
 void capture_counter(long long* counter);
