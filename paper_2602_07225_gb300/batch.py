@@ -95,8 +95,13 @@ class BatchSolver:
         if not concurrent:
             out = [self._solve_one(i) for i in range(len(self.solvers))]
         else:
+            # largest cells first: the long solves start while the small ones
+            # fill the gaps (longest-processing-time-first order)
+            order = sorted(range(len(self.solvers)), key=lambda i: -self.solvers[i].ndof)
+            out = [None] * len(self.solvers)
             with cf.ThreadPoolExecutor(max_workers=self.threads) as ex:
-                out = list(ex.map(self._solve_one, range(len(self.solvers))))
+                for i, r in zip(order, ex.map(self._solve_one, order)):
+                    out[i] = r
         torch.cuda.synchronize()
         return out
 
