@@ -151,8 +151,15 @@ __global__ void __launch_bounds__(kBlock) k_maxpy(const double* __restrict__ V, 
 // y = x * f(*sp): mode 0 f = s, mode 1 f = 1/s, mode 2 f = 1/sqrt(s) (0 if s == 0)
 __global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int64_t len,
                         const double* __restrict__ sp, int mode) {
-  const double v = *sp;
-  const double s = mode == 0 ? v : (v != 0.0 ? (mode == 1 ? 1.0 / v : 1.0 / sqrt(v)) : 0.0);
+  // the factor once per block (an FP64 divide and square root per thread
+  // cost more than the scaling itself on this GPU)
+  __shared__ double sfac;
+  if (threadIdx.x == 0) {
+    const double v = *sp;
+    sfac = mode == 0 ? v : (v != 0.0 ? (mode == 1 ? 1.0 / v : 1.0 / sqrt(v)) : 0.0);
+  }
+  __syncthreads();
+  const double s = sfac;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x)
     y[n] = x[n] * s;
 }

@@ -727,6 +727,18 @@ __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, H
 
 inline unsigned stencil_blocks(int64_t n) { return nblocks(n, kBlock * kNpt); }
 
+// 32-bit (i, j, k) of node n of a level (every level has < 2^31 nodes).
+__device__ __forceinline__ void node_ijk_i32(const LevelDims& d, int n, int& i, int& j, int& k) {
+  const int sxy = d.nnx * d.nny;
+  k = n / sxy;
+  const int r = n - k * sxy;
+  j = r / d.nnx;
+  i = r - j * d.nnx;
+}
+
+// Full-weighting restriction b_c = P^T r over the fine nodes of the mask.
+// The phi_e / c_e masks are all ones (no mask load); elsewhere a masked-out
+// residual is selected away (never multiplied: it may hold stale values).
 template <typename T>
 __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr, Ptr4<const uint8_t> fm, Ptr4<T> cb,
                            HList hl) {
@@ -734,22 +746,32 @@ __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr,
   const int h = pk(hl.h, blockIdx.y);
   if (C >= (int)cd.n) return;
   int I, J, K;
-  node_ijk(cd, C, I, J, K);
+  node_ijk_i32(cd, C, I, J, K);
+  const T* __restrict__ r = pk(fr.p, h);
+  const uint8_t* __restrict__ m = pk(fm.p, h);
+  const bool all_on = h >= 2;
+  const T* swx = supw_t<T>(X.a[0]);
+  const T* swy = supw_t<T>(X.a[1]);
+  const T* swz = supw_t<T>(X.a[2]);
   T acc = 0;
+#pragma unroll
   for (int tz = 0; tz < 3; ++tz) {
     const int fk = X.a[2].sup[K * 3 + tz];
     if (fk < 0) continue;
-    const T wz = (T)X.a[2].supw[K * 3 + tz];
+    const T wz = swz[K * 3 + tz];
+#pragma unroll
     for (int ty = 0; ty < 3; ++ty) {
       const int fj = X.a[1].sup[J * 3 + ty];
       if (fj < 0) continue;
-      const T wy = (T)X.a[1].supw[J * 3 + ty];
+      const T wy = swy[J * 3 + ty];
+#pragma unroll
       for (int tx = 0; tx < 3; ++tx) {
         const int fi = X.a[0].sup[I * 3 + tx];
         if (fi < 0) continue;
         const int f = fi + fd.nnx * (fj + fd.nny * fk);
-        if (!pk(fm.p, h)[f]) continue;
-        acc += (T)X.a[0].supw[I * 3 + tx] * wy * wz * pk(fr.p, h)[f];
+        const T v = r[f];
+        const bool on = all_on || m[f];
+        acc += on ? swx[I * 3 + tx] * wy * wz * v : (T)0;
       }
     }
   }
@@ -762,38 +784,52 @@ __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_,
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   const int h = pk(hl.h, blockIdx.y);
   if (f >= (int)fd.n) return;
-  if (!pk(fm.p, h)[f]) return;
+  if (h < 2 && !pk(fm.p, h)[f]) return;   // phi_e / c_e masks are all ones
   int i, j, k;
-  node_ijk(fd, f, i, j, k);
+  node_ijk_i32(fd, f, i, j, k);
+  const T* __restrict__ cx = pk(cx_.p, h);
+  const T* pwx = parw_t<T>(X.a[0]);
+  const T* pwy = parw_t<T>(X.a[1]);
+  const T* pwz = parw_t<T>(X.a[2]);
   T acc = 0;
+#pragma unroll
   for (int c3 = 0; c3 < 2; ++c3) {
     const int pz = X.a[2].par[k * 2 + c3];
     if (pz < 0) continue;
-    const T wz = (T)X.a[2].parw[k * 2 + c3];
+    const T wz = pwz[k * 2 + c3];
+#pragma unroll
     for (int c2 = 0; c2 < 2; ++c2) {
       const int py = X.a[1].par[j * 2 + c2];
       if (py < 0) continue;
-      const T wy = (T)X.a[1].parw[j * 2 + c2];
+      const T wy = pwy[j * 2 + c2];
+#pragma unroll
       for (int c1 = 0; c1 < 2; ++c1) {
         const int px = X.a[0].par[i * 2 + c1];
         if (px < 0) continue;
-        acc += (T)X.a[0].parw[i * 2 + c1] * wy * wz * pk(cx_.p, h)[px + cd.nnx * (py + cd.nny * pz)];
+        acc += pwx[i * 2 + c1] * wy * wz * cx[px + cd.nnx * (py + cd.nny * pz)];
       }
     }
   }
   pk(fx.p, h)[f] += acc;
 }
 
+// x = A^-1 b at the coarsest level (dense FP64 inverse): one warp per row,
+// lanes over the columns, a fixed-order warp reduction.
+constexpr int kCoarseWarps = 8;
 template <typename T>
-__global__ void k_coarse_solve(int n, const double* __restrict__ inv, Ptr4<const T> b, Ptr4<const uint8_t> mask,
-                               Ptr4<T> x, HList hl) {
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_coarse_solve(int n, const double* __restrict__ inv,
+                                                                    Ptr4<const T> b, Ptr4<const uint8_t> mask,
+                                                                    Ptr4<T> x, HList hl) {
   const int h = pk(hl.h, blockIdx.y);
-  const double* A = inv + (size_t)h * n * n;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int cidx = 0; cidx < n; ++cidx) acc += A[(size_t)r * n + cidx] * (double)pk(b.p, h)[cidx];
-    if (pk(mask.p, h)[r]) pk(x.p, h)[r] = (T)acc;   // masked-out rows are never read (and may be shared)
-  }
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kCoarseWarps + (threadIdx.x >> 5);
+  if (r >= n) return;   // per warp
+  const double* A = inv + (size_t)h * n * n + (size_t)r * n;
+  const T* bb = pk(b.p, h);
+  double acc = 0.0;
+  for (int cidx = lane; cidx < n; cidx += 32) acc += A[cidx] * (double)bb[cidx];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0 && pk(mask.p, h)[r]) pk(x.p, h)[r] = (T)acc;   // masked-out rows are never read (and may be shared)
 }
 
 size_t tsize(int precision, int level) {
@@ -882,7 +918,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> m;
     Ptr4<T> x;
     for (int h = 0; h < kNH; ++h) { b.p[h] = (const T*)C.b[h]; m.p[h] = C.mask[h]; x.p[h] = (T*)C.x[h]; }
-    ::p4d::count_launch(), k_coarse_solve<T><<<dim3(std::max(1, (int)((C.n + 127) / 128)), nhs), 128, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
+    ::p4d::count_launch(), k_coarse_solve<T><<<dim3((unsigned)((C.n + kCoarseWarps - 1) / kCoarseWarps), nhs), 32 * kCoarseWarps, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
   }
   for (int l = L - 2; l >= 0; --l) {
     MGLevel& A = c->lev[l];
