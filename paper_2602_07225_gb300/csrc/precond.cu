@@ -128,9 +128,13 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
   if (n >= nn) return;
   const int32_t e = a.eidx[n];
   const bool act = a.label[n] & kLabActive;
+  // the node couplings are needed only for the FULL condensation and for
+  // BGS corrections (the reduced block-Jacobi load is a pure scaling, and
+  // FP64 arithmetic is the cost of this kernel)
+  const bool coupled = e >= 0 && (FULL || done);
   double u[4] = {0, 0, 0, 0}, v[4] = {0, 0, 0, 0};
   double yN = 0.0, coup = 0.0;
-  if (e >= 0) {
+  if (coupled) {
     local_uv(a, e, act, u, v);
     if (FULL) yN = (double)yc[(int64_t)(a.nc - 1) * a.NE + e];
     if (done) {
@@ -140,10 +144,12 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
     }
   }
   T* bs[3] = {b0, b1, b2};
+#pragma unroll
   for (int f = 0; f < 3; ++f) {
     if (!(fmask & (1 << f))) continue;
-    double rf = r[f * nn + n] * insc(a, scaled, f, f * nn + n);
-    if (e >= 0) {
+    const int64_t row = f * nn + n;
+    double rf = scaled ? (r[row] * a.sqd[row]) * a.iwf[f] : r[row];
+    if (coupled) {
       // A_mc y_c: column c_N is u_m g_s (transposed: M beta v_m)
       if (FULL) rf -= (TRANS ? u[3] * v[f] : u[f] * v[3]) * yN;
       rf -= (TRANS ? v[f] : u[f]) * coup;
