@@ -325,9 +325,10 @@ def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0):
 
 def batched_leg(args):
     """64 gyroid cells of uneven sizes (16x16x24 ... 64x64x96 elements,
-    N_c 10-20): one Newton linear solve per cell per step, all cells
-    concurrently (one stream per cell, autotuned smoother), against the
-    same cells solved one after another."""
+    N_c 10-20): one Newton linear solve per cell per step (linearization on
+    a host thread pool, then all cells' FGMRES in lockstep through one
+    libp4d batch: one CUDA graph per Krylov column over all cells), against
+    one host thread per cell solve and the cells one after another."""
     import torch
     from p4d_inputs import make_gyroid_batch
     from paper_2602_07225_gb300 import BatchSolver
@@ -338,23 +339,26 @@ def batched_leg(args):
     bs = BatchSolver(cells, threads=16, precision=1, mode=1, rtol=1e-8, maxit=600)
     setup_s = time.perf_counter() - t0
     ndof = sum(s.ndof for s in bs.solvers)
-    for _ in range(max(1, args.warmup // 2)):
-        bs.solve_all(concurrent=True)
     lib = bs.solvers[0].lib
-    l0 = lib.p4d_launch_count()
-    t0 = time.perf_counter()
-    its = 0
-    with ClockSampler(0) as clk:
-        for _ in range(args.steps):
-            out = bs.solve_all(concurrent=True)
+
+    def timed(mode, steps):
+        for _ in range(max(1, args.warmup // 2)):
+            bs.solve_all(mode)
+        l0 = lib.p4d_launch_count()
+        t0 = time.perf_counter()
+        its = 0
+        out = None
+        for _ in range(steps):
+            out = bs.solve_all(mode)
             its += sum(info["iters"] for _, info in out)
-    conc_s = (time.perf_counter() - t0) / args.steps
-    launches = lib.p4d_launch_count() - l0
-    t0 = time.perf_counter()
-    out_seq = bs.solve_all(concurrent=False)
-    seq_s = time.perf_counter() - t0
+        return (time.perf_counter() - t0) / steps, its / steps, lib.p4d_launch_count() - l0, out
+
+    with ClockSampler(0) as clk:
+        lock_s, its, launches, out = timed("lockstep", args.steps)
+    thr_s, _, _, _ = timed("threads", max(1, args.steps // 2))
+    seq_s, _, _, _ = timed("sequential", 1)
     bad = sum(1 for _, info in out if info["status"] != 0)
-    return dict(ncells=len(cells), ndof=ndof, conc_s=conc_s, seq_s=seq_s, its=its / args.steps, launches=launches,
+    return dict(ncells=len(cells), ndof=ndof, lock_s=lock_s, thr_s=thr_s, seq_s=seq_s, its=its, launches=launches,
                 setup_s=setup_s, tuned={"%dx%dx%d" % k[:3]: list(v) for k, v in bs.tuned.items()}, failed=bad,
                 clocks=clk.summary())
 
@@ -589,15 +593,18 @@ def main():
         return
     if args.workload == "gyroid64" and args.impl == "gpu":
         r = batched_leg(args)
-        out = {"metric": METRIC, "value": r["ncells"] / r["conc_s"], "unit": "solves/s", "n_gpus": 1,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["conc_s"] * 1e3,
+        out = {"metric": METRIC, "value": r["ncells"] / r["lock_s"], "unit": "solves/s", "n_gpus": 1,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["lock_s"] * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64 outer / f32 preconditioner", "data": "synthetic",
                "config": {"workload": "gyroid64: 64 gyroid cells 16x16x24..64x64x96, N_c 10-20, one Newton "
-                                      "linear solve per cell per step, concurrent per-cell streams, autotuned "
-                                      "Chebyshev", "unknowns": r["ndof"], "l2": "inputs larger than L2"},
-               "fgmres_iters_per_s": r["its"] / r["conc_s"], "sequential_solves_per_s": r["ncells"] / r["seq_s"],
-               "speedup_vs_sequential": r["seq_s"] / r["conc_s"], "setup_s": r["setup_s"], "tuned": r["tuned"],
+                                      "linear solve per cell per step, lockstep batch (one CUDA graph per "
+                                      "Krylov column over all cells), autotuned Chebyshev",
+                          "unknowns": r["ndof"], "l2": "inputs larger than L2"},
+               "fgmres_iters_per_s": r["its"] / r["lock_s"],
+               "threads_solves_per_s": r["ncells"] / r["thr_s"],
+               "sequential_solves_per_s": r["ncells"] / r["seq_s"],
+               "speedup_vs_sequential": r["seq_s"] / r["lock_s"], "setup_s": r["setup_s"], "tuned": r["tuned"],
                "failed_cells": r["failed"], "gpu_launches": r["launches"], "clocks": r["clocks"]}
         print(json.dumps(out))
         return

@@ -36,7 +36,8 @@
  *    passes; the library only reads/writes them during the call (or, for
  *    asynchronous calls, until the handle's stream reaches that point).
  *    The library owns its workspace, allocated in p4d_setup and freed in
- *    p4d_destroy; no other call allocates device memory.
+ *    p4d_destroy (a batch's, in p4d_batch_create and p4d_batch_destroy); no
+ *    other call allocates device memory.
  *  - Streams: work is issued on the stream given to p4d_setup (NULL = the
  *    legacy default stream).  p4d_fgmres_solve / p4d_adjoint_solve
  *    synchronize that stream before returning; the other calls are
@@ -207,6 +208,39 @@ p4d_status p4d_fgmres_solve(p4d_handle h, const double* b, double* x, p4d_info* 
 /* Adjoint solve J^T lam = g with the transposed block preconditioner,
    same conventions as p4d_fgmres_solve. */
 p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_info* info);
+
+/* ---- Many cells solved together (independent electrode cells of uneven
+   sizes, each like the interpenetrating gyroid cell of section 5.1, Case IV).
+   A batch drives the FGMRES solves of its cells in lockstep: the restart
+   cycles start together, and the Arnoldi steps of Krylov column k of every
+   cell form one CUDA graph in which each cell's step sits under a
+   conditional node whose flag a device kernel sets from the host's
+   per-cell convergence mask, so the GPU runs all cells' steps concurrently
+   and the host launches one graph and reads the cells' residual estimates
+   once per column.  Each cell keeps its own options, restart length and
+   stream (its non-Arnoldi work runs there); results and iteration counts
+   are those of p4d_fgmres_solve on each cell alone. */
+typedef struct p4d_batch_ctx* p4d_batch;
+
+/* Group ncells distinct handles of the current device (not owned: destroy
+   the batch before its cells).  Allocates the batch's own small workspace
+   (a stream, per-cell flags and status pairs), freed by p4d_batch_destroy.
+   Errors: INVALID_ARG (NULL or repeated handle, ncells <= 0), OOM, CUDA. */
+p4d_status p4d_batch_create(const p4d_handle* cells, int32_t ncells, p4d_batch* out);
+
+/* J_i x_i = b_i for every cell i: [host] arrays b, x of ncells [device]
+   pointers with each cell's conventions of p4d_fgmres_solve; info: NULL or
+   ncells entries.  Every cell must be linearized, with profile = 0.
+   Synchronizes every cell's stream.  Returns OK when every cell converged,
+   else the status of the first cell that did not (each cell's own status is
+   in info[i].status). */
+p4d_status p4d_batch_fgmres_solve(p4d_batch b, const double* const* rhs, double* const* x, p4d_info* info);
+
+/* J_i^T lam_i = g_i for every cell, as p4d_batch_fgmres_solve. */
+p4d_status p4d_batch_adjoint_solve(p4d_batch b, const double* const* g, double* const* lam, p4d_info* info);
+
+/* Release the batch (NULL is ignored); the cells are untouched. */
+void p4d_batch_destroy(p4d_batch b);
 
 /* Largest number of electrode nodes p4d_jvp_noalloc accepts (size of its
    fixed scratch array: 2^20 doubles = 8 MiB per GPU that loads the library). */

@@ -86,6 +86,10 @@ SIGNATURES = {
     "p4d_voltage_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "p4d_param_grad": (C.c_int, [C.c_void_p, C.POINTER(State), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p4d_adjoint_prev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p4d_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "p4d_batch_fgmres_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(Info)]),
+    "p4d_batch_adjoint_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(Info)]),
+    "p4d_batch_destroy": (None, [C.c_void_p]),
     "p4d_launch_count": (C.c_longlong, []),
     "p4d_status_string": (C.c_char_p, [C.c_int]),
 }

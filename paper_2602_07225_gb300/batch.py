@@ -1,19 +1,25 @@
 """Many independent cells of uneven sizes solved together.
 
-Each cell owns a libp4d handle and a CUDA stream; a pool of host threads
-drives the per-cell Newton linear solves (ctypes releases the GIL during
-library calls), so the many small launches of small cells overlap on the
-GPU instead of running one cell after another.  An autotuner picks the
+Each cell owns a libp4d handle and a CUDA stream.  A pool of host threads
+linearizes the cells (ctypes releases the GIL during library calls); the
+solves then run in lockstep through one libp4d batch (p4d_batch_*): one CUDA
+graph per Krylov column holds every cell's Arnoldi step under a conditional
+node, so the small launches of small cells overlap on the GPU and the host
+synchronizes once per column for the whole batch.  The "threads" mode
+(each thread also drives its cell's solve) and "sequential" mode are kept
+for comparison.  An autotuner picks the
 Chebyshev degree and interval per (mesh shape, N_c, precision) by timing
 one solve of the first cell of each grid shape (N_c does not enter the
 multigrid); results are cached in memory and optionally in a JSON file.
 """
 import concurrent.futures as cf
+import ctypes as C
 import json
 import os
 
 import torch
 
+from . import _native as N
 from .solver import P4DSolver
 
 CANDIDATES = ((1, 4.0), (2, 10.0), (3, 10.0), (3, 20.0), (4, 20.0))
@@ -68,6 +74,7 @@ class BatchSolver:
                 self.solvers.append(s)
                 self.states.append(s.state_tensors(c["state"]))
         torch.cuda.synchronize()
+        self._batch = None
         self.tuner = tuner or (Autotuner() if autotune else None)
         self.tuned = {}
         if self.tuner:
@@ -82,29 +89,81 @@ class BatchSolver:
                 s.set_options(cheb_degree=deg, cheb_ratio=ratio)
         torch.cuda.synchronize()
 
-    def _solve_one(self, i):
+    def _linearize(self, i):
         s, st = self.solvers[i], self.states[i]
         with torch.cuda.stream(s.stream):
             b = s.residual(st).neg_()
             s.jacobian_update(st)
+        return b
+
+    def _solve_one(self, i):
+        s = self.solvers[i]
+        b = self._linearize(i)
+        with torch.cuda.stream(s.stream):
             x, info = s.solve(b)
         return x, info
 
-    def solve_all(self, concurrent=True):
-        """One Newton linear solve per cell; returns [(x, info)]."""
-        if not concurrent:
-            out = [self._solve_one(i) for i in range(len(self.solvers))]
-        else:
-            # largest cells first: the long solves start while the small ones
-            # fill the gaps (longest-processing-time-first order)
-            order = sorted(range(len(self.solvers)), key=lambda i: -self.solvers[i].ndof)
-            out = [None] * len(self.solvers)
+    def _order(self):
+        # largest cells first: the long solves start while the small ones
+        # fill the gaps (longest-processing-time-first order)
+        return sorted(range(len(self.solvers)), key=lambda i: -self.solvers[i].ndof)
+
+    def _batch_handle(self):
+        if self._batch is None:
+            lib = self.solvers[0].lib
+            n = len(self.solvers)
+            hs = (C.c_void_p * n)(*[s.h for s in self.solvers])
+            out = C.c_void_p()
+            N.check(lib.p4d_batch_create(hs, n, C.byref(out)), "p4d_batch_create")
+            self._batch = out
+        return self._batch
+
+    def solve_batched(self, rhs, adjoint=False):
+        """Lockstep FGMRES over all cells: rhs a list of device tensors;
+        returns [(x, info)]."""
+        lib = self.solvers[0].lib
+        n = len(self.solvers)
+        xs = [torch.zeros_like(b) for b in rhs]
+        bp = (C.c_void_p * n)(*[b.data_ptr() for b in rhs])
+        xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        infos = (N.Info * n)()
+        fn = lib.p4d_batch_adjoint_solve if adjoint else lib.p4d_batch_fgmres_solve
+        st = fn(self._batch_handle(), bp, xp, infos)
+        out = []
+        for i in range(n):
+            out.append((xs[i], infos[i].as_dict()))
+        if st not in (N.OK, N.NOT_CONVERGED, N.BREAKDOWN, N.NONFINITE):
+            raise N.P4DError(st, "p4d_batch_fgmres_solve")
+        return out
+
+    def solve_all(self, mode="lockstep"):
+        """One Newton linear solve per cell; returns [(x, info)].
+        mode: "lockstep" (one batch), "threads" (one host thread per cell
+        solve) or "sequential" (cells one after another)."""
+        n = len(self.solvers)
+        if mode == "sequential":
+            out = [self._solve_one(i) for i in range(n)]
+        elif mode == "threads":
+            order = self._order()
+            out = [None] * n
             with cf.ThreadPoolExecutor(max_workers=self.threads) as ex:
                 for i, r in zip(order, ex.map(self._solve_one, order)):
                     out[i] = r
+        elif mode == "lockstep":
+            order = self._order()
+            rhs = [None] * n
+            with cf.ThreadPoolExecutor(max_workers=self.threads) as ex:
+                for i, b in zip(order, ex.map(self._linearize, order)):
+                    rhs[i] = b
+            out = self.solve_batched(rhs)
+        else:
+            raise ValueError("mode: lockstep, threads or sequential")
         torch.cuda.synchronize()
         return out
 
     def close(self):
+        if self._batch is not None:
+            self.solvers[0].lib.p4d_batch_destroy(self._batch)
+            self._batch = None
         for s in self.solvers:
             s.close()

@@ -449,6 +449,72 @@ p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_inf
   return fgmres(h, g, lam, info, 1);
 }
 
+void p4d_batch_destroy(p4d_batch B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  batch_drop_graphs(B);
+  if (B->stream) cudaStreamDestroy(B->stream);
+  if (B->active_dev) cudaFree(B->active_dev);
+  if (B->stat_dev) cudaFree(B->stat_dev);
+  if (B->active_h) cudaFreeHost(B->active_h);
+  if (B->stat_h) cudaFreeHost(B->stat_h);
+  delete B;
+}
+
+p4d_status p4d_batch_create(const p4d_handle* cells, int32_t ncells, p4d_batch* out) {
+  if (!out) return P4D_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cells || ncells <= 0) return P4D_ERR_INVALID_ARG;
+  for (int i = 0; i < ncells; ++i) {
+    if (!cells[i]) return P4D_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (cells[j] == cells[i]) return P4D_ERR_INVALID_ARG;
+  }
+  p4d_batch_ctx* B = new (std::nothrow) p4d_batch_ctx;
+  if (!B) return P4D_ERR_OOM;
+  B->cells.assign(cells, cells + ncells);
+  const size_t n = (size_t)ncells;
+  p4d_status st = P4D_OK;
+  if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) st = P4D_ERR_CUDA;
+  if (st == P4D_OK && (cudaMalloc(&B->active_dev, sizeof(int) * n) != cudaSuccess ||
+                       cudaMalloc(&B->stat_dev, sizeof(double) * 2 * n) != cudaSuccess))
+    st = P4D_ERR_OOM;
+  if (st == P4D_OK && (cudaMallocHost(&B->active_h, sizeof(int) * n) != cudaSuccess ||
+                       cudaMallocHost(&B->stat_h, sizeof(double) * 2 * n) != cudaSuccess))
+    st = P4D_ERR_OOM;
+  if (st == P4D_OK && (cudaMemset(B->active_dev, 0, sizeof(int) * n) != cudaSuccess ||
+                       cudaMemset(B->stat_dev, 0, sizeof(double) * 2 * n) != cudaSuccess))
+    st = P4D_ERR_CUDA;
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    p4d_batch_destroy(B);
+    return st;
+  }
+  std::memset(B->active_h, 0, sizeof(int) * n);
+  std::memset(B->stat_h, 0, sizeof(double) * 2 * n);
+  *out = B;
+  return P4D_OK;
+}
+
+namespace {
+p4d_status batch_solve(p4d_batch B, const double* const* b, double* const* x, p4d_info* info, int trans) {
+  if (!B || !b || !x) return P4D_ERR_INVALID_ARG;
+  for (size_t i = 0; i < B->cells.size(); ++i) {
+    const p4d_ctx* c = B->cells[i];
+    if (!b[i] || !x[i] || b[i] == x[i] || !c->linearized || c->prm.profile) return P4D_ERR_INVALID_ARG;
+  }
+  return fgmres_batched(B, b, x, info, trans);
+}
+}  // namespace
+
+p4d_status p4d_batch_fgmres_solve(p4d_batch B, const double* const* b, double* const* x, p4d_info* info) {
+  return batch_solve(B, b, x, info, 0);
+}
+
+p4d_status p4d_batch_adjoint_solve(p4d_batch B, const double* const* g, double* const* lam, p4d_info* info) {
+  return batch_solve(B, g, lam, info, 1);
+}
+
 long long p4d_launch_count(void) { return p4d::g_launches.load(std::memory_order_relaxed); }
 
 const char* p4d_status_string(p4d_status s) {

@@ -462,178 +462,468 @@ p4d_status launch_step_graph(p4d_ctx* c, int trans, int k, F&& body) {
 
 }  // namespace
 
-p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
-  const int64_t nn = c->g.nn;
-  const bool full = c->prm.mode == 0;
-  const int64_t len = full ? c->ndof : 3 * nn;
-  const int m = std::min(c->prm.restart, c->mcap);
-  const HLay L = hlay(c->mcap);
-  double* hs = c->hs;
-  Reducer R{c};
-  prof_reset(c);
-  cudaEvent_t ev0, ev1;
-  P4D_TRY(cudaEventCreate(&ev0));
-  P4D_TRY(cudaEventCreate(&ev1));
-  P4D_TRY(cudaEventRecord(ev0, c->stream));
-  const double tau = (1.0 - c->prm.tplus) / c->prm.F;
-  const unsigned gb = (unsigned)std::min<int64_t>(4 * 152 * 4, (int64_t)nblocks(len));
+namespace {
 
+// ---------------------------------------------------------------- FGMRES driver
+// One solve advanced in phases: a launch phase issues work on c->stream and
+// returns; its read phase runs after that stream has been synchronized.  The
+// single-cell driver (fgmres) synchronizes after each launch phase; the
+// batched driver (fgmres_batched) runs every cell's launch phase, then one
+// synchronization for all, then every cell's read phase, with the Arnoldi
+// steps of all cells in one graph per Krylov column.
+
+// Status of Arnoldi step k into dst[0..1] (residual estimate, status): the
+// batched step graphs gather every cell's pair in one device array.
+__global__ void k_put_status(const double* __restrict__ src, double* __restrict__ dst) {
+  if (threadIdx.x == 0) {
+    dst[0] = src[0];
+    dst[1] = src[1];
+  }
+}
+
+// Condition of a cell's conditional (IF) node in a batched step graph.
+__global__ void k_set_active(cudaGraphConditionalHandle h, const int* __restrict__ active) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, *active ? 1u : 0u);
+}
+
+struct FgRun {
+  p4d_ctx* c = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int trans = 0;
+  bool full = false;
+  int64_t nn = 0, len = 0;
+  int m = 0;
+  HLay L{};
+  unsigned gb = 0;
+  double tau = 0.0;
+  const double* bk = nullptr;   // Krylov right-hand side (unscaled)
+  double bnorm = 0.0, est = 1.0;
+  int iters = 0, restarts = 0, kk = 0;
+  p4d_status st = P4D_ERR_NOT_CONVERGED;
+  bool stop = false;            // the solve ended at the start of a restart cycle
+  bool cycle_done = true;       // no further Arnoldi step in the current cycle
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double* misc() const { return c->hs + L.misc; }
+  bool active() const { return !stop && st == P4D_ERR_NOT_CONVERGED && iters < c->prm.maxit; }
+};
+
+// Field weights of the right-hand side, the particle condensation (REDUCED)
+// and the norms of the Krylov right-hand side.
+p4d_status fg_begin(FgRun& r, p4d_ctx* c, const double* b, double* x, int trans) {
+  r.c = c;
+  r.b = b;
+  r.x = x;
+  r.trans = trans;
+  r.nn = c->g.nn;
+  r.full = c->prm.mode == 0;
+  r.len = r.full ? c->ndof : 3 * r.nn;
+  r.m = std::min(c->prm.restart, c->mcap);
+  r.L = hlay(c->mcap);
+  r.tau = (1.0 - c->prm.tplus) / c->prm.F;
+  r.gb = (unsigned)std::min<int64_t>(4 * 152 * 4, (int64_t)nblocks(r.len));
+  const HLay& L = r.L;
+  double* hs = c->hs;
+  prof_reset(c);
+  P4D_TRY(cudaEventCreate(&r.ev0));
+  P4D_TRY(cudaEventCreate(&r.ev1));
+  P4D_TRY(cudaEventRecord(r.ev0, c->stream));
   // per-field weights from the full right-hand side
   {
     const int nb = kRedBlocks;
-    ::p4d::count_launch(), k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->rsqd, nn, c->ndof, c->part);
+    ::p4d::count_launch(), k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->rsqd, r.nn, c->ndof, c->part);
     ::p4d::count_launch(), k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->unorm2, 1e-14 / c->prm.rtol, trans,
                                                              c->wf, c->iwf, hs + L.misc + 2 * L.m + 8);
   }
-  const double* bk = b;            // Krylov right-hand side (unscaled)
-  if (!full) {
+  r.bk = b;
+  if (!r.full) {
     // b_m' = b_m - A_mc T^-1 b_c
-    P4D_TRYS(particle_solve64(c, b + 3 * nn, c->tmp + 3 * nn, nullptr, trans));
-    ::p4d::count_launch(), k_condense<<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->nc, tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj,
-                                                      c->ge, c->gc, c->gs, b, c->tmp + 3 * nn, c->bred, trans);
-    bk = c->bred;
+    P4D_TRYS(particle_solve64(c, b + 3 * r.nn, c->tmp + 3 * r.nn, nullptr, trans));
+    ::p4d::count_launch(), k_condense<<<nblocks(r.nn), kBlock, 0, c->stream>>>(
+        c->g, c->nc, r.tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, b, c->tmp + 3 * r.nn,
+        c->bred, trans);
+    r.bk = c->bred;
   }
-  // ||s.b_k|| = sqrt(sum_f w_f^2 ||(b_k / sqrt(d))_f||^2)
+  ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(r.bk, c->rsqd, r.nn, r.len, c->part);
+  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, hs + L.misc + 2 * L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
+  return P4D_OK;
+}
+
+// ||s.b_k|| = sqrt(sum_f w_f^2 ||(b_k / sqrt(d))_f||^2); b_k = 0 gives x = 0.
+p4d_status fg_bnorm(FgRun& r) {
+  p4d_ctx* c = r.c;
+  const double* bn2 = c->hs_h;        // full-b field norms^2 (weights)
+  const double* bk2 = c->hs_h + 8;    // Krylov-rhs field norms^2
   double bnorm = 0.0;
-  {
-    ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(bk, c->rsqd, nn, len, c->part);
-    ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
-    P4D_TRY(cudaMemcpyAsync(c->hs_h, hs + L.misc + 2 * L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
-    P4D_TRY(cudaStreamSynchronize(c->stream));
-    const double* bn2 = c->hs_h;        // full-b field norms^2 (weights)
-    const double* bk2 = c->hs_h + 8;    // Krylov-rhs field norms^2
-    for (int f = 0; f < (full ? 4 : 3); ++f) {
-      const double wf = bn2[f] > 0 ? 1.0 / std::sqrt(bn2[f]) : 1.0;
-      bnorm += wf * wf * bk2[f];
-    }
-    bnorm = std::sqrt(bnorm);
+  for (int f = 0; f < (r.full ? 4 : 3); ++f) {
+    const double wf = bn2[f] > 0 ? 1.0 / std::sqrt(bn2[f]) : 1.0;
+    bnorm += wf * wf * bk2[f];
   }
-  int iters = 0, restarts = 0;
-  p4d_status st = P4D_ERR_NOT_CONVERGED;
-  double est = 1.0;
-  if (bnorm == 0.0) {
-    P4D_TRY(cudaMemsetAsync(x, 0, sizeof(double) * c->ndof, c->stream));
-    st = P4D_OK;
-    est = 0.0;
+  r.bnorm = std::sqrt(bnorm);
+  if (r.bnorm == 0.0) {
+    P4D_TRY(cudaMemsetAsync(r.x, 0, sizeof(double) * c->ndof, c->stream));
+    r.st = P4D_OK;
+    r.est = 0.0;
   }
-  double* misc = hs + L.misc;
-  P4D_TRY(cudaMemsetAsync(misc + 2 * L.m + 7, 0, sizeof(double), c->stream));
-  while (st == P4D_ERR_NOT_CONVERGED && iters < c->prm.maxit) {
-    ++restarts;
-    // V0 = s.(b_k - A x)
-    if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
-    else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
-    R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
-    ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, c->stream>>>(hs, L, c->kdev);
-    ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(c->V, c->V, len, misc + 2 * L.m + 5, 1);
-    P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    P4D_TRY(cudaStreamSynchronize(c->stream));
-    const double beta = c->hs_h[0];
-    est = beta / bnorm;
-    if (!std::isfinite(beta)) { st = P4D_ERR_NONFINITE; break; }
-    if (beta <= c->prm.rtol * bnorm) { st = P4D_OK; break; }
-    int kk = 0;
-    for (int k = 0; k < m && iters < c->prm.maxit; ++k) {
-      // one Arnoldi step: z_k = P^-1 (s^-1 v_k), w = s.J z_k, CGS (second
-      // pass only when needed), Givens, v_{k+1} = w / h_{k+1,k}, and the
-      // residual estimate and status copied to the host
-      auto step = [&](bool graph_precond) -> p4d_status {
-        double* zk = c->Z + (int64_t)k * len;
-        double* w = c->V + (int64_t)(k + 1) * len;
-        prof_mark(c, 0);
-        P4D_TRYS(precond_column(c, trans, graph_precond));   // k read from c->kdev
-        prof_mark(c, 0);
-        prof_mark(c, 1);
-        if (full) P4D_TRYS(jvp_full(c, zk, w, trans, nullptr, true));
-        else P4D_TRYS(jvp_reduced(c, zk, w, trans, nullptr, true));
-        prof_mark(c, 1);
-        prof_mark(c, 2);
-        const double* flag = misc + 2 * L.m + 6;
-        R.mdot(c->V, len, k + 1, w, len, true, misc);                          // h1, ||w||^2 before
-        R.maxpy(c->V, len, k + 1, misc, w, len, 1.0, nullptr, misc + 2 * L.m + 2, gb);   // ||w||^2 after
-        ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(hs, L, k);
-        R.mdot(c->V, len, k + 1, w, len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
-        // ||w||^2 after the second pass (left unchanged when it is skipped)
-        R.maxpy(c->V, len, k + 1, misc + L.m + 1, w, len, 1.0, flag, misc + 2 * L.m + 2, gb);
-        ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(hs, L, k, c->kdev);
-        ::p4d::count_launch(), k_scale<<<gb, kBlock, 0, c->stream>>>(w, w, len, misc + 2 * L.m + 2, 2);
-        prof_mark(c, 2);
-        P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        return P4D_OK;
-      };
-      if (c->prm.profile) P4D_TRYS(step(true));
-      else P4D_TRYS(launch_step_graph(c, trans, k, [&]() { return step(false); }));
-      P4D_TRY(cudaStreamSynchronize(c->stream));
-      ++iters;
-      kk = k + 1;
-      est = c->hs_h[0] / bnorm;
-      const double stt = c->hs_h[1];
-      if (stt == 2.0) { st = P4D_ERR_NONFINITE; break; }
-      if (est <= c->prm.rtol) { st = P4D_OK; break; }
-      if (stt == 1.0) { st = P4D_OK; break; }
-    }
-    if (kk > 0) {
-      ::p4d::count_launch(), k_backsolve<<<1, 1, 0, c->stream>>>(hs, L, kk);
-      // x += Z y  (k_maxpy computes w -= sum h_i V_i; use sign -1)
-      R.maxpy(c->Z, len, kk, hs + L.y, x, len, -1.0, nullptr, nullptr, gb);
-    }
-    if (st == P4D_ERR_NONFINITE) break;
-    if (st == P4D_OK) {
-      // confirm with the true residual
-      if (full) P4D_TRYS(jvp_full(c, x, c->V, trans, bk, true));
-      else P4D_TRYS(jvp_reduced(c, x, c->V, trans, bk, true));
-      R.mdot(c->V, 0, 0, c->V, len, true, misc + 2 * L.m + 2);
-      P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      P4D_TRY(cudaStreamSynchronize(c->stream));
-      est = std::sqrt(c->hs_h[0]) / bnorm;
-      if (!(est <= c->prm.rtol) && iters < c->prm.maxit) st = P4D_ERR_NOT_CONVERGED;
-      if (!std::isfinite(est)) st = P4D_ERR_NONFINITE;
-    }
+  P4D_TRY(cudaMemsetAsync(r.misc() + 2 * r.L.m + 7, 0, sizeof(double), c->stream));
+  return P4D_OK;
+}
+
+// Start of a restart cycle: V0 = s.(b_k - A x), beta = ||V0||, V0 /= beta.
+p4d_status fg_cycle_launch(FgRun& r) {
+  p4d_ctx* c = r.c;
+  Reducer R{c};
+  double* misc = r.misc();
+  const HLay& L = r.L;
+  ++r.restarts;
+  if (r.full) P4D_TRYS(jvp_full(c, r.x, c->V, r.trans, r.bk, true));
+  else P4D_TRYS(jvp_reduced(c, r.x, c->V, r.trans, r.bk, true));
+  R.mdot(c->V, 0, 0, c->V, r.len, true, misc + 2 * L.m + 2);
+  ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, c->stream>>>(c->hs, L, c->kdev);
+  ::p4d::count_launch(), k_scale<<<r.gb, kBlock, 0, c->stream>>>(c->V, c->V, r.len, misc + 2 * L.m + 5, 1);
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return P4D_OK;
+}
+
+void fg_cycle_read(FgRun& r) {
+  const double beta = r.c->hs_h[0];
+  r.est = beta / r.bnorm;
+  r.kk = 0;
+  r.cycle_done = false;
+  if (!std::isfinite(beta)) {
+    r.st = P4D_ERR_NONFINITE;
+    r.stop = true;
+  } else if (beta <= r.c->prm.rtol * r.bnorm) {
+    r.st = P4D_OK;
+    r.stop = true;
   }
-  if (!full) {
+  if (r.stop) r.cycle_done = true;
+}
+
+// Arnoldi step k: z_k = P^-1 (s^-1 v_k), w = s.J z_k, CGS (second pass only
+// when needed), Givens, v_{k+1} = w / h_{k+1,k}; the residual estimate and
+// status go to the host mirror (stat == nullptr) or to stat[0..1] (device).
+p4d_status fg_step_body(FgRun& r, int k, bool graph_precond, double* stat) {
+  p4d_ctx* c = r.c;
+  Reducer R{c};
+  double* misc = r.misc();
+  const HLay& L = r.L;
+  double* zk = c->Z + (int64_t)k * r.len;
+  double* w = c->V + (int64_t)(k + 1) * r.len;
+  prof_mark(c, 0);
+  P4D_TRYS(precond_column(c, r.trans, graph_precond));   // k read from c->kdev
+  prof_mark(c, 0);
+  prof_mark(c, 1);
+  if (r.full) P4D_TRYS(jvp_full(c, zk, w, r.trans, nullptr, true));
+  else P4D_TRYS(jvp_reduced(c, zk, w, r.trans, nullptr, true));
+  prof_mark(c, 1);
+  prof_mark(c, 2);
+  const double* flag = misc + 2 * L.m + 6;
+  R.mdot(c->V, r.len, k + 1, w, r.len, true, misc);                                        // h1, ||w||^2 before
+  R.maxpy(c->V, r.len, k + 1, misc, w, r.len, 1.0, nullptr, misc + 2 * L.m + 2, r.gb);     // ||w||^2 after
+  ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(c->hs, L, k);
+  R.mdot(c->V, r.len, k + 1, w, r.len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
+  // ||w||^2 after the second pass (left unchanged when it is skipped)
+  R.maxpy(c->V, r.len, k + 1, misc + L.m + 1, w, r.len, 1.0, flag, misc + 2 * L.m + 2, r.gb);
+  ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(c->hs, L, k, c->kdev);
+  ::p4d::count_launch(), k_scale<<<r.gb, kBlock, 0, c->stream>>>(w, w, r.len, misc + 2 * L.m + 2, 2);
+  prof_mark(c, 2);
+  if (stat) ::p4d::count_launch(), k_put_status<<<1, 32, 0, c->stream>>>(misc + 2 * L.m + 3, stat);
+  else P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return P4D_OK;
+}
+
+// s2 = (residual estimate, status) of step k.
+void fg_step_read(FgRun& r, int k, const double* s2) {
+  ++r.iters;
+  r.kk = k + 1;
+  r.est = s2[0] / r.bnorm;
+  const double stt = s2[1];
+  if (stt == 2.0) r.st = P4D_ERR_NONFINITE;
+  else if (r.est <= r.c->prm.rtol) r.st = P4D_OK;
+  else if (stt == 1.0) r.st = P4D_OK;
+  if (r.st != P4D_ERR_NOT_CONVERGED || r.kk >= r.m || r.iters >= r.c->prm.maxit) r.cycle_done = true;
+}
+
+// End of a cycle: x += Z y; when the estimate converged, the true residual.
+p4d_status fg_cycle_end_launch(FgRun& r) {
+  p4d_ctx* c = r.c;
+  Reducer R{c};
+  double* misc = r.misc();
+  const HLay& L = r.L;
+  if (r.kk > 0) {
+    ::p4d::count_launch(), k_backsolve<<<1, 1, 0, c->stream>>>(c->hs, L, r.kk);
+    // x += Z y  (k_maxpy computes w -= sum h_i V_i; use sign -1)
+    R.maxpy(c->Z, r.len, r.kk, c->hs + L.y, r.x, r.len, -1.0, nullptr, nullptr, r.gb);
+  }
+  if (r.st == P4D_OK) {
+    if (r.full) P4D_TRYS(jvp_full(c, r.x, c->V, r.trans, r.bk, true));
+    else P4D_TRYS(jvp_reduced(c, r.x, c->V, r.trans, r.bk, true));
+    R.mdot(c->V, 0, 0, c->V, r.len, true, misc + 2 * L.m + 2);
+    P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  return P4D_OK;
+}
+
+// Confirmation by the true residual (only after st == OK was launched).
+void fg_cycle_end_read(FgRun& r) {
+  if (r.st != P4D_OK) return;
+  r.est = std::sqrt(r.c->hs_h[0]) / r.bnorm;
+  if (!(r.est <= r.c->prm.rtol) && r.iters < r.c->prm.maxit) r.st = P4D_ERR_NOT_CONVERGED;
+  if (!std::isfinite(r.est)) r.st = P4D_ERR_NONFINITE;
+}
+
+// Particle back-substitution (REDUCED) and the final true residual.
+p4d_status fg_finish_launch(FgRun& r) {
+  p4d_ctx* c = r.c;
+  const HLay& L = r.L;
+  const int64_t nn = r.nn;
+  if (!r.full) {
     // x_c = T^-1 (b_c - A_cm x_m)
     ::p4d::count_launch(), k_surface_coupling<<<nblocks(std::max<int64_t>(1, c->NE)), kBlock, 0, c->stream>>>(
-        c->NE, tau, c->enode, nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, x, c->tloc, trans);
-    P4D_TRYS(particle_solve64(c, b + 3 * nn, x + 3 * nn, c->tloc, trans));
+        c->NE, r.tau, c->enode, nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, r.x, c->tloc, r.trans);
+    P4D_TRYS(particle_solve64(c, r.b + 3 * nn, r.x + 3 * nn, c->tloc, r.trans));
   }
   // final true residual of the full system in the scaled norm
-  P4D_TRYS(jvp_full(c, x, c->r0, trans, b, true));
+  P4D_TRYS(jvp_full(c, r.x, c->r0, r.trans, r.b, true));
   ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
-  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, misc + 2 * L.m + 24);
-  P4D_TRY(cudaEventRecord(ev1, c->stream));
-  P4D_TRY(cudaMemcpyAsync(c->hs_h, misc + 2 * L.m + 7, sizeof(double) * 25, cudaMemcpyDeviceToHost, c->stream));
-  P4D_TRY(cudaStreamSynchronize(c->stream));
+  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 24);
+  P4D_TRY(cudaEventRecord(r.ev1, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, r.misc() + 2 * L.m + 7, sizeof(double) * 25, cudaMemcpyDeviceToHost, c->stream));
+  return P4D_OK;
+}
+
+void fg_finish_read(FgRun& r, p4d_info* info) {
+  p4d_ctx* c = r.c;
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, ev0, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
-  if (info) {
-    std::memset(info, 0, sizeof(*info));
-    info->iters = iters;
-    info->restarts = restarts;
-    info->status = st;
-    info->reorth = (int)c->hs_h[0];
-    const double* bn2 = c->hs_h + 1;      // field norms^2 of b/sqd (weights: 1/sqrt)
-    const double* rr = c->hs_h + 17;      // field norms^2 of s.(b - Jx)
-    double tot_r = 0.0;
-    const double tot_b = bn2[4];          // ||s.b||^2
-    for (int f = 0; f < 4; ++f) {
-      info->rel_res_block[f] = std::sqrt(rr[f]);   // relative to the field's (floored) rhs norm
-      tot_r += rr[f];
+  cudaEventElapsedTime(&ms, r.ev0, r.ev1);
+  cudaEventDestroy(r.ev0);
+  cudaEventDestroy(r.ev1);
+  r.ev0 = r.ev1 = nullptr;
+  if (!info) return;
+  std::memset(info, 0, sizeof(*info));
+  info->iters = r.iters;
+  info->restarts = r.restarts;
+  info->status = r.st;
+  info->reorth = (int)c->hs_h[0];
+  const double* bn2 = c->hs_h + 1;      // field norms^2 of b/sqd (weights: 1/sqrt)
+  const double* rr = c->hs_h + 17;      // field norms^2 of s.(b - Jx)
+  double tot_r = 0.0;
+  const double tot_b = bn2[4];          // ||s.b||^2
+  for (int f = 0; f < 4; ++f) {
+    info->rel_res_block[f] = std::sqrt(rr[f]);   // relative to the field's (floored) rhs norm
+    tot_r += rr[f];
+  }
+  info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
+  info->ms_total = ms;
+  if (c->prm.profile) {
+    int n = 0;
+    info->ms_precond = prof_sum(c, 0, nullptr);
+    info->ms_jvp = prof_sum(c, 1, &n);
+    info->n_jvp = n;
+    info->ms_ortho = prof_sum(c, 2, nullptr);
+    info->ms_smooth0 = prof_sum(c, 3, &n);
+    info->n_smooth0 = n;
+  }
+}
+
+}  // namespace
+
+p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
+  FgRun r;
+  P4D_TRYS(fg_begin(r, c, b, x, trans));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  P4D_TRYS(fg_bnorm(r));
+  while (r.active()) {
+    P4D_TRYS(fg_cycle_launch(r));
+    P4D_TRY(cudaStreamSynchronize(c->stream));
+    fg_cycle_read(r);
+    if (r.stop) break;
+    for (int k = 0; !r.cycle_done; ++k) {
+      if (c->prm.profile) P4D_TRYS(fg_step_body(r, k, true, nullptr));
+      else P4D_TRYS(launch_step_graph(c, trans, k, [&]() { return fg_step_body(r, k, false, nullptr); }));
+      P4D_TRY(cudaStreamSynchronize(c->stream));
+      fg_step_read(r, k, c->hs_h);
     }
-    info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
-    info->ms_total = ms;
-    if (c->prm.profile) {
-      int n = 0;
-      info->ms_precond = prof_sum(c, 0, nullptr);
-      info->ms_jvp = prof_sum(c, 1, &n);
-      info->n_jvp = n;
-      info->ms_ortho = prof_sum(c, 2, nullptr);
-      info->ms_smooth0 = prof_sum(c, 3, &n);
-      info->n_smooth0 = n;
+    P4D_TRYS(fg_cycle_end_launch(r));
+    if (r.st == P4D_ERR_NONFINITE) break;
+    if (r.st == P4D_OK) {
+      P4D_TRY(cudaStreamSynchronize(c->stream));
+      fg_cycle_end_read(r);
     }
   }
+  P4D_TRYS(fg_finish_launch(r));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  fg_finish_read(r, info);
+  return r.st;
+}
+
+// ---------------------------------------------------------------- batched driver
+namespace {
+
+// What body() launches on c->stream, captured into a new (not instantiated)
+// graph; kernels = its kernel launches.
+template <typename F>
+p4d_status capture_raw(p4d_ctx* c, cudaGraph_t* out, long long* kernels, F&& body) {
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  *kernels = 0;
+  capture_counter(kernels);
+  *out = nullptr;
+  p4d_status st = P4D_OK;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = P4D_ERR_CUDA;
+  if (st == P4D_OK) {
+    st = body();
+    if (cudaStreamEndCapture(c->cap_stream, out) != cudaSuccess && st == P4D_OK) st = P4D_ERR_CUDA;
+  }
+  capture_counter(nullptr);
+  c->stream = user;
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    if (*out) cudaGraphDestroy(*out);
+    *out = nullptr;
+  }
   return st;
+}
+
+// The batched graph of Krylov column k: for every cell whose restart length
+// exceeds k, set_active(cell) -> IF(cell active) { Arnoldi step k of the
+// cell }.  The cells' chains are independent nodes, so the GPU runs them
+// concurrently.
+p4d_status batch_step_graph(p4d_batch_ctx* B, std::vector<FgRun>& R, int k, int trans) {
+  auto& vec = B->gk[trans ? 1 : 0];
+  if ((int)vec.size() <= k) vec.resize(k + 1);
+  p4d_batch_ctx::StepGraph& sg = vec[k];
+  if (sg.exec) return P4D_OK;
+  const int n = (int)B->cells.size();
+  sg.kernels.assign(n, 0);
+  cudaGraph_t G = nullptr;
+  P4D_TRY(cudaGraphCreate(&G, 0));
+  p4d_status st = P4D_OK;
+  for (int i = 0; i < n && st == P4D_OK; ++i) {
+    FgRun& r = R[i];
+    if (k >= r.m) continue;
+    cudaGraph_t step = nullptr;
+    long long kc = 0;
+    st = capture_raw(r.c, &step, &kc, [&]() { return fg_step_body(r, k, false, B->stat_dev + 2 * i); });
+    if (st != P4D_OK) break;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t kn = nullptr, cn = nullptr, ch = nullptr;
+    const int* act = B->active_dev + i;
+    void* args[] = {&h, &act};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_set_active;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    if (cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+        cudaGraphAddKernelNode(&kn, G, nullptr, 0, &kp) != cudaSuccess)
+      st = P4D_ERR_CUDA;
+    cp.conditional.handle = h;
+    if (st == P4D_OK && cudaGraphAddNode(&cn, G, &kn, nullptr, 1, &cp) != cudaSuccess) st = P4D_ERR_CUDA;
+    if (st == P4D_OK && cudaGraphAddChildGraphNode(&ch, cp.conditional.phGraph_out[0], nullptr, 0, step) != cudaSuccess)
+      st = P4D_ERR_CUDA;
+    cudaGraphDestroy(step);
+    sg.kernels[i] = kc;
+  }
+  if (st == P4D_OK && cudaGraphInstantiate(&sg.exec, G, 0) != cudaSuccess) st = P4D_ERR_CUDA;
+  cudaGraphDestroy(G);
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    sg.exec = nullptr;
+  }
+  return st;
+}
+
+p4d_status sync_cells(p4d_batch_ctx* B) {
+  for (size_t i = 0; i < B->cells.size(); ++i) {
+    bool seen = false;
+    for (size_t j = 0; j < i && !seen; ++j) seen = B->cells[j]->stream == B->cells[i]->stream;
+    if (!seen) P4D_TRY(cudaStreamSynchronize(B->cells[i]->stream));
+  }
+  return P4D_OK;
+}
+
+}  // namespace
+
+void batch_drop_graphs(p4d_batch_ctx* B) {
+  for (auto& v : B->gk) {
+    for (auto& g : v)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    v.clear();
+  }
+}
+
+p4d_status fgmres_batched(p4d_batch_ctx* B, const double* const* b, double* const* x, p4d_info* info, int trans) {
+  const int n = (int)B->cells.size();
+  // step graphs captured before a cell's options changed are stale
+  bool stale = (int)B->gen.size() != n;
+  for (int i = 0; i < n && !stale; ++i) stale = B->gen[i] != B->cells[i]->graph_gen;
+  if (stale) {
+    batch_drop_graphs(B);
+    B->gen.resize(n);
+    for (int i = 0; i < n; ++i) B->gen[i] = B->cells[i]->graph_gen;
+  }
+  std::vector<FgRun> R(n);
+  for (int i = 0; i < n; ++i) P4D_TRYS(fg_begin(R[i], B->cells[i], b[i], x[i], trans));
+  P4D_TRYS(sync_cells(B));
+  for (int i = 0; i < n; ++i) P4D_TRYS(fg_bnorm(R[i]));
+  std::vector<int> cyc;
+  while (true) {
+    cyc.clear();
+    for (int i = 0; i < n; ++i)
+      if (R[i].active()) cyc.push_back(i);
+    if (cyc.empty()) break;
+    for (int i : cyc) P4D_TRYS(fg_cycle_launch(R[i]));
+    P4D_TRYS(sync_cells(B));
+    for (int i : cyc) fg_cycle_read(R[i]);
+    // Arnoldi steps in lockstep; a cell leaves the cycle when its step says so
+    for (int k = 0;; ++k) {
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        const bool a = !R[i].cycle_done && k < R[i].m;
+        B->active_h[i] = a ? 1 : 0;
+        any = any || a;
+      }
+      if (!any) break;
+      P4D_TRYS(batch_step_graph(B, R, k, trans));
+      const p4d_batch_ctx::StepGraph& sg = B->gk[trans ? 1 : 0][k];
+      long long launched = 0;
+      for (int i = 0; i < n; ++i)
+        if (sg.kernels[i] > 0) launched += 1 + (B->active_h[i] ? sg.kernels[i] : 0);
+      count_launches(launched);
+      P4D_TRY(cudaMemcpyAsync(B->active_dev, B->active_h, sizeof(int) * n, cudaMemcpyHostToDevice, B->stream));
+      P4D_TRY(cudaGraphLaunch(sg.exec, B->stream));
+      P4D_TRY(cudaMemcpyAsync(B->stat_h, B->stat_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, B->stream));
+      P4D_TRY(cudaStreamSynchronize(B->stream));
+      for (int i = 0; i < n; ++i)
+        if (B->active_h[i]) fg_step_read(R[i], k, B->stat_h + 2 * i);
+    }
+    bool confirm = false;
+    for (int i : cyc)
+      if (!R[i].stop) {
+        P4D_TRYS(fg_cycle_end_launch(R[i]));
+        confirm = confirm || R[i].st == P4D_OK;
+      }
+    if (confirm) {
+      P4D_TRYS(sync_cells(B));
+      for (int i : cyc)
+        if (!R[i].stop) fg_cycle_end_read(R[i]);
+    }
+  }
+  for (int i = 0; i < n; ++i) P4D_TRYS(fg_finish_launch(R[i]));
+  P4D_TRYS(sync_cells(B));
+  p4d_status out = P4D_OK;
+  for (int i = 0; i < n; ++i) {
+    fg_finish_read(R[i], info ? info + i : nullptr);
+    if (out == P4D_OK && R[i].st != P4D_OK) out = R[i].st;
+  }
+  return out;
 }
 
 }  // namespace p4d

@@ -225,11 +225,32 @@ struct p4d_ctx {
     long long kernels = 0;             // kernel nodes (added to the launch counter per launch)
   } pcg[2][2];
   std::vector<PcGraph> itg[2][2];      // Arnoldi step k of FGMRES, [transpose][full][k]
+  unsigned graph_gen = 0;              // incremented whenever the captured graphs are dropped
   cudaStream_t cap_stream = nullptr;
   int* kdev = nullptr;                 // current Krylov column (device)
   double* cheb_dev = nullptr;          // Chebyshev coefficients [kMaxLevels][kMaxDeg][3][kNH]
   float* cheb_dev32 = nullptr;         // the same in FP32
   double* cheb_pin = nullptr;          // pinned staging of cheb_dev and cheb_dev32
+};
+
+// Cells solved together by the lockstep FGMRES driver: one graph per Krylov
+// column k holds every cell's Arnoldi step k inside a conditional (IF) node
+// whose condition a one-thread kernel sets from active[cell]; the host
+// launches one graph per column for the whole batch and reads every cell's
+// residual estimate and status (stat[2 cell ...]) after it.
+struct p4d_batch_ctx {
+  std::vector<p4d_ctx*> cells;          // not owned
+  cudaStream_t stream = nullptr;        // stream of the batched step graphs
+  int* active_dev = nullptr;            // [n] cell takes step k
+  int* active_h = nullptr;              // pinned mirror
+  double* stat_dev = nullptr;           // [n][2] residual estimate, status of each cell's step
+  double* stat_h = nullptr;             // pinned mirror
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> kernels;     // kernel launches of each cell's step (0: cell not in the graph)
+  };
+  std::vector<StepGraph> gk[2];         // [transpose][k]
+  std::vector<unsigned> gen;            // cells' graph generations when gk was built
 };
 
 // ---------------------------------------------------------------- helpers
@@ -343,5 +364,8 @@ void prof_reset(p4d_ctx* c);
 
 // ---- Krylov (krylov.cu)
 p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int transpose);
+// Lockstep FGMRES over the cells of a batch (see p4d_batch_ctx).
+p4d_status fgmres_batched(p4d_batch_ctx* B, const double* const* b, double* const* x, p4d_info* info, int transpose);
+void batch_drop_graphs(p4d_batch_ctx* B);
 
 }  // namespace p4d

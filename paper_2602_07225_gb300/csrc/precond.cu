@@ -369,6 +369,7 @@ p4d_status precond_macro(p4d_ctx* c, const double* rm, double* zm, int transpose
 }
 
 void drop_graphs(p4d_ctx* c) {
+  ++c->graph_gen;
   auto drop = [](p4d_ctx::PcGraph& g) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;

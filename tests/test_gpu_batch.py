@@ -1,5 +1,6 @@
-"""Batched gyroid cells of uneven sizes: concurrent per-cell streams and the
-autotuner, each cell checked against the oracle's direct solve."""
+"""Batched gyroid cells of uneven sizes: the lockstep batch (one graph per
+Krylov column over all cells), per-cell threads and the autotuner, each cell
+checked against the oracle's direct solve and against its own solve."""
 import numpy as np
 import pytest
 import torch
@@ -34,15 +35,55 @@ def test_batch_matches_oracle_and_sequential():
     assert len(bs.tuned) == len({c["gyroid"]["n"] for c in cells})   # one tuning per grid shape
     for deg, ratio in bs.tuned.values():
         assert deg in (1, 2, 3, 4) and ratio > 1
-    conc = bs.solve_all(concurrent=True)
-    seq = bs.solve_all(concurrent=False)
-    for c, (x, info), (x2, info2) in zip(cells, conc, seq):
+    lock = bs.solve_all("lockstep")
+    thr = bs.solve_all("threads")
+    seq = bs.solve_all("sequential")
+    for c, (x, info), (x2, info2), (x3, info3) in zip(cells, lock, thr, seq):
         assert info["status"] == 0
-        assert torch.equal(x, x2)        # same kernels, same order: bit-identical
+        assert torch.equal(x, x2) and torch.equal(x, x3)   # same kernels, same order: bit-identical
+        assert info["iters"] == info2["iters"] == info3["iters"]
         if c["gyroid"]["n"] != 16:
             continue
         d = Disc(c["mesh"], c["params"])
         ref = LinearSolve(d, d.state_from_case(c["state"])).direct(refine=3)
         # gyroid voids amplify the scaled residual into solution error by ~25x
         assert per_field_error(d, x.cpu().numpy(), ref)[0] < 1e-8, info
+    bs.close()
+
+
+def test_lockstep_equals_each_cells_own_solve():
+    """The lockstep batch gives each cell exactly its own p4d_fgmres_solve /
+    p4d_adjoint_solve: uneven restart lengths (several restart cycles while
+    other cells have stopped), a zero right-hand side, the transpose, and an
+    option change between batched solves (the batch rebuilds its graphs)."""
+    from paper_2602_07225_gb300 import BatchSolver
+    cells = _cells()
+    bs = BatchSolver(cells, threads=4, autotune=False, precision=1, rtol=1e-9, maxit=400)
+    bs.solvers[1].set_options(restart=4)
+    bs.solvers[2].set_options(restart=7)
+    rhs = [bs._linearize(i) for i in range(len(cells))]
+    torch.cuda.synchronize()
+    rhs[3] = torch.zeros_like(rhs[3])
+
+    def own(i, adjoint=False):
+        s = bs.solvers[i]
+        with torch.cuda.stream(s.stream):
+            x, info = s.solve(rhs[i], adjoint=adjoint, check=False)
+        torch.cuda.synchronize()
+        return x, info
+
+    for adjoint in (False, True):
+        out = bs.solve_batched(rhs, adjoint=adjoint)
+        for i in range(len(cells)):
+            x, info = own(i, adjoint)
+            xb, ib = out[i]
+            assert ib["status"] == info["status"] == 0
+            assert (ib["iters"], ib["restarts"]) == (info["iters"], info["restarts"])
+            assert torch.equal(xb, x)
+        assert out[1][1]["restarts"] > 1                     # restart 4: several cycles
+        assert out[3][1]["iters"] == 0 and float(out[3][0].abs().max()) == 0.0
+    bs.solvers[0].set_options(cheb_degree=2)
+    out = bs.solve_batched(rhs)
+    x0, i0 = own(0)
+    assert torch.equal(out[0][0], x0) and out[0][1]["iters"] == i0["iters"]
     bs.close()
