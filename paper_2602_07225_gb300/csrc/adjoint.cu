@@ -20,30 +20,20 @@
 namespace p4d {
 namespace {
 
-// field norms^2 of a vector, optionally weighted row-wise (phi_s, phi_e, c_e, c_s)
+// field norms^2 of a vector, optionally weighted row-wise (phi_s, phi_e,
+// c_e, c_s): per-block partials, one contiguous range per field
 __global__ void k_fnorm(const double* __restrict__ r, const double* __restrict__ wgt, int64_t nn, int64_t len,
-                        double* __restrict__ out4) {
-  __shared__ double red[4][kBlock / 32];
-  double acc[4] = {0, 0, 0, 0};
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
-    const double v = wgt ? r[n] * wgt[n] : r[n];
-    acc_field(acc, f, v);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  #pragma unroll
+                        double* __restrict__ partial) {
+  double acc[4];
+#pragma unroll
   for (int f = 0; f < 4; ++f) {
-    double a = acc[f];
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) red[f][warp] = a;
+    const int64_t lo = f * nn, hi = f < 3 ? (f + 1) * nn : len;
+    acc[f] = hi <= lo ? 0.0 : (wgt ? sumsq_share<true>(r + lo, wgt + lo, hi - lo) : sumsq_share<false>(r + lo, nullptr, hi - lo));
   }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) s += red[threadIdx.x][w];
-    atomicAdd(out4 + threadIdx.x, s);
-  }
+  block_sum4(acc, partial);
 }
+
+__global__ void k_fnorm_sum(const double* __restrict__ partial, int nblk, double* out) { sum4_warps(partial, nblk, out); }
 
 // trial = u - lam * dlt, in the full layout, from the four state arrays
 __global__ void k_newton_trial(int64_t nn, int64_t ncs, const double* __restrict__ phis,
@@ -198,8 +188,8 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
   double* fn_d = h->nrm4;
   // ||.||^2 per field, optionally with the frozen row scaling
   auto fnorms = [&](const double* r, const double* w, double* out) -> p4d_status {
-    P4D_TRY(cudaMemsetAsync(fn_d, 0, 4 * sizeof(double), h->stream));
-    ::p4d::count_launch(), k_fnorm<<<4 * 152, kBlock, 0, h->stream>>>(r, w, nn, ndof, fn_d);
+    ::p4d::count_launch(), k_fnorm<<<4 * 152, kBlock, 0, h->stream>>>(r, w, nn, ndof, h->part);
+    ::p4d::count_launch(), k_fnorm_sum<<<1, 128, 0, h->stream>>>(h->part, 4 * 152, fn_d);
     P4D_TRY(cudaMemcpyAsync(fn, fn_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     P4D_TRY(cudaStreamSynchronize(h->stream));
     for (int f = 0; f < 4; ++f) out[f] = fn[f];

@@ -270,33 +270,16 @@ __global__ void k_diag(Grid g, int64_t NE, int nc, double tau, double idt, const
 // scale of each field's residual terms, used to floor the Krylov weights).
 __global__ void k_state_scale(int64_t nn, int64_t ncs, const double* __restrict__ sqd, const double* __restrict__ phis,
                               const double* __restrict__ phie, const double* __restrict__ ce,
-                              const double* __restrict__ cs, double* __restrict__ out4) {
-  __shared__ double red[4][kBlock / 32];
-  double acc[4] = {0, 0, 0, 0};
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 3 * nn + ncs; q += (int64_t)gridDim.x * blockDim.x) {
-    double u;
-    int f;
-    if (q < nn) { u = phis[q]; f = 0; }
-    else if (q < 2 * nn) { u = phie[q - nn]; f = 1; }
-    else if (q < 3 * nn) { u = ce[q - 2 * nn]; f = 2; }
-    else { u = cs[q - 3 * nn]; f = 3; }
-    const double v = sqd[q] * u;
-    acc_field(acc, f, v);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  #pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    double a = acc[f];
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) red[f][warp] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) t += red[threadIdx.x][w];
-    atomicAdd(out4 + threadIdx.x, t);
-  }
+                              const double* __restrict__ cs, double* __restrict__ partial) {
+  double acc[4];
+  acc[0] = sumsq_share<true>(phis, sqd, nn);
+  acc[1] = sumsq_share<true>(phie, sqd + nn, nn);
+  acc[2] = sumsq_share<true>(ce, sqd + 2 * nn, nn);
+  acc[3] = sumsq_share<true>(cs, sqd + 3 * nn, ncs);
+  block_sum4(acc, partial);
 }
+
+__global__ void k_state_sum(const double* __restrict__ partial, int nblk, double* out4) { sum4_warps(partial, nblk, out4); }
 
 // Fixed off-diagonal sums of the level-0 multigrid operators (setup).
 __global__ void k_fixed_sums(Grid g, const double* __restrict__ Jst, const uint8_t* __restrict__ label,
@@ -486,9 +469,9 @@ p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
   ::p4d::count_launch(), k_diag<<<nblocks(nn + NE * nc), kBlock, 0, c->stream>>>(c->g, NE, nc, kn.tau, 1.0 / c->prm.dt, c->Jst, c->label,
                                                           c->eidx, c->Aj, c->Mj, c->kapj, c->betaj, c->rref,
                                                           c->ge, c->gc, c->gs, c->sqd, c->rsqd);
-  P4D_TRY(cudaMemsetAsync(c->unorm2, 0, 4 * sizeof(double), c->stream));
   ::p4d::count_launch(), k_state_scale<<<4 * 152, kBlock, 0, c->stream>>>(nn, NE * nc, c->sqd, st->phis, st->phie, st->ce,
-                                                                         st->cs, c->unorm2);
+                                                                         st->cs, c->part);
+  ::p4d::count_launch(), k_state_sum<<<1, 128, 0, c->stream>>>(c->part, 4 * 152, c->unorm2);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }

@@ -164,29 +164,17 @@ __global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, in
     y[n] = x[n] * s;
 }
 
-// Per-field squared norms of (b / sqrt(d)) over the 4 fields (c_s optional).
+// Per-field squared norms of (b / sqrt(d)) over the 4 fields (c_s optional),
+// one contiguous range per field.
 __global__ void k_field_norms(const double* __restrict__ b, const double* __restrict__ rsqd, int64_t nn, int64_t len,
                               double* __restrict__ partial) {
-  __shared__ double red[4][kRedThreads / 32];
-  double acc[4] = {0, 0, 0, 0};
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
-    const double v = b[n] * rsqd[n];
-    acc_field(acc, f, v);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  #pragma unroll
+  double acc[4];
+#pragma unroll
   for (int f = 0; f < 4; ++f) {
-    double a = acc[f];
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) red[f][warp] = a;
+    const int64_t lo = f * nn, hi = f < 3 ? (f + 1) * nn : len;
+    acc[f] = hi > lo ? sumsq_share<true>(b + lo, rsqd + lo, hi - lo) : 0.0;
   }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[threadIdx.x][wv];
-    partial[blockIdx.x * 4 + threadIdx.x] = s;
-  }
+  block_sum4(acc, partial);
 }
 
 // Field weights of the Krylov norm: w_f = 1 / max(||b~_f||, floor_f), b~ = b/sqrt(d).
@@ -198,14 +186,12 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
 __global__ void k_weights(const double* __restrict__ partial, int nblk, const double* __restrict__ unorm2,
                           double floor_rel, int adjoint, double* __restrict__ wf, double* __restrict__ iwf,
                           double* bn2) {
+  __shared__ double s4[4];
+  sum4_warps(partial, nblk, s4);
+  __syncthreads();
   if (threadIdx.x != 0) return;
-  double s4[4], all = 0.0;
-  for (int f = 0; f < 4; ++f) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[b * 4 + f];
-    s4[f] = s;
-    all += s;
-  }
+  double all = 0.0;
+  for (int f = 0; f < 4; ++f) all += s4[f];
   double tot = 0.0;
   for (int f = 0; f < 4; ++f) {
     const double fl = adjoint ? 1e-4 * all : floor_rel * floor_rel * unorm2[f];
@@ -220,33 +206,16 @@ __global__ void k_weights(const double* __restrict__ partial, int nblk, const do
 
 // Per-field squared norms of an already scaled vector.
 __global__ void k_field_norms_plain(const double* __restrict__ r, int64_t nn, int64_t len, double* __restrict__ partial) {
-  __shared__ double red[4][kRedThreads / 32];
-  double acc[4] = {0, 0, 0, 0};
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (n >= nn) + (n >= 2 * nn) + (n >= 3 * nn);   // field of row n, without a 64-bit division
-    acc_field(acc, f, r[n]);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  #pragma unroll
+  double acc[4];
+#pragma unroll
   for (int f = 0; f < 4; ++f) {
-    double a = acc[f];
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) red[f][warp] = a;
+    const int64_t lo = f * nn, hi = f < 3 ? (f + 1) * nn : len;
+    acc[f] = hi > lo ? sumsq_share<false>(r + lo, nullptr, hi - lo) : 0.0;
   }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int wv = 0; wv < kRedThreads / 32; ++wv) s += red[threadIdx.x][wv];
-    partial[blockIdx.x * 4 + threadIdx.x] = s;
-  }
+  block_sum4(acc, partial);
 }
 
-__global__ void k_sum4(const double* __restrict__ partial, int nblk, double* out) {
-  if (threadIdx.x >= 4) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[b * 4 + threadIdx.x];
-  out[threadIdx.x] = s;
-}
+__global__ void k_sum4(const double* __restrict__ partial, int nblk, double* out) { sum4_warps(partial, nblk, out); }
 
 // Hessenberg layout in hs: H[(m+1) x m] column-major, cs[m], sn[m], g[m+1], y[m], misc
 struct HLay {
@@ -532,7 +501,7 @@ p4d_status fg_begin(FgRun& r, p4d_ctx* c, const double* b, double* x, int trans)
   {
     const int nb = kRedBlocks;
     ::p4d::count_launch(), k_field_norms<<<nb, kRedThreads, 0, c->stream>>>(b, c->rsqd, r.nn, c->ndof, c->part);
-    ::p4d::count_launch(), k_weights<<<1, 32, 0, c->stream>>>(c->part, nb, c->unorm2, 1e-14 / c->prm.rtol, trans,
+    ::p4d::count_launch(), k_weights<<<1, 128, 0, c->stream>>>(c->part, nb, c->unorm2, 1e-14 / c->prm.rtol, trans,
                                                              c->wf, c->iwf, hs + L.misc + 2 * L.m + 8);
   }
   r.bk = b;
@@ -545,7 +514,7 @@ p4d_status fg_begin(FgRun& r, p4d_ctx* c, const double* b, double* x, int trans)
     r.bk = c->bred;
   }
   ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(r.bk, c->rsqd, r.nn, r.len, c->part);
-  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
+  ::p4d::count_launch(), k_sum4<<<1, 128, 0, c->stream>>>(c->part, kRedBlocks, hs + L.misc + 2 * L.m + 16);
   P4D_TRY(cudaMemcpyAsync(c->hs_h, hs + L.misc + 2 * L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
   return P4D_OK;
 }
@@ -688,7 +657,7 @@ p4d_status fg_finish_launch(FgRun& r) {
   // final true residual of the full system in the scaled norm
   P4D_TRYS(jvp_full(c, r.x, c->r0, r.trans, r.b, true));
   ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
-  ::p4d::count_launch(), k_sum4<<<1, 32, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 24);
+  ::p4d::count_launch(), k_sum4<<<1, 128, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 24);
   P4D_TRY(cudaEventRecord(r.ev1, c->stream));
   P4D_TRY(cudaMemcpyAsync(c->hs_h, r.misc() + 2 * L.m + 7, sizeof(double) * 25, cudaMemcpyDeviceToHost, c->stream));
   return P4D_OK;

@@ -268,17 +268,66 @@ inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 
 // site is written "count_launch(), kernel<<<...>>>(...)").
 void count_launch();
 
-// acc[f] += v^2 for a field index f known only at run time: one FP64 FMA
-// (a select over the four accumulators would issue four) and no run-time
-// index into the register array.
-__device__ __forceinline__ void acc_field(double (&acc)[4], int f, double v) {
-  switch (f) {
-    case 0: acc[0] = fma(v, v, acc[0]); break;
-    case 1: acc[1] = fma(v, v, acc[1]); break;
-    case 2: acc[2] = fma(v, v, acc[2]); break;
-    default: acc[3] = fma(v, v, acc[3]); break;
+// This thread's grid-stride share of sum_i (a_i s_i)^2, i in [0, n)
+// (SCALED = false: s_i = 1), with four independent loads in flight per
+// step (one per step leaves the loop waiting on memory latency).
+template <bool SCALED>
+__device__ __forceinline__ double sumsq_share(const double* __restrict__ a, const double* __restrict__ s, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    double v0 = a[i], v1 = a[i + stride], v2 = a[i + 2 * stride], v3 = a[i + 3 * stride];
+    if (SCALED) {
+      v0 *= s[i];
+      v1 *= s[i + stride];
+      v2 *= s[i + 2 * stride];
+      v3 *= s[i + 3 * stride];
+    }
+    q0 = fma(v0, v0, q0);
+    q1 = fma(v1, v1, q1);
+    q2 = fma(v2, v2, q2);
+    q3 = fma(v3, v3, q3);
+  }
+  for (; i < n; i += stride) {
+    double v = a[i];
+    if (SCALED) v *= s[i];
+    q0 = fma(v, v, q0);
+  }
+  return (q0 + q1) + (q2 + q3);
+}
+
+// Block sums of four per-thread values into partial[blockIdx.x * 4 + f]
+// (fixed order: warp shuffles, then the warps in order).  blockDim.x is a
+// multiple of 32, at most 1024.
+__device__ __forceinline__ void block_sum4(const double (&acc)[4], double* __restrict__ partial) {
+  __shared__ double red[4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    double a = acc[f];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) red[f][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    partial[blockIdx.x * 4 + threadIdx.x] = t;
   }
 }
+
+// out[f] = sum_b partial[b * 4 + f] by warp f of a 128-thread block (fixed
+// order: lanes stride over the blocks, then a butterfly).
+__device__ __forceinline__ void sum4_warps(const double* __restrict__ partial, int nblk, double* out) {
+  const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
+  if (f >= 4) return;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[b * 4 + f];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[f] = s;
+}
+
 
 // While a thread captures a graph its launches are counted into *counter
 // (the graph's kernel nodes) instead of the global launch counter.
