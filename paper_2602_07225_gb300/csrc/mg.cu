@@ -56,7 +56,6 @@ __device__ __forceinline__ void node_ijk(const LevelDims& d, int64_t n, int& i, 
 // (struct Axis / Xfer: p4d_common.cuh)
 
 // ---------------------------------------------------------------- masks
-// ---------------------------------------------------------------- masks
 __global__ void k_mask0(int64_t nn, const uint8_t* __restrict__ label, uint8_t* m0, uint8_t* m1, uint8_t* m2,
                         uint8_t* m3) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -67,6 +66,16 @@ __global__ void k_mask0(int64_t nn, const uint8_t* __restrict__ label, uint8_t* 
   m1[n] = act && (l & kLabCathode);
   m2[n] = 1;
   m3[n] = 1;
+}
+
+// First and last node of each hierarchy's mask: ext[2 h] = min, ext[2 h + 1]
+// = max (initialised to n and -1).
+__global__ void k_mask_extent(int64_t n, Ptr4<const uint8_t> m, int* __restrict__ ext) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (i >= n || !pk(m.p, h)[i]) return;
+  atomicMin(ext + 2 * h, (int)i);
+  atomicMax(ext + 2 * h + 1, (int)i);
 }
 
 __global__ void k_mask_coarse(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const uint8_t> fm, Ptr4<uint8_t> cm) {
@@ -580,9 +589,6 @@ struct LvlPtrs {
 // in flight; on cube128 level 0 one row per thread with plane-batched loads
 // and two rows with per-offset loads were fastest (4.9-5.0 TB/s), four or
 // more rows per thread slower (register pressure).
-#ifndef P4D_CHEB_EARLY
-#define P4D_CHEB_EARLY 1
-#endif
 #ifndef P4D_STENCIL_NPT
 #define P4D_STENCIL_NPT 1
 #endif
@@ -643,81 +649,81 @@ __device__ __forceinline__ T cheb_at(const T* tab, int level, int step, int j, i
   return tab[((level * kMaxDeg + step) * 3 + j) * kNH + h];
 }
 
-// Rows of this thread: n[q] = block base + q blockDim + tid, active where in
-// range and inside the hierarchy's mask.
-// all_on: the hierarchy's mask is all ones (phi_e, c_e at every level), so
-// the row's other loads need not wait for a mask load.
-__device__ __forceinline__ void stencil_nodes(int N, const uint8_t* __restrict__ mask, bool all_on, int (&n)[kNpt],
-                                              bool (&on)[kNpt]) {
-  const int base = blockIdx.x * (blockDim.x * kNpt) + threadIdx.x;
+// Rows of this thread: n[q] = base + q blockDim + tid with base the first
+// row of block blo[h] + blockIdx.x (the launch covers only the blocks that
+// hold rows of the hierarchy's mask).  ld[q]: the row is in range, so its
+// loads are issued at once -- every array of a level is finite at every
+// node, and a row outside the mask computes a value that is never stored;
+// on[q]: the row is also inside the mask and its results are written.
+// all_on: the hierarchy's mask is all ones (phi_e, c_e at every level), no
+// mask load.
+__device__ __forceinline__ void stencil_nodes(int N, const uint8_t* __restrict__ mask, bool all_on, int blo,
+                                              int (&n)[kNpt], bool (&ld)[kNpt], bool (&on)[kNpt]) {
+  const int base = (blo + (int)blockIdx.x) * (blockDim.x * kNpt) + threadIdx.x;
 #pragma unroll
   for (int q = 0; q < kNpt; ++q) {
     n[q] = base + q * blockDim.x;
-#if P4D_CHEB_EARLY
-    on[q] = n[q] < N && (all_on || mask[n[q]]);
-#else
-    on[q] = n[q] < N && mask[n[q]];
-#endif
+    ld[q] = n[q] < N;
+    on[q] = ld[q] && (all_on || mask[n[q]]);
   }
 }
 
+// Block ranges of the listed hierarchies for one launch.
+struct BRange {
+  int lo[kNH];
+  int cnt[kNH];
+};
+
 // One Chebyshev step, x_out = x + d.
 template <typename TS, typename T>
-__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, const T* __restrict__ ctab,
-                                              int level, int step, int first) {
+__global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, BRange br,
+                                              const T* __restrict__ ctab, int level, int step, int first) {
   const int hi = blockIdx.y;
   const int h = pk(hl.h, hi);
+  if ((int)blockIdx.x >= pk(br.cnt, h)) return;
   int n[kNpt];
-  bool on[kNpt];
-  stencil_nodes((int)dd.n, pk(P.mask, h), h >= 2, n, on);
+  bool ld[kNpt], on[kNpt];
+  stencil_nodes((int)dd.n, pk(P.mask, h), h >= 2, pk(br.lo, h), n, ld, on);
   const T* __restrict__ b = pk(P.b, h);
   const T* __restrict__ dinv = pk(P.dinv, h);
   const T* __restrict__ x = pk(P.x, h);
   T* __restrict__ d = pk(P.d, h);
   T* __restrict__ xo = pk(P.xo, h);
-#if P4D_CHEB_EARLY
   // the row's own values, loaded before the stencil so that their latency
   // overlaps with the stencil loads
   T bq[kNpt], dq[kNpt], iq[kNpt];
 #pragma unroll
   for (int q = 0; q < kNpt; ++q) {
-    bq[q] = on[q] ? b[n[q]] : (T)0;
-    iq[q] = on[q] ? dinv[n[q]] : (T)0;
-    dq[q] = (on[q] && step != 0) ? d[n[q]] : (T)0;
+    bq[q] = ld[q] ? b[n[q]] : (T)0;
+    iq[q] = ld[q] ? dinv[n[q]] : (T)0;
+    dq[q] = (ld[q] && step != 0) ? d[n[q]] : (T)0;
   }
-#endif
   T ax[kNpt];
-  if (!first) stencil_rows<TS, T>(pk(P.st, h), x, dd, n, on, ax);
+  if (!first) stencil_rows<TS, T>(pk(P.st, h), x, dd, n, ld, ax);
   const T c0 = cheb_at(ctab, level, step, 0, h), ca = cheb_at(ctab, level, step, 1, h),
           cb = cheb_at(ctab, level, step, 2, h);
 #pragma unroll
   for (int q = 0; q < kNpt; ++q) {
     if (!on[q]) continue;
     const int m = n[q];
-#if P4D_CHEB_EARLY
     T res = bq[q];
     if (!first) res -= ax[q];
     const T z = iq[q] * res;
     const T dn = step == 0 ? c0 * z : ca * dq[q] + cb * z;
-#else
-    T res = b[m];
-    if (!first) res -= ax[q];
-    const T z = dinv[m] * res;
-    const T dn = step == 0 ? c0 * z : ca * d[m] + cb * z;
-#endif
     d[m] = dn;
     xo[m] = (first ? (T)0 : x[m]) + dn;
   }
 }
 
 template <typename TS, typename T>
-__global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl) {
+__global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl, BRange br) {
   const int h = pk(hl.h, blockIdx.y);
+  if ((int)blockIdx.x >= pk(br.cnt, h)) return;
   int n[kNpt];
-  bool on[kNpt];   // level-0 phi_s hierarchies share r: never write masked-out nodes
-  stencil_nodes((int)dd.n, pk(P.mask, h), h >= 2, n, on);
+  bool ld[kNpt], on[kNpt];   // level-0 phi_s hierarchies share r: never write masked-out nodes
+  stencil_nodes((int)dd.n, pk(P.mask, h), h >= 2, pk(br.lo, h), n, ld, on);
   T ax[kNpt];
-  stencil_rows<TS, T>(pk(P.st, h), pk(P.x, h), dd, n, on, ax);
+  stencil_rows<TS, T>(pk(P.st, h), pk(P.x, h), dd, n, ld, ax);
   const T* __restrict__ b = pk(P.b, h);
   T* __restrict__ r = pk(P.r, h);
 #pragma unroll
@@ -725,7 +731,6 @@ __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, H
     if (on[q]) r[n[q]] = b[n[q]] - ax[q];
 }
 
-inline unsigned stencil_blocks(int64_t n) { return nblocks(n, kBlock * kNpt); }
 
 // 32-bit (i, j, k) of node n of a level (every level has < 2^31 nodes).
 __device__ __forceinline__ void node_ijk_i32(const LevelDims& d, int n, int& i, int& j, int& k) {
@@ -888,6 +893,20 @@ template <typename T> const T* cheb_tab(const p4d_ctx* c);
 template <> const double* cheb_tab<double>(const p4d_ctx* c) { return c->cheb_dev; }
 template <> const float* cheb_tab<float>(const p4d_ctx* c) { return c->cheb_dev32; }
 
+// Block ranges of a level for the listed hierarchies, and the launch's
+// grid width (the widest range).
+BRange brange(const MGLevel& A, const int* hs, int nhs, unsigned* gx) {
+  BRange r{};
+  int w = 1;
+  for (int h = 0; h < kNH; ++h) {
+    r.lo[h] = A.blo[h];
+    r.cnt[h] = A.bcnt[h];
+  }
+  for (int t = 0; t < nhs; ++t) w = std::max(w, A.bcnt[hs[t]]);
+  *gx = (unsigned)w;
+  return r;
+}
+
 template <typename TS0, typename TS, typename T>
 p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   const int L = c->nlev;
@@ -896,16 +915,18 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   for (int l = 0; l < L - 1; ++l) {
     MGLevel& A = c->lev[l];
     MGLevel& B = c->lev[l + 1];
-    const dim3 grid(stencil_blocks(A.n), nhs);
+    unsigned gx = 1;
+    const BRange br = brange(A, hs, nhs, &gx);
+    const dim3 grid(gx, nhs);
     for (int s = 0; s < deg; ++s) {
       if (l == 0 && s > 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cheb_tab<T>(c), l, s, s == 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cheb_tab<T>(c), l, s, s == 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
       if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
-    if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl);
-    else ::p4d::count_launch(), k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl);
+    if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br);
+    else ::p4d::count_launch(), k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br);
     Ptr4<const T> fr;
     Ptr4<const uint8_t> fm;
     Ptr4<T> cb;
@@ -927,12 +948,14 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> fm;
     Ptr4<T> fx;
     for (int h = 0; h < kNH; ++h) { cxp.p[h] = (const T*)B.x[h]; fm.p[h] = A.mask[h]; fx.p[h] = (T*)A.x[h]; }
-    const dim3 grid(stencil_blocks(A.n), nhs);
+    unsigned gx = 1;
+    const BRange br = brange(A, hs, nhs, &gx);
+    const dim3 grid(gx, nhs);
     ::p4d::count_launch(), k_prolong<T><<<dim3(nblocks(A.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
     for (int s = 0; s < deg; ++s) {
       if (l == 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, cheb_tab<T>(c), l, s, 0);
-      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, cheb_tab<T>(c), l, s, 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
       if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
@@ -1070,6 +1093,33 @@ p4d_status mg_plan(p4d_ctx* c) {
       P4D_TRYS(dalloc_t(c, &lv.inv, (size_t)2 * kNH * n * n));
       P4D_TRYS(dalloc_t(c, &lv.perm, (size_t)kNH * n));
     }
+  }
+  // per level and hierarchy, the stencil-kernel blocks that hold mask rows
+  {
+    int* ext = nullptr;
+    P4D_TRYS(dalloc_t(c, &ext, (size_t)2 * kNH * L));
+    std::vector<int> init(2 * kNH * L);
+    for (int l = 0; l < L; ++l)
+      for (int h = 0; h < kNH; ++h) {
+        init[2 * (l * kNH + h)] = (int)c->lev[l].n;
+        init[2 * (l * kNH + h) + 1] = -1;
+      }
+    P4D_TRY(cudaMemcpyAsync(ext, init.data(), init.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    for (int l = 0; l < L; ++l) {
+      Ptr4<const uint8_t> m;
+      for (int h = 0; h < kNH; ++h) m.p[h] = c->lev[l].mask[h];
+      ::p4d::count_launch(), k_mask_extent<<<dim3(nblocks(c->lev[l].n), kNH), kBlock, 0, c->stream>>>(
+          c->lev[l].n, m, ext + 2 * kNH * l);
+    }
+    P4D_TRY(cudaMemcpyAsync(init.data(), ext, init.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    P4D_TRY(cudaStreamSynchronize(c->stream));
+    const int rows = kBlock * kNpt;
+    for (int l = 0; l < L; ++l)
+      for (int h = 0; h < kNH; ++h) {
+        const int lo = init[2 * (l * kNH + h)], hi = init[2 * (l * kNH + h) + 1];
+        c->lev[l].blo[h] = hi < 0 ? 0 : lo / rows;
+        c->lev[l].bcnt[h] = hi < 0 ? 0 : hi / rows - lo / rows + 1;
+      }
   }
   // level-0 particle work and variable row sums
   P4D_TRYS(dalloc(c, &c->yc, (prec == 0 ? sizeof(double) : sizeof(float)) * (size_t)std::max<int64_t>(1, c->NE) * c->nc));

@@ -115,6 +115,10 @@ struct MGLevel {
   void* r[kNH] = {};
   void* d[kNH] = {};
   double* lam = nullptr;               // [kNH] Gershgorin bound of D^-1 A
+  // stencil-kernel blocks holding rows of each hierarchy's mask: blocks
+  // [blo, blo + bcnt) (set at planning; the masks do not change)
+  int blo[kNH] = {};
+  int bcnt[kNH] = {};
   // coarsest level only: dense inverse [kNH][n][n] FP64 (+ scratch), LU row permutation
   double* inv = nullptr;
   int* perm = nullptr;
