@@ -27,9 +27,9 @@ METRIC = "Newton linear solves/s & FGMRES iters/s to 1e-8 rel. residual; mixed v
 WORKLOAD = "cube128"
 # unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
 # the 82 electrode node layers (41 anode + 41 cathode)
-# DRAM bytes per algorithmic byte of the level-0 Chebyshev step, from the ncu
-# capture in profiles/k_cheb_level0_cube96.md (255,476,864 / 259,039,179)
-TRAFFIC_PER_ALG_BYTE = 255476864 / 259039179
+# DRAM bytes per algorithmic byte of the level-0 Chebyshev step, from an ncu
+# capture of two of its launches on cube96 (254,608,256 / 259,039,179)
+TRAFFIC_PER_ALG_BYTE = 254608256 / 259039179
 FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (3, 20.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms
 WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40)",

@@ -746,9 +746,10 @@ __device__ __forceinline__ void node_ijk_i32(const LevelDims& d, int n, int& i, 
 // residual is selected away (never multiplied: it may hold stale values).
 template <typename T>
 __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr, Ptr4<const uint8_t> fm, Ptr4<T> cb,
-                           HList hl) {
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+                           HList hl, BRange br) {
   const int h = pk(hl.h, blockIdx.y);
+  if ((int)blockIdx.x >= pk(br.cnt, h)) return;   // coarse blocks without rows of the coarse mask
+  const int C = (pk(br.lo, h) + (int)blockIdx.x) * blockDim.x + threadIdx.x;
   if (C >= (int)cd.n) return;
   int I, J, K;
   node_ijk_i32(cd, C, I, J, K);
@@ -785,11 +786,15 @@ __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr,
 
 template <typename T>
 __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_, Ptr4<const uint8_t> fm, Ptr4<T> fx,
-                          HList hl) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+                          HList hl, BRange br) {
   const int h = pk(hl.h, blockIdx.y);
+  if ((int)blockIdx.x >= pk(br.cnt, h)) return;   // fine blocks without rows of the mask
+  const int f = (pk(br.lo, h) + (int)blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= (int)fd.n) return;
-  if (h < 2 && !pk(fm.p, h)[f]) return;   // phi_e / c_e masks are all ones
+  // the mask gates only the write: the interpolation's loads do not wait on it
+  // (phi_e / c_e masks are all ones)
+  const bool on = h >= 2 || pk(fm.p, h)[f];
+  const T xf = pk(fx.p, h)[f];
   int i, j, k;
   node_ijk_i32(fd, f, i, j, k);
   const T* __restrict__ cx = pk(cx_.p, h);
@@ -815,7 +820,7 @@ __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_,
       }
     }
   }
-  pk(fx.p, h)[f] += acc;
+  if (on) pk(fx.p, h)[f] = xf + acc;
 }
 
 // x = A^-1 b at the coarsest level (dense FP64 inverse): one warp per row,
@@ -894,7 +899,9 @@ template <> const double* cheb_tab<double>(const p4d_ctx* c) { return c->cheb_de
 template <> const float* cheb_tab<float>(const p4d_ctx* c) { return c->cheb_dev32; }
 
 // Block ranges of a level for the listed hierarchies, and the launch's
-// grid width (the widest range).
+// grid width (the widest range).  The transfer kernels take one row per
+// thread in blocks of kBlock and share these ranges.
+static_assert(kNpt == 1, "block ranges are shared by the one-row-per-thread transfer kernels");
 BRange brange(const MGLevel& A, const int* hs, int nhs, unsigned* gx) {
   BRange r{};
   int w = 1;
@@ -931,7 +938,9 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> fm;
     Ptr4<T> cb;
     for (int h = 0; h < kNH; ++h) { fr.p[h] = (const T*)A.r[h]; fm.p[h] = A.mask[h]; cb.p[h] = (T*)B.b[h]; }
-    ::p4d::count_launch(), k_restrict<T><<<dim3(nblocks(B.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fr, fm, cb, hl);
+    unsigned gxc = 1;
+    const BRange brc = brange(B, hs, nhs, &gxc);
+    ::p4d::count_launch(), k_restrict<T><<<dim3(gxc, nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fr, fm, cb, hl, brc);
   }
   {
     MGLevel& C = c->lev[L - 1];
@@ -951,7 +960,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     unsigned gx = 1;
     const BRange br = brange(A, hs, nhs, &gx);
     const dim3 grid(gx, nhs);
-    ::p4d::count_launch(), k_prolong<T><<<dim3(nblocks(A.n), nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl);
+    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl, br);
     for (int s = 0; s < deg; ++s) {
       if (l == 0) prof_mark(c, 3);
       if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
