@@ -120,6 +120,8 @@ __device__ __forceinline__ void local_uv(const PcArgs& a, int64_t e, bool act, d
 template <typename T, bool TRANS, bool FULL>
 __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref_, int fmask, int done, bool scaled,
                        T* b0, T* b1, T* b2) {
+  pdl_wait();
+  pdl_trigger();
   const double* __restrict__ r = rref_.get();
   const double* zm = zref_.get();
   double* zout = zref_.get();
@@ -165,6 +167,8 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
 template <typename T>
 __global__ void k_store(Grid g, const uint8_t* __restrict__ label, int fmask, const T* __restrict__ x0,
                         const T* __restrict__ x1, const T* __restrict__ x2, VRef zref_) {
+  pdl_wait();
+  pdl_trigger();
   double* __restrict__ zm = zref_.get();
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
@@ -257,24 +261,25 @@ p4d_status apply_t(p4d_ctx* c, VRef r, VRef z, bool scaled) {
   MGLevel& l0 = c->lev[0];
   T* b[3] = {(T*)l0.b[0], (T*)l0.b[2], (T*)l0.b[3]};
   if (c->prm.combine == 0) {
-    ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 7, 0, scaled, b[0], b[1], b[2]);
+    launch_pdl(k_load<T, TRANS, FULL>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, a, r, yc, z, 7, 0, scaled, b[0], b[1],
+               b[2]);
     const int hs[4] = {0, 1, 2, 3};
     P4D_TRYS(mg_vcycle(c, hs, 4));
-    ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 7, (const T*)l0.x[0], (const T*)l0.x[2],
-                                                      (const T*)l0.x[3], z);
+    launch_pdl(k_store<T>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, c->g, c->label, 7, (const T*)l0.x[0],
+               (const T*)l0.x[2], (const T*)l0.x[3], z);
   } else {
     int done = 0;
     for (int t = 0; t < 3; ++t) {
       const int f = TRANS ? c->prm.order[2 - t] : c->prm.order[t];
-      ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 1 << f, done, scaled, b[0], b[1],
-                                                                   b[2]);
+      launch_pdl(k_load<T, TRANS, FULL>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, a, r, yc, z, 1 << f, done, scaled,
+                 b[0], b[1], b[2]);
       int hs[2];
       int nh = 0;
       for (int q = 0; q < 2; ++q)
         if (kHOfField[f][q] >= 0) hs[nh++] = kHOfField[f][q];
       P4D_TRYS(mg_vcycle(c, hs, nh));
-      ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 1 << f, (const T*)l0.x[0], (const T*)l0.x[2],
-                                                        (const T*)l0.x[3], z);
+      launch_pdl(k_store<T>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, c->g, c->label, 1 << f, (const T*)l0.x[0],
+                 (const T*)l0.x[2], (const T*)l0.x[3], z);
       done |= 1 << f;
     }
   }
