@@ -120,21 +120,53 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def make_workload(name):
+# generator seeds of the named workloads; rank r > 0 of a multi-GPU run
+# solves its own cell of the same shape, seeded SEEDS[name] + 7919 r
+SEEDS = {"cube8": 1001, "cube128": 1002, "cube96": 1002, "hetero128": 1003}
+
+
+def make_workload(name, rank=0):
     from p4d_inputs import make_case
-    return make_case(name)
+    if rank == 0:
+        return make_case(name)
+    return make_case(name, seed=SEEDS[name] + 7919 * rank)
+
+
+def shard(n, rank, world):
+    """Units of this rank: round-robin over the ranks, every unit once."""
+    return list(range(rank, n, world))
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(ms, iters, world, device=None):
+    """(max over ranks of the timed milliseconds, sum of their iterations).
+    The ranks' units are independent, so this timing reduction is the only
+    exchange between them."""
+    if world == 1:
+        return ms, iters
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], device=device, dtype=torch.float64)
+    dist.all_reduce(it)
+    return t.item(), it.item()
 
 
 def gpu_leg(args, rank, world, local):
     import torch
-    import torch.distributed as dist
     from paper_2602_07225_gb300 import P4DSolver
     from paper_2602_07225_gb300 import build as pbuild
 
     pbuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = make_workload(args.workload)
+    case = make_workload(args.workload, rank)
     opts_mixed = dict(precision=1, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0],
                       cheb_ratio=CHEB[1])
     s = P4DSolver(case, device=dev, **opts_mixed)
@@ -148,21 +180,17 @@ def gpu_leg(args, rank, world, local):
         x, info = solver.solve(b)
         return x, info
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     for _ in range(args.warmup):
         x, info = step(s, st)
     torch.cuda.synchronize()
-    barrier()
+    barrier(world)
     iters = 0
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lib = s.lib
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        barrier()
+        barrier(world)
         l0 = lib.p4d_launch_count()
         e0.record(stream)
         for _ in range(args.steps):
@@ -171,17 +199,8 @@ def gpu_leg(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         launches = lib.p4d_launch_count() - l0
-        barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-        it = torch.tensor([iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(it)
-        iters_all = it.item()
-    else:
-        iters_all = iters
+        barrier(world)
+    ms, iters_all = aggregate(e0.elapsed_time(e1), iters, world, dev)
     ms_per_step = ms / args.steps
     solves_per_s = world * args.steps / (ms / 1e3)
     iters_per_s = iters_all / (ms / 1e3)
@@ -323,20 +342,24 @@ def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0):
             "scaled_solves_per_s": (1.0 / dt) * d.ndof / full_dof}
 
 
-def batched_leg(args):
+def batched_leg(args, rank=0, world=1, local=0):
     """64 gyroid cells of uneven sizes (16x16x24 ... 64x64x96 elements,
     N_c 10-20): one Newton linear solve per cell per step (linearization on
     a host thread pool, then all cells' FGMRES in lockstep through one
-    libp4d batch: one CUDA graph per Krylov column over all cells), against
-    one host thread per cell solve and the cells one after another."""
+    libp4d batch: one CUDA graph per Krylov column over all cells).  Under
+    torchrun every rank takes its round-robin share of the cells.  At N=1
+    also one host thread per cell solve and the cells one after another."""
     import torch
     from p4d_inputs import make_gyroid_batch
     from paper_2602_07225_gb300 import BatchSolver
     from paper_2602_07225_gb300 import build as pbuild
     pbuild.build()
-    cells = make_gyroid_batch(64, seed=1004)
+    torch.cuda.set_device(local)
+    allc = make_gyroid_batch(64, seed=1004)
+    cells = [allc[i] for i in shard(len(allc), rank, world)]
     t0 = time.perf_counter()
-    bs = BatchSolver(cells, threads=16, precision=1, mode=1, rtol=1e-8, maxit=600)
+    bs = BatchSolver(cells, threads=16, device=torch.device("cuda", local), precision=1, mode=1, rtol=1e-8,
+                     maxit=600)
     setup_s = time.perf_counter() - t0
     ndof = sum(s.ndof for s in bs.solvers)
     lib = bs.solvers[0].lib
@@ -344,6 +367,7 @@ def batched_leg(args):
     def timed(mode, steps):
         for _ in range(max(1, args.warmup // 2)):
             bs.solve_all(mode)
+        barrier(world)
         l0 = lib.p4d_launch_count()
         t0 = time.perf_counter()
         its = 0
@@ -351,16 +375,23 @@ def batched_leg(args):
         for _ in range(steps):
             out = bs.solve_all(mode)
             its += sum(info["iters"] for _, info in out)
-        return (time.perf_counter() - t0) / steps, its / steps, lib.p4d_launch_count() - l0, out
+        el = time.perf_counter() - t0
+        barrier(world)
+        return el / steps, its / steps, lib.p4d_launch_count() - l0, out
 
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         lock_s, its, launches, out = timed("lockstep", args.steps)
-    thr_s, _, _, _ = timed("threads", max(1, args.steps // 2))
-    seq_s, _, _, _ = timed("sequential", 1)
     bad = sum(1 for _, info in out if info["status"] != 0)
-    return dict(ncells=len(cells), ndof=ndof, lock_s=lock_s, thr_s=thr_s, seq_s=seq_s, its=its, launches=launches,
-                setup_s=setup_s, tuned={"%dx%dx%d" % k[:3]: list(v) for k, v in bs.tuned.items()}, failed=bad,
-                clocks=clk.summary())
+    ms, its_all = aggregate(lock_s * 1e3, its, world, torch.device("cuda", local))
+    _, nd_all = aggregate(0.0, ndof, world, torch.device("cuda", local))
+    _, bad_all = aggregate(0.0, bad, world, torch.device("cuda", local))
+    thr_s = seq_s = None
+    if world == 1:
+        thr_s, _, _, _ = timed("threads", max(1, args.steps // 2))
+        seq_s, _, _, _ = timed("sequential", 1)
+    return dict(ncells=len(allc), ndof=int(nd_all), lock_s=ms / 1e3, thr_s=thr_s, seq_s=seq_s, its=its_all,
+                launches=launches, setup_s=setup_s, tuned={"%dx%dx%d" % k[:3]: list(v) for k, v in bs.tuned.items()},
+                failed=int(bad_all), clocks=clk.summary())
 
 
 def _field_errors(x, ref, nn):
@@ -592,19 +623,26 @@ def main():
         precision_study(args)
         return
     if args.workload == "gyroid64" and args.impl == "gpu":
-        r = batched_leg(args)
-        out = {"metric": METRIC, "value": r["ncells"] / r["lock_s"], "unit": "solves/s", "n_gpus": 1,
+        rank, world, local = dist_env()
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        r = batched_leg(args, rank, world, local)
+        if rank != 0:
+            return
+        seq = {} if r["seq_s"] is None else {
+            "threads_solves_per_s": r["ncells"] / r["thr_s"],
+            "sequential_solves_per_s": r["ncells"] / r["seq_s"],
+            "speedup_vs_sequential": r["seq_s"] / r["lock_s"]}
+        out = {"metric": METRIC, "value": r["ncells"] / r["lock_s"], "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["lock_s"] * 1e3,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
                "dtype": "f64 outer / f32 preconditioner", "data": "synthetic",
                "config": {"workload": "gyroid64: 64 gyroid cells 16x16x24..64x64x96, N_c 10-20, one Newton "
                                       "linear solve per cell per step, lockstep batch (one CUDA graph per "
                                       "Krylov column over all cells), autotuned Chebyshev",
                           "unknowns": r["ndof"], "l2": "inputs larger than L2"},
-               "fgmres_iters_per_s": r["its"] / r["lock_s"],
-               "threads_solves_per_s": r["ncells"] / r["thr_s"],
-               "sequential_solves_per_s": r["ncells"] / r["seq_s"],
-               "speedup_vs_sequential": r["seq_s"] / r["lock_s"], "setup_s": r["setup_s"], "tuned": r["tuned"],
+               "fgmres_iters_per_s": r["its"] / r["lock_s"], **seq, "setup_s": r["setup_s"], "tuned": r["tuned"],
                "failed_cells": r["failed"], "gpu_launches": r["launches"], "clocks": r["clocks"]}
         print(json.dumps(out))
         return
