@@ -455,6 +455,9 @@ __global__ void k_set_active(cudaGraphConditionalHandle h, const int* __restrict
   if (threadIdx.x == 0) cudaGraphSetConditional(h, *active ? 1u : 0u);
 }
 
+struct FgRun;
+void fg_release(FgRun& r);
+
 struct FgRun {
   p4d_ctx* c = nullptr;
   const double* b = nullptr;
@@ -475,7 +478,17 @@ struct FgRun {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double* misc() const { return c->hs + L.misc; }
   bool active() const { return !stop && st == P4D_ERR_NOT_CONVERGED && iters < c->prm.maxit; }
+  FgRun() = default;
+  FgRun(const FgRun&) = delete;
+  FgRun& operator=(const FgRun&) = delete;
+  ~FgRun() { fg_release(*this); }   // the timing events, also on an early error return
 };
+
+void fg_release(FgRun& r) {
+  if (r.ev0) cudaEventDestroy(r.ev0);
+  if (r.ev1) cudaEventDestroy(r.ev1);
+  r.ev0 = r.ev1 = nullptr;
+}
 
 // Field weights of the right-hand side, the particle condensation (REDUCED)
 // and the norms of the Krylov right-hand side.
@@ -667,9 +680,7 @@ void fg_finish_read(FgRun& r, p4d_info* info) {
   p4d_ctx* c = r.c;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, r.ev0, r.ev1);
-  cudaEventDestroy(r.ev0);
-  cudaEventDestroy(r.ev1);
-  r.ev0 = r.ev1 = nullptr;
+  fg_release(r);
   if (!info) return;
   std::memset(info, 0, sizeof(*info));
   info->iters = r.iters;

@@ -33,6 +33,9 @@ __device__ __forceinline__ double insc(const PcArgs& a, bool scaled, int f, int6
   return scaled ? a.sqd[row] * a.iwf[f] : 1.0;
 }
 
+#ifndef P4D_LOAD32
+#define P4D_LOAD32 1
+#endif
 constexpr int kPartBlock = 128;   // nodes per block of the staged particle kernels
 
 // LU factors of T_j / M_j in precision T, radial-major ([nc][NE]): 1/pivot
@@ -150,6 +153,14 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
   for (int f = 0; f < 3; ++f) {
     if (!(fmask & (1 << f))) continue;
     const int64_t row = f * nn + n;
+#if P4D_LOAD32
+    if (sizeof(T) == sizeof(float) && scaled && !coupled && !(f == 0 && !act)) {
+      // FP32 right-hand side of an FP32 cycle: the scaling in FP32
+      const float w = (float)(a.iwf[f] * a.sc[f]);
+      bs[f][n] = (T)(((float)r[row] * (float)a.sqd[row]) * w);
+      continue;
+    }
+#endif
     double rf = scaled ? (r[row] * a.sqd[row]) * a.iwf[f] : r[row];
     if (coupled) {
       // A_mc y_c: column c_N is u_m g_s (transposed: M beta v_m)
