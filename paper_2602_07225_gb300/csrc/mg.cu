@@ -678,8 +678,6 @@ struct BRange {
 template <typename TS, typename T>
 __global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HList hl, BRange br,
                                               const T* __restrict__ ctab, int level, int step, int first) {
-  pdl_wait();
-  pdl_trigger();
   const int hi = blockIdx.y;
   const int h = pk(hl.h, hi);
   if ((int)blockIdx.x >= pk(br.cnt, h)) return;
@@ -719,8 +717,6 @@ __global__ void __launch_bounds__(256) k_cheb(LevelDims dd, LvlPtrs<TS, T> P, HL
 
 template <typename TS, typename T>
 __global__ void __launch_bounds__(256) k_resid(LevelDims dd, LvlPtrs<TS, T> P, HList hl, BRange br) {
-  pdl_wait();
-  pdl_trigger();
   const int h = pk(hl.h, blockIdx.y);
   if ((int)blockIdx.x >= pk(br.cnt, h)) return;
   int n[kNpt];
@@ -751,8 +747,6 @@ __device__ __forceinline__ void node_ijk_i32(const LevelDims& d, int n, int& i, 
 template <typename T>
 __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr, Ptr4<const uint8_t> fm, Ptr4<T> cb,
                            HList hl, BRange br) {
-  pdl_wait();
-  pdl_trigger();
   const int h = pk(hl.h, blockIdx.y);
   if ((int)blockIdx.x >= pk(br.cnt, h)) return;   // coarse blocks without rows of the coarse mask
   const int C = (pk(br.lo, h) + (int)blockIdx.x) * blockDim.x + threadIdx.x;
@@ -793,8 +787,6 @@ __global__ void k_restrict(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> fr,
 template <typename T>
 __global__ void k_prolong(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const T> cx_, Ptr4<const uint8_t> fm, Ptr4<T> fx,
                           HList hl, BRange br) {
-  pdl_wait();
-  pdl_trigger();
   const int h = pk(hl.h, blockIdx.y);
   if ((int)blockIdx.x >= pk(br.cnt, h)) return;   // fine blocks without rows of the mask
   const int f = (pk(br.lo, h) + (int)blockIdx.x) * blockDim.x + threadIdx.x;
@@ -838,8 +830,6 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kCoarseWarps) k_coarse_solve(int n, const double* __restrict__ inv,
                                                                     Ptr4<const T> b, Ptr4<const uint8_t> mask,
                                                                     Ptr4<T> x, HList hl) {
-  pdl_wait();
-  pdl_trigger();
   const int h = pk(hl.h, blockIdx.y);
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * kCoarseWarps + (threadIdx.x >> 5);
@@ -937,20 +927,20 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     const dim3 grid(gx, nhs);
     for (int s = 0; s < deg; ++s) {
       if (l == 0 && s > 0) prof_mark(c, 3);
-      if (l == 0) launch_pdl(k_cheb<TS0, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
-      else launch_pdl(k_cheb<TS, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
       if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
-    if (l == 0) launch_pdl(k_resid<TS0, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS0, T>(A), hl, br);
-    else launch_pdl(k_resid<TS, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS, T>(A), hl, br);
+    if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br);
+    else ::p4d::count_launch(), k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br);
     Ptr4<const T> fr;
     Ptr4<const uint8_t> fm;
     Ptr4<T> cb;
     for (int h = 0; h < kNH; ++h) { fr.p[h] = (const T*)A.r[h]; fm.p[h] = A.mask[h]; cb.p[h] = (T*)B.b[h]; }
     unsigned gxc = 1;
     const BRange brc = brange(B, hs, nhs, &gxc);
-    launch_pdl(k_restrict<T>, dim3(gxc, nhs), dim3(kBlock), 0, c->stream, dims(A), dims(B), A.X, fr, fm, cb, hl, brc);
+    ::p4d::count_launch(), k_restrict<T><<<dim3(gxc, nhs), kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, fr, fm, cb, hl, brc);
   }
   {
     MGLevel& C = c->lev[L - 1];
@@ -958,8 +948,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     Ptr4<const uint8_t> m;
     Ptr4<T> x;
     for (int h = 0; h < kNH; ++h) { b.p[h] = (const T*)C.b[h]; m.p[h] = C.mask[h]; x.p[h] = (T*)C.x[h]; }
-    launch_pdl(k_coarse_solve<T>, dim3((unsigned)((C.n + kCoarseWarps - 1) / kCoarseWarps), nhs), dim3(32 * kCoarseWarps), 0,
-               c->stream, (int)C.n, (const double*)C.inv, b, m, x, hl);
+    ::p4d::count_launch(), k_coarse_solve<T><<<dim3((unsigned)((C.n + kCoarseWarps - 1) / kCoarseWarps), nhs), 32 * kCoarseWarps, 0, c->stream>>>((int)C.n, C.inv, b, m, x, hl);
   }
   for (int l = L - 2; l >= 0; --l) {
     MGLevel& A = c->lev[l];
@@ -971,11 +960,11 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     unsigned gx = 1;
     const BRange br = brange(A, hs, nhs, &gx);
     const dim3 grid(gx, nhs);
-    launch_pdl(k_prolong<T>, grid, dim3(kBlock), 0, c->stream, dims(A), dims(B), A.X, cxp, fm, fx, hl, br);
+    ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl, br);
     for (int s = 0; s < deg; ++s) {
       if (l == 0) prof_mark(c, 3);
-      if (l == 0) launch_pdl(k_cheb<TS0, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
-      else launch_pdl(k_cheb<TS, T>, grid, dim3(kBlock), 0, c->stream, dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
+      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
+      else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
       if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }

@@ -16,7 +16,6 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
-#include <utility>
 #include <vector>
 #include "p4d.h"
 
@@ -270,39 +269,8 @@ inline p4d_status dalloc_t(p4d_ctx* c, T** p, size_t count) {
 inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
 // Process-wide count of kernel launches issued by the library (every launch
-// site is written "count_launch(), kernel<<<...>>>(...)" or goes through
-// launch_pdl).
+// site is written "count_launch(), kernel<<<...>>>(...)").
 void count_launch();
-
-// ---- programmatic dependent launch
-// A kernel launched by launch_pdl may be scheduled while its predecessor on
-// the stream is still running, once every block of the predecessor has
-// started and called pdl_trigger (or exited); it calls pdl_wait before its
-// first access to global memory, which returns when the predecessor grid has
-// completed and its writes are visible.  The launch latency and the
-// predecessor's last partial wave overlap instead of adding up.  Outside
-// such a launch both instructions do nothing.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-#ifndef P4D_PDL
-#define P4D_PDL 1
-#endif
-template <typename... K, typename... A>
-void launch_pdl(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
-  count_launch();
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = P4D_PDL ? 1 : 0;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
-}
 
 // This thread's grid-stride share of sum_i (a_i s_i)^2, i in [0, n)
 // (SCALED = false: s_i = 1), with four independent loads in flight per

@@ -33,9 +33,6 @@ __device__ __forceinline__ double insc(const PcArgs& a, bool scaled, int f, int6
   return scaled ? a.sqd[row] * a.iwf[f] : 1.0;
 }
 
-#ifndef P4D_LOAD32
-#define P4D_LOAD32 1
-#endif
 constexpr int kPartBlock = 128;   // nodes per block of the staged particle kernels
 
 // LU factors of T_j / M_j in precision T, radial-major ([nc][NE]): 1/pivot
@@ -123,8 +120,6 @@ __device__ __forceinline__ void local_uv(const PcArgs& a, int64_t e, bool act, d
 template <typename T, bool TRANS, bool FULL>
 __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref_, int fmask, int done, bool scaled,
                        T* b0, T* b1, T* b2) {
-  pdl_wait();
-  pdl_trigger();
   const double* __restrict__ r = rref_.get();
   const double* zm = zref_.get();
   double* zout = zref_.get();
@@ -153,14 +148,13 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
   for (int f = 0; f < 3; ++f) {
     if (!(fmask & (1 << f))) continue;
     const int64_t row = f * nn + n;
-#if P4D_LOAD32
     if (sizeof(T) == sizeof(float) && scaled && !coupled && !(f == 0 && !act)) {
-      // FP32 right-hand side of an FP32 cycle: the scaling in FP32
+      // FP32 right-hand side of an FP32 cycle: the scaling in FP32 (FP64
+      // multiplies are this kernel's cost)
       const float w = (float)(a.iwf[f] * a.sc[f]);
       bs[f][n] = (T)(((float)r[row] * (float)a.sqd[row]) * w);
       continue;
     }
-#endif
     double rf = scaled ? (r[row] * a.sqd[row]) * a.iwf[f] : r[row];
     if (coupled) {
       // A_mc y_c: column c_N is u_m g_s (transposed: M beta v_m)
@@ -178,8 +172,6 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
 template <typename T>
 __global__ void k_store(Grid g, const uint8_t* __restrict__ label, int fmask, const T* __restrict__ x0,
                         const T* __restrict__ x1, const T* __restrict__ x2, VRef zref_) {
-  pdl_wait();
-  pdl_trigger();
   double* __restrict__ zm = zref_.get();
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
@@ -272,25 +264,24 @@ p4d_status apply_t(p4d_ctx* c, VRef r, VRef z, bool scaled) {
   MGLevel& l0 = c->lev[0];
   T* b[3] = {(T*)l0.b[0], (T*)l0.b[2], (T*)l0.b[3]};
   if (c->prm.combine == 0) {
-    launch_pdl(k_load<T, TRANS, FULL>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, a, r, yc, z, 7, 0, scaled, b[0], b[1],
-               b[2]);
+    ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 7, 0, scaled, b[0], b[1], b[2]);
     const int hs[4] = {0, 1, 2, 3};
     P4D_TRYS(mg_vcycle(c, hs, 4));
-    launch_pdl(k_store<T>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, c->g, c->label, 7, (const T*)l0.x[0],
-               (const T*)l0.x[2], (const T*)l0.x[3], z);
+    ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 7, (const T*)l0.x[0], (const T*)l0.x[2],
+                                                      (const T*)l0.x[3], z);
   } else {
     int done = 0;
     for (int t = 0; t < 3; ++t) {
       const int f = TRANS ? c->prm.order[2 - t] : c->prm.order[t];
-      launch_pdl(k_load<T, TRANS, FULL>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, a, r, yc, z, 1 << f, done, scaled,
-                 b[0], b[1], b[2]);
+      ::p4d::count_launch(), k_load<T, TRANS, FULL><<<nblocks(nn), kBlock, 0, c->stream>>>(a, r, yc, z, 1 << f, done, scaled, b[0], b[1],
+                                                                   b[2]);
       int hs[2];
       int nh = 0;
       for (int q = 0; q < 2; ++q)
         if (kHOfField[f][q] >= 0) hs[nh++] = kHOfField[f][q];
       P4D_TRYS(mg_vcycle(c, hs, nh));
-      launch_pdl(k_store<T>, dim3(nblocks(nn)), dim3(kBlock), 0, c->stream, c->g, c->label, 1 << f, (const T*)l0.x[0],
-                 (const T*)l0.x[2], (const T*)l0.x[3], z);
+      ::p4d::count_launch(), k_store<T><<<nblocks(nn), kBlock, 0, c->stream>>>(c->g, c->label, 1 << f, (const T*)l0.x[0], (const T*)l0.x[2],
+                                                        (const T*)l0.x[3], z);
       done |= 1 << f;
     }
   }
