@@ -8,12 +8,15 @@ node, so the small launches of small cells overlap on the GPU and the host
 synchronizes once per column for the whole batch.  The "threads" mode
 (each thread also drives its cell's solve) and "sequential" mode are kept
 for comparison.  An autotuner picks the
-Chebyshev degree and interval per (mesh shape, N_c, precision) by timing
-one solve of the first cell of each grid shape (N_c does not enter the
-multigrid); results are cached in memory and optionally in a JSON file.
+Chebyshev degree and interval per (mesh shape, precision) by timing one
+solve of the first cell of each grid shape (N_c does not enter the
+multigrid: the particle blocks are eliminated exactly), then the block combination (block Jacobi or block Gauss-Seidel
+in each order of the fields) with that smoother; results are cached in
+memory and optionally in a JSON file.
 """
 import concurrent.futures as cf
 import ctypes as C
+import itertools
 import json
 import os
 
@@ -23,6 +26,10 @@ from . import _native as N
 from .solver import P4DSolver
 
 CANDIDATES = ((1, 4.0), (2, 10.0), (3, 10.0), (3, 20.0), (4, 20.0))
+# block combinations after the smoother: block Jacobi, then block
+# Gauss-Seidel in every order of the fields (0 phi_s, 1 phi_e, 2 c_e)
+BJ = (0, (1, 0, 2))
+COMBOS = (BJ,) + tuple((1, o) for o in itertools.permutations((0, 1, 2)))
 
 
 class Autotuner:
@@ -39,16 +46,33 @@ class Autotuner:
         m = case["mesh"]
         return (int(m["nx"]), int(m["ny"]), int(m["nz"]), int(solver.params.precision))
 
+    @staticmethod
+    def _time(solver, b):
+        """Device time of one FGMRES solve with the current options (the first
+        solve after an option change captures the CUDA graphs and is not
+        timed); inf when it does not converge."""
+        solver.solve(b, check=False)
+        _, info = solver.solve(b, check=False)
+        return info["ms_total"] if info["status"] == 0 else float("inf")
+
     def tune(self, solver, state, b):
-        """Best (cheb_degree, cheb_ratio) for this solver's shape by device time
-        of one FGMRES solve per candidate (the linearization is shared)."""
-        best, best_ms = None, float("inf")
+        """(cheb_degree, cheb_ratio, combine, order) for this solver's shape:
+        first the Chebyshev smoother under block Jacobi, then the block
+        combination with that smoother, each by device time of one FGMRES
+        solve (the linearization is shared)."""
+        best_s, best_ms = (2, 10.0), float("inf")
         for deg, ratio in CANDIDATES:
-            solver.set_options(cheb_degree=deg, cheb_ratio=ratio)
-            _, info = solver.solve(b, check=False)
-            if info["status"] == 0 and info["ms_total"] < best_ms:
-                best, best_ms = (deg, ratio), info["ms_total"]
-        return best if best is not None else (2, 10.0)
+            solver.set_options(cheb_degree=deg, cheb_ratio=ratio, combine=BJ[0], order=BJ[1])
+            ms = self._time(solver, b)
+            if ms < best_ms:
+                best_s, best_ms = (deg, ratio), ms
+        best = best_s + BJ
+        for combine, order in COMBOS[1:]:
+            solver.set_options(cheb_degree=best_s[0], cheb_ratio=best_s[1], combine=combine, order=order)
+            ms = self._time(solver, b)
+            if ms < best_ms:
+                best, best_ms = best_s + (combine, order), ms
+        return best
 
     def get(self, solver, case, state, b):
         k = self.key(solver, case)
@@ -85,8 +109,8 @@ class BatchSolver:
                         b = s.residual(self.states[i]).neg_()
                         s.jacobian_update(self.states[i])
                         self.tuned[k] = self.tuner.get(s, c, self.states[i], b)
-                deg, ratio = self.tuned[k]
-                s.set_options(cheb_degree=deg, cheb_ratio=ratio)
+                deg, ratio, combine, order = self.tuned[k]
+                s.set_options(cheb_degree=deg, cheb_ratio=ratio, combine=combine, order=tuple(order))
         torch.cuda.synchronize()
 
     def _linearize(self, i):

@@ -33,8 +33,9 @@ def test_batch_matches_oracle_and_sequential():
     cells = _cells()
     bs = BatchSolver(cells, threads=4, precision=1, rtol=1e-11, maxit=800)
     assert len(bs.tuned) == len({c["gyroid"]["n"] for c in cells})   # one tuning per grid shape
-    for deg, ratio in bs.tuned.values():
+    for deg, ratio, combine, order in bs.tuned.values():
         assert deg in (1, 2, 3, 4) and ratio > 1
+        assert combine in (0, 1) and sorted(order) == [0, 1, 2]
     lock = bs.solve_all("lockstep")
     thr = bs.solve_all("threads")
     seq = bs.solve_all("sequential")
