@@ -15,6 +15,7 @@
 // inverse on the coarsest level.  Stencils are in difference form (slot 13
 // = row sum), see p4d_common.cuh.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 #include <cmath>
 #include "p4d_common.cuh"
@@ -343,17 +344,36 @@ __global__ void k_level_combine(LevelDims d, Ptr4<const double> F, Ptr4<const TV
     const double sc = h == 0 ? sc0 : (h == 1 ? sc1 : (h == 2 ? sc2 : sc3));
     const double* f = pk(F.p, h);
     const TV* v = pk(V.p, h);
-    double diag = 0.0, absoff = 0.0, s = 0.0;
-    for (int o = 0; o < 27; ++o) {
-      const double a = f[o * d.n + n] + (double)v[o * d.n + n];
-      pk(st.p, h)[o * d.n + n] = fromd<TS>(sc * a);
-      if (o == 13) s = a;
-      else { diag -= a; absoff += fabs(a); }
+    if (std::is_same<T, float>::value) {
+      // FP32 cycle: the sum of the fixed and variable parts, the scaling, the
+      // diagonal and the Gershgorin sums in FP32 (the results are stored in
+      // FP32 or BF16; the row sum in slot 13 adds its two parts directly)
+      const float scf = (float)sc;
+      float diag = 0.f, absoff = 0.f, s = 0.f;
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        const float a = (float)f[o * d.n + n] + (float)v[o * d.n + n];
+        pk(st.p, h)[o * d.n + n] = (TS)(scf * a);
+        if (o == 13) s = a;
+        else { diag -= a; absoff += fabsf(a); }
+      }
+      diag += s;
+      if (!(diag > 0.f)) diag = fmaxf(absoff, 1e-30f);
+      pk(dinv.p, h)[n] = (T)(1.0f / (scf * diag));
+      if (pk(mask.p, h)[n]) gl = (double)((absoff + fabsf(diag)) / diag);
+    } else {
+      double diag = 0.0, absoff = 0.0, s = 0.0;
+      for (int o = 0; o < 27; ++o) {
+        const double a = f[o * d.n + n] + (double)v[o * d.n + n];
+        pk(st.p, h)[o * d.n + n] = fromd<TS>(sc * a);
+        if (o == 13) s = a;
+        else { diag -= a; absoff += fabs(a); }
+      }
+      diag += s;
+      if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
+      pk(dinv.p, h)[n] = fromd<T>(1.0 / (sc * diag));
+      if (pk(mask.p, h)[n]) gl = (absoff + fabs(diag)) / diag;
     }
-    diag += s;
-    if (!(diag > 0.0)) diag = fmax(absoff, 1e-300);
-    pk(dinv.p, h)[n] = fromd<T>(1.0 / (sc * diag));
-    if (pk(mask.p, h)[n]) gl = (absoff + fabs(diag)) / diag;
   }
   block_max_to(lam + h, gl);
 }
