@@ -607,12 +607,10 @@ struct LvlPtrs {
 // (9 coefficients and 9 neighbour values per row) issued before their
 // updates.  The kernels are bound by memory latency unless enough loads are
 // in flight; on cube128 level 0 one row per thread with plane-batched loads
-// and two rows with per-offset loads were fastest (4.9-5.0 TB/s), four or
-// more rows per thread slower (register pressure).
-#ifndef P4D_STENCIL_NPT
-#define P4D_STENCIL_NPT 1
-#endif
-constexpr int kNpt = P4D_STENCIL_NPT;
+// was fastest (two rows per thread with per-offset loads came close, four or
+// more were slower from register pressure).  The block ranges of the masks
+// are shared with the one-row-per-thread transfer kernels.
+constexpr int kNpt = 1;
 
 // ax[q] = (A x)_{n[q]} in difference form, for the rows with on[q]:
 // ax = s_13 x_n + sum_{o != 13} s_o (x_{n+off(o)} - x_n).  Every row takes
