@@ -558,7 +558,8 @@ def slab_adjoint(args):
     sig0 = np.where(region == 0, p["sigma_n"], np.where(region == 2, p["sigma_p"], 0.0))
     D0 = np.full(region.size, 1e-14)
     eps0 = np.asarray(m["eps"], float).copy()
-    opts = dict(precision=1, mode=1, rtol=1e-10, maxit=1500, newton_rtol=1e-12, newton_maxit=30,
+    # FGMRES(100): the restart length of the paper's jelly-roll runs
+    opts = dict(precision=1, mode=1, rtol=1e-10, restart=100, maxit=1500, newton_rtol=1e-12, newton_maxit=30,
                 cheb_degree=CHEB[0], cheb_ratio=CHEB[1])
 
     def V_of(s_, d_, e_):
