@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(kBlock) k_maxpy(const double* __restrict__ V, 
   }
 }
 
-// y = x * f(*sp): mode 0 f = s, mode 1 f = 1/s, mode 2 f = 1/sqrt(s) (0 if s == 0)
-__global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int64_t len,
-                        const double* __restrict__ sp, int mode) {
+// y = x * f(*sp): mode 0 f = s, mode 1 f = 1/s, mode 2 f = 1/sqrt(s) (0 if
+// s == 0); x and y may be the same vector (no __restrict__ on them).
+__global__ void k_scale(const double* x, double* y, int64_t len, const double* __restrict__ sp, int mode) {
   // the factor once per block (an FP64 divide and square root per thread
   // cost more than the scaling itself on this GPU)
   __shared__ double sfac;
