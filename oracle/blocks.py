@@ -131,7 +131,8 @@ class BlockPrecond:
             elif f == 0:
                 self.solvers.append(self._phis_solver(disc, dims, degree, coarse_max, ratio))
             else:
-                mg = GMG(self.blocks[f][f], dims, degree=degree, coarse_max=coarse_max, ratio=ratio)
+                mg = GMG(self.blocks[f][f], dims, degree=degree, coarse_max=coarse_max, ratio=ratio,
+                         lengths=disc.lengths)
                 self.solvers.append(mg.vcycle)
         self.idx = idx
         # exact_schur: the whole Schur complement solved by sparse LU, which
@@ -147,7 +148,7 @@ class BlockPrecond:
         node_elec = np.full(disc.nn, -1)
         node_elec[disc.enodes] = disc.etype
         mgs = [GMG(A, dims, mask=disc.act & (node_elec == e), degree=degree,
-                   coarse_max=coarse_max, ratio=ratio) for e in (0, 1)]
+                   coarse_max=coarse_max, ratio=ratio, lengths=disc.lengths) for e in (0, 1)]
         ina = ~disc.act
         dinv = 1.0 / A.diagonal()
 

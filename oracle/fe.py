@@ -136,6 +136,9 @@ class Disc:
             conn[:, l] = (i + a) + self.nnx * ((j + b) + self.nny * (k + c))
         self.conn = conn
         hx, hy, hz = (np.asarray(mesh[h], float) for h in ("hx", "hy", "hz"))
+        # axis lengths, summed in element order (the multigrid's coarsening
+        # rule compares mean element sizes)
+        self.lengths = tuple(sum(float(v) for v in a) for a in (hx, hy, hz))
         self.h = np.stack([hx[i], hy[j], hz[k]], axis=1)          # (nelem, 3)
         self.vol = self.h.prod(axis=1)
         region = np.asarray(mesh["region"])

@@ -7,8 +7,10 @@ algebraic-multigrid V-cycle (section 4, "Preconditioning").  On the
 structured box meshes used here the same role is played by a geometric
 V-cycle, written out plainly:
 
-* coarsening by two along every axis with at least two elements (an odd
-  count keeps its last fine node as a coarse node), until at most
+* coarsening by two (an odd count keeps its last fine node as a coarse
+  node) along the axes with at least two elements -- given the axes'
+  physical lengths, only along those whose mean element size is at most
+  twice the smallest among them (see ``coarsen_flags``) -- until at most
   ``coarse_max`` nodes remain;
 * trilinear prolongation P (Kronecker product of 1D linear interpolations),
   with the rows of masked-out fine nodes set to zero (phi_s has unknowns
@@ -44,8 +46,22 @@ def interp_1d(n_fine_nodes, coarsen):
     return sp.csr_matrix((vals, (rows, cols)), shape=(n_fine_nodes, nc))
 
 
-def coarsen_flags(dims):
-    return tuple((n - 1) >= 2 for n in dims)
+def coarsen_flags(dims, lengths=None):
+    """Axes coarsened from a level with node counts ``dims``.  Without
+    ``lengths``: every axis with at least two elements.  With the axes'
+    physical lengths: of those, only the axes whose mean element size
+    L_a / (n_a - 1) is at most twice the smallest.  The Q1 stiffness couples
+    most strongly across the short element edges and a point smoother
+    removes only errors that are smooth along the weak directions, so the
+    weakly coupled axes are left fine until the elements are near isotropic
+    (the structured-grid counterpart of algebraic coarsening along strong
+    connections, which the paper's AMG performs)."""
+    can = [(n - 1) >= 2 for n in dims]
+    if lengths is None or not any(can):
+        return tuple(can)
+    h = [float(L) / (n - 1) if n >= 2 else 0.0 for L, n in zip(lengths, dims)]
+    hmin = min(ha for ha, c in zip(h, can) if c)
+    return tuple(c and ha <= 2.0 * hmin for c, ha in zip(can, h))
 
 
 def coarse_dims(dims, flags):
@@ -74,7 +90,7 @@ def chebyshev(A, dinv, b, x, degree, lam, ratio):
 
 
 class GMG:
-    def __init__(self, A, dims, mask=None, degree=2, coarse_max=128, ratio=10.0, max_levels=20):
+    def __init__(self, A, dims, mask=None, degree=2, coarse_max=128, ratio=10.0, max_levels=20, lengths=None):
         self.degree = degree
         self.ratio = ratio
         A = sp.csr_matrix(A)
@@ -84,7 +100,7 @@ class GMG:
         self.A, self.P, self.dinv, self.lam, self.dims = [], [], [], [], []
         while True:
             self._add_level(A, dims)
-            flags = coarsen_flags(dims)
+            flags = coarsen_flags(dims, lengths)
             if A.shape[0] <= coarse_max or not any(flags) or len(self.A) >= max_levels:
                 break
             cd = coarse_dims(dims, flags)

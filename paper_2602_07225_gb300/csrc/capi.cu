@@ -229,6 +229,17 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
         for (int l = 0; l < 4; ++l) gpw[node(i + (l & 1), j + ((l >> 1) & 1), nz)] += a4;
       }
 
+  // ---- axis lengths for the multigrid's coarsening rule
+  {
+    const double* hs[3] = {m->hx, m->hy, m->hz};
+    const int ne[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+      double L = 0.0;
+      for (int i = 0; i < ne[a]; ++i) L += hs[a][i];
+      c->len[a] = L;
+    }
+  }
+
   // ---- upload
   P4D_TRYS(upload(c, &c->hx, m->hx, nx));
   P4D_TRYS(upload(c, &c->hy, m->hy, ny));

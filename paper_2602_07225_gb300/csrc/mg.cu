@@ -1016,8 +1016,23 @@ p4d_status mg_plan(p4d_ctx* c) {
     MGLevel& lv = c->lev[L];
     lv.nnx = nnx; lv.nny = nny; lv.nnz = nnz;
     lv.n = (int64_t)nnx * nny * nnz;
-    // every axis with >= 2 elements is coarsened (odd counts included)
-    const int cx = (nnx - 1) >= 2, cy = (nny - 1) >= 2, cz = (nnz - 1) >= 2;
+    // coarsened axes: those with >= 2 elements (odd counts included) whose
+    // mean element size is at most twice the smallest among them -- the
+    // stiffness couples most strongly across short element edges, and the
+    // point smoother reduces only errors smooth along the weak directions,
+    // so weakly coupled axes stay fine until the elements are near isotropic
+    const int nd[3] = {nnx, nny, nnz};
+    int can[3];
+    double hm[3], hmin = 0.0;
+    bool any = false;
+    for (int a = 0; a < 3; ++a) {
+      can[a] = (nd[a] - 1) >= 2;
+      hm[a] = nd[a] >= 2 ? c->len[a] / (nd[a] - 1) : 0.0;
+      if (can[a] && (!any || hm[a] < hmin)) hmin = hm[a];
+      any = any || can[a];
+    }
+    const int cx = can[0] && hm[0] <= 2.0 * hmin, cy = can[1] && hm[1] <= 2.0 * hmin,
+              cz = can[2] && hm[2] <= 2.0 * hmin;
     ++L;
     if (lv.n <= c->prm.coarse_max || !(cx || cy || cz) || L >= kMaxLevels) break;
     lv.cx = cx; lv.cy = cy; lv.cz = cz;

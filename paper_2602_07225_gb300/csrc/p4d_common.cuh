@@ -129,6 +129,7 @@ struct MGLevel {
 struct p4d_ctx {
   // sizes
   int nx = 0, ny = 0, nz = 0;
+  double len[3] = {0.0, 0.0, 0.0};     // axis lengths (element sizes summed in order)
   p4d::Grid g{};
   int64_t nelem = 0, NE = 0, ndof = 0;
   int nc = 0;
