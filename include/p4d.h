@@ -146,7 +146,7 @@ typedef struct {
 } p4d_info;
 
 /* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,
-   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 3, ratio 20). */
+   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10). */
 void p4d_params_default(p4d_params* p);
 
 /* Build a handle for one cell (paper sections 3-4): validates the mesh,

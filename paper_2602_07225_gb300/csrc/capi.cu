@@ -349,8 +349,8 @@ void p4d_params_default(p4d_params* p) {
   p->ocp_p[0] = 4.948384; p->ocp_p[1] = -1.535617;
   p->dt = 10.0; p->i_app = -40.2022; p->diffpot_sign = 1.0;
   p->precision = 1; p->combine = 0; p->order[0] = 1; p->order[1] = 0; p->order[2] = 2;
-  p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 3; p->coarse_max = 128;
-  p->cheb_ratio = 20.0; p->rtol = 1e-8; p->profile = 0;
+  p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
+  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,
