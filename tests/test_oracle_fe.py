@@ -359,3 +359,47 @@ def test_preconditioner_transpose_is_adjoint(combine):
     a = P.apply(x) @ y
     b = x @ P.apply_transpose(y)
     assert abs(a - b) <= 1e-10 * (abs(a) + np.linalg.norm(P.apply(x)) * np.linalg.norm(y) * 1e-6)
+
+
+def test_coarsening_follows_strong_coupling():
+    """The coarsening rule: an axis with >= 2 elements is coarsened only while
+    its mean element size is within twice the smallest; without lengths every
+    such axis is."""
+    from oracle.mg import coarsen_flags, coarse_dims
+    L = (100e-6, 100e-6, 225e-6)                       # cube128: 0.78 / 0.78 / 2.34 um
+    assert coarsen_flags((129, 129, 97), L) == (True, True, False)
+    assert coarsen_flags((65, 65, 97), L) == (True, True, True)
+    assert coarsen_flags((129, 129, 97)) == (True, True, True)
+    assert coarsen_flags((9, 9, 13), (1.0, 1.0, 1.5)) == (True, True, True)   # isotropic enough
+    assert coarsen_flags((9, 2, 13), (1.0, 5.0, 1.0)) == (True, False, True)  # one element: kept
+    assert coarsen_flags((2, 2, 2), (1.0, 1.0, 1.0)) == (False, False, False)
+    # slab-like: z kept for two levels, then everything
+    dims, seq = (2049, 17, 49), []
+    Ls = (2048 * 100e-6 / 128, 16 * 100e-6 / 128, 225e-6)
+    for _ in range(3):
+        f = coarsen_flags(dims, Ls)
+        seq.append(f)
+        dims = coarse_dims(dims, f)
+    assert seq == [(True, True, False), (True, True, False), (True, True, True)]
+
+
+def test_multigrid_factor_with_anisotropic_coarsening():
+    """V-cycle convergence factor on the phi_e block of a box with 3.2:1
+    elements (the bench's aspect ratio): with x, y-only coarsening on the
+    first level it is well below the factor with full coarsening."""
+    from oracle.mg import GMG
+    case = make_box_case(32, 32, (10, 4, 10), 100e-6, (100e-6, 25e-6, 100e-6), 3, 1, state="initial")
+    d, st = _disc(case)
+    J = d.jacobian(st)
+    nn = d.nn
+    A = J[nn:2 * nn, nn:2 * nn].tocsr()
+    rho = {}
+    for name, lengths in (("full", None), ("strong", d.lengths)):
+        mg = GMG(A, (d.nnx, d.nny, d.nnz), degree=2, ratio=10.0, lengths=lengths)
+        x = np.random.default_rng(0).standard_normal(nn)
+        e0 = np.linalg.norm(x)
+        for _ in range(10):
+            x = x + mg.vcycle(-(A @ x))
+        rho[name] = (np.linalg.norm(x) / e0) ** 0.1
+    # measured: 0.46 with full coarsening, 0.24 with the rule
+    assert rho["strong"] < 0.3 and rho["strong"] < 0.6 * rho["full"], rho
