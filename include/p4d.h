@@ -114,7 +114,10 @@ typedef struct {
   int32_t maxit;        /* maximum FGMRES iterations per solve */
   int32_t mode;         /* 0: FULL (Krylov on all unknowns); 1: REDUCED (Krylov on the Schur system) */
   int32_t cheb_degree;  /* Chebyshev smoothing steps before and after the coarse correction (>= 1) */
-  int32_t coarse_max;   /* coarsen while a level has more than this many nodes (>= 8) */
+  int32_t coarse_max;   /* coarsen while a level has more than this many nodes (>= 8); a
+                           level coarsens by two the axes with >= 2 elements whose
+                           mean element size is at most twice the smallest of them
+                           (weakly coupled axes of anisotropic elements stay fine) */
   double cheb_ratio;    /* Chebyshev interval [lam/ratio, lam] on D^-1 A */
   double rtol;          /* relative residual target of FGMRES in the scaled norm */
   int32_t profile;      /* 1: time phases and kernel classes of each solve with CUDA events
