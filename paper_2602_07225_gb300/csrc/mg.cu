@@ -262,6 +262,129 @@ __global__ void __launch_bounds__(32 * kRapWarps) k_rap_diag(LevelDims fd, Level
   rap_finish<TV>(my, rs_l, cin, 0, lane, pk(out.p, h), cd.n, C);
 }
 
+// V_1 = P^T diag(m s) P by gathering: with a diagonal operator and a
+// tensor-product P, entry (C, C + o) is sum_f w_C(f) m_f s_f w_{C+o}(f) over
+// the fine nodes f in both supports, and it factors by axis.  One thread per
+// coarse node: the m s values of its (at most 3 x 3 x 3) support nodes, the
+// per-axis weight products q_a[d][t] = w_C(t) w_{C+d-1}(t) of support entry t,
+// then three passes (x, y, z) give all 27 slots.  Slot 13 holds the row sum
+// sum_f w_C(f) m_f s_f (a fine node's interpolation weights sum to one).
+template <typename TV>
+__global__ void __launch_bounds__(128) k_rap_diag_g(LevelDims fd, LevelDims cd, Xfer X, Ptr4<const double> s,
+                                                    Ptr4<const uint8_t> fm, Ptr4<const uint8_t> cm,
+                                                    Ptr4<TV> out) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = blockIdx.y;
+  if (C >= (int)cd.n) return;
+  TV* o_ = pk(out.p, h);
+  const int64_t cn = cd.n;
+  if (!pk(cm.p, h)[C]) {
+#pragma unroll
+    for (int o = 0; o < 27; ++o) o_[o * cn + C] = (TV)0;
+    return;
+  }
+  int I, J, K;
+  node_ijk(cd, (int64_t)C, I, J, K);
+  const int Ic[3] = {I, J, K};
+  const int ncd[3] = {cd.nnx, cd.nny, cd.nnz};
+  int f[3][3];      // support fine index per axis and entry (-1: none)
+  TV w[3][3];       // its weight w_C
+  TV q[3][3][3];    // [axis][offset d][entry t]: w_C(t) w_{C+d-1}(t)
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int* sup = X.a[a].sup;
+    const TV* sw = supw_t<TV>(X.a[a]);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      f[a][t] = sup[Ic[a] * 3 + t];
+      w[a][t] = f[a][t] >= 0 ? sw[Ic[a] * 3 + t] : (TV)0;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int I2 = Ic[a] + d - 1;
+      const bool in = I2 >= 0 && I2 < ncd[a];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        TV wv = (TV)0;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int g = in ? sup[I2 * 3 + u] : -1;
+          if (f[a][t] >= 0 && g == f[a][t]) wv = sw[I2 * 3 + u];
+        }
+        q[a][d][t] = w[a][t] * wv;
+      }
+    }
+  }
+  // m s of the support nodes
+  const double* sv = pk(s.p, h);
+  const uint8_t* m = pk(fm.p, h);
+  TV S[3][3][3];   // [tz][ty][tx]
+#pragma unroll
+  for (int tz = 0; tz < 3; ++tz)
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) {
+        TV v = (TV)0;
+        if (f[0][tx] >= 0 && f[1][ty] >= 0 && f[2][tz] >= 0) {
+          const int64_t fi = f[0][tx] + (int64_t)fd.nnx * (f[1][ty] + (int64_t)fd.nny * f[2][tz]);
+          if (m[fi]) v = (TV)sv[fi];
+        }
+        S[tz][ty][tx] = v;
+      }
+  // row sum
+  TV rs = (TV)0;
+#pragma unroll
+  for (int tz = 0; tz < 3; ++tz)
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) rs += w[2][tz] * (w[1][ty] * (w[0][tx] * S[tz][ty][tx]));
+  // x pass: T1[dx][tz][ty]; y pass: T2[dx][dy][tz]; z pass: the slots
+  TV T1[3][3][3];
+#pragma unroll
+  for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+    for (int tz = 0; tz < 3; ++tz)
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty) {
+        TV acc = (TV)0;
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) acc += q[0][dx][tx] * S[tz][ty][tx];
+        T1[dx][tz][ty] = acc;
+      }
+  TV T2[3][3][3];
+#pragma unroll
+  for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int tz = 0; tz < 3; ++tz) {
+        TV acc = (TV)0;
+#pragma unroll
+        for (int ty = 0; ty < 3; ++ty) acc += q[1][dy][ty] * T1[dx][tz][ty];
+        T2[dx][dy][tz] = acc;
+      }
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int o = dx + 3 * dy + 9 * dz;
+        TV v;
+        if (o == 13) {
+          v = rs;
+        } else {
+          TV acc = (TV)0;
+#pragma unroll
+          for (int tz = 0; tz < 3; ++tz) acc += q[2][dz][tz] * T2[dx][dy][tz];
+          v = acc;
+        }
+        o_[o * cn + C] = v;
+      }
+}
+
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
@@ -1250,7 +1373,7 @@ p4d_status mg_update_levels(p4d_ctx* c, const double* svar, const double* sch) {
     if (l == 1) {
       Ptr4<const double> s;
       for (int h = 0; h < kNH; ++h) s.p[h] = svar + (size_t)fh[h] * nn;
-      ::p4d::count_launch(), k_rap_diag<TV><<<dim3(nblocks(B.n, kRapWarps), kNH), 32 * kRapWarps, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
+      ::p4d::count_launch(), k_rap_diag_g<TV><<<dim3(nblocks(B.n, 128), kNH), 128, 0, c->stream>>>(dims(A), dims(B), A.X, s, fm, cm, out);
     } else {
       Ptr4<const TV> fst, frs;
       for (int h = 0; h < kNH; ++h) { fst.p[h] = (const TV*)A.Vvar + (size_t)h * 27 * A.n; frs.p[h] = nullptr; }
