@@ -233,35 +233,6 @@ __global__ void __launch_bounds__(32 * kRapWarps) k_rap(LevelDims fd, LevelDims 
   rap_finish<TV>(my, rs_l, cin, identity_out, lane, pk(out.p, h), cd.n, C);
 }
 
-// V_1 = P^T diag(m s) P (level-0 variable part is diagonal), in precision TV.
-template <typename TV>
-__global__ void __launch_bounds__(32 * kRapWarps) k_rap_diag(LevelDims fd, LevelDims cd, Xfer X,
-                                                             Ptr4<const double> s, Ptr4<const uint8_t> fm,
-                                                             Ptr4<const uint8_t> cm, Ptr4<TV> out) {
-  __shared__ TV part[kRapWarps][27 * kRapLd];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t C = (int64_t)blockIdx.x * kRapWarps + warp;
-  const int h = blockIdx.y;
-  if (C >= cd.n) return;   // per warp
-  TV* my = part[warp];
-  if (lane < 27)
-    for (int o = 0; o < 27; ++o) my[o * kRapLd + lane] = (TV)0;
-  int I, J, K;
-  node_ijk(cd, C, I, J, K);
-  const bool cin = pk(cm.p, h)[C];
-  TV rs_l = 0;
-  int fi, fj, fk;
-  int64_t f;
-  TV wf;
-  if (cin && lane < 27 && rap_support<TV>(fd, X, pk(fm.p, h), I, J, K, lane, fi, fj, fk, f, wf)) {
-    const TV a = wf * (TV)pk(s.p, h)[f];
-    rs_l = a;
-    rap_scatter<TV>(X, fi, fj, fk, I, J, K, a, my + lane, kRapLd);
-  }
-  __syncwarp();
-  rap_finish<TV>(my, rs_l, cin, 0, lane, pk(out.p, h), cd.n, C);
-}
-
 // V_1 = P^T diag(m s) P by gathering: with a diagonal operator and a
 // tensor-product P, entry (C, C + o) is sum_f w_C(f) m_f s_f w_{C+o}(f) over
 // the fine nodes f in both supports, and it factors by axis.  One thread per
