@@ -671,7 +671,6 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:
         try:
-            import multiprocessing as mp
             cores = os.cpu_count()
             c = cpu_oracle_leg(r["ndof"])
             cpu = {"value": c["scaled_solves_per_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
