@@ -10,7 +10,6 @@ the discrete adjoint runs backwards in time:
     rhs_{n-1} = -(dR_n/du_{n-1})^T lam_n   (p4d_adjoint_prev)
 with rhs_N = dV/du_N (p4d_voltage_weights).  Every step is a libp4d call.
 """
-import numpy as np
 import torch
 
 from .solver import P4DSolver
