@@ -202,10 +202,15 @@ p4d_status p4d_jvp(p4d_handle h, const double* x, double* y, int transpose);
 p4d_status p4d_precond_apply(p4d_handle h, const double* r, double* z, int transpose);
 
 /* Solve J x = b by right-preconditioned FGMRES(m) to
-   ||s.(b - J x)|| <= rtol ||s.b|| (s: Jacobi scaling with per-field
-   balancing, see the design notes), [device] b and x (in: initial guess,
-   out: solution) of ndof doubles.  info may be NULL.  Returns OK,
-   NOT_CONVERGED (x = last iterate), BREAKDOWN or NONFINITE. */
+   ||s.(b - J x)|| <= rtol ||s.b||, [device] b and x (in: initial guess,
+   out: solution) of ndof doubles.  s is a Jacobi scaling with per-field
+   balancing: s_i = w_f / sqrt(J_ii) for row i of field f, with
+   w_f = 1 / max(||(b / sqrt(diag J))_f||, floor_f) and
+   floor_f = (1e-14 / rtol) ||(sqrt(diag J) u)_f|| (u the linearization
+   state), so every field's residual block counts equally unless its
+   right-hand side is at the rounding level of its own terms.  info may be
+   NULL.  Returns OK, NOT_CONVERGED (x = last iterate), BREAKDOWN or
+   NONFINITE. */
 p4d_status p4d_fgmres_solve(p4d_handle h, const double* b, double* x, p4d_info* info);
 
 /* Adjoint solve J^T lam = g with the transposed block preconditioner,

@@ -14,8 +14,7 @@ What is computed, following the paper:
 * backward Euler in time (section 3, "Temporal discretization");
 * Butler-Volmer kinetics (section 2, "Interfacial kinetics").
 
-Readings taken where the paper is silent or inconsistent (each also listed in
-the design notes of the repository):
+Readings taken where the paper is silent or inconsistent:
 * the particle state lives on electrode *nodes* (one particle per node);
 * the surface flux term of eq. LR enters with a minus sign (derived from
   the flux condition -D dc/dr = i_n/F);
@@ -25,8 +24,12 @@ the design notes of the repository):
   identity grad(c_e)/c_e = grad(ln c_e) with ln c_e replaced by its Q1
   nodal interpolant (the quadrature of the quotient is not specified by the
   paper): the term becomes the kappa_eff-weighted stiffness matrix applied
-  to the nodal values of ln c_e, so it stays in divergence form and its
-  Jacobian block is K_kappa diag(gamma / c_e);
+  to the nodal values of ln c_e and its Jacobian block is
+  K_kappa diag(gamma / c_e).  Unlike the quotient grad(c_h)/c_h taken at the
+  Gauss points (``diffpot_form="quad"``, kept for comparison), this form
+  carries no ionic current when phi_e + gamma ln c_e is uniform, as in the
+  continuous equations; on smooth fields the two forms' solutions differ by
+  a vanishing fraction of the discretization error;
 * the separator regularisation of phi_s is taken to its sigma -> 0 limit:
   phi_s exists only at electrode nodes; other nodes and the grounded face
   carry identity rows, and their phi_s values are lifted to zero wherever
@@ -121,9 +124,12 @@ def radial_operator(r, D, F):
 class Disc:
     """Mesh bookkeeping and coefficients of one cell."""
 
-    def __init__(self, mesh, params):
+    def __init__(self, mesh, params, diffpot_form="ln"):
         self.mesh = mesh
         self.p = dict(params)
+        if diffpot_form not in ("ln", "quad"):
+            raise ValueError(diffpot_form)
+        self.diffpot_form = diffpot_form
         nx, ny, nz = int(mesh["nx"]), int(mesh["ny"]), int(mesh["nz"])
         self.nx, self.ny, self.nz = nx, ny, nz
         self.nnx, self.nny, self.nnz = nx + 1, ny + 1, nz + 1
@@ -261,6 +267,33 @@ class Disc:
         ky = np.kron(K1, M1)
         return sig_t * ((b / a)[:, None, None] * kx[None] + (a / b)[:, None, None] * ky[None])
 
+    def _diffpot_quad(self, ce_e):
+        """The diffusion-potential integrals with the quotient grad(c_h)/c_h
+        of the Q1 field c_h evaluated at the 2x2x2 Gauss points (the other
+        reading of eq. phie-weak): (nelem, 8) values of
+        int_e grad(c_h)/c_h . grad(N_l)."""
+        cq = ce_e @ NREF.T                                   # (nelem, 8 points)
+        out = np.zeros_like(ce_e)
+        for d in range(3):
+            g = (ce_e @ DREF[:, :, d].T) / self.h[:, d][:, None]      # d c_h / dx_d at the points
+            w = (self.vol / 8.0 / self.h[:, d])[:, None]
+            out += (w * g / cq) @ DREF[:, :, d]
+        return out
+
+    def _diffpot_quad_jac(self, ce_e):
+        """Derivative of ``_diffpot_quad`` with respect to the element's
+        nodal c_e: (nelem, 8, 8), [row l, column m]."""
+        cq = ce_e @ NREF.T
+        out = np.zeros((ce_e.shape[0], 8, 8))
+        for d in range(3):
+            hd = self.h[:, d][:, None, None]
+            g = (ce_e @ DREF[:, :, d].T)[:, :, None] / hd                # (e, q, 1)
+            dNq = DREF[None, :, :, d] / hd                               # (e, q, m)
+            dcol = dNq / cq[:, :, None] - g * NREF[None] / cq[:, :, None] ** 2
+            w = (self.vol / 8.0)[:, None, None]
+            out += w * np.einsum("eql,eqm->elm", np.broadcast_to(dNq, dcol.shape), dcol)
+        return out
+
     def _scatter(self, vals):
         return np.bincount(self.conn.ravel(), weights=vals.ravel(), minlength=self.nn)
 
@@ -313,9 +346,13 @@ class Disc:
                                weights=np.einsum("fij,fj->fi", Ke, pf - pf.mean(axis=1, keepdims=True)).ravel(),
                                minlength=self.nn)
         # ionic charge (eq. phie-weak); diffusion potential through the Q1
-        # interpolant of ln c_e
-        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn])
-                            + self._gamma() * self.kap[:, None] * self._lap(np.log(ce)[self.conn]))
+        # interpolant of ln c_e (or, for comparison, the quotient at the
+        # Gauss points)
+        if self.diffpot_form == "quad":
+            dp = self._gamma() * self.kap[:, None] * self._diffpot_quad(ce[self.conn])
+        else:
+            dp = self._gamma() * self.kap[:, None] * self._lap(np.log(ce)[self.conn])
+        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn]) + dp)
         # electrolyte transport (eq. ce-weak), consistent mass
         dce = (ce - st["ce_prev"])[self.conn]
         R_c = self._scatter((self.eps * self.vol)[:, None] * (dce @ MREF) / dt
@@ -371,7 +408,10 @@ class Disc:
         # phi_e - phi_e
         add(nn + R8, nn + C8, self.kap[:, None, None] * Ke)
         # phi_e - c_e: derivative of the diffusion-potential term, K_kappa diag(gamma / c_e)
-        Be = (self._gamma() * self.kap)[:, None, None] * Ke / ce[self.conn][:, None, :]
+        if self.diffpot_form == "quad":
+            Be = (self._gamma() * self.kap)[:, None, None] * self._diffpot_quad_jac(ce[self.conn])
+        else:
+            Be = (self._gamma() * self.kap)[:, None, None] * Ke / ce[self.conn][:, None, :]
         add(nn + R8, 2 * nn + C8, Be)
         # c_e - c_e
         add(2 * nn + R8, 2 * nn + C8, (self.eps / dt)[:, None, None] * Me + self.Deff[:, None, None] * Ke)
