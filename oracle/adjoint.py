@@ -37,8 +37,8 @@ def voltage_weights(d):
     return q
 
 
-def forward(case, nsteps, sigma_e=None, Ds_e=None, eps_e=None, rtol=1e-13):
-    d = Disc(_with_params(case, sigma_e, Ds_e, eps_e), case["params"])
+def forward(case, nsteps, sigma_e=None, Ds_e=None, eps_e=None, rtol=1e-13, material=None, **disc_kw):
+    d = Disc(_with_params(case, sigma_e, Ds_e, eps_e), case["params"], material=material, **disc_kw)
     st = d.state_from_case(case["state"])
     states = [st]
     for _ in range(nsteps):
@@ -72,9 +72,10 @@ def dR_dp_dot(d, st, lam):
     dc = (st["ce"] - st["ce_prev"])[d.conn]
     form = lambda l, M, u: np.einsum("el,elm,em->e", l, M, u)
     g_sig = np.where(d.el, d.eps_s_e ** b * form(lam_s, Ke, phis_l), 0.0)
-    deps = b * d.eps ** (b - 1)
-    g_eps = (deps * p["kappa"] * form(lam_e, Ke, ue) + form(lam_c, Me, dc) / p["dt"]
-             + deps * p["De"] * form(lam_c, Ke, uc))
+    # d(eps^b coef(c_e))/d eps = (b / eps) eps^b coef(c_e)
+    kap_eff, D_eff, _, _ = d.transport(st["ce"])
+    g_eps = ((b / d.eps) * kap_eff * form(lam_e, Ke, ue) + form(lam_c, Me, dc) / p["dt"]
+             + (b / d.eps) * D_eff * form(lam_c, Ke, uc))
     # D_s: dR_cs,j/dD_j = -M_j (L_h c_j)/D_j without the flux; dD_j/dD_e = (vol_e/8)/M_j
     lo, di, up, beta = radial_operator(d.r, d.Ds, p["F"])
     c = st["cs"]
@@ -89,9 +90,9 @@ def dR_dp_dot(d, st, lam):
     return g_sig, g_D, g_eps
 
 
-def gradient(case, nsteps, sigma_e=None, Ds_e=None, eps_e=None, rtol=1e-13):
+def gradient(case, nsteps, sigma_e=None, Ds_e=None, eps_e=None, rtol=1e-13, material=None, **disc_kw):
     """Returns (V, dV/dsigma_e, dV/dDs_e, dV/deps_e)."""
-    d, states, V = forward(case, nsteps, sigma_e, Ds_e, eps_e, rtol)
+    d, states, V = forward(case, nsteps, sigma_e, Ds_e, eps_e, rtol, material, **disc_kw)
     nn = d.nn
     rhs = voltage_weights(d)
     g = [np.zeros(d.nelem) for _ in range(3)]

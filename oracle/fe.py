@@ -121,15 +121,73 @@ def radial_operator(r, D, F):
     return lo, di, up, beta
 
 
-class Disc:
-    """Mesh bookkeeping and coefficients of one cell."""
+def ocp_paper(theta, cathode):
+    """The paper's open-circuit potentials (Appendix "Model Parameters",
+    eqs. ocp_cathode and ocp_anode) and their derivatives dU/dtheta, for the
+    surface stoichiometry theta; `cathode` selects the LiCoO2 curve per entry
+    (else graphite)."""
+    theta = np.asarray(theta, float)
+    cathode = np.broadcast_to(np.asarray(cathode, bool), theta.shape)
+    # LiCoO2, with t = 1.062 theta
+    t = 1.062 * theta
+    ta = [np.tanh(30.834 - 54.4806 * t), np.tanh(52.294 - 50.294 * t), np.tanh(11.0923 - 19.8543 * t),
+          np.tanh(1.4684 - 5.4888 * t), np.tanh((-t + 0.56478) / 0.1316), np.tanh((t - 0.525) / 0.006)]
+    Up = 2.16216 + 0.07645 * ta[0] + 2.1581 * ta[1] - 0.14169 * ta[2] + 0.2051 * ta[3] + 0.2531 * ta[4] \
+        - 0.02167 * ta[5]
+    dUp_dt = (0.07645 * -54.4806 * (1 - ta[0] ** 2) + 2.1581 * -50.294 * (1 - ta[1] ** 2)
+              - 0.14169 * -19.8543 * (1 - ta[2] ** 2) + 0.2051 * -5.4888 * (1 - ta[3] ** 2)
+              + 0.2531 * (-1.0 / 0.1316) * (1 - ta[4] ** 2) - 0.02167 * (1.0 / 0.006) * (1 - ta[5] ** 2))
+    dUp = 1.062 * dUp_dt
+    # graphite
+    terms = [(0.0351, 0.286, 0.083), (-0.0045, 0.849, 0.119), (-0.035, 0.9233, 0.05), (-0.0147, 0.5, 0.034),
+             (-0.102, 0.194, 0.142), (-0.022, 0.9, 0.0164), (-0.011, 0.124, 0.0226), (0.0155, 0.105, 0.029)]
+    ex = np.exp(-120.0 * theta)
+    Un = 0.194 + 1.5 * ex
+    dUn = -180.0 * ex
+    for amp, c0, w in terms:
+        th = np.tanh((theta - c0) / w)
+        Un = Un + amp * th
+        dUn = dUn + amp / w * (1 - th ** 2)
+    return np.where(cathode, Up, Un), np.where(cathode, dUp, dUn)
 
-    def __init__(self, mesh, params, diffpot_form="ln"):
+
+def transport_paper(ce):
+    """Bulk electrolyte conductivity kappa(c_e) and diffusivity D_e(c_e) of
+    the paper (Appendix "Model Parameters", eqs. kappa_app and De_app, at
+    T = 298.15 K where the Arrhenius factors are 1), with their derivatives
+    with respect to c_e (mol/m^3)."""
+    c = np.asarray(ce, float) / 1000.0
+    kap = 0.0911 + 1.9101 * c - 1.052 * c ** 2 + 0.1554 * c ** 3
+    dkap = (1.9101 - 2.104 * c + 0.4662 * c ** 2) / 1000.0
+    De = 5.34e-10 * np.exp(-0.65 * c)
+    dDe = -0.65e-3 * De
+    return kap, dkap, De, dDe
+
+
+class Disc:
+    """Mesh bookkeeping and coefficients of one cell.
+
+    ocp = "linear": the secant OCP of the parameters (the benchmark
+    workloads); "paper": the paper's OCP curves.  transport = "constant":
+    kappa and D_e of the parameters; "paper": the paper's
+    concentration-dependent kappa(c_e), D_e(c_e), taken per element at the
+    element mean of the nodal c_e (a reading: one-point quadrature of the
+    coefficient; the Q1 integrals stay exact for it).  material = "paper"
+    selects both."""
+
+    def __init__(self, mesh, params, diffpot_form="ln", material=None, ocp="linear", transport="constant"):
         self.mesh = mesh
         self.p = dict(params)
-        if diffpot_form not in ("ln", "quad"):
-            raise ValueError(diffpot_form)
+        if material == "paper":
+            ocp, transport = "paper", "paper"
+        elif material not in (None, "constant"):
+            raise ValueError(material)
+        if diffpot_form not in ("ln", "quad") or ocp not in ("linear", "paper") or \
+                transport not in ("constant", "paper"):
+            raise ValueError((diffpot_form, ocp, transport))
         self.diffpot_form = diffpot_form
+        self.ocp_model = ocp
+        self.transport_model = transport
         nx, ny, nz = int(mesh["nx"]), int(mesh["ny"]), int(mesh["nz"])
         self.nx, self.ny, self.nz = nx, ny, nz
         self.nnx, self.nny, self.nnz = nx + 1, ny + 1, nz + 1
@@ -308,15 +366,32 @@ class Disc:
         al = p["alpha"]
         f = p["F"] / (p["R"] * p["T"])
         theta = cs_surf / self.cmax
-        eta = ph_s - ph_e - (self.u0 + self.u1 * theta)
+        U, dU = self.ocp(theta)
+        eta = ph_s - ph_e - U
         i0 = self.kr * c_e ** al * (self.cmax - cs_surf) ** al * cs_surf ** (1.0 - al)
         ea = np.exp(al * f * eta)
         ec = np.exp(-(1.0 - al) * f * eta)
         i_n = i0 * (ea - ec)
         g_eta = i0 * f * (al * ea + (1.0 - al) * ec)
         g_c = al * i_n / c_e
-        g_s = i_n * ((1.0 - al) / cs_surf - al / (self.cmax - cs_surf)) - g_eta * self.u1 / self.cmax
+        g_s = i_n * ((1.0 - al) / cs_surf - al / (self.cmax - cs_surf)) - g_eta * dU / self.cmax
         return i_n, g_eta, g_c, g_s
+
+    def ocp(self, theta):
+        """Open-circuit potential U and dU/dtheta at the electrode nodes."""
+        if self.ocp_model == "paper":
+            return ocp_paper(theta, self.etype == 1)
+        return self.u0 + self.u1 * theta, self.u1
+
+    def transport(self, ce):
+        """Per-element kappa_eff, D_eff and their derivatives with respect to
+        the element-mean c_e (zero for constant coefficients)."""
+        epb = self.eps ** self.p["brug"]
+        if self.transport_model == "constant":
+            z = np.zeros(self.nelem)
+            return epb * self.p["kappa"], epb * self.p["De"], z, z
+        kap, dkap, De, dDe = transport_paper(ce[self.conn].mean(axis=1))
+        return epb * kap, epb * De, epb * dkap, epb * dDe
 
     def _gamma(self):
         p = self.p
@@ -348,15 +423,16 @@ class Disc:
         # ionic charge (eq. phie-weak); diffusion potential through the Q1
         # interpolant of ln c_e (or, for comparison, the quotient at the
         # Gauss points)
+        kap, Deff, _, _ = self.transport(ce)
         if self.diffpot_form == "quad":
-            dp = self._gamma() * self.kap[:, None] * self._diffpot_quad(ce[self.conn])
+            dp = self._gamma() * kap[:, None] * self._diffpot_quad(ce[self.conn])
         else:
-            dp = self._gamma() * self.kap[:, None] * self._lap(np.log(ce)[self.conn])
-        R_e = self._scatter(self.kap[:, None] * self._lap(phie[self.conn]) + dp)
+            dp = self._gamma() * kap[:, None] * self._lap(np.log(ce)[self.conn])
+        R_e = self._scatter(kap[:, None] * self._lap(phie[self.conn]) + dp)
         # electrolyte transport (eq. ce-weak), consistent mass
         dce = (ce - st["ce_prev"])[self.conn]
         R_c = self._scatter((self.eps * self.vol)[:, None] * (dce @ MREF) / dt
-                            + self.Deff[:, None] * self._lap(ce[self.conn]))
+                            + Deff[:, None] * self._lap(ce[self.conn]))
         # reactions (vertex quadrature)
         i_n, *_ = self.kinetics(phis_l, phie, ce, cs[:, -1])
         tau = (1.0 - p["tplus"]) / p["F"]
@@ -405,16 +481,24 @@ class Disc:
             C4 = np.broadcast_to(fconn[:, None, :], Kf.shape)
             kf = self.act[R4] & self.act[C4]
             add(R4[kf], C4[kf], Kf[kf])
+        kap, Deff, dkap, dDeff = self.transport(ce)
         # phi_e - phi_e
-        add(nn + R8, nn + C8, self.kap[:, None, None] * Ke)
+        add(nn + R8, nn + C8, kap[:, None, None] * Ke)
         # phi_e - c_e: derivative of the diffusion-potential term, K_kappa diag(gamma / c_e)
         if self.diffpot_form == "quad":
-            Be = (self._gamma() * self.kap)[:, None, None] * self._diffpot_quad_jac(ce[self.conn])
+            Be = (self._gamma() * kap)[:, None, None] * self._diffpot_quad_jac(ce[self.conn])
+            ue = self._gamma() * self._diffpot_quad(ce[self.conn])
         else:
-            Be = (self._gamma() * self.kap)[:, None, None] * Ke / ce[self.conn][:, None, :]
+            Be = (self._gamma() * kap)[:, None, None] * Ke / ce[self.conn][:, None, :]
+            ue = self._gamma() * self._lap(np.log(ce)[self.conn])
+        # ... and of kappa(c_e) through the element mean: (dkappa/8) (K_e u)_l in every column
+        ue = ue + self._lap(phie[self.conn])
+        Be = Be + (dkap / 8.0)[:, None, None] * ue[:, :, None]
         add(nn + R8, 2 * nn + C8, Be)
-        # c_e - c_e
-        add(2 * nn + R8, 2 * nn + C8, (self.eps / dt)[:, None, None] * Me + self.Deff[:, None, None] * Ke)
+        # c_e - c_e (with dD_e/dc_e through the element mean)
+        Ce = (self.eps / dt)[:, None, None] * Me + Deff[:, None, None] * Ke
+        Ce = Ce + (dDeff / 8.0)[:, None, None] * self._lap(ce[self.conn])[:, :, None]
+        add(2 * nn + R8, 2 * nn + C8, Ce)
         # identity rows of phi_s
         ina = np.flatnonzero(~self.act)
         add(ina, ina, 1.0)

@@ -123,24 +123,32 @@ def per_field_error(disc, x, ref):
 
 
 def newton(disc, st, rtol=1e-10, maxit=20, linear="direct", **kw):
-    """Newton's method on the monolithic residual with backtracking (halving,
-    at most 8 times) on ||R||."""
+    """Newton's method on the monolithic residual, measured in the
+    Jacobi-scaled norm ||D^-1/2 R|| with D = |diag J| at the initial guess
+    (the rows of R span ~17 orders of magnitude, so the plain 2-norm sees
+    only the potential rows), with backtracking (halving, at most 8 times)
+    on that norm.  Converged when the norm has dropped by rtol or when the
+    full step is below 1e-13 of the state in every field (the residual's
+    rounding floor)."""
     st = dict(st)
     x = disc.pack(st)
-    r0 = np.linalg.norm(disc.residual(st))
+    w = 1.0 / np.sqrt(np.abs(disc.jacobian(st).diagonal()))
+    r0 = np.linalg.norm(w * disc.residual(st))
     hist = [r0]
     for it in range(maxit):
+        if hist[-1] <= rtol * r0:
+            break
         ls = LinearSolve(disc, st)
         if linear == "direct":
             dx = ls.direct()
         else:
             dx, _, _ = ls.fgmres(**kw)
-        rn_old = np.linalg.norm(ls.b)
+        rn_old = np.linalg.norm(w * ls.b)
         lam = 1.0
         for _ in range(9):
             trial = disc.with_values(st, x + lam * dx)
             try:
-                rn = np.linalg.norm(disc.residual(trial))
+                rn = np.linalg.norm(w * disc.residual(trial))
             except ValueError:
                 rn = np.inf
             if rn < rn_old or lam < 1e-2:
@@ -149,7 +157,9 @@ def newton(disc, st, rtol=1e-10, maxit=20, linear="direct", **kw):
         x = x + lam * dx
         st = disc.with_values(st, x)
         hist.append(rn)
-        if rn <= rtol * r0:
+        tiny = all(np.linalg.norm(dx[sl]) <= 1e-13 * np.linalg.norm(x[sl]) for sl in disc.field_slices()
+                   if np.linalg.norm(x[sl]) > 0)
+        if tiny:
             break
     return st, hist
 

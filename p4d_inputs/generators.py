@@ -21,35 +21,40 @@ PARAMS_DEFAULT = dict(
 CASES = ("tiny", "cube8", "cube128", "hetero128")
 
 
+def ocp_curve_p(th):
+    """The paper's LiCoO2 open-circuit potential (Appendix, eq. for the
+    cathode), used here only to draw the linear secants."""
+    t = 1.062 * th
+    return (2.16216 + 0.07645 * math.tanh(30.834 - 54.4806 * t)
+            + 2.1581 * math.tanh(52.294 - 50.294 * t)
+            - 0.14169 * math.tanh(11.0923 - 19.8543 * t)
+            + 0.2051 * math.tanh(1.4684 - 5.4888 * t)
+            + 0.2531 * math.tanh((-t + 0.56478) / 0.1316)
+            - 0.02167 * math.tanh((t - 0.525) / 0.006))
+
+
+def ocp_curve_n(th):
+    """The paper's graphite open-circuit potential (Appendix, eq. for the
+    anode), used here only to draw the linear secants."""
+    return (0.194 + 1.5 * math.exp(-120.0 * th)
+            + 0.0351 * math.tanh((th - 0.286) / 0.083)
+            - 0.0045 * math.tanh((th - 0.849) / 0.119)
+            - 0.035 * math.tanh((th - 0.9233) / 0.05)
+            - 0.0147 * math.tanh((th - 0.5) / 0.034)
+            - 0.102 * math.tanh((th - 0.194) / 0.142)
+            - 0.022 * math.tanh((th - 0.9) / 0.0164)
+            - 0.011 * math.tanh((th - 0.124) / 0.0226)
+            + 0.0155 * math.tanh((th - 0.105) / 0.029))
+
+
 def ocp_linear_secants():
-    """Secant lines of the paper's OCP curves (Appendix, eqs. for LiCoO2 and
-    graphite) over the stoichiometry ranges the seeded states draw from:
-    anode theta in [0.5, 0.8], cathode theta in [0.4, 0.6].  Returns
-    ((c0_n, c1_n), (c0_p, c1_p))."""
-    def u_p(th):
-        t = 1.062 * th
-        return (2.16216 + 0.07645 * math.tanh(30.834 - 54.4806 * t)
-                + 2.1581 * math.tanh(52.294 - 50.294 * t)
-                - 0.14169 * math.tanh(11.0923 - 19.8543 * t)
-                + 0.2051 * math.tanh(1.4684 - 5.4888 * t)
-                + 0.2531 * math.tanh((-t + 0.56478) / 0.1316)
-                - 0.02167 * math.tanh((t - 0.525) / 0.006))
-
-    def u_n(th):
-        return (0.194 + 1.5 * math.exp(-120.0 * th)
-                + 0.0351 * math.tanh((th - 0.286) / 0.083)
-                - 0.0045 * math.tanh((th - 0.849) / 0.119)
-                - 0.035 * math.tanh((th - 0.9233) / 0.05)
-                - 0.0147 * math.tanh((th - 0.5) / 0.034)
-                - 0.102 * math.tanh((th - 0.194) / 0.142)
-                - 0.022 * math.tanh((th - 0.9) / 0.0164)
-                - 0.011 * math.tanh((th - 0.124) / 0.0226)
-                + 0.0155 * math.tanh((th - 0.105) / 0.029))
-
+    """Secant lines of the paper's OCP curves over the stoichiometry ranges
+    the seeded states draw from: anode theta in [0.5, 0.8], cathode theta in
+    [0.4, 0.6].  Returns ((c0_n, c1_n), (c0_p, c1_p))."""
     def secant(f, a, b):
         s = (f(b) - f(a)) / (b - a)
         return (f(a) - s * a, s)
-    return secant(u_n, 0.5, 0.8), secant(u_p, 0.4, 0.6)
+    return secant(ocp_curve_n, 0.5, 0.8), secant(ocp_curve_p, 0.4, 0.6)
 
 
 def theoretical_iapp(Lx, Ly, Ln, Lp, eps_s_n, eps_s_p, cmax_n, cmax_p, F, crate=1.0):
@@ -84,9 +89,25 @@ def _node_types(nx, ny, nz, region):
     return an.ravel(), ca.ravel()
 
 
+def radial_grid(nc, theta_bar=None):
+    """Radial node positions r / R_s, r_0 = 0 and r_{nc-1} = 1.  Uniform when
+    theta_bar is None; otherwise a geometric progression (paper section 3,
+    the regular graded particle mesh) whose spacings shrink toward the
+    surface by the constant factor theta_bar^(1/(nc-2)), so that the last
+    spacing is theta_bar times the first (0 < theta_bar < 1)."""
+    if theta_bar is None:
+        return np.linspace(0.0, 1.0, nc)
+    q = theta_bar ** (1.0 / (nc - 2))
+    dr = q ** np.arange(nc - 1)
+    r = np.concatenate([[0.0], np.cumsum(dr)])
+    r /= r[-1]
+    r[-1] = 1.0
+    return r
+
+
 def make_box_case(nx, ny, nz_layers, L_lat, L_layers, nc, seed, *, params=None,
                   hetero=False, rs_cv=0.0, state="seeded", Rs=5e-6, Ds=1e-14,
-                  eps_e=0.3, eps_s=(0.6, 0.5)):
+                  eps_e=0.3, eps_s=(0.6, 0.5), theta_bar=None):
     """Layered anode/separator/cathode box.
 
     state="seeded": linearization state with c_e = 1000(1 + U(-0.05, 0.05)),
@@ -147,7 +168,7 @@ def make_box_case(nx, ny, nz_layers, L_lat, L_layers, nc, seed, *, params=None,
     phie = np.full(nn, -un_ref)
     mesh = dict(nx=nx, ny=ny, nz=nz, hx=hx, hy=hy, hz=hz, region=region, eps=eps,
                 eps_s=eps_s_arr, Rs=Rs_node, Ds=Ds_node, gamma_p=gamma_p,
-                gamma_n=gamma_n, nc=nc, rgrid=np.linspace(0.0, 1.0, nc))
+                gamma_n=gamma_n, nc=nc, rgrid=radial_grid(nc, theta_bar))
     st = dict(phis=phis, phie=phie, ce=ce, cs_node=cs_node, ce_prev=ce.copy(),
               cs_prev_node=cs_node.copy())
     return dict(mesh=mesh, params=p, state=st, seed=seed)

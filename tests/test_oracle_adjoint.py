@@ -11,7 +11,8 @@ def _case():
     return make_box_case(3, 3, (3, 2, 3), 30e-6, (40e-6, 20e-6, 40e-6), 4, 21, state="initial")
 
 
-def test_adjoint_gradient_matches_central_differences():
+@pytest.mark.parametrize("material", ["constant", "paper"])
+def test_adjoint_gradient_matches_central_differences(material):
     case = _case()
     nelem = 3 * 3 * 8
     region = case["mesh"]["region"]
@@ -19,7 +20,7 @@ def test_adjoint_gradient_matches_central_differences():
     Ds0 = np.full(nelem, 1e-14)
     eps0 = case["mesh"]["eps"].copy()
     nsteps = 3
-    V, gs, gD, ge = gradient(case, nsteps, sigma_e=sig0, Ds_e=Ds0, eps_e=eps0)
+    V, gs, gD, ge = gradient(case, nsteps, sigma_e=sig0, Ds_e=Ds0, eps_e=eps0, material=material)
     rng = np.random.default_rng(5)
     el = np.flatnonzero((region == 0) | (region == 2))
     for e in rng.choice(el, 4, replace=False):
@@ -31,6 +32,6 @@ def test_adjoint_gradient_matches_central_differences():
                 p[e] += sgn * h
                 kw = dict(sigma_e=sig0, Ds_e=Ds0, eps_e=eps0)
                 kw[{"sigma": "sigma_e", "Ds": "Ds_e", "eps": "eps_e"}[name]] = p
-                vals.append(forward(case, nsteps, **kw)[2])
+                vals.append(forward(case, nsteps, material=material, **kw)[2])
             fd = (vals[0] - vals[1]) / (2 * h)
             assert g[e] == pytest.approx(fd, rel=2e-4, abs=1e-9 * abs(V) / base[e]), (name, e, g[e], fd)
