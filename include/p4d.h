@@ -122,6 +122,10 @@ typedef struct {
   double rtol;          /* relative residual target of FGMRES in the scaled norm */
   int32_t profile;      /* 1: time phases and kernel classes of each solve with CUDA events
                            (fields ms_* / n_* of p4d_info); 0: off */
+  int32_t ocp_model;    /* 0: the linear OCP of ocp_n / ocp_p; 1: the paper's open-circuit
+                           potential curves (Appendix "Model Parameters": graphite anode,
+                           LiCoO2 cathode with theta~ = 1.062 theta), U and dU/dtheta in the
+                           kinetics of the residual and the Jacobian */
 } p4d_params;
 
 /* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */
@@ -146,10 +150,15 @@ typedef struct {
   double ms_smooth0;      /* level-0 Chebyshev steps that apply the stencil (all hierarchies) */
   int32_t n_smooth0;      /* number of those launches */
   int32_t n_jvp;          /* number of operator applications timed in ms_jvp */
+  double rel_res_unscaled;          /* final ||b - J x||_2 / ||b||_2, unscaled, full system */
+  double rel_res_block_unscaled[4]; /* ||(b - J x)_f|| / ||b_f|| per field phi_s, phi_e, c_e, c_s */
+  int32_t nsolves;        /* linear solves behind this report (1; p4d_newton_solve: all of its solves) */
+  int32_t iters_total;    /* FGMRES iterations summed over those solves */
 } p4d_info;
 
 /* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,
-   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10). */
+   restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10,
+   linear OCP). */
 void p4d_params_default(p4d_params* p);
 
 /* Build a handle for one cell (paper sections 3-4): validates the mesh,
@@ -267,9 +276,12 @@ void p4d_batch_destroy(p4d_batch b);
    first call before any stream capture.  All calls share the one array, so
    calls whose kernels overlap on the GPU (several streams or handles at
    once) race; nothing in it needs to start at zero (each entry is written
-   before it is read within a call).  Returns INVALID_ARG when the handle has
-   more than P4D_NOALLOC_MAX_NELEC electrode nodes, when x == y or before a
-   p4d_jacobian_update; otherwise as p4d_jvp. */
+   before it is read within a call).  The result agrees with p4d_jvp's to
+   rounding (the non-transposed product forms phi_e + (gamma/c_e) c_e inside
+   the stencil loop rather than in a separate pass).  Returns INVALID_ARG
+   when the handle has more than P4D_NOALLOC_MAX_NELEC electrode nodes, when
+   x == y, before a p4d_jacobian_update, or when the current device is not
+   the one the handle was set up on; otherwise as p4d_jvp. */
 p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose);
 
 /* Newton's method for one backward-Euler step (paper section 4: the
@@ -282,7 +294,8 @@ p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpo
    decreases.  Converged when ||D^-1/2 R|| <= rtol ||D^-1/2 R_0|| or when the
    full Newton step is below 1e-10 of the state in every field (the
    residual has a rounding floor); NOT_CONVERGED after maxit iterations.
-   iters and info (last linear solve) may be NULL.  Returns OK,
+   iters and info may be NULL; info describes the last linear solve, except
+   nsolves and iters_total, which count all of the step's linear solves.  Returns OK,
    NOT_CONVERGED, DOMAIN or a linear-solve failure.  Leaves the handle
    linearized at the last accepted iterate but one. */
 p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce, double* cs,
@@ -293,6 +306,13 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
    doubles): the mean of phi_s over the applied-current face Gamma_p
    (bilinear face weights; phi_s = 0 on the grounded face). */
 p4d_status p4d_voltage_weights(p4d_handle h, double* q);
+
+/* Terminal voltage V = q . u = the mean of phi_s over Gamma_p (the
+   objective of the adjoint, paper section 3's sensitivity motivation),
+   from phis [device, nnode doubles] into v [device, one double].
+   Asynchronous on the handle's stream.  Errors: INVALID_ARG (NULL, or no
+   applied-current face). */
+p4d_status p4d_terminal_voltage(p4d_handle h, const double* phis, double* v);
 
 /* Accumulate g_p += -lam^T dR/dp at `state` (the residual of one
    backward-Euler step, paper section 4) for the per-element parameters
@@ -311,6 +331,14 @@ p4d_status p4d_adjoint_prev(p4d_handle h, const double* lam, double* out);
 /* Number of CUDA kernels the library has launched in this process so far
    (instrumentation for benchmarks; thread-safe, never reset). */
 long long p4d_launch_count(void);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops
+   per FMA; eight independent dependent-FMA chains per thread over 8 blocks
+   of 256 threads per SM, best of three timed launches on the legacy default
+   stream, which it synchronizes).  The denominator of the FP64 kernels'
+   roofline fractions (instrumentation for benchmarks, like
+   p4d_launch_count).  Errors: INVALID_ARG (NULL), CUDA. */
+p4d_status p4d_fp64_fma_rate(double* tflops);
 
 /* Human-readable name of a status. */
 const char* p4d_status_string(p4d_status s);

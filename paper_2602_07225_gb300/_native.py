@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("combine", C.c_int32), ("order", C.c_int32 * 3),
                 ("restart", C.c_int32), ("maxit", C.c_int32), ("mode", C.c_int32),
                 ("cheb_degree", C.c_int32), ("coarse_max", C.c_int32), ("cheb_ratio", C.c_double),
-                ("rtol", C.c_double), ("profile", C.c_int32)]
+                ("rtol", C.c_double), ("profile", C.c_int32), ("ocp_model", C.c_int32)]
 
 
 class State(C.Structure):
@@ -56,13 +56,18 @@ class Info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32), ("reorth", C.c_int32),
                 ("rel_res", C.c_double), ("rel_res_block", C.c_double * 4), ("ms_total", C.c_double),
                 ("ms_precond", C.c_double), ("ms_jvp", C.c_double), ("ms_ortho", C.c_double),
-                ("ms_smooth0", C.c_double), ("n_smooth0", C.c_int32), ("n_jvp", C.c_int32)]
+                ("ms_smooth0", C.c_double), ("n_smooth0", C.c_int32), ("n_jvp", C.c_int32),
+                ("rel_res_unscaled", C.c_double), ("rel_res_block_unscaled", C.c_double * 4),
+                ("nsolves", C.c_int32), ("iters_total", C.c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, restarts=self.restarts, status=self.status, reorth=self.reorth,
                     rel_res=self.rel_res, rel_res_block=list(self.rel_res_block), ms_total=self.ms_total,
                     ms_precond=self.ms_precond, ms_jvp=self.ms_jvp, ms_ortho=self.ms_ortho,
-                    ms_smooth0=self.ms_smooth0, n_smooth0=self.n_smooth0, n_jvp=self.n_jvp)
+                    ms_smooth0=self.ms_smooth0, n_smooth0=self.n_smooth0, n_jvp=self.n_jvp,
+                    rel_res_unscaled=self.rel_res_unscaled,
+                    rel_res_block_unscaled=list(self.rel_res_block_unscaled), nsolves=self.nsolves,
+                    iters_total=self.iters_total)
 
 
 # name -> (restype, argtypes); every symbol declared in include/p4d.h
@@ -84,6 +89,7 @@ SIGNATURES = {
     "p4d_newton_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(Info)]),
     "p4d_voltage_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "p4d_terminal_voltage": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "p4d_param_grad": (C.c_int, [C.c_void_p, C.POINTER(State), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p4d_adjoint_prev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "p4d_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
@@ -91,6 +97,7 @@ SIGNATURES = {
     "p4d_batch_adjoint_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(Info)]),
     "p4d_batch_destroy": (None, [C.c_void_p]),
     "p4d_launch_count": (C.c_longlong, []),
+    "p4d_fp64_fma_rate": (C.c_int, [C.POINTER(C.c_double)]),
     "p4d_status_string": (C.c_char_p, [C.c_int]),
 }
 

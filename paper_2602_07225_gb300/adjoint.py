@@ -41,7 +41,7 @@ class TerminalVoltage(torch.autograd.Function):
             if n % checkpoint == 0 or n == nsteps:
                 ckpt[n] = _clone(st)
         q = s.voltage_weights()
-        V = torch.dot(q[: s.nn], st["phis"])
+        V = s.terminal_voltage(st["phis"])[0]
         ctx.solver, ctx.ckpt, ctx.nsteps, ctx.checkpoint, ctx.q, ctx.newton = s, ckpt, nsteps, checkpoint, q, newton
         ctx.in_device = sigma_e.device
         return V.detach().to(sigma_e.device)

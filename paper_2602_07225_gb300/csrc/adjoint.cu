@@ -57,6 +57,23 @@ __global__ void k_voltage_weights(int64_t nn, int64_t ndof, const double* __rest
   q[i] = i < nn ? gpw[i] * inv_area : 0.0;
 }
 
+// V = sum_n gpw_n phi_s,n / |Gamma_p| in one block (fixed order: strided
+// partial sums, then a tree over the threads).
+__global__ void __launch_bounds__(256) k_terminal_voltage(int64_t nn, const double* __restrict__ gpw,
+                                                          const double* __restrict__ phis, double inv_area,
+                                                          double* __restrict__ v) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t n = threadIdx.x; n < nn; n += 256) acc = fma(gpw[n], phis[n], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *v = red[0] * inv_area;
+}
+
 // P_j = lam_cs,j^T Lref c_s,j / R_j^2 per electrode node
 __global__ void k_grad_particle(int64_t NE, int nc, int64_t nn, const double* __restrict__ lam,
                                 const double* __restrict__ cs, const double* __restrict__ rref,
@@ -205,6 +222,7 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
   const double r0 = total(f0);
   double rel = r0 > 0 ? 1.0 : 0.0;
   int it = 0;
+  int nsolves = 0, iters_total = 0;
   p4d_status result = P4D_ERR_NOT_CONVERGED;
   bool linearized_here = true;
   for (; it <= maxit; ++it) {
@@ -215,6 +233,10 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
     P4D_TRY(cudaMemsetAsync(dlt, 0, ndof * sizeof(double), h->stream));
     p4d_info li;
     const p4d_status ls = fgmres(h, R, dlt, &li, 0);   // J dlt = R, step = -dlt
+    ++nsolves;
+    iters_total += li.iters;
+    li.nsolves = nsolves;
+    li.iters_total = iters_total;
     if (info) *info = li;
     if (ls != P4D_OK && ls != P4D_ERR_NOT_CONVERGED) return ls;
     // step-length test: the residual has a rounding floor (the phi_s rows,
@@ -260,6 +282,13 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
 p4d_status p4d_voltage_weights(p4d_handle h, double* q) {
   if (!h || !q || !(h->gp_area > 0)) return P4D_ERR_INVALID_ARG;
   ::p4d::count_launch(), k_voltage_weights<<<nblocks(h->ndof), kBlock, 0, h->stream>>>(h->g.nn, h->ndof, h->gpw, 1.0 / h->gp_area, q);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status p4d_terminal_voltage(p4d_handle h, const double* phis, double* v) {
+  if (!h || !phis || !v || !(h->gp_area > 0)) return P4D_ERR_INVALID_ARG;
+  ::p4d::count_launch(), k_terminal_voltage<<<1, 256, 0, h->stream>>>(h->g.nn, h->gpw, phis, 1.0 / h->gp_area, v);
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }

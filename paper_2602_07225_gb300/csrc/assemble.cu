@@ -123,7 +123,50 @@ __global__ void k_maxdiag(const double* __restrict__ st, int64_t nn, unsigned lo
 struct Kin {
   double F, Rg, T, alpha, tau, i_app, gamma;
   double k[2], cmax[2], u0[2], u1[2];
+  int ocp_model;   // 0 linear, 1 the paper's curves
 };
+
+// Open-circuit potential U(theta) and dU/dtheta of electrode et (0 graphite
+// anode, 1 LiCoO2 cathode).  ocp_model 1: the paper's curves (Appendix
+// "Model Parameters"), written as base + sum_i amp_i tanh(a_i + b_i t) with
+// t = 1.062 theta for the cathode and t = theta (plus 1.5 exp(-120 theta))
+// for the anode; dU/dtheta = dt/dtheta sum_i amp_i b_i (1 - tanh^2).
+__device__ inline void ocp_eval(const Kin& kn, int et, double theta, double& U, double& dU) {
+  if (kn.ocp_model == 0) {
+    U = kn.u0[et] + kn.u1[et] * theta;
+    dU = kn.u1[et];
+    return;
+  }
+  if (et == 1) {
+    constexpr double amp[6] = {0.07645, 2.1581, -0.14169, 0.2051, 0.2531, -0.02167};
+    constexpr double a[6] = {30.834, 52.294, 11.0923, 1.4684, 0.56478 / 0.1316, -0.525 / 0.006};
+    constexpr double b[6] = {-54.4806, -50.294, -19.8543, -5.4888, -1.0 / 0.1316, 1.0 / 0.006};
+    const double t = 1.062 * theta;
+    double u = 2.16216, du = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double th = tanh(a[q] + b[q] * t);
+      u += amp[q] * th;
+      du += amp[q] * b[q] * (1.0 - th * th);
+    }
+    U = u;
+    dU = 1.062 * du;
+  } else {
+    constexpr double amp[8] = {0.0351, -0.0045, -0.035, -0.0147, -0.102, -0.022, -0.011, 0.0155};
+    constexpr double c0[8] = {0.286, 0.849, 0.9233, 0.5, 0.194, 0.9, 0.124, 0.105};
+    constexpr double w[8] = {0.083, 0.119, 0.05, 0.034, 0.142, 0.0164, 0.0226, 0.029};
+    const double ex = exp(-120.0 * theta);
+    double u = 0.194 + 1.5 * ex, du = -180.0 * ex;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double th = tanh((theta - c0[q]) / w[q]);
+      u += amp[q] * th;
+      du += amp[q] / w[q] * (1.0 - th * th);
+    }
+    U = u;
+    dU = du;
+  }
+}
 
 // Butler-Volmer (paper section 2, "Interfacial kinetics") at one electrode
 // node; returns false outside the domain of the exchange current.
@@ -136,7 +179,9 @@ __device__ inline bool kinetics(const Kin& kn, int et, double phis, double phie,
   }
   const double f = kn.F / (kn.Rg * kn.T);
   const double al = kn.alpha;
-  const double eta = phis - phie - (kn.u0[et] + kn.u1[et] * cs / cmax);
+  double U, dU;
+  ocp_eval(kn, et, cs / cmax, U, dU);
+  const double eta = phis - phie - U;
   double i0;
   if (al == 0.5) i0 = kn.k[et] * sqrt(ce) * sqrt(cmax - cs) * sqrt(cs);
   else i0 = kn.k[et] * pow(ce, al) * pow(cmax - cs, al) * pow(cs, 1.0 - al);
@@ -145,7 +190,7 @@ __device__ inline bool kinetics(const Kin& kn, int et, double phis, double phie,
   in = i0 * (ea - ec);
   ge = i0 * f * (al * ea + (1.0 - al) * ec);
   gc = al * in / ce;
-  gs = in * ((1.0 - al) / cs - al / (cmax - cs)) - ge * kn.u1[et] / cmax;
+  gs = in * ((1.0 - al) / cs - al / (cmax - cs)) - ge * dU / cmax;
   return true;
 }
 
@@ -418,6 +463,7 @@ Kin make_kin(const p4d_params& p) {
   k.cmax[0] = p.cmax_n; k.cmax[1] = p.cmax_p;
   k.u0[0] = p.ocp_n[0]; k.u0[1] = p.ocp_p[0];
   k.u1[0] = p.ocp_n[1]; k.u1[1] = p.ocp_p[1];
+  k.ocp_model = p.ocp_model;
   return k;
 }
 

@@ -122,6 +122,7 @@ bool valid_params(const p4d_params* p) {
   if (p->coarse_max < 8) return false;
   if (!(p->rtol > 0)) return false;
   if (!(p->alpha > 0 && p->alpha < 1)) return false;
+  if (p->ocp_model < 0 || p->ocp_model > 1) return false;
   bool seen[3] = {false, false, false};
   for (int i = 0; i < 3; ++i) {
     if (p->order[i] < 0 || p->order[i] > 2 || seen[p->order[i]]) return false;
@@ -302,6 +303,7 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRYS(assemble_fixed(c, c->eps_e, c->epss_e, c->region));
   P4D_TRYS(mg_plan(c));
   P4D_TRYS(mg_setup_fixed(c));
+  P4D_TRYS(mf_setup(c));
 
   // ---- Krylov workspace
   c->mcap = prm->restart;
@@ -350,7 +352,7 @@ void p4d_params_default(p4d_params* p) {
   p->dt = 10.0; p->i_app = -40.2022; p->diffpot_sign = 1.0;
   p->precision = 1; p->combine = 0; p->order[0] = 1; p->order[1] = 0; p->order[2] = 2;
   p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
-  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0;
+  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0; p->ocp_model = 0;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,
@@ -372,6 +374,11 @@ p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* 
   p4d_ctx* c = new (std::nothrow) p4d_ctx();
   if (!c) return P4D_ERR_OOM;
   c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return P4D_ERR_CUDA;
+  }
   p4d_status s = setup_impl(c, m, prm);
   if (s == P4D_OK && st) s = p4d_jacobian_update(c, st);
   if (s != P4D_OK && s != P4D_ERR_DOMAIN) {
@@ -527,6 +534,64 @@ p4d_status p4d_batch_adjoint_solve(p4d_batch B, const double* const* g, double* 
 }
 
 long long p4d_launch_count(void) { return p4d::g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"
+
+namespace p4d {
+namespace {
+// Sink of the FP64 rate probe (keeps its arithmetic live).
+__device__ double g_fma_sink;
+
+// Eight independent dependent-FMA chains per thread: the FP64 pipe is the
+// only busy unit (no memory traffic inside the loop).
+__global__ void __launch_bounds__(256) k_fp64_fma(int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = 1.0 + 1e-3 * (threadIdx.x + q);
+  for (int t = 0; t < iters; ++t) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = fma(a[q], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += a[q];
+  if (s == 12345.678) g_fma_sink = s;   // never true; the compiler cannot drop the chains
+}
+}  // namespace
+}  // namespace p4d
+
+extern "C" {
+
+p4d_status p4d_fp64_fma_rate(double* tflops) {
+  if (!tflops) return P4D_ERR_INVALID_ARG;
+  *tflops = 0.0;
+  int dev = 0, sms = 0;
+  P4D_TRY(cudaGetDevice(&dev));
+  P4D_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  P4D_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return P4D_ERR_CUDA;
+  }
+  float best = 0.f;
+  p4d_status st = P4D_OK;
+  for (int rep = 0; rep < 4 && st == P4D_OK; ++rep) {
+    cudaEventRecord(e0, 0);
+    ::p4d::count_launch(), p4d::k_fp64_fma<<<blocks, threads>>>(iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = P4D_ERR_CUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;   // the first launch warms up
+  }
+  if (cudaGetLastError() != cudaSuccess) st = P4D_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == P4D_OK && best > 0.f) *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+  return st;
+}
 
 const char* p4d_status_string(p4d_status s) {
   switch (s) {

@@ -203,12 +203,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of g_noalloc_tloc on the current device, looked up once per
+// Device address of g_noalloc_tloc on the handle's device, looked up once per
 // device with that device current (in host code the array's name is only a
-// stand-in for the device symbol, never a device address).
-p4d_status noalloc_scratch(double** out) {
+// stand-in for the device symbol, never a device address).  The handle's
+// kernels run on its stream, on the device it was set up on; a caller with
+// another device current gets INVALID_ARG instead of another GPU's array.
+p4d_status noalloc_scratch(const p4d_ctx* h, double** out) {
   int dev = -1;
   P4D_TRY(cudaGetDevice(&dev));
+  if (dev != h->device) return P4D_ERR_INVALID_ARG;
   if (dev < 0 || dev >= kMaxDevices) return P4D_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
@@ -231,7 +234,7 @@ extern "C" p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, 
   if (!h || !x || !y || x == y || !h->linearized) return P4D_ERR_INVALID_ARG;
   if (h->NE > (int64_t)P4D_NOALLOC_MAX_NELEC) return P4D_ERR_INVALID_ARG;
   double* tloc = nullptr;
-  P4D_TRYS(noalloc_scratch(&tloc));
+  P4D_TRYS(noalloc_scratch(h, &tloc));
   JvpArgs a = make_args(h);
   a.tloc = tloc;   // each entry read by the particle rows is written first by the macro rows
   const int64_t nn = h->g.nn;

@@ -671,8 +671,13 @@ p4d_status fg_finish_launch(FgRun& r) {
   P4D_TRYS(jvp_full(c, r.x, c->r0, r.trans, r.b, true));
   ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, nn, c->ndof, c->part);
   ::p4d::count_launch(), k_sum4<<<1, 128, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 24);
+  // and unscaled: ||(b - J x)_f||^2 = ||(sqrt(d) r0)_f||^2 / w_f^2, ||b_f||^2
+  ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->r0, c->sqd, nn, c->ndof, c->part);
+  ::p4d::count_launch(), k_sum4<<<1, 128, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 32);
+  ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, c->stream>>>(r.b, nn, c->ndof, c->part);
+  ::p4d::count_launch(), k_sum4<<<1, 128, 0, c->stream>>>(c->part, kRedBlocks, r.misc() + 2 * L.m + 36);
   P4D_TRY(cudaEventRecord(r.ev1, c->stream));
-  P4D_TRY(cudaMemcpyAsync(c->hs_h, r.misc() + 2 * L.m + 7, sizeof(double) * 25, cudaMemcpyDeviceToHost, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, r.misc() + 2 * L.m + 7, sizeof(double) * 33, cudaMemcpyDeviceToHost, c->stream));
   return P4D_OK;
 }
 
@@ -696,6 +701,18 @@ void fg_finish_read(FgRun& r, p4d_info* info) {
     tot_r += rr[f];
   }
   info->rel_res = tot_b > 0 ? std::sqrt(tot_r / tot_b) : std::sqrt(tot_r);
+  const double* ru = c->hs_h + 25;      // field norms^2 of sqrt(d) s.(b - Jx)
+  const double* bu = c->hs_h + 29;      // field norms^2 of b
+  double ur = 0.0, ub = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    const double rf = ru[f] * (bn2[f] > 0 ? bn2[f] : 1.0);   // 1 / w_f^2
+    info->rel_res_block_unscaled[f] = bu[f] > 0 ? std::sqrt(rf / bu[f]) : std::sqrt(rf);
+    ur += rf;
+    ub += bu[f];
+  }
+  info->rel_res_unscaled = ub > 0 ? std::sqrt(ur / ub) : std::sqrt(ur);
+  info->nsolves = 1;
+  info->iters_total = r.iters;
   info->ms_total = ms;
   if (c->prm.profile) {
     int n = 0;

@@ -386,7 +386,7 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
                                 const double* __restrict__ Aj, const double* __restrict__ ge,
                                 const double* __restrict__ gc, const double* __restrict__ zeta, double s0,
                                 double s1, double s2, TS* st0, TS* st1, TS* st2, T* di0, T* di1, T* di2,
-                                double* __restrict__ svar, double* lam) {
+                                double* __restrict__ svar, double* lam, T* __restrict__ svs) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
   double gl[kNH] = {0.0, 0.0, 0.0, 0.0};
@@ -410,6 +410,7 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
       const double ab = absoff[f * nn + n];
       if (!(diag > 0.0)) diag = fmax(ab, 1e-300);   // keep the smoother finite on a degenerate row
       svar[f * nn + n] = sv[f];
+      svs[f * nn + n] = (T)(sc[f] * sv[f]);   // the matrix-free level 0 adds it to the element part
       sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
       const T dsc = (T)(sc[f] * diag);
       dis[f][n] = (T)1 / dsc;
@@ -1026,6 +1027,32 @@ BRange brange(const MGLevel& A, const int* hs, int nhs, unsigned* gx) {
   return r;
 }
 
+// A level-0 step that applies the operator to a nonzero x (mode 0: a
+// Chebyshev step, mode 1: the residual) for the hierarchies hs: the fields
+// with a matrix-free operator in one mf launch, the others (phi_s with
+// collector shells) with the stored stencils.
+template <typename TS0, typename T>
+p4d_status level0_stencil_step(p4d_ctx* c, MGLevel& A, const int* hs, int nhs, const HList& hl, const BRange& br,
+                               dim3 grid, int mode, int step) {
+  int fmask = 0, shs[kNH], ns = 0;
+  for (int t = 0; t < nhs; ++t) {
+    const int f = hs[t] < 2 ? 0 : hs[t] - 1;
+    if (mf_field_on(c, f)) fmask |= 1 << f;
+    else shs[ns++] = hs[t];
+  }
+  if (fmask) P4D_TRYS(mf_level0(c, fmask, mode, step));
+  if (ns) {
+    const HList hl2 = make_hl<T>(shs, ns);
+    const dim3 g2(grid.x, ns);
+    if (mode == 0)
+      ::p4d::count_launch(), k_cheb<TS0, T><<<g2, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl2, br, cheb_tab<T>(c), 0, step, 0);
+    else
+      ::p4d::count_launch(), k_resid<TS0, T><<<g2, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl2, br);
+  }
+  (void)hl;
+  return P4D_OK;
+}
+
 template <typename TS0, typename TS, typename T>
 p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
   const int L = c->nlev;
@@ -1039,12 +1066,13 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     const dim3 grid(gx, nhs);
     for (int s = 0; s < deg; ++s) {
       if (l == 0 && s > 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
+      if (l == 0 && s > 0) P4D_TRYS((level0_stencil_step<TS0, T>(c, A, hs, nhs, hl, br, grid, 0, s)));
+      else if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 1);
       else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, s == 0);
       if (l == 0 && s > 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
     }
-    if (l == 0) ::p4d::count_launch(), k_resid<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br);
+    if (l == 0) P4D_TRYS((level0_stencil_step<TS0, T>(c, A, hs, nhs, hl, br, grid, 1, 0)));
     else ::p4d::count_launch(), k_resid<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br);
     Ptr4<const T> fr;
     Ptr4<const uint8_t> fm;
@@ -1075,7 +1103,7 @@ p4d_status vcycle_t(p4d_ctx* c, const int* hs, int nhs) {
     ::p4d::count_launch(), k_prolong<T><<<grid, kBlock, 0, c->stream>>>(dims(A), dims(B), A.X, cxp, fm, fx, hl, br);
     for (int s = 0; s < deg; ++s) {
       if (l == 0) prof_mark(c, 3);
-      if (l == 0) ::p4d::count_launch(), k_cheb<TS0, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS0, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
+      if (l == 0) P4D_TRYS((level0_stencil_step<TS0, T>(c, A, hs, nhs, hl, br, grid, 0, s)));
       else ::p4d::count_launch(), k_cheb<TS, T><<<grid, kBlock, 0, c->stream>>>(dims(A), ptrs<TS, T>(A), hl, br, cheb_tab<T>(c), l, s, 0);
       if (l == 0) prof_mark(c, 3);
       swap_x(A, hs, nhs);
@@ -1410,12 +1438,12 @@ p4d_status mg_update(p4d_ctx* c) {
     ::p4d::count_launch(), k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3], (double*)l0.dinv[0], (double*)l0.dinv[2],
-        (double*)l0.dinv[3], svar, l0.lam);
+        (double*)l0.dinv[3], svar, l0.lam, (double*)c->mf_svs);
   else
     ::p4d::count_launch(), k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3], (float*)l0.dinv[0], (float*)l0.dinv[2],
-        (float*)l0.dinv[3], svar, l0.lam);
+        (float*)l0.dinv[3], svar, l0.lam, (float*)c->mf_svs);
   if (prec == 0) P4D_TRYS(mg_update_levels<double>(c, svar, sch));
   else P4D_TRYS(mg_update_levels<float>(c, svar, sch));
   P4D_TRY(cudaGetLastError());

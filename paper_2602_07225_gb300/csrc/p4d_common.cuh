@@ -135,6 +135,7 @@ struct p4d_ctx {
   int nc = 0;
   p4d_params prm{};
   cudaStream_t stream = nullptr;
+  int device = -1;                     // CUDA device current at p4d_setup (the handle's memory lives there)
   bool linearized = false;
   std::vector<int32_t> enodes_h;
   double scale_f[3] = {1, 1, 1};       // multigrid per-field scaling (FP32 range)
@@ -202,6 +203,16 @@ struct p4d_ctx {
   double lam_h[p4d::kMaxLevels][p4d::kNH] = {};   // Gershgorin bounds (host copy, per Newton update)
   double* lam_pin = nullptr;           // pinned staging for lam
   void* yc = nullptr;                  // [NE][nc] particle solve work (compute precision)
+
+  // matrix-free level 0 (mf.cu), compute precision of the preconditioner
+  void* mf_coef = nullptr;             // [4][nelem] sc_0 sigma_eff, sc_1 kappa_eff, sc_2 D_eff, sc_2 eps/dt
+  void* mf_geo = nullptr;              // per-axis factors (2/h, h/2, h/6) [3][nx] / 8, [3][ny], [3][nz]
+  void* mf_svs = nullptr;              // [3][nn] sc_f * variable node diagonal (per linearization)
+  int4* mf_items = nullptr;            // work items (field, tile, k0, k1), phi_s then phi_e then c_e
+  int mf_off[3] = {0, 0, 0}, mf_cnt[3] = {0, 0, 0};
+  int mf_ntx = 0, mf_nty = 0;          // node tiles per axis
+  size_t mf_smem = 0;                  // dynamic shared memory per block
+  bool mf_phis = false;                // phi_s matrix-free (no collector shells)
 
   // Krylov workspace
   int mcap = 0;                        // allocated restart capacity
@@ -405,6 +416,12 @@ p4d_status mg_update(p4d_ctx* c);
 p4d_status mg_fetch_lam(p4d_ctx* c);
 // run the V-cycles of the listed hierarchies on the level-0 right-hand sides already in place
 p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs);
+// matrix-free level 0 (mf.cu): setup after mg_setup_fixed; whether field f
+// (0 phi_s, 1 phi_e, 2 c_e) is applied matrix-free; one launch over the
+// fields in fmask: mode 0 Chebyshev step `step` (x -> x2, d), mode 1 r = b - A x
+p4d_status mf_setup(p4d_ctx* c);
+bool mf_field_on(const p4d_ctx* c, int f);
+p4d_status mf_level0(p4d_ctx* c, int fmask, int mode, int step);
 // level-0 rhs from an FP64 macro vector: b_h = scale * (r_f - corr)  (see mg.cu)
 p4d_status mg_load_rhs(p4d_ctx* c, const double* rm, const double* sinv_m, const int* hs, int nhs);
 p4d_status mg_store_out(p4d_ctx* c, const double* rm_unscaled_src, const double* sinv_m, double* zm,

@@ -26,8 +26,33 @@ struct PcArgs {
   const int32_t* enode;
   const double *Aj, *Mj, *iMj, *betaj, *kapj, *rref;
   const double *ge, *gc, *gs, *zeta, *sqd, *iwf;
+  const double* Kk;     // K_kappa stencil [27][nn] (FP64, fixed)
+  const double* gdc;    // gamma / c_e per node
   double sc[3];
 };
+
+// The one stencil coupling between the electrode-level blocks: the
+// diffusion-potential block S[phi_e][c_e] = K_kappa diag(gamma / c_e)
+// (eq. phie-weak; every other coupling is node-local).  Forward:
+// (K_kappa diag(gamma/c_e) z_ce)_n; transposed: (diag(gamma/c_e) K_kappa z_phie)_n
+// (K_kappa is symmetric).  zsrc: the done field's solution.
+template <bool TRANS>
+__device__ __forceinline__ double diffpot_coupling(const PcArgs& a, int64_t n, const double* __restrict__ zsrc) {
+  const int64_t nn = a.g.nn;
+  const int i = (int)(n % a.g.nnx);
+  const int j = (int)((n / a.g.nnx) % a.g.nny);
+  const int k = (int)(n / ((int64_t)a.g.nnx * a.g.nny));
+  double acc = 0.0;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= a.g.nnx || jj >= a.g.nny || kk >= a.g.nnz) continue;
+    const int64_t m = n + dx + (int64_t)a.g.nnx * (dy + (int64_t)a.g.nny * dz);
+    acc += a.Kk[o * nn + n] * (TRANS ? zsrc[m] : a.gdc[m] * zsrc[m]);
+  }
+  return TRANS ? a.gdc[n] * acc : acc;
+}
 
 __device__ __forceinline__ double insc(const PcArgs& a, bool scaled, int f, int64_t row) {
   return scaled ? a.sqd[row] * a.iwf[f] : 1.0;
@@ -148,7 +173,8 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
   for (int f = 0; f < 3; ++f) {
     if (!(fmask & (1 << f))) continue;
     const int64_t row = f * nn + n;
-    if (sizeof(T) == sizeof(float) && scaled && !coupled && !(f == 0 && !act)) {
+    const bool dpc = (!TRANS && f == 1 && (done & 4)) || (TRANS && f == 2 && (done & 2));
+    if (sizeof(T) == sizeof(float) && scaled && !coupled && !dpc && !(f == 0 && !act)) {
       // FP32 right-hand side of an FP32 cycle: the scaling in FP32 (FP64
       // multiplies are this kernel's cost)
       const float w = (float)(a.iwf[f] * a.sc[f]);
@@ -161,6 +187,8 @@ __global__ void k_load(PcArgs a, VRef rref_, const T* __restrict__ yc, VRef zref
       if (FULL) rf -= (TRANS ? u[3] * v[f] : u[f] * v[3]) * yN;
       rf -= (TRANS ? v[f] : u[f]) * coup;
     }
+    // BGS: the diffusion-potential block couples phi_e to c_e over the stencil
+    if (dpc) rf -= TRANS ? diffpot_coupling<true>(a, n, zm + nn) : diffpot_coupling<false>(a, n, zm + 2 * nn);
     if (f == 0 && !act) {
       zout[n] = rf;   // identity row
       continue;
@@ -243,6 +271,7 @@ PcArgs make_pc(p4d_ctx* c) {
   a.label = c->label; a.eidx = c->eidx; a.enode = c->enode;
   a.Aj = c->Aj; a.Mj = c->Mj; a.iMj = c->iMj; a.betaj = c->betaj; a.kapj = c->kapj; a.rref = c->rref;
   a.ge = c->ge; a.gc = c->gc; a.gs = c->gs; a.zeta = c->zeta; a.sqd = c->sqd; a.iwf = c->iwf;
+  a.Kk = c->Jst + 27 * c->g.nn; a.gdc = c->gdc;
   for (int f = 0; f < 3; ++f) a.sc[f] = c->scale_f[f];
   return a;
 }

@@ -158,6 +158,12 @@ class P4DSolver:
         N.check(self.lib.p4d_voltage_weights(self.h, _ptr(q)), "p4d_voltage_weights")
         return q
 
+    def terminal_voltage(self, phis):
+        """V = mean of phi_s over Gamma_p, as a one-element device tensor."""
+        v = torch.empty(1, dtype=torch.float64, device=self.device)
+        N.check(self.lib.p4d_terminal_voltage(self.h, _ptr(_dev(phis)), _ptr(v)), "p4d_terminal_voltage")
+        return v
+
     def param_grad(self, s, lam, g_sigma, g_Ds, g_eps):
         N.check(self.lib.p4d_param_grad(self.h, C.byref(self._state(s)), _ptr(_dev(lam)), _ptr(_dev(g_sigma)),
                                         _ptr(_dev(g_Ds)), _ptr(_dev(g_eps))), "p4d_param_grad")

@@ -22,7 +22,28 @@ CASES = {
     # anisotropic elements: the first multigrid level(s) coarsen x and y only
     "aniso": lambda: make_box_case(13, 11, (7, 3, 7), 30e-6, (40e-6, 15e-6, 40e-6), 5, 124),
     "aniso2": lambda: make_box_case(16, 16, (6, 3, 6), 24e-6, (40e-6, 15e-6, 40e-6), 4, 125),
+    # particles on the paper's graded radial mesh (spacings shrink toward the
+    # surface, last/first = 0.5) with lognormal radii
+    "graded": lambda: make_box_case(6, 5, (4, 2, 4), 30e-6, (40e-6, 15e-6, 40e-6), 8, 126, rs_cv=0.3,
+                                    theta_bar=0.5),
+    # the paper's open-circuit potential curves in the kinetics (the seeded
+    # cathode stoichiometries cross the steep step of the LiCoO2 curve)
+    "paper_ocp": lambda: make_case("cube8"),
 }
+# options of the oracle (Disc) and of the library per case
+ORACLE_KW = {"paper_ocp": dict(ocp="paper")}
+LIB_KW = {"paper_ocp": dict(ocp_model=1)}
+
+# FGMRES rtol (scaled norm) per mesh.  The solution error per unit of scaled
+# residual is ~1-2 on the layered cubes but reaches ~25 on meshes whose
+# coarse grids keep half-width last elements (an odd element count along an
+# axis) and on the anisotropic boxes (measured 2.3e-9 at rtol 1e-10 on
+# "odd", 2.0e-9 on "graded", 2.1e-7 at rtol 1e-8 on "aniso"), so those
+# meshes are solved to a 100x tighter rtol.  The error bounds are the same
+# for every mesh: 1e-9 for the FP64 path, 1e-7 for the mixed paths.
+TIGHT = {"odd", "oddcoarse", "aniso", "aniso2", "graded"}
+RTOL_FP64 = {name: (1e-12 if name in TIGHT else 1e-10) for name in CASES}
+RTOL_MIXED = {name: (1e-10 if name in TIGHT else 1e-8) for name in CASES}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,9 +57,9 @@ def _built():
 def _setup(name, **opts):
     from paper_2602_07225_gb300 import P4DSolver
     case = CASES[name]()
-    d = Disc(case["mesh"], case["params"])
+    d = Disc(case["mesh"], case["params"], **ORACLE_KW.get(name, {}))
     ref = d.state_from_case(case["state"])
-    s = P4DSolver(case, **opts)
+    s = P4DSolver(case, **LIB_KW.get(name, {}), **opts)
     st = s.state_tensors(case["state"])
     return case, d, ref, s, st
 
@@ -128,41 +149,88 @@ def test_adjointness_on_gpu(name):
         assert abs(a - b) <= 1e-12 * scale, (op.__name__, a, b)
 
 
-# solution error per unit of scaled residual: ~1-2 for the layered cubes,
-# ~25 for meshes with odd element counts, whose coarse grids keep a
-# half-width last element (measured 2.3e-9 at rel_res 1e-10 on "odd")
-# solution error per unit of scaled residual: up to ~25 on meshes whose
-# coarse grids keep half-width last elements and on the anisotropic boxes
-# (measured 2.1e-7 at rtol 1e-8 on "aniso")
-AMPLIFICATION = {"odd": 25.0, "oddcoarse": 25.0, "aniso": 25.0, "aniso2": 25.0}
-
-
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fgmres_fp64_matches_direct(name, mode):
-    case, d, ref, s, st = _setup(name, precision=0, mode=mode, rtol=1e-10, maxit=400)
+    rtol = RTOL_FP64[name]
+    case, d, ref, s, st = _setup(name, precision=0, mode=mode, rtol=rtol, maxit=600)
     s.jacobian_update(st)
     b = -s.residual(st)
     x, info = s.solve(b)
     x_ref = LinearSolve(d, ref).direct()
     err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
     assert info["status"] == 0, info
-    assert info["rel_res"] <= 2e-10, info
-    assert err <= 1e-9 * AMPLIFICATION.get(name, 1.0), (err, info)
+    assert info["rel_res"] <= 2 * rtol, info
+    assert err <= 1e-9, (err, info)
 
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("combine", [0, 1])
 def test_fgmres_mixed_matches_direct(name, precision, combine):
-    case, d, ref, s, st = _setup(name, precision=precision, combine=combine, mode=1, rtol=1e-8, maxit=400)
+    rtol = RTOL_MIXED[name]
+    case, d, ref, s, st = _setup(name, precision=precision, combine=combine, mode=1, rtol=rtol, maxit=600)
     s.jacobian_update(st)
     b = -s.residual(st)
     x, info = s.solve(b)
     x_ref = LinearSolve(d, ref).direct()
     err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
     assert info["status"] == 0, info
-    assert err <= 1e-7 * AMPLIFICATION.get(name, 1.0), (err, info)
+    assert info["rel_res"] <= 2 * rtol, info
+    assert err <= 1e-7, (err, info)
+
+
+ORDERS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+@pytest.mark.parametrize("name", ["cube8", "aniso", "tabshell"])
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_precond_bgs_every_order_matches_oracle(name, order, transpose):
+    """Block Gauss-Seidel (eq. PGS) in each of the six orders of the three
+    electrode-level blocks, plain and transposed, FP64, against the oracle's
+    block Gauss-Seidel in the same order."""
+    case, d, ref, s, st = _setup(name, precision=0, combine=1, order=order, mode=0)
+    s.jacobian_update(st)
+    J = d.jacobian(ref)
+    P = BlockPrecond(d, J, combine="multiplicative", order=order)
+    r = np.random.default_rng(19).standard_normal(d.ndof) * np.sqrt(J.diagonal())
+    z = s.precond(torch.tensor(r, device="cuda"), transpose=transpose).cpu().numpy()
+    z_ref = P.apply_transpose(r) if transpose else P.apply(r)
+    errs = [np.linalg.norm(z[sl] - z_ref[sl]) / np.linalg.norm(z_ref[sl]) for sl in d.field_slices()]
+    # The phi_s blocks' conditioning (see the BJ/BGS test above) amplifies
+    # rounding-order differences of their cycles to ~1e-7 (measured 1.6e-7);
+    # every block solved after phi_s inherits that through its coupling, and
+    # c_s through the back substitution.  A block solved before phi_s agrees
+    # to rounding.  (A missing coupling block shows up as 1e-2 to 1.)
+    seq = list(reversed(order)) if transpose else list(order)
+    tol = [1e-6 if f == 0 or seq.index(f) > seq.index(0) else 1e-10 for f in range(3)] + [1e-6]
+    assert all(e < t for e, t in zip(errs, tol)), (errs, tol)
+
+
+def test_fgmres_large_box_matches_oracle_fgmres():
+    """64x64x48 elements (20/8/20), N_c = 8: 2,040,675 unknowns and six
+    multigrid levels, the first of which coarsens x and y only (3:1
+    elements, as in the 128x128x96 workload).  The GPU FP64 solve (FULL and
+    REDUCED) and the FP32-preconditioned one are compared per field with the
+    oracle's FGMRES solved to rtol 1e-13."""
+    from oracle.krylov import LinearSolve as OLS
+    case = make_box_case(64, 64, (20, 8, 20), 100e-6, (100e-6, 25e-6, 100e-6), 8, 2064)
+    d = Disc(case["mesh"], case["params"])
+    ref = d.state_from_case(case["state"])
+    x_ref, its_ref, _ = OLS(d, ref).fgmres(rtol=1e-13)
+    from paper_2602_07225_gb300 import P4DSolver
+    # solution error per unit of scaled residual ~130 at this size (measured
+    # 1.3e-9 at rtol 1e-11): the FP64 solves go to 1e-12, the mixed to 1e-10
+    for precision, mode, rtol, bound in ((0, 0, 1e-12, 1e-9), (0, 1, 1e-12, 1e-9), (1, 1, 1e-10, 1e-7)):
+        s = P4DSolver(case, precision=precision, mode=mode, rtol=rtol, maxit=400)
+        st = s.state_tensors(case["state"])
+        s.jacobian_update(st)
+        x, info = s.solve(-s.residual(st))
+        err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
+        assert info["status"] == 0 and info["rel_res"] <= 2 * rtol, info
+        assert err <= bound, (precision, mode, err, info)
+        s.close()
 
 
 def test_iteration_counts_match_oracle():
