@@ -290,9 +290,11 @@ p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpo
    in place] hold the initial guess and receive the solution; ce_prev,
    cs_prev [device] are the previous time level.  The residual is measured
    in the Jacobi-scaled norm ||D^-1/2 R|| (D = diag J at the initial
-   guess); backtracking halves the step (at most 8 times) until that norm
-   decreases.  Converged when ||D^-1/2 R|| <= rtol ||D^-1/2 R_0|| or when the
-   full Newton step is below 1e-10 of the state in every field (the
+   guess).  Full Newton steps (the paper uses its nonlinear solver's
+   default, basic, line search); a step is halved (at most 8 times) only
+   while the trial state leaves the kinetics' domain or gives a non-finite
+   residual.  Converged when ||D^-1/2 R|| <= rtol ||D^-1/2 R_0|| or when a
+   full Newton step is at most rtol times the state in every field (the
    residual has a rounding floor); NOT_CONVERGED after maxit iterations.
    iters and info may be NULL; info describes the last linear solve, except
    nsolves and iters_total, which count all of the step's linear solves.  Returns OK,

@@ -319,6 +319,80 @@ def make_gyroid_cell(n, t, periods, nc, seed, L_lat=100e-6, L_layers=(100e-6, 25
     return case
 
 
+def make_tpms_cell(nx, ny, nz, nc=6, seed=1006, L=(1e-3, 1e-3, 0.5e-3), t=1.104, state="seeded"):
+    """The paper's interpenetrating gyroid electrodes (section 5, Case IV)
+    voxelised on an nx x ny x nz box mesh of L = (1, 1, 0.5) mm: with
+    (X, Y, Z) = (pi x/Lx, pi y/Ly, pi z/Lz) at the element centre,
+        s_n = sin X cos Y + sin Y cos Z + sin Z cos X - 1.3,
+        s_p = sin X cos(Y + pi) + sin(Y + pi) cos(-Z) + sin(-Z) cos X - 1.3,
+    an element is anode where |s_n| <= t/2, cathode where |s_p| <= t/2
+    (t = 1.104), electrolyte-only elsewhere.  Cathode elements that share a
+    node with an anode element become electrolyte-only (the two electrodes
+    never touch).  The grounded face Gamma_n is the bottom (z = 0) face of
+    the anode elements, the applied-current face Gamma_p the top face of the
+    cathode elements; i_app is 1C of the active material's theoretical
+    capacity.  N_c = 6 as in the paper's Case IV (Table tab:meshes)."""
+    Lx, Ly, Lz = L
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = dict(PARAMS_DEFAULT)
+    hx = np.full(nx, Lx / nx)
+    hy = np.full(ny, Ly / ny)
+    hz = np.full(nz, Lz / nz)
+    xc = (np.arange(nx) + 0.5) / nx
+    yc = (np.arange(ny) + 0.5) / ny
+    zc = (np.arange(nz) + 0.5) / nz
+    Z, Y, X = np.meshgrid(np.pi * zc, np.pi * yc, np.pi * xc, indexing="ij")
+    s_n = np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X) - 1.3
+    s_p = np.sin(X) * np.cos(Y + np.pi) + np.sin(Y + np.pi) * np.cos(-Z) + np.sin(-Z) * np.cos(X) - 1.3
+    region = np.full((nz, ny, nx), 3, np.uint8)
+    region[np.abs(s_p) <= t / 2] = 2
+    region[np.abs(s_n) <= t / 2] = 0
+    an, _ = _node_types(nx, ny, nz, region.ravel())
+    an3 = an.reshape(nz + 1, ny + 1, nx + 1)
+    touch = np.zeros((nz, ny, nx), bool)
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                touch |= an3[dk:dk + nz, dj:dj + ny, di:di + nx]
+    region[(region == 2) & touch] = 3
+    region = region.ravel()
+    el = (region == 0) | (region == 2)
+    eps = np.where(el, 0.3, 1.0)
+    eps_s = np.where(region == 0, 0.6, np.where(region == 2, 0.5, 0.0))
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    r3 = region.reshape(nz, ny, nx)
+    gamma_p = (r3[-1] == 2).astype(np.uint8).ravel()
+    gamma_n = (r3[0] == 0).astype(np.uint8).ravel()
+    vol = (hx[None, None, :] * hy[None, :, None] * hz[:, None, None]).ravel()
+    qn = p["F"] / 3600 * np.sum((eps_s * vol)[region == 0]) * p["cmax_n"]
+    qp = p["F"] / 3600 * np.sum((eps_s * vol)[region == 2]) * p["cmax_p"]
+    area = np.sum((hx[None, :] * hy[:, None]).ravel()[gamma_p.astype(bool)])
+    p["i_app"] = -min(qn, qp) / area if area > 0 else 0.0
+    an, ca = _node_types(nx, ny, nz, region)
+    (c0n, c1n), (c0p, c1p) = p["ocp_n"], p["ocp_p"]
+    if state == "seeded":
+        ce = 1000.0 * (1.0 + rng.uniform(-0.05, 0.05, nn))
+        th_n = rng.uniform(0.5, 0.8, nn)
+        th_p = rng.uniform(0.4, 0.6, nn)
+        thn_ref, thp_ref = 0.65, 0.5
+    else:
+        ce = np.full(nn, 1000.0)
+        th_n = np.full(nn, 0.8)
+        th_p = np.full(nn, 0.6)
+        thn_ref, thp_ref = 0.8, 0.6
+    cs_node = np.zeros((nn, nc))
+    cs_node[an] = (th_n[an] * p["cmax_n"])[:, None]
+    cs_node[ca] = (th_p[ca] * p["cmax_p"])[:, None]
+    phis = np.zeros(nn)
+    phis[ca] = (c0p + c1p * thp_ref) - (c0n + c1n * thn_ref)
+    phie = np.full(nn, -(c0n + c1n * thn_ref))
+    mesh = dict(nx=nx, ny=ny, nz=nz, hx=hx, hy=hy, hz=hz, region=region, eps=eps, eps_s=eps_s,
+                Rs=np.full(nn, 5e-6), Ds=np.full(nn, 1e-14), gamma_p=gamma_p, gamma_n=gamma_n, nc=nc,
+                rgrid=np.linspace(0.0, 1.0, nc))
+    st = dict(phis=phis, phie=phie, ce=ce, cs_node=cs_node, ce_prev=ce.copy(), cs_prev_node=cs_node.copy())
+    return dict(mesh=mesh, params=p, state=st, seed=seed, tpms=dict(nx=nx, ny=ny, nz=nz, t=t))
+
+
 def make_gyroid_batch(ncells=64, seed=1004, sizes=(16, 24, 32, 40, 48, 56, 64)):
     """Seeded batch of gyroid cells of uneven sizes: lateral n uniform over
     `sizes` (nz = 1.5 n), t ~ U(-0.3, 0.3), periods in {1, 2, 3}, N_c in 10..20."""

@@ -249,6 +249,9 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
     double step_rel = 0.0;
     for (int q = 0; q < 4; ++q)
       if (fu[q] > 0) step_rel = std::max(step_rel, std::sqrt(fd[q] / fu[q]));
+    // full Newton steps (the basic line search of the paper's default
+    // nonlinear solver settings), halved only while the trial state leaves
+    // the kinetics' domain or gives a non-finite residual
     double lam = 1.0;
     bool accepted = false;
     for (int bt = 0; bt < 9; ++bt, lam *= 0.5) {
@@ -260,7 +263,7 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
       P4D_TRYS(fnorms(Rt, wsc, fc));
       const double rt = total(fc) / r0;
       if (!std::isfinite(rt)) continue;
-      if (rt < rel || bt == 8 || step_rel <= 1e-10) {
+      {
         P4D_TRY(cudaMemcpyAsync(phis, trial, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         P4D_TRY(cudaMemcpyAsync(phie, trial + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         P4D_TRY(cudaMemcpyAsync(ce, trial + 2 * nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -272,7 +275,7 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
       }
     }
     if (!accepted) { result = P4D_ERR_DOMAIN; break; }
-    if (step_rel <= 1e-10) { ++it; result = P4D_OK; break; }
+    if (step_rel <= rtol && lam == 1.0) { ++it; result = P4D_OK; break; }
   }
   P4D_TRY(cudaStreamSynchronize(h->stream));
   if (iters_out) *iters_out = it;

@@ -27,8 +27,8 @@
 // phi_s is lifted by its zero values at the nodes without a phi_s unknown
 // (the multigrid never writes them).
 //
-// Layout of a launch: each block owns a tile of W x H nodes (W, H up to
-// twice the nominal 32 x 8: the last tile of an axis takes the remainder)
+// Layout of a launch: each block owns a tile of W x H nodes (nominally
+// 32 x 8; the last tile of an axis takes the remainder, at most one more)
 // and marches in z over a chunk of node planes.  Per plane it stages the
 // (W+2) x (H+2) tile of x in shared memory, evaluates the (W+1) x (H+1)
 // elements between that plane and the next (their lower-corner outputs go
@@ -113,8 +113,15 @@ __device__ __forceinline__ void element_apply(T (&v)[8], const T (&lam)[8]) {
 
 // MODE 0: Chebyshev step on a nonzero x: d = c0 D^-1 (b - A x) (step 0) or
 // d = ca d + cb D^-1 (b - A x), then x_out = x + d.  MODE 1: r = b - A x.
+//
+// Tiles are at most (kTX + 1) x (kTY + 1) nodes, so every thread owns at
+// most two x loads, two elements and two nodes of a plane (slot r: index
+// tid + 256 r).  The global loads of the next plane (x of plane k + 2, the
+// element coefficients of element plane k + 1, the node data of plane
+// k + 1) are issued into registers one iteration ahead, so their latency
+// overlaps the current plane's element and node work.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kMfThreads) k_mf_level0(MfArgs<T> a) {
+__global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 it = a.items[blockIdx.x];
   const int f = it.x;
@@ -125,87 +132,155 @@ __global__ void __launch_bounds__(kMfThreads) k_mf_level0(MfArgs<T> a) {
   const int H = tiy == a.nty - 1 ? a.nny - j0 : kTY;
   const int k0 = it.z, k1 = it.w;
   const int XW = W + 2, XH = H + 2, EW = W + 1, EH = H + 1;
-  const int XN = XW * XH, EN = EW * EH;
-  T* xs = reinterpret_cast<T*>(smem_raw);          // [2][XN] x planes (ring)
-  T* lo = xs + 2 * XN;                              // [4][EN] lower-corner outputs of the current element plane
+  const int XN = XW * XH, EN = EW * EH, NN = W * H;
+  T* xs = reinterpret_cast<T*>(smem_raw);          // [3][XN] x planes (ring)
+  T* lo = xs + 3 * XN;                              // [4][EN] lower-corner outputs of the current element plane
   T* upA = lo + 4 * EN;                             // [4][EN] upper-corner outputs (two buffers)
   T* upB = upA + 4 * EN;
-  T* sgx = upB + 4 * EN;                            // [3][EW] x factors of the tile's element columns
-  T* sgy = sgx + 3 * EW;                            // [3][EH]
   const MfField<T>& F = fsel(a, f);
   const int tid = threadIdx.x;
-  const int64_t sxy = (int64_t)a.nnx * a.nny;
-  const int hA = f == 0 ? 0 : f + 1;               // hierarchy of the field (phi_s: per node)
+  // 32-bit offsets: every level-0 array has fewer than 2^31 entries
+  const int sxy = a.nnx * a.nny;
+  const int sexy = a.nx * a.ny;
+  const bool mass = F.mc != nullptr;
 
-  for (int q = tid; q < EW; q += kMfThreads) {
-    const int ie = i0 - 1 + q;
-    const bool in = ie >= 0 && ie < a.nx;
-    sgx[q] = in ? a.gx[ie] : (T)0;
-    sgx[EW + q] = in ? a.gx[a.nx + ie] : (T)0;
-    sgx[2 * EW + q] = in ? a.gx[2 * a.nx + ie] : (T)0;
-  }
-  for (int q = tid; q < EH; q += kMfThreads) {
-    const int je = j0 - 1 + q;
-    const bool in = je >= 0 && je < a.ny;
-    sgy[q] = in ? a.gy[je] : (T)0;
-    sgy[EH + q] = in ? a.gy[a.ny + je] : (T)0;
-    sgy[2 * EH + q] = in ? a.gy[2 * a.ny + je] : (T)0;
-  }
-
-  // x plane k (nodes (i0-1 .. i0+W) x (j0-1 .. j0+H)) into ring slot k & 1;
-  // nodes outside the grid read 0
-  auto load_plane = [&](int k) {
-    T* dst = xs + (k & 1) * XN;
-    const bool kin = k >= 0 && k < a.nnz;
-    for (int q = tid; q < XN; q += kMfThreads) {
+  // per-slot constants (slot r: index tid + 256 r of the plane's x entries,
+  // elements and nodes), computed once for the whole z march
+  int xoff[2], xsm[2];       // x entry: in-plane offset (-1 outside the grid), tile index (-1: none)
+  int eoff[2], ebase[2];     // element: in-plane offset (-1 outside), x-tile index of its lower-left node
+  int eq[2];                 // element slot (-1: none)
+  T ex[2][3], ey[2][3];      // element: x factors (2/h, h/2, h/6)/8 and y factors (2/h, h/2, h/6)
+  int noff[2], nq[2], nsm[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int q = tid + r * kMfThreads;
+    xoff[r] = -1;
+    xsm[r] = q < XN ? q : -1;
+    if (q < XN) {
       const int jj = q / XW, ii = q - jj * XW;
       const int gi = i0 - 1 + ii, gj = j0 - 1 + jj;
-      T v = (T)0;
-      if (kin && gi >= 0 && gi < a.nnx && gj >= 0 && gj < a.nny) v = F.x[gi + (int64_t)a.nnx * gj + sxy * k];
-      dst[q] = v;
+      if (gi >= 0 && gi < a.nnx && gj >= 0 && gj < a.nny) xoff[r] = gi + a.nnx * gj;
+    }
+    eoff[r] = -1;
+    eq[r] = q < EN ? q : -1;
+    ebase[r] = 0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) ex[r][t] = ey[r][t] = (T)0;
+    if (q < EN) {
+      const int ej = q / EW, ei = q - ej * EW;
+      ebase[r] = ei + XW * ej;
+      const int gi = i0 - 1 + ei, gj = j0 - 1 + ej;
+      if (gi >= 0 && gi < a.nx && gj >= 0 && gj < a.ny) {
+        eoff[r] = gi + a.nx * gj;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          ex[r][t] = a.gx[t * a.nx + gi];
+          ey[r][t] = a.gy[t * a.ny + gj];
+        }
+      }
+    }
+    noff[r] = -1;
+    nq[r] = 0;
+    nsm[r] = 0;
+    if (q < NN) {
+      const int jj = q / W, ii = q - jj * W;
+      noff[r] = (i0 + ii) + a.nnx * (j0 + jj);
+      nq[r] = ii + EW * jj;
+      nsm[r] = (ii + 1) + XW * (jj + 1);
+    }
+  }
+  // Chebyshev coefficients of the block's hierarchies (phi_s: both electrodes)
+  T cA[2], cB[2];
+  {
+    const int hs0 = f == 0 ? 0 : f + 1, hs1 = f == 0 ? 1 : f + 1;
+    if (MODE == 0) {
+      cA[0] = a.step == 0 ? (T)0 : cheb_coef(a.ctab, a.step, 1, hs0);
+      cB[0] = a.step == 0 ? cheb_coef(a.ctab, 0, 0, hs0) : cheb_coef(a.ctab, a.step, 2, hs0);
+      cA[1] = a.step == 0 ? (T)0 : cheb_coef(a.ctab, a.step, 1, hs1);
+      cB[1] = a.step == 0 ? cheb_coef(a.ctab, 0, 0, hs1) : cheb_coef(a.ctab, a.step, 2, hs1);
+    }
+  }
+
+  T xr[2];                         // prefetched x of one plane
+  T kr[2], mr[2];                  // prefetched element coefficients of one element plane
+  T br[2], dr[2], ir[2], sr[2];    // prefetched node data (b, d, 1/diag, variable diagonal)
+  int lr[2];
+  auto fetch_x = [&](int k) {
+    const bool kin = k >= 0 && k < a.nnz;
+    const int base = k * sxy;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) xr[r] = (kin && xoff[r] >= 0) ? F.x[xoff[r] + base] : (T)0;
+  };
+  auto store_x = [&](int slot) {
+    T* dst = xs + slot * XN;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (xsm[r] >= 0) dst[xsm[r]] = xr[r];
+  };
+  auto fetch_coef = [&](int ke) {
+    const bool kin = ke >= 0 && ke < a.nz;
+    const int base = ke * sexy;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const bool on = kin && eoff[r] >= 0;
+      kr[r] = on ? F.kc[eoff[r] + base] : (T)0;
+      mr[r] = (on && mass) ? F.mc[eoff[r] + base] : (T)0;
+    }
+  };
+  auto fetch_nodes = [&](int k) {
+    const bool kin = k < k1;
+    const int base = k * sxy;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const bool on = kin && noff[r] >= 0;
+      const int n = noff[r] + base;
+      lr[r] = (on && f == 0) ? (int)a.label[n] : 0;
+      br[r] = on ? F.b[n] : (T)0;
+      sr[r] = on ? F.svs[n] : (T)0;
+      if (MODE == 0) {
+        ir[r] = on ? F.dinv[n] : (T)0;
+        dr[r] = (on && a.step != 0) ? F.d[n] : (T)0;
+      }
     }
   };
 
-  // element plane ke (between node planes ke and ke + 1): lower corners to
-  // lo, upper corners to up; elements outside the grid give zero
-  auto element_plane = [&](int ke, T* up) {
-    const T* xl = xs + (ke & 1) * XN;
-    const T* xu = xs + ((ke + 1) & 1) * XN;
-    const bool kin = ke >= 0 && ke < a.nz;
+  // element plane ke between the x planes in ring slots sl (lower) and su
+  // (upper), coefficients in kr / mr: lower corners to lo, upper to up
+  auto element_plane = [&](int ke, int sl, int su, T* up) {
+    const T* xl = xs + sl * XN;
+    const T* xu = xs + su * XN;
     T Ksz = 0, Msz = 0, Mdz = 0;
-    if (kin) {
+    if (ke >= 0 && ke < a.nz) {
       Ksz = a.gz[ke];
       Msz = a.gz[a.nz + ke];
       Mdz = a.gz[2 * a.nz + ke];
     }
-    for (int q = tid; q < EN; q += kMfThreads) {
-      const int ej = q / EW, ei = q - ej * EW;
-      const int gi = i0 - 1 + ei, gj = j0 - 1 + ej;
-      T kc = 0, mc = 0;
-      if (kin && gi >= 0 && gi < a.nx && gj >= 0 && gj < a.ny) {
-        const int64_t e = gi + (int64_t)a.nx * (gj + (int64_t)a.ny * ke);
-        kc = F.kc[e];
-        if (F.mc) mc = F.mc[e];
-      }
-      T v[8];
-      const int base = ei + XW * ej;
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int off = base + (l & 1) + XW * (l >> 1);
-        v[l] = xl[off];
-        v[4 + l] = xu[off];
-      }
-      // eigenvalues (the x factors carry the 1/8)
-      const T Kdx = sgx[ei], Msx = sgx[EW + ei], Mdx = sgx[2 * EW + ei];
-      const T Kdy = sgy[ej], Msy = sgy[EH + ej], Mdy = sgy[2 * EH + ej];
-      // per (y, z) component b + 2c: P = My Mz, Q = Ky Mz + My Kz
+    for (int r = 0; r < 2; ++r) {
+      const int q = eq[r];
+      if (q < 0) continue;
+      const T kc = kr[r], mc = mr[r];
+      T v[8];
+      const int base = ebase[r];
+      v[0] = xl[base];
+      v[1] = xl[base + 1];
+      v[2] = xl[base + XW];
+      v[3] = xl[base + XW + 1];
+      v[4] = xu[base];
+      v[5] = xu[base + 1];
+      v[6] = xu[base + XW];
+      v[7] = xu[base + XW + 1];
+      // eigenvalues (the x factors carry the 1/8); per (y, z) component
+      // b + 2c: P = My Mz, Q = Ky Mz + My Kz
+      const T Kdx = ex[r][0], Msx = ex[r][1], Mdx = ex[r][2];
+      const T Kdy = ey[r][0], Msy = ey[r][1], Mdy = ey[r][2];
       const T P0 = Msy * Msz, P1 = Mdy * Msz, P2 = Msy * Mdz, P3 = Mdy * Mdz;
-      const T Q0 = (T)0, Q1 = Kdy * Msz, Q2 = Msy * Ksz, Q3 = Kdy * Mdz + Mdy * Ksz;
-      const T As = Msx * mc, Bs = Msx * kc;          // lambda(s, .) = As P + Bs Q
+      const T Q1 = Kdy * Msz, Q2 = Msy * Ksz, Q3 = Kdy * Mdz + Mdy * Ksz;
+      const T As = Msx * mc, Bs = Msx * kc;            // lambda(s, .) = As P + Bs Q
       const T Ad = kc * Kdx + mc * Mdx, Bd = kc * Mdx; // lambda(d, .) = Ad P + Bd Q
       T lam[8];
-      lam[0] = As * P0 + Bs * Q0;
-      lam[1] = Ad * P0 + Bd * Q0;
+      lam[0] = As * P0;
+      lam[1] = Ad * P0;
       lam[2] = As * P1 + Bs * Q1;
       lam[3] = Ad * P1 + Bd * Q1;
       lam[4] = As * P2 + Bs * Q2;
@@ -223,55 +298,61 @@ __global__ void __launch_bounds__(kMfThreads) k_mf_level0(MfArgs<T> a) {
 
   T* upPrev = upA;
   T* upCur = upB;
-  load_plane(k0 - 1);
-  load_plane(k0);
+  // ring slots of x planes k - 1, k, k + 1 (plane k + 2 reuses k - 1's)
+  int sm1 = 0, s0 = 1, s1 = 2;
+  // prologue: x planes k0 - 1 and k0 in the ring, element plane k0 - 1's
+  // upper corners, and the loads for the first iteration in flight
+  fetch_x(k0 - 1);
+  fetch_coef(k0 - 1);
+  store_x(sm1);
+  fetch_x(k0);
+  store_x(s0);
+  fetch_x(k0 + 1);
   __syncthreads();
-  if (k0 > 0) {
-    element_plane(k0 - 1, upPrev);
-  } else {
-    for (int q = tid; q < 4 * EN; q += kMfThreads) upPrev[q] = (T)0;
-  }
-  __syncthreads();
+  element_plane(k0 - 1, sm1, s0, upPrev);   // zero outputs when k0 = 0
+  fetch_coef(k0);
+  fetch_nodes(k0);
 
   for (int k = k0; k < k1; ++k) {
-    load_plane(k + 1);          // the slot of plane k - 1, no longer read
+    store_x(s1);                // ring slot of plane k - 2, no longer read
+    fetch_x(k + 2);
+    __syncthreads();            // plane k + 1 visible; the previous node pass is done with lo / upPrev
+    element_plane(k, s0, s1, upCur);   // zero outputs when k = nz (no element plane)
+    fetch_coef(k + 1);
     __syncthreads();
-    element_plane(k, upCur);    // zero outputs when k = nz (no element plane)
-    __syncthreads();
-    const T* xk = xs + (k & 1) * XN;
-    for (int q = tid; q < W * H; q += kMfThreads) {
-      const int jj = q / W, ii = q - jj * W;
-      const int64_t n = (i0 + ii) + (int64_t)a.nnx * (j0 + jj) + sxy * k;
-      int h = hA;
+    const T* xk = xs + s0 * XN;
+    const int base = k * sxy;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (noff[r] < 0) continue;
+      int hsel = 0;
       if (f == 0) {
-        const uint8_t lb = a.label[n];
-        if (!(lb & kLabActive)) continue;
-        h = (lb & kLabAnode) ? 0 : 1;
+        if (!(lr[r] & kLabActive)) continue;
+        hsel = (lr[r] & kLabAnode) ? 0 : 1;
       }
-      T ax = F.svs[n] * xk[(ii + 1) + XW * (jj + 1)];
-#pragma unroll
-      for (int qq = 0; qq < 2; ++qq)
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const int corner = (1 - pp) + 2 * (1 - qq);
-          const int e = (ii + pp) + EW * (jj + qq);
-          ax += lo[corner * EN + e] + upPrev[corner * EN + e];
-        }
-      const T res = F.b[n] - ax;
+      const int e = nq[r];
+      const T xn = xk[nsm[r]];
+      T ax = sr[r] * xn;
+      ax += (lo[3 * EN + e] + upPrev[3 * EN + e]) + (lo[2 * EN + e + 1] + upPrev[2 * EN + e + 1]);
+      ax += (lo[1 * EN + e + EW] + upPrev[1 * EN + e + EW]) + (lo[e + EW + 1] + upPrev[e + EW + 1]);
+      const T res = br[r] - ax;
+      const int n = noff[r] + base;
       if (MODE == 1) {
         F.r[n] = res;
       } else {
-        const T z = F.dinv[n] * res;
-        const T dn = a.step == 0 ? cheb_coef(a.ctab, 0, 0, h) * z
-                                 : cheb_coef(a.ctab, a.step, 1, h) * F.d[n] + cheb_coef(a.ctab, a.step, 2, h) * z;
+        const T dn = (hsel ? cA[1] : cA[0]) * dr[r] + (hsel ? cB[1] : cB[0]) * (ir[r] * res);
         F.d[n] = dn;
-        F.xo[n] = xk[(ii + 1) + XW * (jj + 1)] + dn;
+        F.xo[n] = xn + dn;
       }
     }
-    __syncthreads();            // lo, upPrev and plane k are reused below
+    fetch_nodes(k + 1);
     T* t = upPrev;
     upPrev = upCur;
     upCur = t;
+    const int st = sm1;
+    sm1 = s0;
+    s0 = s1;
+    s1 = st;
   }
 }
 
@@ -336,11 +417,20 @@ p4d_status mf_setup_t(p4d_ctx* c) {
 // matrix-free only without collector shells (their face stiffness lives in
 // the stored stencils).
 p4d_status mf_setup(p4d_ctx* c) {
+  // The FP64 preconditioner keeps the stored stencils: in FP64 the element
+  // arithmetic (~100 operations per element) runs at GB300's FP64 rate, 58x
+  // below FP32, and costs more than the 27 stored coefficients' traffic.
+  if (c->prm.precision == 0) return P4D_OK;
   const int nnx = c->g.nnx, nny = c->g.nny, nnz = c->g.nnz;
   c->mf_phis = !(c->shell_p > 0.0) && !(c->shell_n > 0.0);
-  c->mf_ntx = std::max(1, (nnx - 1) / kTX);
-  c->mf_nty = std::max(1, (nny - 1) / kTY);
-  const int mw = nnx - (c->mf_ntx - 1) * kTX, mh = nny - (c->mf_nty - 1) * kTY;
+  // tiles of kTX x kTY nodes; the last of an axis takes the remainder, at
+  // most kTX + 1 (kTY + 1) nodes: nnx - 1 elements need ceil((nnx - 1) / kTX) tiles
+  c->mf_ntx = std::max(1, (nnx - 2) / kTX + 1);
+  c->mf_nty = std::max(1, (nny - 2) / kTY + 1);
+  // largest tile: a single tile spans the axis; otherwise the nominal size
+  // or the last tile's remainder (which can be smaller or one larger)
+  const int mw = c->mf_ntx == 1 ? nnx : std::max(kTX, nnx - (c->mf_ntx - 1) * kTX);
+  const int mh = c->mf_nty == 1 ? nny : std::max(kTY, nny - (c->mf_nty - 1) * kTY);
   int zc = kDefaultZChunk;
   if (const char* s = std::getenv("P4D_MF_ZCHUNK")) zc = std::max(1, std::atoi(s));
   // planes holding phi_s unknowns
@@ -367,29 +457,22 @@ p4d_status mf_setup(p4d_ctx* c) {
   P4D_TRYS(dalloc_t(c, &d, std::max<size_t>(1, items.size())));
   if (!items.empty()) P4D_TRY(cudaMemcpy(d, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   c->mf_items = d;
-  const size_t ts = c->prm.precision == 0 ? sizeof(double) : sizeof(float);
+  const size_t ts = sizeof(float);
   const size_t xn = (size_t)(mw + 2) * (mh + 2), en = (size_t)(mw + 1) * (mh + 1);
-  c->mf_smem = ts * (2 * xn + 12 * en + 3 * (mw + 1) + 3 * (mh + 1));
+  c->mf_smem = ts * (3 * xn + 12 * en);
+  if (mw > kTX + 1 || mh > kTY + 1 || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
   // The kernels' shared-memory limit is a process-wide attribute shared by
   // every handle: set it to the largest tile any grid can have (64 x 16
   // nodes), never to this handle's size, which would fail the launches of
   // larger handles set up before.
-  const size_t smax = sizeof(double) * (2 * 66 * 18 + 12 * 65 * 17 + 3 * 65 + 3 * 17);
-  if (c->mf_smem > smax) return P4D_ERR_INVALID_ARG;   // cannot happen: tiles are at most 64 x 16 nodes
-  P4D_TRY(cudaFuncSetAttribute(k_mf_level0<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-  P4D_TRY(cudaFuncSetAttribute(k_mf_level0<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+  const size_t smax = sizeof(float) * (3 * (kTX + 3) * (kTY + 3) + 12 * (kTX + 2) * (kTY + 2));
+  if (c->mf_smem > smax) return P4D_ERR_INVALID_ARG;   // cannot happen: tiles are at most (kTX+1) x (kTY+1) nodes
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-  if (c->prm.precision == 0) return mf_setup_t<double>(c);
   return mf_setup_t<float>(c);
 }
 
-// The FP64 preconditioner keeps the stored stencils: in FP64 the element
-// arithmetic (~100 operations per element) runs at GB300's FP64 rate, 58x
-// below FP32, and costs more than the 27 stored coefficients' traffic.
-bool mf_field_on(const p4d_ctx* c, int f) {
-  return c->mf_items && c->prm.precision != 0 && (f != 0 || c->mf_phis);
-}
+bool mf_field_on(const p4d_ctx* c, int f) { return c->mf_items && (f != 0 || c->mf_phis); }
 
 namespace {
 template <typename T, int MODE>
@@ -433,8 +516,7 @@ p4d_status mf_launch(p4d_ctx* c, int fmask, int step) {
 }  // namespace
 
 p4d_status mf_level0(p4d_ctx* c, int fmask, int mode, int step) {
-  if (c->prm.precision == 0)
-    return mode == 0 ? mf_launch<double, 0>(c, fmask, step) : mf_launch<double, 1>(c, fmask, step);
+  if (!c->mf_items) return P4D_ERR_INVALID_ARG;   // FP64 preconditioner: stored stencils only
   return mode == 0 ? mf_launch<float, 0>(c, fmask, step) : mf_launch<float, 1>(c, fmask, step);
 }
 

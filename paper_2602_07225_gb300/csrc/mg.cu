@@ -410,7 +410,7 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
       const double ab = absoff[f * nn + n];
       if (!(diag > 0.0)) diag = fmax(ab, 1e-300);   // keep the smoother finite on a degenerate row
       svar[f * nn + n] = sv[f];
-      svs[f * nn + n] = (T)(sc[f] * sv[f]);   // the matrix-free level 0 adds it to the element part
+      if (svs) svs[f * nn + n] = (T)(sc[f] * sv[f]);   // the matrix-free level 0 adds it to the element part
       sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
       const T dsc = (T)(sc[f] * diag);
       dis[f][n] = (T)1 / dsc;
@@ -1438,7 +1438,7 @@ p4d_status mg_update(p4d_ctx* c) {
     ::p4d::count_launch(), k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3], (double*)l0.dinv[0], (double*)l0.dinv[2],
-        (double*)l0.dinv[3], svar, l0.lam, (double*)c->mf_svs);
+        (double*)l0.dinv[3], svar, l0.lam, (double*)nullptr);
   else
     ::p4d::count_launch(), k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],

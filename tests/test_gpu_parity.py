@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from p4d_inputs import make_case, make_box_case, make_slab_case
+from p4d_inputs import make_case, make_box_case, make_slab_case, make_tpms_cell
 from oracle.fe import Disc
 from oracle.krylov import LinearSolve, per_field_error
 from oracle.blocks import BlockPrecond
@@ -29,6 +29,8 @@ CASES = {
     # the paper's open-circuit potential curves in the kinetics (the seeded
     # cathode stoichiometries cross the steep step of the LiCoO2 curve)
     "paper_ocp": lambda: make_case("cube8"),
+    # the paper's interpenetrating gyroid electrodes (Case IV), voxelised
+    "tpms": lambda: make_tpms_cell(16, 16, 8),
 }
 # options of the oracle (Disc) and of the library per case
 ORACLE_KW = {"paper_ocp": dict(ocp="paper")}

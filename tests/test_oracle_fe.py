@@ -403,3 +403,19 @@ def test_multigrid_factor_with_anisotropic_coarsening():
         rho[name] = (np.linalg.norm(x) / e0) ** 0.1
     # measured: 0.46 with full coarsening, 0.24 with the rule
     assert rho["strong"] < 0.3 and rho["strong"] < 0.6 * rho["full"], rho
+
+
+def test_tpms_cell_charge_balance():
+    """The voxelised interpenetrating gyroid (the paper's Case IV): the
+    electrodes never share a node, and a converged step balances charge."""
+    from p4d_inputs import make_tpms_cell
+    case = make_tpms_cell(8, 8, 6, state="initial")
+    d, st0 = _disc(case)
+    st1, hist = time_step(d, st0, rtol=1e-13)
+    p = d.p
+    phis_l = np.where(d.act, st1["phis"], 0.0)
+    i_n, *_ = d.kinetics(phis_l, st1["phie"], st1["ce"], st1["cs"][:, -1])
+    I = p["i_app"] * d.gpw.sum()
+    an = d.etype == 0
+    assert np.sum(d.A[~an] * i_n[~an]) == pytest.approx(I, rel=1e-8)
+    assert np.sum(d.A[an] * i_n[an]) == pytest.approx(-I, rel=1e-8)
