@@ -38,10 +38,16 @@ TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of the level-0 k_cheb on cube96 (0
                   "scaled by rows processed")
 FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (2, 10.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms
+# FGMRES rtol of the precision study's second set: the scaled residual's
+# error amplification on hetero128 is ~17 (1.72e-7 at 1e-8), so 3e-9 keeps
+# the solution error within 1e-7
+PRECISION_RTOL = 3e-9
 CYCLE = "V(%d,%d) Chebyshev (eigenvalue ratio %g), coarsening along the strongly coupled axes" % (
     CHEB[0], CHEB[0], CHEB[1])
-WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40)",
-                 "cube96": "cube96 (profiling case): Q1 hex 96x96x72 (anode/sep/cathode 30/12/30)"}
+WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16/40), N_c=20",
+                 "cube96": "cube96 (profiling case): Q1 hex 96x96x72 (anode/sep/cathode 30/12/30), N_c=20",
+                 "tpms128": "tpms128: the paper's interpenetrating gyroid electrodes (Case IV) voxelised on "
+                            "128x128x64 hex elements of a 1 x 1 x 0.5 mm box, N_c=6"}
 CUBE128_DOF = 3 * 129 * 129 * 97 + 20 * 82 * 129 * 129
 
 
@@ -130,11 +136,13 @@ def peaks():
 
 # generator seeds of the named workloads; rank r > 0 of a multi-GPU run
 # solves its own cell of the same shape, seeded SEEDS[name] + 7919 r
-SEEDS = {"cube8": 1001, "cube128": 1002, "cube96": 1002, "hetero128": 1003}
+SEEDS = {"cube8": 1001, "cube128": 1002, "cube96": 1002, "hetero128": 1003, "tpms128": 1006}
 
 
 def make_workload(name, rank=0, **kw):
-    from p4d_inputs import make_case
+    from p4d_inputs import make_case, make_tpms_cell
+    if name == "tpms128":
+        return make_tpms_cell(128, 128, 64, seed=SEEDS[name] + 7919 * rank, **kw)
     if rank == 0:
         return make_case(name, **kw)
     return make_case(name, seed=SEEDS[name] + 7919 * rank, **kw)
@@ -321,6 +329,19 @@ ALG_BYTES_SMOOTH0 = 24
 KERNEL_BYTES_SMOOTH0 = 133
 
 
+def n_grounded(m):
+    """Nodes of the grounded faces (z = 0 faces flagged in gamma_n): they are
+    anode electrode nodes without a phi_s unknown."""
+    import numpy as np
+    nx, ny = int(m["nx"]), int(m["ny"])
+    g = np.asarray(m["gamma_n"]).reshape(ny, nx).astype(bool)
+    nodes = np.zeros((ny + 1, nx + 1), bool)
+    for dj in (0, 1):
+        for di in (0, 1):
+            nodes[dj:dj + ny, di:di + nx] |= g
+    return int(nodes.sum())
+
+
 def roofline_smooth(s, st, case):
     """Level-0 Chebyshev steps that apply the fine-level operator (the
     largest kernel class of a step in the ncu launch list), averaged over
@@ -333,8 +354,7 @@ def roofline_smooth(s, st, case):
     s.set_options(profile=1)
     _, info = s.solve(b)
     s.set_options(profile=0)
-    m = case["mesh"]
-    n_act = s.NE - (int(m["nx"]) + 1) * (int(m["ny"]) + 1)   # grounded z = 0 face is anode (cube)
+    n_act = s.NE - n_grounded(case["mesh"])
     rows = n_act + 2 * s.nn
     ms = info["ms_smooth0"] / max(1, info["n_smooth0"])
     # reduced FP64 JVP of the same solve (k_jvp_combine + k_jvp_macro): FP64
@@ -487,12 +507,14 @@ def _field_errors(x, ref, nn):
 
 
 def precision_study(args):
-    """Mixed-precision contract on the heterogeneous cube: one Newton linear
-    solve (rtol 1e-8) with the FP64, FP32 and FP32 + BF16-level
-    preconditioners, each solution's per-field error against the FP64 GPU
-    path solved to 1e-12 and its iteration count; and, on a 16x16x96 column
-    of the same physics, the same three solves against the oracle's direct
-    solve."""
+    """Mixed-precision contract on the heterogeneous cube (hetero128): one
+    Newton linear solve with the FP64, FP32 and FP32 + BF16-level
+    preconditioners, at FGMRES rtol 1e-8 and at the tighter rtol that keeps
+    the solution error within 1e-7; each solution's per-field error against
+    the FP64 GPU path solved to 1e-12, its iteration count and time.  On a
+    64x64x48 heterogeneous box of the same physics (N_c = 10, ~2.2M
+    unknowns) the same solves are compared with the oracle's FGMRES solved to
+    1e-12."""
     import torch
     from p4d_inputs import make_case, make_box_case
     from paper_2602_07225_gb300 import P4DSolver
@@ -500,11 +522,11 @@ def precision_study(args):
     pbuild.build()
     dev = torch.device("cuda", 0)
     names = {0: "fp64", 1: "fp32", 2: "fp32+bf16 levels"}
+    rtols = (1e-8, PRECISION_RTOL)
 
     def solve_set(case, ref_fn):
         rows = []
         ref = None
-        x64 = None
         for prec in (0, 1, 2):
             s = P4DSolver(case, device=dev, precision=prec, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600,
                           cheb_degree=CHEB[0], cheb_ratio=CHEB[1])
@@ -513,31 +535,30 @@ def precision_study(args):
             s.jacobian_update(st)
             if ref is None:
                 ref = ref_fn(s, b)
-            x, info = s.solve(b)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(3):
+            for rtol in rtols:
+                s.set_options(rtol=rtol)
                 x, info = s.solve(b)
-            e1.record()
-            torch.cuda.synchronize()
-            err = _field_errors(x, ref, s.nn)
-            if x64 is None:
-                x64 = x.clone()
-            dif = _field_errors(x, x64, s.nn)
-            rows.append({"precision": names[prec], "iters": info["iters"], "ms_per_solve": e0.elapsed_time(e1) / 3,
-                         "rel_res": info["rel_res"], "err_phis_phie_ce_cs": err, "max_err": max(err),
-                         "max_diff_vs_fp64_preconditioner_same_rtol": max(dif)})
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(3):
+                    x, info = s.solve(b)
+                e1.record()
+                torch.cuda.synchronize()
+                err = _field_errors(x, ref, s.nn)
+                rows.append({"precision": names[prec], "rtol": rtol, "iters": info["iters"],
+                             "ms_per_solve": e0.elapsed_time(e1) / 3, "rel_res": info["rel_res"],
+                             "rel_res_unscaled": info["rel_res_unscaled"], "err_phis_phie_ce_cs": err,
+                             "max_err": max(err)})
             s.close()
-        base = rows[0]["iters"]
+        base = {r["rtol"]: r["iters"] for r in rows if r["precision"] == "fp64"}
         for r in rows:
-            r["delta_iters_vs_fp64"] = r["iters"] - base
+            r["delta_iters_vs_fp64"] = r["iters"] - base[r["rtol"]]
         return rows
 
     def gpu_ref(s, b):
         s.set_options(rtol=1e-12, maxit=2000)
-        s2 = s
-        x, info = s2.solve(b)
+        x, info = s.solve(b)
         s.set_options(rtol=1e-8, maxit=600)
         return x.clone()
 
@@ -545,25 +566,28 @@ def precision_study(args):
 
     from oracle.fe import Disc
     from oracle.krylov import LinearSolve
-    L = 100e-6 * 16 / 128
-    col = make_box_case(16, 16, (40, 16, 40), L, (100e-6, 25e-6, 100e-6), 20, 1003, hetero=True, rs_cv=0.3)
-    d = Disc(col["mesh"], col["params"])
+    mid = make_box_case(64, 64, (20, 8, 20), 100e-6, (100e-6, 25e-6, 100e-6), 10, 1003, hetero=True, rs_cv=0.3)
+    d = Disc(mid["mesh"], mid["params"])
     t0 = time.perf_counter()
-    x_or = LinearSolve(d, d.state_from_case(col["state"])).direct()
+    x_or, its_or, _ = LinearSolve(d, d.state_from_case(mid["state"])).fgmres(rtol=1e-12, degree=CHEB[0],
+                                                                               ratio=CHEB[1])
     t_or = time.perf_counter() - t0
     ref_or = torch.tensor(x_or, device=dev)
-    small = solve_set(col, lambda s, b: ref_or)
+    midrows = solve_set(mid, lambda s, b: ref_or)
+    fp32 = [r for r in full if r["precision"] == "fp32"]
     out = {"study": "precision", "metric": METRIC, "unit": "solves/s",
-           "value": 1e3 / full[1]["ms_per_solve"], "n_gpus": 1, "higher_is_better": True,
+           "value": 1e3 / fp32[-1]["ms_per_solve"], "n_gpus": 1, "higher_is_better": True,
            "dtype": "f64 outer / {f64, f32, f32+bf16} preconditioner", "data": "synthetic",
            "config": {"workload": "hetero128: Q1 hex 128x128x96 (40/16/40), lognormal porosity (mean 0.3, CV 0.2, "
                                   "correlation 8 elements), lognormal R_s (CV 0.3), N_c=20, seed 1003; REDUCED, BJ, "
-                                  + CYCLE + ", FGMRES(30) rtol 1e-8",
+                                  + CYCLE + ", FGMRES(30) at rtol 1e-8 and %g; value = FP32 preconditioner at %g"
+                                  % (PRECISION_RTOL, PRECISION_RTOL),
                       "reference": "FP64 GPU path solved to rtol 1e-12"},
            "results": full,
-           "oracle_column": {"workload": "16x16x96 column of hetero128's physics (seed 1003), %d unknowns" % d.ndof,
-                             "reference": "oracle equilibrated sparse LU with refinement (%.1f s)" % t_or,
-                             "results": small}}
+           "oracle_box": {"workload": "64x64x48 (20/8/20) heterogeneous box of hetero128's physics, N_c = 10 "
+                                      "(seed 1003), %d unknowns" % d.ndof,
+                          "reference": "oracle FGMRES to rtol 1e-12 (%d iterations, %.1f s)" % (its_or, t_or),
+                          "results": midrows}}
     print(json.dumps(out))
 
 
@@ -781,7 +805,7 @@ def main():
         "dtype": "f64 outer / f32 preconditioner",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload) +
-                               ", N_c=20, 1C discharge from rest (theta_n 0.8, theta_p 0.6, c_e 1000), "
+                               ", 1C discharge from rest (theta_n 0.8, theta_p 0.6, c_e 1000), "
                                "one step = one backward-Euler step of 10 s by Newton (scaled residual 1e-8), "
                                "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8",
                    "time_steps": args.steps, "unknowns": r["ndof"],

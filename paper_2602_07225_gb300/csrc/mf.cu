@@ -45,7 +45,7 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8;        // nominal node tile (one thread per node)
 constexpr int kMfThreads = kTX * kTY;
-constexpr int kDefaultZChunk = 16;     // node planes per block (tunable: P4D_MF_ZCHUNK)
+constexpr int kDefaultZChunk = 8;      // node planes per block (tunable: P4D_MF_ZCHUNK)
 
 template <typename T>
 struct MfField {
@@ -133,17 +133,31 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   const int k0 = it.z, k1 = it.w;
   const int XW = W + 2, XH = H + 2, EW = W + 1, EH = H + 1;
   const int XN = XW * XH, EN = EW * EH, NN = W * H;
-  T* xs = reinterpret_cast<T*>(smem_raw);          // [3][XN] x planes (ring)
-  T* lo = xs + 3 * XN;                              // [4][EN] lower-corner outputs of the current element plane
-  T* upA = lo + 4 * EN;                             // [4][EN] upper-corner outputs (two buffers)
-  T* upB = upA + 4 * EN;
-  const MfField<T>& F = fsel(a, f);
+  // ring buffers: x planes [4][XN]; element planes' lower-corner outputs
+  // [2][4][EN] and upper-corner outputs [3][4][EN]
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  T* Lb = xs + 4 * XN;
+  T* Ub = Lb + 8 * EN;
+  // the block's field pointers, selected once (not per access)
+  const T* __restrict__ Fx = fsel(a, f).x;
+  T* __restrict__ Fxo = fsel(a, f).xo;
+  const T* __restrict__ Fb = fsel(a, f).b;
+  const T* __restrict__ Fdinv = fsel(a, f).dinv;
+  T* __restrict__ Fd = fsel(a, f).d;
+  T* __restrict__ Fr = fsel(a, f).r;
+  const T* __restrict__ Fsvs = fsel(a, f).svs;
+  const T* __restrict__ Fkc = fsel(a, f).kc;
+  const T* __restrict__ Fmc = fsel(a, f).mc;
   const int tid = threadIdx.x;
   // 32-bit offsets: every level-0 array has fewer than 2^31 entries
   const int sxy = a.nnx * a.nny;
   const int sexy = a.nx * a.ny;
-  const bool mass = F.mc != nullptr;
+  const bool mass = Fmc != nullptr;
 
+  // warp-uniform: does any lane of this warp own a second x entry, element
+  // or node (most warps do not; they skip the second slot's code)
+  const int wb = (tid & ~31) + kMfThreads;
+  const bool wx2 = wb < XN, we2 = wb < EN, wn2 = wb < NN;
   // per-slot constants (slot r: index tid + 256 r of the plane's x entries,
   // elements and nodes), computed once for the whole z march
   int xoff[2], xsm[2];       // x entry: in-plane offset (-1 outside the grid), tile index (-1: none)
@@ -208,23 +222,23 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   auto fetch_x = [&](int k) {
     const bool kin = k >= 0 && k < a.nnz;
     const int base = k * sxy;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) xr[r] = (kin && xoff[r] >= 0) ? F.x[xoff[r] + base] : (T)0;
+    xr[0] = (kin && xoff[0] >= 0) ? Fx[xoff[0] + base] : (T)0;
+    if (wx2) xr[1] = (kin && xoff[1] >= 0) ? Fx[xoff[1] + base] : (T)0;
   };
   auto store_x = [&](int slot) {
     T* dst = xs + slot * XN;
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-      if (xsm[r] >= 0) dst[xsm[r]] = xr[r];
+    if (xsm[0] >= 0) dst[xsm[0]] = xr[0];
+    if (wx2 && xsm[1] >= 0) dst[xsm[1]] = xr[1];
   };
   auto fetch_coef = [&](int ke) {
     const bool kin = ke >= 0 && ke < a.nz;
     const int base = ke * sexy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !we2) break;
       const bool on = kin && eoff[r] >= 0;
-      kr[r] = on ? F.kc[eoff[r] + base] : (T)0;
-      mr[r] = (on && mass) ? F.mc[eoff[r] + base] : (T)0;
+      kr[r] = on ? Fkc[eoff[r] + base] : (T)0;
+      mr[r] = (on && mass) ? Fmc[eoff[r] + base] : (T)0;
     }
   };
   auto fetch_nodes = [&](int k) {
@@ -232,23 +246,26 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     const int base = k * sxy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !wn2) break;
       const bool on = kin && noff[r] >= 0;
       const int n = noff[r] + base;
       lr[r] = (on && f == 0) ? (int)a.label[n] : 0;
-      br[r] = on ? F.b[n] : (T)0;
-      sr[r] = on ? F.svs[n] : (T)0;
+      br[r] = on ? Fb[n] : (T)0;
+      sr[r] = on ? Fsvs[n] : (T)0;
       if (MODE == 0) {
-        ir[r] = on ? F.dinv[n] : (T)0;
-        dr[r] = (on && a.step != 0) ? F.d[n] : (T)0;
+        ir[r] = on ? Fdinv[n] : (T)0;
+        dr[r] = (on && a.step != 0) ? Fd[n] : (T)0;
       }
     }
   };
 
-  // element plane ke between the x planes in ring slots sl (lower) and su
-  // (upper), coefficients in kr / mr: lower corners to lo, upper to up
-  auto element_plane = [&](int ke, int sl, int su, T* up) {
-    const T* xl = xs + sl * XN;
-    const T* xu = xs + su * XN;
+  // element plane ke between x planes ke and ke + 1 of the ring,
+  // coefficients in kr / mr: lower corners to L[ke & 1], upper to U[ke % 3]
+  auto element_plane = [&](int ke) {
+    const T* xl = xs + ((ke + 4) & 3) * XN;
+    const T* xu = xs + ((ke + 5) & 3) * XN;
+    T* lo = Lb + ((ke + 2) & 1) * 4 * EN;
+    T* up = Ub + ((ke + 3) % 3) * 4 * EN;
     T Ksz = 0, Msz = 0, Mdz = 0;
     if (ke >= 0 && ke < a.nz) {
       Ksz = a.gz[ke];
@@ -257,6 +274,7 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !we2) break;
       const int q = eq[r];
       if (q < 0) continue;
       const T kc = kr[r], mc = mr[r];
@@ -296,34 +314,43 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     }
   };
 
-  T* upPrev = upA;
-  T* upCur = upB;
-  // ring slots of x planes k - 1, k, k + 1 (plane k + 2 reuses k - 1's)
-  int sm1 = 0, s0 = 1, s1 = 2;
-  // prologue: x planes k0 - 1 and k0 in the ring, element plane k0 - 1's
-  // upper corners, and the loads for the first iteration in flight
+  // Software pipeline, one barrier per node plane p: x plane p + 3 goes to
+  // the ring, element plane p + 1 is evaluated and node plane p updated
+  // from element planes p (lower corners) and p - 1 (upper corners), with
+  // the loads for the next plane in flight.  Within a phase the writes
+  // (x slot (p+3) & 3, L[(p+1) & 1], U[(p+1) % 3]) and the reads (x slots of
+  // planes p .. p+2, L[p & 1], U[(p-1) % 3]) never overlap.
+  auto store_plane = [&](int k) { store_x((k + 4) & 3); };
   fetch_x(k0 - 1);
-  fetch_coef(k0 - 1);
-  store_x(sm1);
+  store_plane(k0 - 1);
   fetch_x(k0);
-  store_x(s0);
+  store_plane(k0);
   fetch_x(k0 + 1);
+  store_plane(k0 + 1);
+  fetch_x(k0 + 2);
+  store_plane(k0 + 2);
+  fetch_coef(k0 - 1);
   __syncthreads();
-  element_plane(k0 - 1, sm1, s0, upPrev);   // zero outputs when k0 = 0
+  element_plane(k0 - 1);   // zero outputs when k0 = 0; its lower corners are never read
   fetch_coef(k0);
+  element_plane(k0);
+  fetch_coef(k0 + 1);
+  fetch_x(k0 + 3);
   fetch_nodes(k0);
+  __syncthreads();
 
   for (int k = k0; k < k1; ++k) {
-    store_x(s1);                // ring slot of plane k - 2, no longer read
-    fetch_x(k + 2);
-    __syncthreads();            // plane k + 1 visible; the previous node pass is done with lo / upPrev
-    element_plane(k, s0, s1, upCur);   // zero outputs when k = nz (no element plane)
-    fetch_coef(k + 1);
-    __syncthreads();
-    const T* xk = xs + s0 * XN;
+    store_plane(k + 3);         // the slot of plane k - 1, no longer read
+    fetch_x(k + 4);
+    element_plane(k + 1);       // zero outputs beyond the last element plane
+    fetch_coef(k + 2);
+    const T* xk = xs + ((k + 4) & 3) * XN;
+    const T* lo = Lb + ((k + 2) & 1) * 4 * EN;
+    const T* upPrev = Ub + ((k + 2) % 3) * 4 * EN;
     const int base = k * sxy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !wn2) break;
       if (noff[r] < 0) continue;
       int hsel = 0;
       if (f == 0) {
@@ -338,21 +365,15 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
       const T res = br[r] - ax;
       const int n = noff[r] + base;
       if (MODE == 1) {
-        F.r[n] = res;
+        Fr[n] = res;
       } else {
         const T dn = (hsel ? cA[1] : cA[0]) * dr[r] + (hsel ? cB[1] : cB[0]) * (ir[r] * res);
-        F.d[n] = dn;
-        F.xo[n] = xn + dn;
+        Fd[n] = dn;
+        Fxo[n] = xn + dn;
       }
     }
     fetch_nodes(k + 1);
-    T* t = upPrev;
-    upPrev = upCur;
-    upCur = t;
-    const int st = sm1;
-    sm1 = s0;
-    s0 = s1;
-    s1 = st;
+    __syncthreads();
   }
 }
 
@@ -459,13 +480,13 @@ p4d_status mf_setup(p4d_ctx* c) {
   c->mf_items = d;
   const size_t ts = sizeof(float);
   const size_t xn = (size_t)(mw + 2) * (mh + 2), en = (size_t)(mw + 1) * (mh + 1);
-  c->mf_smem = ts * (3 * xn + 12 * en);
+  c->mf_smem = ts * (4 * xn + 20 * en);
   if (mw > kTX + 1 || mh > kTY + 1 || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
   // The kernels' shared-memory limit is a process-wide attribute shared by
   // every handle: set it to the largest tile any grid can have (64 x 16
   // nodes), never to this handle's size, which would fail the launches of
   // larger handles set up before.
-  const size_t smax = sizeof(float) * (3 * (kTX + 3) * (kTY + 3) + 12 * (kTX + 2) * (kTY + 2));
+  const size_t smax = sizeof(float) * (4 * (kTX + 3) * (kTY + 3) + 20 * (kTX + 2) * (kTY + 2));
   if (c->mf_smem > smax) return P4D_ERR_INVALID_ARG;   // cannot happen: tiles are at most (kTX+1) x (kTY+1) nodes
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
