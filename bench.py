@@ -31,11 +31,13 @@ METRIC = "Newton linear solves/s & FGMRES iters/s to 1e-8 rel. residual; mixed v
 WORKLOAD = "cube128"
 # unknowns of cube128: 3 fields on 129*129*97 nodes + N_c = 20 radial nodes on
 # the 82 electrode node layers (41 anode + 41 cathode)
-# DRAM bytes per byte the level-0 Chebyshev kernel itself moves, from an ncu
-# capture of two of its launches on cube96 (254,608,256 / 259,039,179)
-TRAFFIC_PER_KERNEL_BYTE = 254608256 / 259039179
-TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of the level-0 k_cheb on cube96 (0.983 x its own bytes), "
-                  "scaled by rows processed")
+# DRAM bytes per row of one level-0 Chebyshev step (k_mf_level0, all four
+# hierarchies), from an ncu capture of that launch on cube128 itself
+# (dram__bytes_read.sum + dram__bytes_write.sum = 99.46 + 15.47 MB for
+# 4,576,275 rows; a one-pass metric set, so the full-size capture is safe)
+TRAFFIC_PER_ROW = (99.46e6 + 15.47e6) / 4576275
+TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of one level-0 k_mf_level0 launch on cube128 (1.05 x the "
+                  "24 B/row algorithmic bytes), per row x rows")
 FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (2, 10.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms
 # FGMRES rtol of the precision study's second set: the scaled residual's
@@ -324,9 +326,12 @@ def measure_fp64(s):
 # 1/diag and d, write d and x_out: 6 x 4 B of FP32 vectors), the per-unit
 # figure of the survey's measurement plan.
 ALG_BYTES_SMOOTH0 = 24
-# Bytes the level-0 step of this build moves per node and field (stored
-# 27-point FP32 stencil, x, b, 1/diag, d, mask, d and x_out).
-KERNEL_BYTES_SMOOTH0 = 133
+# Bytes the matrix-free level-0 step reads and writes per node and field:
+# x, b, 1/diag, d and the variable diagonal in, d and x_out out (7 x 4 B),
+# the element coefficients (~4 B per node; 8 for c_e) and the phi_s label
+# byte, ~33 B; ncu measures ~25 B of DRAM traffic per row on cube128 (part of
+# the x tiles' halo and the coefficients come from L2).
+KERNEL_BYTES_SMOOTH0 = 33
 
 
 def n_grounded(m):
@@ -363,7 +368,8 @@ def roofline_smooth(s, st, case):
     # electrode node (Schur coupling)
     fma = 27 * n_act + 55 * s.nn + 10 * s.NE
     jvp_ms = info["ms_jvp"] / max(1, info["n_jvp"])
-    return {"kernel": "level-0 Chebyshev step (FP32, 4 hierarchies)", "ms": ms, "rows": rows,
+    return {"kernel": "k_mf_level0: level-0 Chebyshev step, matrix-free (FP32, 4 hierarchies)", "ms": ms,
+            "rows": rows,
             "bytes": ALG_BYTES_SMOOTH0 * rows, "kernel_bytes": KERNEL_BYTES_SMOOTH0 * rows,
             "gbs": ALG_BYTES_SMOOTH0 * rows / (ms * 1e-3) / 1e9,
             "kernel_gbs": KERNEL_BYTES_SMOOTH0 * rows / (ms * 1e-3) / 1e9, "launches": info["n_smooth0"],
@@ -788,9 +794,7 @@ def main():
     tot = r["tot"]
     roof = r["roof"]
     f64 = r["fp64_rate"]
-    traffic = None
-    if args.workload in ("cube128", "cube96") and TRAFFIC_PER_KERNEL_BYTE is not None:
-        traffic = TRAFFIC_PER_KERNEL_BYTE * roof["kernel_bytes"]
+    traffic = TRAFFIC_PER_ROW * roof["rows"] if args.workload == "cube128" else None
     out = {
         "metric": METRIC,
         "value": r["solves_per_s"],
@@ -829,8 +833,9 @@ def main():
                      "traffic_source": TRAFFIC_SOURCE,
                      "kernel": roof["kernel"], "peak_source": src, "ms_per_launch": roof["ms"],
                      "bytes_per_launch": roof["bytes"],
-                     "bytes_note": "%d B per node and field (matrix-free fine-level Chebyshev step: x, b, 1/diag, "
-                                   "d in, d and x out) x %d rows" % (ALG_BYTES_SMOOTH0, roof["rows"]),
+                     "bytes_note": "%d B per node and field (the survey's algorithmic bytes of a fine-level "
+                                   "Chebyshev step: x, b, 1/diag, d in, d and x out) x %d rows"
+                                   % (ALG_BYTES_SMOOTH0, roof["rows"]),
                      "kernel_bytes_per_launch": roof["kernel_bytes"],
                      "kernel_gbs": roof["kernel_gbs"], "kernel_frac": roof["kernel_gbs"] / peak},
         "solve_phases_ms": roof["phases_ms"],
