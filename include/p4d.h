@@ -126,6 +126,11 @@ typedef struct {
                            potential curves (Appendix "Model Parameters": graphite anode,
                            LiCoO2 cathode with theta~ = 1.062 theta), U and dU/dtheta in the
                            kinetics of the residual and the Jacobian */
+  int32_t transport_model; /* 0: constant kappa and De; 1: the paper's kappa(c_e), D_e(c_e)
+                           (eqs. kappa_app, De_app with their Arrhenius factors at T), per
+                           element at the element mean of the nodal c_e; kappa and De are then
+                           ignored, and the multigrid preconditioner uses the laws at
+                           c_e = 1000 mol/m^3.  Fixed at p4d_setup */
 } p4d_params;
 
 /* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */
@@ -158,7 +163,7 @@ typedef struct {
 
 /* Fill *p with the defaults (paper constants, BJ, FP32 preconditioner,
    restart 30, rtol 1e-8, REDUCED mode, Chebyshev degree 2, ratio 10,
-   linear OCP). */
+   linear OCP, constant transport coefficients). */
 void p4d_params_default(p4d_params* p);
 
 /* Build a handle for one cell (paper sections 3-4): validates the mesh,
@@ -184,7 +189,7 @@ p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out);
 /* Change solver options (combine, order, restart, maxit, rtol, cheb_ratio,
    cheb_degree, mode, profile) and the kinetics constants.  precision,
    coarse_max and the parameters assembled at setup (dt, F, brug, De, kappa,
-   sigma_n, sigma_p) cannot change (INVALID_ARG). */
+   sigma_n, sigma_p, transport_model) cannot change (INVALID_ARG). */
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* params);
 
 /* Nonlinear residual R(u) (paper section 4, block residual [R_phis; R_phie;
@@ -276,7 +281,9 @@ void p4d_batch_destroy(p4d_batch b);
    first call before any stream capture.  All calls share the one array, so
    calls whose kernels overlap on the GPU (several streams or handles at
    once) race; nothing in it needs to start at zero (each entry is written
-   before it is read within a call).  The result agrees with p4d_jvp's to
+   before it is read within a call).  Not available with transport_model 1
+   (INVALID_ARG: those products need per-element scratch of the handle).
+   The result agrees with p4d_jvp's to
    rounding (the non-transposed product forms phi_e + (gamma/c_e) c_e inside
    the stencil loop rather than in a separate pass).  Returns INVALID_ARG
    when the handle has more than P4D_NOALLOC_MAX_NELEC electrode nodes, when

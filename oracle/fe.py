@@ -151,15 +151,17 @@ def ocp_paper(theta, cathode):
     return np.where(cathode, Up, Un), np.where(cathode, dUp, dUn)
 
 
-def transport_paper(ce):
+def transport_paper(ce, T=298.15, R=8.31446):
     """Bulk electrolyte conductivity kappa(c_e) and diffusivity D_e(c_e) of
-    the paper (Appendix "Model Parameters", eqs. kappa_app and De_app, at
-    T = 298.15 K where the Arrhenius factors are 1), with their derivatives
-    with respect to c_e (mol/m^3)."""
+    the paper (Appendix "Model Parameters", eqs. kappa_app and De_app, with
+    their Arrhenius factors exp(E/R (1/298.15 - 1/T)), E = 34700 and
+    37040 J/mol), with their derivatives with respect to c_e (mol/m^3)."""
     c = np.asarray(ce, float) / 1000.0
-    kap = 0.0911 + 1.9101 * c - 1.052 * c ** 2 + 0.1554 * c ** 3
-    dkap = (1.9101 - 2.104 * c + 0.4662 * c ** 2) / 1000.0
-    De = 5.34e-10 * np.exp(-0.65 * c)
+    ak = np.exp(34700.0 / R * (1.0 / 298.15 - 1.0 / T))
+    ad = np.exp(37040.0 / R * (1.0 / 298.15 - 1.0 / T))
+    kap = ak * (0.0911 + 1.9101 * c - 1.052 * c ** 2 + 0.1554 * c ** 3)
+    dkap = ak * (1.9101 - 2.104 * c + 0.4662 * c ** 2) / 1000.0
+    De = ad * 5.34e-10 * np.exp(-0.65 * c)
     dDe = -0.65e-3 * De
     return kap, dkap, De, dDe
 
@@ -390,7 +392,7 @@ class Disc:
         if self.transport_model == "constant":
             z = np.zeros(self.nelem)
             return epb * self.p["kappa"], epb * self.p["De"], z, z
-        kap, dkap, De, dDe = transport_paper(ce[self.conn].mean(axis=1))
+        kap, dkap, De, dDe = transport_paper(ce[self.conn].mean(axis=1), self.p["T"], self.p["R"])
         return epb * kap, epb * De, epb * dkap, epb * dDe
 
     def _gamma(self):

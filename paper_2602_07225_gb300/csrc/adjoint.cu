@@ -96,6 +96,8 @@ struct GradArgs {
   Grid g;
   int nx, ny, nz;
   double brug, kappa, De, idt, gamma;
+  int transport;         // 1: bulk kappa, D_e of the paper at the element mean of c_e
+  double T, Rg;
   const double *hx, *hy, *hz;
   const uint8_t* region;
   const double *eps, *eps_s;
@@ -149,8 +151,14 @@ __global__ void k_grad_elem(GradArgs a, const double* __restrict__ lam, const do
   const bool el = r == 0 || r == 2;
   const double ep = a.eps[e];
   const double dpb = a.brug * pow(ep, a.brug - 1.0);
+  double kb = a.kappa, Db = a.De;
+  if (a.transport) {
+    double cbar = 0.0, dk, dd;
+    for (int l = 0; l < 8; ++l) cbar += uc[l];
+    transport_bulk(0.125 * cbar, a.T, a.Rg, kb, dk, Db, dd);
+  }
   if (g_sig && el) g_sig[e] += -pow(a.eps_s[e], a.brug) * Ks;
-  if (g_eps) g_eps[e] += -(dpb * a.kappa * Ke + Mc * a.idt + dpb * a.De * Kc);
+  if (g_eps) g_eps[e] += -(dpb * kb * Ke + Mc * a.idt + dpb * Db * Kc);
   if (g_Ds && el) {
     double s = 0.0;
     for (int l = 0; l < 8; ++l) s += P[a.eidx[nd[l]]];
@@ -308,6 +316,7 @@ p4d_status p4d_param_grad(p4d_handle h, const p4d_state* st, const double* lam, 
   a.gamma = h->prm.diffpot_sign * 2.0 * h->prm.R * h->prm.T * (1.0 - h->prm.tplus) / h->prm.F;
   a.hx = h->hx; a.hy = h->hy; a.hz = h->hz; a.region = h->region; a.eps = h->eps_e; a.eps_s = h->epss_e;
   a.label = h->label; a.eidx = h->eidx;
+  a.transport = h->prm.transport_model; a.T = h->prm.T; a.Rg = h->prm.R;
   ::p4d::count_launch(), k_grad_elem<<<nblocks(h->nelem, 128), 128, 0, h->stream>>>(a, lam, st->phis, st->phie, st->ce, st->ce_prev, P,
                                                                 g_sigma, g_Ds, g_eps);
   P4D_TRY(cudaGetLastError());

@@ -365,7 +365,8 @@ __global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
                                  const double* __restrict__ phis, const double* __restrict__ phie,
                                  const double* __restrict__ ce, const double* __restrict__ ce_prev,
                                  const double* __restrict__ lnce, const double* __restrict__ rin,
-                                 const double* __restrict__ sfix, double* __restrict__ r) {
+                                 const double* __restrict__ sfix, const double* __restrict__ trows,
+                                 double* __restrict__ r) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
   if (n >= nn) return;
@@ -398,8 +399,11 @@ __global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
   } else {
     r[n] = phis[n];
   }
-  const double se = stencil_apply(Jst + 1 * 27 * nn, nn, g, n, i, j, k,
-                                  [&](int64_t m) { return phie[m] + kn.gamma * lnce[m]; });
+  // transport rows: the fixed stencils, or (concentration-dependent
+  // coefficients) the element integrals at this state, trows[0..1][n]
+  const double se = trows ? trows[n]
+                          : stencil_apply(Jst + 1 * 27 * nn, nn, g, n, i, j, k,
+                                          [&](int64_t m) { return phie[m] + kn.gamma * lnce[m]; });
   r[nn + n] = se - ain;
   // mass part on (c_e - c_e_prev), diffusion part (C - M_eps/dt) on c_e: no cancellation between
   // the two time levels
@@ -414,9 +418,10 @@ __global__ void k_residual_macro(Grid g, Kin kn, const double* __restrict__ Jst,
       if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nnx || jj >= g.nny || kk >= g.nnz) continue;
       const int64_t m = n + dx + (int64_t)g.nnx * (dy + (int64_t)g.nny * dz);
       const double mo = Mm[o * nn + n];
-      sc += mo * (ce[m] - ce_prev[m]) + (Cc[o * nn + n] - mo) * ce[m];
+      sc += mo * (ce[m] - ce_prev[m]) + (trows ? 0.0 : (Cc[o * nn + n] - mo) * ce[m]);
     }
   }
+  if (trows) sc += trows[nn + n];
   r[2 * nn + n] = sc - kn.tau * ain;
 }
 
@@ -473,7 +478,7 @@ p4d_status assemble_fixed(p4d_ctx* c, const double* eps, const double* eps_s, co
   const int64_t nn = c->g.nn;
   P4D_TRYS(dalloc_t(c, &c->Jst, (size_t)4 * 27 * nn));
   P4D_TRYS(dalloc_t(c, &c->sfix, (size_t)3 * nn));
-  Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->prm.kappa, c->prm.De, c->prm.dt, c->shell_p, c->shell_n};
+  Phys ph{c->prm.brug, c->prm.sigma_n, c->prm.sigma_p, c->kappa_fix, c->De_fix, c->prm.dt, c->shell_p, c->shell_n};
   ::p4d::count_launch(), k_assemble<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, c->nx, c->ny, c->nz, c->hx, c->hy, c->hz, region,
                                                        eps, eps_s, c->sig_e, c->label, ph, c->Jst, c->sfix);
   P4D_TRY(cudaGetLastError());
@@ -507,6 +512,7 @@ p4d_status linearize(p4d_ctx* c, const p4d_state* st) {
   Kin kn = make_kin(c->prm);
   P4D_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
   ::p4d::count_launch(), k_node_ln<<<nblocks(nn), kBlock, 0, c->stream>>>(nn, st->ce, kn.gamma, c->lnce, c->gdc, c->flags);
+  P4D_TRYS(transport_linearize(c, st));   // K_kappa, C at the state (transport_model 1)
   if (NE > 0)
     ::p4d::count_launch(), k_linearize<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype,
                                                         st->phis, st->phie, st->ce, st->cs, c->Mj, c->betaj,
@@ -531,9 +537,10 @@ p4d_status residual(p4d_ctx* c, const p4d_state* st, double* r) {
   if (NE > 0)
     ::p4d::count_launch(), k_kinetics_only<<<nblocks(NE), kBlock, 0, c->stream>>>(NE, nc, kn, c->enode, c->label, c->etype, st->phis,
                                                             st->phie, st->ce, st->cs, c->rin, c->flags);
+  const double* trows = transport_residual_rows(c, st, c->lnce_r);
   ::p4d::count_launch(), k_residual_macro<<<nblocks(nn, 128), 128, 0, c->stream>>>(c->g, kn, c->Jst, c->label, c->eidx, c->Aj, c->gpw,
                                                              st->phis, st->phie, st->ce, st->ce_prev,
-                                                             c->lnce_r, c->rin, c->sfix, r);
+                                                             c->lnce_r, c->rin, c->sfix, trows, r);
   if (NE > 0)
     ::p4d::count_launch(), k_residual_particle<<<nblocks(NE * nc), kBlock, 0, c->stream>>>(NE, nc, 1.0 / c->prm.dt, st->cs, st->cs_prev, c->Mj,
                                                                     c->kapj, c->betaj, c->rref, c->rin,

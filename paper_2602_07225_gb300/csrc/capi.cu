@@ -123,6 +123,7 @@ bool valid_params(const p4d_params* p) {
   if (!(p->rtol > 0)) return false;
   if (!(p->alpha > 0 && p->alpha < 1)) return false;
   if (p->ocp_model < 0 || p->ocp_model > 1) return false;
+  if (p->transport_model < 0 || p->transport_model > 1) return false;
   bool seen[3] = {false, false, false};
   for (int i = 0; i < 3; ++i) {
     if (p->order[i] < 0 || p->order[i] > 2 || seen[p->order[i]]) return false;
@@ -300,6 +301,10 @@ p4d_status setup_impl(p4d_ctx* c, const p4d_mesh* m, const p4d_params* prm) {
   P4D_TRY(cudaMallocHost(&c->flags_h, sizeof(unsigned)));
   P4D_TRY(cudaMemset(c->flags, 0, sizeof(unsigned)));
 
+  c->kappa_fix = prm->kappa;
+  c->De_fix = prm->De;
+  if (prm->transport_model == 1) transport_reference(*prm, &c->kappa_fix, &c->De_fix);
+  P4D_TRYS(transport_alloc(c));
   P4D_TRYS(assemble_fixed(c, c->eps_e, c->epss_e, c->region));
   P4D_TRYS(mg_plan(c));
   P4D_TRYS(mg_setup_fixed(c));
@@ -352,7 +357,7 @@ void p4d_params_default(p4d_params* p) {
   p->dt = 10.0; p->i_app = -40.2022; p->diffpot_sign = 1.0;
   p->precision = 1; p->combine = 0; p->order[0] = 1; p->order[1] = 0; p->order[2] = 2;
   p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
-  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0; p->ocp_model = 0;
+  p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0; p->ocp_model = 0; p->transport_model = 0;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,
@@ -414,6 +419,7 @@ p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
   // parameters baked into the assembled stencils, the particle factors and
   // the surface-flux factors at setup cannot change
   const p4d_params& o = h->prm;
+  if (p->transport_model != o.transport_model) return P4D_ERR_INVALID_ARG;
   if (p->dt != o.dt || p->F != o.F || p->brug != o.brug || p->De != o.De || p->kappa != o.kappa ||
       p->sigma_n != o.sigma_n || p->sigma_p != o.sigma_p)
     return P4D_ERR_INVALID_ARG;

@@ -168,6 +168,7 @@ p4d_status jvp_full(p4d_ctx* c, const double* x, double* y, int transpose, const
     if (transpose) ::p4d::count_launch(), k_jvp_particle<true><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
     else ::p4d::count_launch(), k_jvp_particle<false><<<nblocks(np), kBlock, 0, c->stream>>>(a, x, b, y, scaled);
   }
+  P4D_TRYS(transport_jvp(c, x, y, transpose, b, scaled));
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -181,6 +182,7 @@ p4d_status jvp_reduced(p4d_ctx* c, const double* x, double* y, int transpose, co
   }
   if (transpose) ::p4d::count_launch(), k_jvp_macro<true, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
   else ::p4d::count_launch(), k_jvp_macro<false, true><<<nblocks(nn, 128), 128, 0, c->stream>>>(a, x, b, y, scaled);
+  P4D_TRYS(transport_jvp(c, x, y, transpose, b, scaled));
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
 }
@@ -232,7 +234,7 @@ p4d_status noalloc_scratch(const p4d_ctx* h, double** out) {
 extern "C" p4d_status p4d_jvp_noalloc(p4d_handle h, const double* x, double* y, int transpose) {
   using namespace p4d;
   if (!h || !x || !y || x == y || !h->linearized) return P4D_ERR_INVALID_ARG;
-  if (h->NE > (int64_t)P4D_NOALLOC_MAX_NELEC) return P4D_ERR_INVALID_ARG;
+  if (h->NE > (int64_t)P4D_NOALLOC_MAX_NELEC || h->prm.transport_model != 0) return P4D_ERR_INVALID_ARG;
   double* tloc = nullptr;
   P4D_TRYS(noalloc_scratch(h, &tloc));
   JvpArgs a = make_args(h);

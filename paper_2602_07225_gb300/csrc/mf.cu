@@ -399,7 +399,7 @@ p4d_status mf_setup_t(p4d_ctx* c) {
   T* coef = nullptr;
   P4D_TRYS(dalloc_t(c, &coef, (size_t)4 * nelem));
   ::p4d::count_launch(), k_mf_coef<T><<<nblocks(nelem), kBlock, 0, c->stream>>>(
-      nelem, c->region, c->eps_e, c->epss_e, c->sig_e, c->prm.brug, c->prm.kappa, c->prm.De, c->prm.dt,
+      nelem, c->region, c->eps_e, c->epss_e, c->sig_e, c->prm.brug, c->kappa_fix, c->De_fix, c->prm.dt,
       c->scale_f[0], c->scale_f[1], c->scale_f[2], coef);
   c->mf_coef = coef;
   // per-axis factors (2/h, h/2, h/6), the x ones divided by 8

@@ -12,6 +12,7 @@
 // the reaction/Schur terms that anchor the near-constant modes of the
 // potential blocks; keeping them apart keeps those modes exact in FP32/BF16.
 #pragma once
+#include <cmath>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -203,6 +204,15 @@ struct p4d_ctx {
   double lam_h[p4d::kMaxLevels][p4d::kNH] = {};   // Gershgorin bounds (host copy, per Newton update)
   double* lam_pin = nullptr;           // pinned staging for lam
   void* yc = nullptr;                  // [NE][nc] particle solve work (compute precision)
+
+  // concentration-dependent transport (transport.cu, transport_model 1)
+  double kappa_fix = 0.0, De_fix = 0.0;  // bulk kappa, D_e of the fixed assembly and the preconditioner
+  double* tr_coefL = nullptr;          // [4][nelem] kappa_eff, D_eff and derivatives at the linearization
+  double* tr_GHL = nullptr;            // [16][nelem] K_e u_e, K_e c_e at the linearization
+  double* tr_coefR = nullptr;          // the same at the state of the last residual evaluation
+  double* tr_GHR = nullptr;
+  double* tr_sc = nullptr;             // [2][nelem] per-element scalars of a Jacobian product
+  double* tr_rows = nullptr;           // [2][nn] transport rows of the last residual evaluation
 
   // matrix-free level 0 (mf.cu), compute precision of the preconditioner
   void* mf_coef = nullptr;             // [4][nelem] sc_0 sigma_eff, sc_1 kappa_eff, sc_2 D_eff, sc_2 eps/dt
@@ -420,6 +430,26 @@ p4d_status mg_vcycle(p4d_ctx* c, const int* hs, int nhs);
 // (0 phi_s, 1 phi_e, 2 c_e) is applied matrix-free; one launch over the
 // fields in fmask: mode 0 Chebyshev step `step` (x -> x2, d), mode 1 r = b - A x
 p4d_status mf_setup(p4d_ctx* c);
+// The paper's bulk electrolyte conductivity kappa(c_e) (S/m) and diffusivity
+// D_e(c_e) (m^2/s) (Appendix "Model Parameters", eqs. kappa_app and De_app,
+// with their Arrhenius factors at temperature T) and their derivatives with
+// respect to c_e (mol/m^3).
+__host__ __device__ inline void transport_bulk(double ce, double T, double Rg, double& kap, double& dkap,
+                                               double& De, double& dDe) {
+  const double c = ce / 1000.0;
+  const double ak = exp(34700.0 / Rg * (1.0 / 298.15 - 1.0 / T));
+  const double ad = exp(37040.0 / Rg * (1.0 / 298.15 - 1.0 / T));
+  kap = ak * (0.0911 + 1.9101 * c - 1.052 * c * c + 0.1554 * c * c * c);
+  dkap = ak * (1.9101 - 2.104 * c + 0.4662 * c * c) / 1000.0;
+  De = ad * 5.34e-10 * exp(-0.65 * c);
+  dDe = -0.65e-3 * De;
+}
+// concentration-dependent transport (transport.cu); no-ops for transport_model 0
+void transport_reference(const p4d_params& p, double* kap, double* De);
+p4d_status transport_alloc(p4d_ctx* c);
+p4d_status transport_linearize(p4d_ctx* c, const p4d_state* st);
+const double* transport_residual_rows(p4d_ctx* c, const p4d_state* st, const double* lnce);
+p4d_status transport_jvp(p4d_ctx* c, const double* x, double* y, int transpose, const double* b, bool scaled);
 bool mf_field_on(const p4d_ctx* c, int f);
 p4d_status mf_level0(p4d_ctx* c, int fmask, int mode, int step);
 // level-0 rhs from an FP64 macro vector: b_h = scale * (r_f - corr)  (see mg.cu)

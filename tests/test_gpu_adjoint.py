@@ -28,18 +28,21 @@ def _params(case):
     return sig0, np.full(region.size, 1e-14), case["mesh"]["eps"].copy()
 
 
-@pytest.mark.parametrize("ocp_model", [0, 1])
-def test_newton_step_matches_oracle(ocp_model):
-    """One backward-Euler step by Newton, with the linear and with the
-    paper's OCP curves (ocp_model 1)."""
+@pytest.mark.parametrize("laws", ["linear", "paper_ocp", "paper"])
+def test_newton_step_matches_oracle(laws):
+    """One backward-Euler step by Newton, with the linear OCP and constant
+    transport, with the paper's OCP curves, and with the paper's OCP and
+    concentration-dependent kappa(c_e), D_e(c_e)."""
     from paper_2602_07225_gb300 import P4DSolver
     from oracle.fe import Disc
     from oracle.krylov import time_step, per_field_error
     case = _case()
-    d = Disc(case["mesh"], case["params"], ocp="paper" if ocp_model else "linear")
+    okw = {"linear": {}, "paper_ocp": dict(ocp="paper"), "paper": dict(material="paper")}[laws]
+    lkw = {"linear": {}, "paper_ocp": dict(ocp_model=1), "paper": dict(ocp_model=1, transport_model=1)}[laws]
+    d = Disc(case["mesh"], case["params"], **okw)
     st0 = d.state_from_case(case["state"])
     st1, _ = time_step(d, st0, rtol=1e-13)
-    s = P4DSolver(case, precision=1, rtol=1e-10, ocp_model=ocp_model)
+    s = P4DSolver(case, precision=1, rtol=1e-10, **lkw)
     st = s.state_tensors(case["state"])
     it, info = s.newton(st, rtol=1e-11)
     x = np.concatenate([st[k].cpu().numpy().ravel() for k in ("phis", "phie", "ce", "cs")])
@@ -47,17 +50,18 @@ def test_newton_step_matches_oracle(ocp_model):
     assert it <= 10
 
 
-@pytest.mark.parametrize("checkpoint,ocp_model", [(1, 0), (2, 0), (2, 1)])
-def test_gradient_matches_oracle_adjoint(checkpoint, ocp_model):
+@pytest.mark.parametrize("checkpoint,laws", [(1, "linear"), (2, "linear"), (2, "paper_ocp"), (2, "paper")])
+def test_gradient_matches_oracle_adjoint(checkpoint, laws):
     from paper_2602_07225_gb300 import terminal_voltage
     from oracle.adjoint import gradient
     case = _case()
     sig0, Ds0, eps0 = _params(case)
     nsteps = 3
-    V_ref, gs, gD, ge = gradient(case, nsteps, sigma_e=sig0, Ds_e=Ds0, eps_e=eps0,
-                                 ocp="paper" if ocp_model else "linear")
+    okw = {"linear": {}, "paper_ocp": dict(ocp="paper"), "paper": dict(material="paper")}[laws]
+    lkw = {"linear": {}, "paper_ocp": dict(ocp_model=1), "paper": dict(ocp_model=1, transport_model=1)}[laws]
+    V_ref, gs, gD, ge = gradient(case, nsteps, sigma_e=sig0, Ds_e=Ds0, eps_e=eps0, **okw)
     t = [torch.tensor(a, requires_grad=True) for a in (sig0, Ds0, eps0)]
-    V = terminal_voltage(*t, case, nsteps, checkpoint=checkpoint, ocp_model=ocp_model)
+    V = terminal_voltage(*t, case, nsteps, checkpoint=checkpoint, **lkw)
     V.backward()
     assert V.item() == pytest.approx(V_ref, rel=1e-10)
     for g, ref in zip((t[0].grad, t[1].grad, t[2].grad), (gs, gD, ge)):

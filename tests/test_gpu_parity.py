@@ -31,10 +31,12 @@ CASES = {
     "paper_ocp": lambda: make_case("cube8"),
     # the paper's interpenetrating gyroid electrodes (Case IV), voxelised
     "tpms": lambda: make_tpms_cell(16, 16, 8),
+    # the paper's OCP curves and concentration-dependent kappa(c_e), D_e(c_e)
+    "paper_laws": lambda: make_case("cube8"),
 }
 # options of the oracle (Disc) and of the library per case
-ORACLE_KW = {"paper_ocp": dict(ocp="paper")}
-LIB_KW = {"paper_ocp": dict(ocp_model=1)}
+ORACLE_KW = {"paper_ocp": dict(ocp="paper"), "paper_laws": dict(material="paper")}
+LIB_KW = {"paper_ocp": dict(ocp_model=1), "paper_laws": dict(ocp_model=1, transport_model=1)}
 
 # FGMRES rtol (scaled norm) per mesh.  The solution error per unit of scaled
 # residual is ~1-2 on the layered cubes but reaches ~25 on meshes whose
