@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--laws", default="linear", choices=["linear", "paper"],
+                    help="material laws: linear OCP and constant transport (the workload definition), or the "
+                         "paper's OCP curves and kappa(c_e), D_e(c_e)")
     ap.add_argument("--slab-nx", type=int, default=2048, help="slab2048: elements along the long axis")
     ap.add_argument("--slab-steps", type=int, default=30, help="slab2048: backward-Euler steps")
     ap.add_argument("--slab-fd", type=int, default=6, help="slab2048: directional finite-difference checks")
@@ -220,6 +223,8 @@ def gpu_leg(args, rank, world, local):
     dev = torch.device("cuda", local)
     case = make_workload(args.workload, rank, state="initial")
     opts = dict(mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0], cheb_ratio=CHEB[1])
+    if args.laws == "paper":
+        opts.update(ocp_model=1, transport_model=1)
     s = P4DSolver(case, device=dev, precision=1, **opts)
     st0 = s.state_tensors(case["state"])
     work = {k: v.clone() for k, v in st0.items()}
@@ -811,7 +816,8 @@ def main():
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload) +
                                ", 1C discharge from rest (theta_n 0.8, theta_p 0.6, c_e 1000), "
                                "one step = one backward-Euler step of 10 s by Newton (scaled residual 1e-8), "
-                               "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8",
+                               "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8"
+                               + (", the paper's OCP curves and kappa(c_e), D_e(c_e)" if args.laws == "paper" else ""),
                    "time_steps": args.steps, "unknowns": r["ndof"],
                    "l2": "inputs larger than L2 (Krylov basis and stencils > 129 MB)"},
         "fgmres_iters_per_s": r["iters_per_s"],
