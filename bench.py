@@ -53,6 +53,10 @@ WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16
 CUBE128_DOF = 3 * 129 * 129 * 97 + 20 * 82 * 129 * 129
 
 
+CGS_DESC = {0: "classical Gram-Schmidt without refinement", 1: "classical Gram-Schmidt, second pass when needed",
+            2: "classical Gram-Schmidt twice"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -65,6 +69,8 @@ def parse():
     ap.add_argument("--laws", default="linear", choices=["linear", "paper"],
                     help="material laws: linear OCP and constant transport (the workload definition), or the "
                          "paper's OCP curves and kappa(c_e), D_e(c_e)")
+    ap.add_argument("--cgs-refine", type=int, default=1, choices=[0, 1, 2],
+                    help="second Gram-Schmidt pass: 0 never (the paper's GMRES setting), 1 when needed, 2 always")
     ap.add_argument("--slab-nx", type=int, default=2048, help="slab2048: elements along the long axis")
     ap.add_argument("--slab-steps", type=int, default=30, help="slab2048: backward-Euler steps")
     ap.add_argument("--slab-fd", type=int, default=6, help="slab2048: directional finite-difference checks")
@@ -222,7 +228,8 @@ def gpu_leg(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case = make_workload(args.workload, rank, state="initial")
-    opts = dict(mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0], cheb_ratio=CHEB[1])
+    opts = dict(mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0], cheb_ratio=CHEB[1],
+                cgs_refine=args.cgs_refine)
     if args.laws == "paper":
         opts.update(ocp_model=1, transport_model=1)
     s = P4DSolver(case, device=dev, precision=1, **opts)
@@ -816,7 +823,8 @@ def main():
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload) +
                                ", 1C discharge from rest (theta_n 0.8, theta_p 0.6, c_e 1000), "
                                "one step = one backward-Euler step of 10 s by Newton (scaled residual 1e-8), "
-                               "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8"
+                               "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8, "
+                               + CGS_DESC[args.cgs_refine]
                                + (", the paper's OCP curves and kappa(c_e), D_e(c_e)" if args.laws == "paper" else ""),
                    "time_steps": args.steps, "unknowns": r["ndof"],
                    "l2": "inputs larger than L2 (Krylov basis and stencils > 129 MB)"},

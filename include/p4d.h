@@ -131,6 +131,11 @@ typedef struct {
                            element at the element mean of the nodal c_e; kappa and De are then
                            ignored, and the multigrid preconditioner uses the laws at
                            c_e = 1000 mol/m^3.  Fixed at p4d_setup */
+  int32_t cgs_refine;   /* second classical Gram-Schmidt pass of each Arnoldi step:
+                           0 never (the GMRES settings of the paper's Appendix "Solver
+                           parameters" keep the default classical Gram-Schmidt without
+                           refinement), 1 when the first pass leaves ||w|| < 0.7 ||w_0||
+                           (default), 2 always */
 } p4d_params;
 
 /* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */

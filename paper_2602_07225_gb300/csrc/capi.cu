@@ -124,6 +124,7 @@ bool valid_params(const p4d_params* p) {
   if (!(p->alpha > 0 && p->alpha < 1)) return false;
   if (p->ocp_model < 0 || p->ocp_model > 1) return false;
   if (p->transport_model < 0 || p->transport_model > 1) return false;
+  if (p->cgs_refine < 0 || p->cgs_refine > 2) return false;
   bool seen[3] = {false, false, false};
   for (int i = 0; i < 3; ++i) {
     if (p->order[i] < 0 || p->order[i] > 2 || seen[p->order[i]]) return false;
@@ -358,6 +359,7 @@ void p4d_params_default(p4d_params* p) {
   p->precision = 1; p->combine = 0; p->order[0] = 1; p->order[1] = 0; p->order[2] = 2;
   p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
   p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0; p->ocp_model = 0; p->transport_model = 0;
+  p->cgs_refine = 1;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,

@@ -253,7 +253,8 @@ __global__ void k_init_cycle(double* hs, HLay L, int* kdev) {
 }
 
 // Column k: h = h1 + h2, h_{k+1,k} = ||w||, previous rotations, new rotation.
-__global__ void k_givens(double* hs, HLay L, int k, int* kdev) {
+// refine = 0: no second Gram-Schmidt pass ran, h2 is not read.
+__global__ void k_givens(double* hs, HLay L, int k, int* kdev, int refine) {
   if (threadIdx.x != 0) return;
   *kdev = k + 1;
   const int m = L.m;
@@ -265,7 +266,7 @@ __global__ void k_givens(double* hs, HLay L, int k, int* kdev) {
   const double* h2 = hs + L.misc + m + 1;
   const double nw = sqrt(hs[L.misc + 2 * m + 2]);
   double* col = H + (int64_t)k * (m + 1);
-  for (int i = 0; i <= k; ++i) col[i] = h1[i] + h2[i];
+  for (int i = 0; i <= k; ++i) col[i] = refine ? h1[i] + h2[i] : h1[i];
   col[k + 1] = nw;
   for (int i = 0; i < k; ++i) {
     const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -294,12 +295,14 @@ __global__ void k_givens(double* hs, HLay L, int k, int* kdev) {
 // Reorthogonalise only when the first Gram-Schmidt pass cancelled more than
 // half of the vector (||w_after|| < 0.7 ||w_before||, Daniel-Gragg-Kaufman-
 // Stewart); count the passes in misc+2m+7.
-__global__ void k_reorth_flag(double* hs, HLay L, int k) {
+// eta2 = 0.49: a second pass when ||w|| fell below 0.7 ||w_0||; eta2 = 2:
+// always (||w|| never grows in a pass).
+__global__ void k_reorth_flag(double* hs, HLay L, int k, double eta2) {
   if (threadIdx.x != 0) return;
   double* misc = hs + L.misc;
   const double before = misc[k + 1];
   const double after = misc[2 * L.m + 2];
-  const double f = (after < 0.49 * before) ? 1.0 : 0.0;
+  const double f = (after < eta2 * before) ? 1.0 : 0.0;
   misc[2 * L.m + 6] = f;
   misc[2 * L.m + 7] += f;
 }
@@ -604,11 +607,13 @@ p4d_status fg_step_body(FgRun& r, int k, bool graph_precond, double* stat) {
   const double* flag = misc + 2 * L.m + 6;
   R.mdot(c->V, r.len, k + 1, w, r.len, true, misc);                                        // h1, ||w||^2 before
   R.maxpy(c->V, r.len, k + 1, misc, w, r.len, 1.0, nullptr, misc + 2 * L.m + 2, r.gb);     // ||w||^2 after
-  ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(c->hs, L, k);
-  R.mdot(c->V, r.len, k + 1, w, r.len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
-  // ||w||^2 after the second pass (left unchanged when it is skipped)
-  R.maxpy(c->V, r.len, k + 1, misc + L.m + 1, w, r.len, 1.0, flag, misc + 2 * L.m + 2, r.gb);
-  ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(c->hs, L, k, c->kdev);
+  if (c->prm.cgs_refine > 0) {
+    ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, c->stream>>>(c->hs, L, k, c->prm.cgs_refine == 2 ? 2.0 : 0.49);
+    R.mdot(c->V, r.len, k + 1, w, r.len, false, misc + L.m + 1, flag, 1);   // h2 (or 0)
+    // ||w||^2 after the second pass (left unchanged when it is skipped)
+    R.maxpy(c->V, r.len, k + 1, misc + L.m + 1, w, r.len, 1.0, flag, misc + 2 * L.m + 2, r.gb);
+  }
+  ::p4d::count_launch(), k_givens<<<1, 1, 0, c->stream>>>(c->hs, L, k, c->kdev, c->prm.cgs_refine);
   ::p4d::count_launch(), k_scale<<<r.gb, kBlock, 0, c->stream>>>(w, w, r.len, misc + 2 * L.m + 2, 2);
   prof_mark(c, 2);
   if (stat) ::p4d::count_launch(), k_put_status<<<1, 32, 0, c->stream>>>(misc + 2 * L.m + 3, stat);

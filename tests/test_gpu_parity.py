@@ -168,6 +168,25 @@ def test_fgmres_fp64_matches_direct(name, mode):
     assert err <= 1e-9, (err, info)
 
 
+@pytest.mark.parametrize("name", ["cube8", "hetero", "aniso", "graded"])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("refine", [0, 2])
+def test_fgmres_cgs_refine_matches_direct(name, precision, refine):
+    # one Gram-Schmidt pass (the paper's GMRES setting) or always two: the same
+    # solution; the true-residual check ends every solve
+    rtol = (RTOL_FP64 if precision == 0 else RTOL_MIXED)[name]
+    case, d, ref, s, st = _setup(name, precision=precision, mode=1, rtol=rtol, maxit=600, cgs_refine=refine)
+    s.jacobian_update(st)
+    b = -s.residual(st)
+    x, info = s.solve(b)
+    x_ref = LinearSolve(d, ref).direct()
+    err = per_field_error(d, x.cpu().numpy(), x_ref)[0]
+    assert info["status"] == 0, info
+    assert info["rel_res"] <= 2 * rtol, info
+    assert err <= (1e-9 if precision == 0 else 1e-7), (err, info)
+    assert info["reorth"] == (0 if refine == 0 else info["iters"]), info
+
+
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("combine", [0, 1])
