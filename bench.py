@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--laws", default="linear", choices=["linear", "paper"],
                     help="material laws: linear OCP and constant transport (the workload definition), or the "
                          "paper's OCP curves and kappa(c_e), D_e(c_e)")
-    ap.add_argument("--cgs-refine", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--cgs-refine", type=int, default=0, choices=[0, 1, 2],
                     help="second Gram-Schmidt pass: 0 never (the paper's GMRES setting), 1 when needed, 2 always")
     ap.add_argument("--slab-nx", type=int, default=2048, help="slab2048: elements along the long axis")
     ap.add_argument("--slab-steps", type=int, default=30, help="slab2048: backward-Euler steps")
