@@ -269,6 +269,65 @@ p4d_status p4d_batch_adjoint_solve(p4d_batch b, const double* const* g, double* 
 /* Release the batch (NULL is ignored); the cells are untouched. */
 void p4d_batch_destroy(p4d_batch b);
 
+/* ---- Slab domain decomposition of one cell (paper section 5, the strong
+   and weak scaling runs partition the cell over MPI ranks).  The cell is
+   cut along z into slabs, each built as its own handle from the sub-mesh of
+   its elements plus one element layer of each neighbour: consecutive slabs
+   share one element layer, so the lowest local node plane of every slab but
+   the first and the highest of every slab but the last are ghost planes,
+   owned by the neighbour (the slab's owned planes are the rest).  The slab
+   meshes and states are the cell's restricted to those elements and nodes;
+   Gamma_n and the z = 0 foil belong to the first slab only, Gamma_p and the
+   z = Lz foil to the last.  A stencil application exchanges the ghost
+   planes of its input with the owners (pack, transfer, unpack); every inner
+   product sums the slabs' owned-row partial sums.  In this library all
+   slabs of a decomposition live on one GPU and one stream (a transfer is a
+   device-to-device copy; the sum runs over the slabs' staged partials);
+   with one slab per rank the same steps are a send/recv pair per message
+   and an allreduce. */
+typedef struct p4d_dd_ctx* p4d_dd;
+
+/* Halo messages of nparts slabs with nplanes[p] local node planes each
+   ([host], no device work, callable without a GPU): writes 4 int32 per
+   message to plan (if not NULL): source slab, source local plane,
+   destination slab, destination local plane (a ghost plane), and returns
+   the number of messages, 2 (nparts - 1); -1 when nparts < 1 or a slab has
+   no owned plane (nplanes[p] < 1 + its ghost planes). */
+int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan);
+
+/* Group the slab handles parts[0..nparts) (bottom to top; not owned:
+   destroy the decomposition before them).  They must share the device, the
+   stream, nx, ny and nc.  Allocates the message buffers and one
+   right-hand-side copy per slab.  Errors: INVALID_ARG (NULL or repeated
+   handle, mismatch, a slab without owned planes), OOM, CUDA. */
+p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out);
+
+/* Linearize every slab at states[p] (each the cell's state restricted to
+   the slab, ghost planes included), then set the norm floor of the Krylov
+   weights from the owned rows of all slabs.  Synchronizes the stream. */
+p4d_status p4d_dd_jacobian_update(p4d_dd dd, const p4d_state* states);
+
+/* y = J x on the owned rows of every slab ([host] arrays of [device] slab
+   vectors in the full layout).  The ghost planes of x[p] (phi_s, phi_e,
+   c_e) are overwritten with the owners' values first; the ghost rows of
+   y[p] (and the particle rows of the ghost planes' electrode nodes) are
+   zero.  Asynchronous. */
+p4d_status p4d_dd_jvp(p4d_dd dd, double* const* x, double* const* y);
+
+/* J x = b for the whole cell by FGMRES over the slabs (REDUCED mode only,
+   every slab with the same rtol, restart, maxit and cgs_refine, profile
+   off).  b[p], x[p] as p4d_fgmres_solve per slab; the ghost rows of b are
+   ignored, the owned rows of x are the solution (its ghost planes hold the
+   owners' values).  The preconditioner of each slab is its own block
+   preconditioner on the slab: block Jacobi across the slabs, so the
+   iteration count grows with the number of slabs while the converged
+   solution is the cell's.  info (one report for the cell) as
+   p4d_fgmres_solve.  Synchronizes the stream. */
+p4d_status p4d_dd_fgmres_solve(p4d_dd dd, const double* const* b, double* const* x, p4d_info* info);
+
+/* Release the decomposition (NULL is ignored); the slabs are untouched. */
+void p4d_dd_destroy(p4d_dd dd);
+
 /* Largest number of electrode nodes p4d_jvp_noalloc accepts (size of its
    fixed scratch array: 2^20 doubles = 8 MiB per GPU that loads the library). */
 #define P4D_NOALLOC_MAX_NELEC (1 << 20)

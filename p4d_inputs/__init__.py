@@ -24,3 +24,4 @@ from .generators import (  # noqa: F401
     PARAMS_DEFAULT, make_case, make_box_case, make_tiny_case, make_slab_case, theoretical_iapp,
     ocp_linear_secants, CASES, make_gyroid_cell, make_gyroid_batch, radial_grid, make_tpms_cell,
 )
+from .partition import owned_plane_bounds, slab_cases, slab_node_rows  # noqa: F401

@@ -19,9 +19,11 @@ One Newton linear solve of a cell::
 Many cells together: ``BatchSolver(cases).solve_all()`` (lockstep FGMRES
 of all cells, autotuned smoother per grid shape).  Gradients of the
 terminal voltage: ``terminal_voltage(sigma, Ds, eps, case, nsteps)`` is
-differentiable through ``torch.autograd``.
+differentiable through ``torch.autograd``.  One cell cut into z slabs
+(domain decomposition, one handle per slab): ``SlabSolver(slab_cases(case,
+nparts)).solve(...)``.
 """
 from ._native import P4DError, load  # noqa: F401
-from .solver import P4DSolver, default_params  # noqa: F401
+from .solver import P4DSolver, SlabSolver, default_params, halo_plan  # noqa: F401
 from .adjoint import TerminalVoltage, terminal_voltage  # noqa: F401
 from .batch import BatchSolver, Autotuner  # noqa: F401

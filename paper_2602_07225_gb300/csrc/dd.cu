@@ -1,0 +1,308 @@
+// Slab domain decomposition of one cell along z (the partitioning the
+// paper's strong and weak scaling studies, section 5, run over MPI ranks):
+// one handle per slab, consecutive slabs sharing one element layer, so that
+// every interior interface has one ghost node plane on either side.  A
+// stencil application (the JVP) needs the owners' values in the ghost
+// planes (the halo exchange: pack on the owner, one transfer per message,
+// unpack on the receiver); every inner product is a sum of the slabs'
+// owned-row partial sums (the allreduce).  Here all slabs live on one GPU
+// and one stream: a transfer is a device-to-device copy and the allreduce
+// gathers the slabs' partial sums by copies, adds them in slab order and
+// copies the sum back to every slab, which is what a send/recv pair and an
+// allreduce over ranks do with one slab per rank.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "p4d_common.cuh"
+
+namespace p4d {
+namespace {
+
+constexpr int kDDThreads = 256;
+constexpr int kDDBlocks = 2 * 152;
+
+// buf[f][j] = x[f nn + off + j], f = phi_s, phi_e, c_e
+__global__ void k_dd_pack(const double* __restrict__ x, int64_t nn, int64_t off, int64_t nxy,
+                          double* __restrict__ buf) {
+  const int64_t n = 3 * nxy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / nxy, j = i - f * nxy;
+    buf[i] = x[f * nn + off + j];
+  }
+}
+
+__global__ void k_dd_unpack(double* __restrict__ x, int64_t nn, int64_t off, int64_t nxy,
+                            const double* __restrict__ buf) {
+  const int64_t n = 3 * nxy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / nxy, j = i - f * nxy;
+    x[f * nn + off + j] = buf[i];
+  }
+}
+
+// Zero the ghost rows of a slab vector: node rows [0, lo) and [hi, nn) of
+// fields 0..2, and (cs_rows) the particle rows [3nn, 3nn + cs_lo nc) and
+// [3nn + cs_hi nc, 3nn + ne nc) of the ghost planes' electrode nodes.
+__global__ void k_dd_zero_ghost(double* __restrict__ v, int64_t nn, int64_t lo, int64_t hi, int cs_rows,
+                                int64_t cs_lo, int64_t cs_hi, int64_t ne, int nc) {
+  const int64_t nlo = lo, nhi = nn - hi;
+  const int64_t nodes = 3 * (nlo + nhi);
+  const int64_t clo = cs_rows ? cs_lo * nc : 0, chi = cs_rows ? (ne - cs_hi) * nc : 0;
+  const int64_t total = nodes + clo + chi;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nodes) {
+      const int64_t f = i / (nlo + nhi), j = i - f * (nlo + nhi);
+      v[f * nn + (j < nlo ? j : hi + (j - nlo))] = 0.0;
+    } else {
+      const int64_t q = i - nodes;
+      v[3 * nn + (q < clo ? q : cs_hi * nc + (q - clo))] = 0.0;
+    }
+  }
+}
+
+// Owned-row sums of squares of up to four ranges, (v w)^2 (w = null: 1),
+// as block partials partial[block][4].
+struct DDRanges {
+  const double* v[4];
+  const double* w[4];
+  int64_t n[4];
+};
+
+__global__ void __launch_bounds__(kDDThreads) k_dd_sumsq(DDRanges r, double* __restrict__ partial) {
+  double acc[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+    acc[f] = r.n[f] <= 0 ? 0.0 : (r.w[f] ? sumsq_share<true>(r.v[f], r.w[f], r.n[f])
+                                         : sumsq_share<false>(r.v[f], nullptr, r.n[f]));
+  block_sum4(acc, partial);
+}
+
+__global__ void k_dd_sum_blocks(const double* __restrict__ partial, int nblk, double* out) {
+  sum4_warps(partial, nblk, out);
+}
+
+// out[i] = sum over slabs p (in order) of red[p n + i]
+__global__ void k_dd_sum(const double* __restrict__ red, int nparts, int n, double* __restrict__ out) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += red[(int64_t)p * n + i];
+    out[i] = s;
+  }
+}
+
+}  // namespace
+
+p4d_status dd_halo(p4d_dd_ctx* D, double* const* v) {
+  const int nmsg = (int)D->plan.size() / 4;
+  const int64_t nxy = D->nxy;
+  const unsigned gb = nblocks(3 * nxy);
+  for (int m = 0; m < nmsg; ++m) {
+    const int* q = &D->plan[4 * m];
+    p4d_ctx* s = D->parts[q[0]];
+    ::p4d::count_launch(), k_dd_pack<<<gb, kBlock, 0, D->stream>>>(v[q[0]], s->g.nn, q[1] * nxy, nxy,
+                                                                  D->sbuf + (int64_t)m * 3 * nxy);
+  }
+  for (int m = 0; m < nmsg; ++m)
+    P4D_TRY(cudaMemcpyAsync(D->rbuf + (int64_t)m * 3 * nxy, D->sbuf + (int64_t)m * 3 * nxy,
+                            sizeof(double) * 3 * nxy, cudaMemcpyDeviceToDevice, D->stream));
+  for (int m = 0; m < nmsg; ++m) {
+    const int* q = &D->plan[4 * m];
+    p4d_ctx* d = D->parts[q[2]];
+    ::p4d::count_launch(), k_dd_unpack<<<gb, kBlock, 0, D->stream>>>(v[q[2]], d->g.nn, q[3] * nxy, nxy,
+                                                                    D->rbuf + (int64_t)m * 3 * nxy);
+  }
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status dd_zero_ghost(p4d_dd_ctx* D, int p, double* v, bool cs_rows) {
+  p4d_ctx* c = D->parts[p];
+  const int64_t lo = (int64_t)D->own_lo[p] * D->nxy, hi = (int64_t)D->own_hi[p] * D->nxy;
+  const int64_t rows = 3 * (lo + c->g.nn - hi) + (cs_rows ? (D->cs_lo[p] + c->NE - D->cs_hi[p]) * c->nc : 0);
+  if (rows == 0) return P4D_OK;
+  ::p4d::count_launch(), k_dd_zero_ghost<<<std::min<int64_t>(nblocks(rows), 4 * 152), kBlock, 0, D->stream>>>(
+      v, c->g.nn, lo, hi, cs_rows ? 1 : 0, D->cs_lo[p], D->cs_hi[p], c->NE, c->nc);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status dd_allreduce(p4d_dd_ctx* D, double* const* ptrs, int n) {
+  const int P = (int)D->parts.size();
+  if (n <= 0) return P4D_OK;
+  if (n > kDDRed) return P4D_ERR_INVALID_ARG;
+  for (int p = 0; p < P; ++p)
+    P4D_TRY(cudaMemcpyAsync(D->red + (int64_t)p * n, ptrs[p], sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                            D->stream));
+  double* sum = D->red + (int64_t)P * kDDRed;
+  ::p4d::count_launch(), k_dd_sum<<<1, 128, 0, D->stream>>>(D->red, P, n, sum);
+  for (int p = 0; p < P; ++p)
+    P4D_TRY(cudaMemcpyAsync(ptrs[p], sum, sizeof(double) * n, cudaMemcpyDeviceToDevice, D->stream));
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+// Owned-row sums of squares of (v w) per field of slab p: v laid out as the
+// full system (fields 0..2 at f nn, particles at 3 nn), w the same layout
+// or null; out[0..3] on the device.
+p4d_status dd_owned_sumsq(p4d_dd_ctx* D, int p, const double* const* v, const double* w, double* out) {
+  p4d_ctx* c = D->parts[p];
+  const int64_t nn = c->g.nn, lo = (int64_t)D->own_lo[p] * D->nxy, hi = (int64_t)D->own_hi[p] * D->nxy;
+  DDRanges r{};
+  for (int f = 0; f < 3; ++f) {
+    r.v[f] = v[f] + lo;
+    r.w[f] = w ? w + f * nn + lo : nullptr;
+    r.n[f] = hi - lo;
+  }
+  r.v[3] = v[3] ? v[3] + D->cs_lo[p] * c->nc : nullptr;
+  r.w[3] = w ? w + 3 * nn + D->cs_lo[p] * c->nc : nullptr;
+  r.n[3] = v[3] ? (D->cs_hi[p] - D->cs_lo[p]) * c->nc : 0;
+  ::p4d::count_launch(), k_dd_sumsq<<<kDDBlocks, kDDThreads, 0, D->stream>>>(r, D->part);
+  ::p4d::count_launch(), k_dd_sum_blocks<<<1, 128, 0, D->stream>>>(D->part, kDDBlocks, out);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+}  // namespace p4d
+
+using namespace p4d;
+
+extern "C" {
+
+int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan) {
+  if (nparts < 1 || !nplanes) return -1;
+  for (int p = 0; p < nparts; ++p) {
+    const int ghosts = (p > 0) + (p < nparts - 1);
+    if (nplanes[p] < ghosts + 1) return -1;   // at least one owned plane
+  }
+  int m = 0;
+  for (int p = 0; p + 1 < nparts; ++p) {
+    if (plan) {
+      // the upper slab's bottom ghost plane <- the lower slab's last owned plane
+      plan[4 * m + 0] = p; plan[4 * m + 1] = nplanes[p] - 2; plan[4 * m + 2] = p + 1; plan[4 * m + 3] = 0;
+      // the lower slab's top ghost plane <- the upper slab's first owned plane
+      plan[4 * m + 4] = p + 1; plan[4 * m + 5] = 1; plan[4 * m + 6] = p; plan[4 * m + 7] = nplanes[p] - 1;
+    }
+    m += 2;
+  }
+  return m;
+}
+
+p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
+  if (!out) return P4D_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!parts || nparts < 1) return P4D_ERR_INVALID_ARG;
+  for (int i = 0; i < nparts; ++i) {
+    if (!parts[i]) return P4D_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (parts[j] == parts[i]) return P4D_ERR_INVALID_ARG;
+    const p4d_ctx* a = parts[0];
+    const p4d_ctx* b = parts[i];
+    if (b->device != a->device || b->stream != a->stream || b->g.nnx != a->g.nnx || b->g.nny != a->g.nny ||
+        b->nc != a->nc)
+      return P4D_ERR_INVALID_ARG;
+  }
+  std::vector<int32_t> nz1(nparts);
+  for (int i = 0; i < nparts; ++i) nz1[i] = parts[i]->g.nnz;
+  const int nmsg = p4d_dd_halo_plan(nparts, nz1.data(), nullptr);
+  if (nmsg < 0) return P4D_ERR_INVALID_ARG;
+  p4d_dd_ctx* D = new (std::nothrow) p4d_dd_ctx;
+  if (!D) return P4D_ERR_OOM;
+  D->parts.assign(parts, parts + nparts);
+  D->stream = parts[0]->stream;
+  D->nxy = (int64_t)parts[0]->g.nnx * parts[0]->g.nny;
+  D->plan.assign(4 * (size_t)nmsg, 0);
+  p4d_dd_halo_plan(nparts, nz1.data(), D->plan.data());
+  for (int p = 0; p < nparts; ++p) {
+    const p4d_ctx* c = parts[p];
+    D->own_lo.push_back(p > 0 ? 1 : 0);
+    D->own_hi.push_back(p < nparts - 1 ? nz1[p] - 1 : nz1[p]);
+    // electrode nodes are numbered in node order, so a slab's owned ones are
+    // one contiguous range of its list
+    const int64_t lo = (int64_t)D->own_lo[p] * D->nxy, hi = (int64_t)D->own_hi[p] * D->nxy;
+    const auto& en = c->enodes_h;
+    D->cs_lo.push_back(std::lower_bound(en.begin(), en.end(), (int32_t)lo) - en.begin());
+    D->cs_hi.push_back(std::lower_bound(en.begin(), en.end(), (int32_t)hi) - en.begin());
+  }
+  p4d_status st = P4D_OK;
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  if (cudaSetDevice(parts[0]->device) != cudaSuccess) st = P4D_ERR_CUDA;
+  const size_t msg = (size_t)std::max(nmsg, 1) * 3 * D->nxy;
+  if (st == P4D_OK &&
+      (cudaMalloc(&D->sbuf, sizeof(double) * msg) != cudaSuccess ||
+       cudaMalloc(&D->rbuf, sizeof(double) * msg) != cudaSuccess ||
+       cudaMalloc(&D->red, sizeof(double) * (size_t)(nparts + 1) * kDDRed) != cudaSuccess ||
+       cudaMalloc(&D->part, sizeof(double) * 4 * 2 * 152) != cudaSuccess))
+    st = P4D_ERR_OOM;
+  for (int p = 0; p < nparts && st == P4D_OK; ++p) {
+    double* b = nullptr;
+    if (cudaMalloc(&b, sizeof(double) * (size_t)parts[p]->ndof) != cudaSuccess) st = P4D_ERR_OOM;
+    D->bw.push_back(b);
+  }
+  if (dev_prev >= 0) cudaSetDevice(dev_prev);
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    p4d_dd_destroy(D);
+    return st;
+  }
+  *out = D;
+  return P4D_OK;
+}
+
+void p4d_dd_destroy(p4d_dd D) {
+  if (!D) return;
+  if (D->sbuf) cudaFree(D->sbuf);
+  if (D->rbuf) cudaFree(D->rbuf);
+  if (D->red) cudaFree(D->red);
+  if (D->part) cudaFree(D->part);
+  for (double* b : D->bw)
+    if (b) cudaFree(b);
+  delete D;
+}
+
+p4d_status p4d_dd_jacobian_update(p4d_dd D, const p4d_state* states) {
+  if (!D || !states) return P4D_ERR_INVALID_ARG;
+  const int P = (int)D->parts.size();
+  for (int p = 0; p < P; ++p) P4D_TRYS(p4d_jacobian_update(D->parts[p], &states[p]));
+  // the norm floor of the Krylov weights uses ||sqrt(d) u_f|| of the whole
+  // cell: owned rows of every slab, summed over the slabs
+  std::vector<double*> ptr(P);
+  for (int p = 0; p < P; ++p) {
+    const double* v[4] = {states[p].phis, states[p].phie, states[p].ce, states[p].cs};
+    P4D_TRYS(dd_owned_sumsq(D, p, v, D->parts[p]->sqd, D->parts[p]->unorm2));
+    ptr[p] = D->parts[p]->unorm2;
+  }
+  P4D_TRYS(dd_allreduce(D, ptr.data(), 4));
+  P4D_TRY(cudaStreamSynchronize(D->stream));
+  return P4D_OK;
+}
+
+p4d_status p4d_dd_jvp(p4d_dd D, double* const* x, double* const* y) {
+  if (!D || !x || !y) return P4D_ERR_INVALID_ARG;
+  const int P = (int)D->parts.size();
+  for (int p = 0; p < P; ++p)
+    if (!x[p] || !y[p] || x[p] == y[p] || !D->parts[p]->linearized) return P4D_ERR_INVALID_ARG;
+  P4D_TRYS(dd_halo(D, x));
+  for (int p = 0; p < P; ++p) {
+    P4D_TRYS(jvp_full(D->parts[p], x[p], y[p], 0, nullptr, false));
+    P4D_TRYS(dd_zero_ghost(D, p, y[p], true));
+  }
+  return P4D_OK;
+}
+
+p4d_status p4d_dd_fgmres_solve(p4d_dd D, const double* const* b, double* const* x, p4d_info* info) {
+  if (!D || !b || !x) return P4D_ERR_INVALID_ARG;
+  const int P = (int)D->parts.size();
+  const p4d_params& p0 = D->parts[0]->prm;
+  for (int p = 0; p < P; ++p) {
+    const p4d_ctx* c = D->parts[p];
+    if (!b[p] || !x[p] || b[p] == x[p] || !c->linearized || c->prm.profile || c->prm.mode != 1) return P4D_ERR_INVALID_ARG;
+    if (c->prm.rtol != p0.rtol || c->prm.restart != p0.restart || c->prm.maxit != p0.maxit ||
+        c->prm.cgs_refine != p0.cgs_refine)
+      return P4D_ERR_INVALID_ARG;
+  }
+  return fgmres_dd(D, b, x, info);
+}
+
+}  // extern "C"

@@ -183,13 +183,8 @@ __global__ void k_field_norms(const double* __restrict__ b, const double* __rest
 // others unless it lies below the rounding level of the field's own terms
 // (then FGMRES could never reduce its residual by rtol).  Adjoint solves:
 // floor_f = 1e-2 ||b~|| (the adjoint variable has no state scale).
-__global__ void k_weights(const double* __restrict__ partial, int nblk, const double* __restrict__ unorm2,
-                          double floor_rel, int adjoint, double* __restrict__ wf, double* __restrict__ iwf,
-                          double* bn2) {
-  __shared__ double s4[4];
-  sum4_warps(partial, nblk, s4);
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+__device__ void weights_of(const double* s4, const double* __restrict__ unorm2, double floor_rel, int adjoint,
+                           double* __restrict__ wf, double* __restrict__ iwf, double* bn2) {
   double all = 0.0;
   for (int f = 0; f < 4; ++f) all += s4[f];
   double tot = 0.0;
@@ -202,6 +197,30 @@ __global__ void k_weights(const double* __restrict__ partial, int nblk, const do
     tot += s > 0.0 ? s4[f] / s : 0.0;
   }
   bn2[4] = tot;
+}
+
+__global__ void k_weights(const double* __restrict__ partial, int nblk, const double* __restrict__ unorm2,
+                          double floor_rel, int adjoint, double* __restrict__ wf, double* __restrict__ iwf,
+                          double* bn2) {
+  __shared__ double s4[4];
+  sum4_warps(partial, nblk, s4);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  weights_of(s4, unorm2, floor_rel, adjoint, wf, iwf, bn2);
+}
+
+// The same from the four field sums already in sums[0..3] (bn2 may alias sums).
+__global__ void k_weights_sums(const double* sums, const double* __restrict__ unorm2, double floor_rel,
+                               double* __restrict__ wf, double* __restrict__ iwf, double* bn2) {
+  if (threadIdx.x != 0) return;
+  double s4[4];
+  for (int f = 0; f < 4; ++f) s4[f] = sums[f];
+  weights_of(s4, unorm2, floor_rel, 0, wf, iwf, bn2);
+}
+
+// dst = src when the second Gram-Schmidt pass ran (flag), else unchanged.
+__global__ void k_take_if(double* dst, const double* __restrict__ src, const double* __restrict__ flag) {
+  if (threadIdx.x == 0 && *flag != 0.0) *dst = *src;
 }
 
 // Per-field squared norms of an already scaled vector.
@@ -926,6 +945,225 @@ p4d_status fgmres_batched(p4d_batch_ctx* B, const double* const* b, double* cons
     if (out == P4D_OK && R[i].st != P4D_OK) out = R[i].st;
   }
   return out;
+}
+
+// ---------------------------------------------------------------- slab-decomposed driver
+// FGMRES over the z slabs of one cell (REDUCED mode, J x = b).  Every slab
+// runs the single-cell steps on its own rows.  The Krylov vectors keep their
+// ghost rows at zero, so an inner product is the allreduce of the slabs'
+// partial sums, and every slab repeats the Givens update on the same reduced
+// scalars (identical on all slabs).  The operator is the cell's J: before
+// each application the ghost planes of its input receive the owners' values.
+// The preconditioner of a slab is its own block preconditioner on the slab
+// (block Jacobi across the slabs).
+p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4d_info* info) {
+  const int P = (int)D->parts.size();
+  std::vector<FgRun> R(P);
+  std::vector<double*> ptr(P), vec(P);
+  auto reduce = [&](auto&& at, int n) -> p4d_status {
+    for (int p = 0; p < P; ++p) ptr[p] = at(R[p]);
+    return dd_allreduce(D, ptr.data(), n);
+  };
+  auto at_off = [](int64_t mult2m, int64_t add) {
+    return [=](FgRun& r) { return r.misc() + mult2m * r.L.m + add; };
+  };
+  p4d_ctx* c0 = D->parts[0];
+  FgRun& r0 = R[0];
+  const int refine = c0->prm.cgs_refine;
+  for (int p = 0; p < P; ++p) {
+    FgRun& r = R[p];
+    p4d_ctx* c = D->parts[p];
+    r.c = c;
+    r.b = D->bw[p];
+    r.x = x[p];
+    r.trans = 0;
+    r.nn = c->g.nn;
+    r.full = false;
+    r.len = 3 * r.nn;
+    r.m = std::min(c->prm.restart, c->mcap);
+    r.L = hlay(c->mcap);
+    r.tau = (1.0 - c->prm.tplus) / c->prm.F;
+    r.gb = (unsigned)std::min<int64_t>(4 * 152 * 4, (int64_t)nblocks(r.len));
+    prof_reset(c);
+  }
+  P4D_TRY(cudaEventCreate(&r0.ev0));
+  P4D_TRY(cudaEventCreate(&r0.ev1));
+  P4D_TRY(cudaEventRecord(r0.ev0, D->stream));
+  // the right-hand side without its ghost rows
+  for (int p = 0; p < P; ++p) {
+    P4D_TRY(cudaMemcpyAsync(D->bw[p], b[p], sizeof(double) * D->parts[p]->ndof, cudaMemcpyDeviceToDevice, D->stream));
+    P4D_TRYS(dd_zero_ghost(D, p, D->bw[p], true));
+  }
+  // field weights of the whole cell's right-hand side
+  for (int p = 0; p < P; ++p) {
+    p4d_ctx* c = D->parts[p];
+    ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, D->stream>>>(D->bw[p], c->rsqd, R[p].nn, c->ndof,
+                                                                                   c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 128, 0, D->stream>>>(c->part, kRedBlocks, R[p].misc() + 2 * R[p].L.m + 8);
+  }
+  P4D_TRYS(reduce(at_off(2, 8), 4));
+  for (int p = 0; p < P; ++p) {
+    p4d_ctx* c = D->parts[p];
+    double* s4 = R[p].misc() + 2 * R[p].L.m + 8;
+    ::p4d::count_launch(), k_weights_sums<<<1, 32, 0, D->stream>>>(s4, c->unorm2, 1e-14 / c->prm.rtol, c->wf, c->iwf, s4);
+  }
+  // particle condensation (node-local) and the norms of the Krylov right-hand side
+  for (int p = 0; p < P; ++p) {
+    FgRun& r = R[p];
+    p4d_ctx* c = r.c;
+    P4D_TRYS(particle_solve64(c, r.b + 3 * r.nn, c->tmp + 3 * r.nn, nullptr, 0));
+    ::p4d::count_launch(), k_condense<<<nblocks(r.nn), kBlock, 0, D->stream>>>(
+        c->g, c->nc, r.tau, c->eidx, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, r.b, c->tmp + 3 * r.nn,
+        c->bred, 0);
+    r.bk = c->bred;
+    ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, D->stream>>>(r.bk, c->rsqd, r.nn, r.len, c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 128, 0, D->stream>>>(c->part, kRedBlocks, r.misc() + 2 * r.L.m + 16);
+  }
+  P4D_TRYS(reduce(at_off(2, 16), 4));
+  P4D_TRY(cudaMemcpyAsync(c0->hs_h, r0.misc() + 2 * r0.L.m + 8, sizeof(double) * 12, cudaMemcpyDeviceToHost, D->stream));
+  P4D_TRY(cudaStreamSynchronize(D->stream));
+  for (int p = 0; p < P; ++p) {
+    if (p > 0) std::memcpy(D->parts[p]->hs_h, c0->hs_h, sizeof(double) * 12);
+    P4D_TRYS(fg_bnorm(R[p]));
+  }
+  auto share_host = [&](int n) {
+    for (int p = 1; p < P; ++p) std::memcpy(D->parts[p]->hs_h, c0->hs_h, sizeof(double) * n);
+  };
+  // V_0 = s.(b_k - J x), ||V_0|| and the true residual use the same sequence
+  auto residual_norm = [&]() -> p4d_status {
+    P4D_TRYS(dd_halo(D, x));
+    for (int p = 0; p < P; ++p) {
+      p4d_ctx* c = D->parts[p];
+      P4D_TRYS(jvp_reduced(c, x[p], c->V, 0, R[p].bk, true));
+      P4D_TRYS(dd_zero_ghost(D, p, c->V, false));
+      Reducer{c}.mdot(c->V, 0, 0, c->V, R[p].len, true, R[p].misc() + 2 * R[p].L.m + 2);
+    }
+    return reduce(at_off(2, 2), 1);
+  };
+  while (r0.active()) {
+    P4D_TRYS(residual_norm());
+    for (int p = 0; p < P; ++p) {
+      FgRun& r = R[p];
+      p4d_ctx* c = r.c;
+      ++r.restarts;
+      ::p4d::count_launch(), k_init_cycle<<<1, 1, 0, D->stream>>>(c->hs, r.L, c->kdev);
+      ::p4d::count_launch(), k_scale<<<r.gb, kBlock, 0, D->stream>>>(c->V, c->V, r.len, r.misc() + 2 * r.L.m + 5, 1);
+    }
+    P4D_TRY(cudaMemcpyAsync(c0->hs_h, r0.misc() + 2 * r0.L.m + 5, sizeof(double), cudaMemcpyDeviceToHost, D->stream));
+    P4D_TRY(cudaStreamSynchronize(D->stream));
+    share_host(1);
+    for (int p = 0; p < P; ++p) fg_cycle_read(R[p]);
+    if (r0.stop) break;
+    for (int k = 0; !r0.cycle_done; ++k) {
+      // z_k = P_slab^-1 (s^-1 v_k), then the owners' values in its ghost planes
+      for (int p = 0; p < P; ++p) {
+        P4D_TRYS(precond_column(D->parts[p], 0, true));
+        vec[p] = D->parts[p]->Z + (int64_t)k * R[p].len;
+      }
+      P4D_TRYS(dd_halo(D, vec.data()));
+      // w = s.J z_k on the owned rows; h = V^T w, ||w||^2
+      for (int p = 0; p < P; ++p) {
+        p4d_ctx* c = D->parts[p];
+        double* w = c->V + (int64_t)(k + 1) * R[p].len;
+        P4D_TRYS(jvp_reduced(c, vec[p], w, 0, nullptr, true));
+        P4D_TRYS(dd_zero_ghost(D, p, w, false));
+        Reducer{c}.mdot(c->V, R[p].len, k + 1, w, R[p].len, true, R[p].misc());
+      }
+      P4D_TRYS(reduce(at_off(0, 0), k + 2));
+      for (int p = 0; p < P; ++p) {
+        p4d_ctx* c = D->parts[p];
+        FgRun& r = R[p];
+        Reducer{c}.maxpy(c->V, r.len, k + 1, r.misc(), c->V + (int64_t)(k + 1) * r.len, r.len, 1.0, nullptr,
+                         r.misc() + 2 * r.L.m + 2, r.gb);
+      }
+      P4D_TRYS(reduce(at_off(2, 2), 1));
+      if (refine > 0) {
+        // second pass, decided on every slab from the same reduced norms
+        for (int p = 0; p < P; ++p) {
+          p4d_ctx* c = D->parts[p];
+          FgRun& r = R[p];
+          const double* flag = r.misc() + 2 * r.L.m + 6;
+          ::p4d::count_launch(), k_reorth_flag<<<1, 1, 0, D->stream>>>(c->hs, r.L, k, refine == 2 ? 2.0 : 0.49);
+          Reducer{c}.mdot(c->V, r.len, k + 1, c->V + (int64_t)(k + 1) * r.len, r.len, false, r.misc() + r.L.m + 1,
+                          flag, 1);
+        }
+        P4D_TRYS(reduce(at_off(1, 1), k + 1));
+        for (int p = 0; p < P; ++p) {
+          p4d_ctx* c = D->parts[p];
+          FgRun& r = R[p];
+          const double* flag = r.misc() + 2 * r.L.m + 6;
+          ::p4d::count_launch(), k_maxpy<<<r.gb, kBlock, 0, D->stream>>>(c->V, r.len, k + 1, r.misc() + r.L.m + 1,
+                                                                         c->V + (int64_t)(k + 1) * r.len, r.len, 1.0,
+                                                                         flag, c->part);
+          ::p4d::count_launch(), k_reduce_partials<<<1, 256, 0, D->stream>>>(c->part, (int)r.gb, 1, 1,
+                                                                             r.misc() + 2 * r.L.m + 44, flag, 1);
+        }
+        P4D_TRYS(reduce(at_off(2, 44), 1));
+        for (int p = 0; p < P; ++p)
+          ::p4d::count_launch(), k_take_if<<<1, 32, 0, D->stream>>>(R[p].misc() + 2 * R[p].L.m + 2,
+                                                                    R[p].misc() + 2 * R[p].L.m + 44,
+                                                                    R[p].misc() + 2 * R[p].L.m + 6);
+      }
+      for (int p = 0; p < P; ++p) {
+        p4d_ctx* c = D->parts[p];
+        FgRun& r = R[p];
+        double* w = c->V + (int64_t)(k + 1) * r.len;
+        ::p4d::count_launch(), k_givens<<<1, 1, 0, D->stream>>>(c->hs, r.L, k, c->kdev, refine);
+        ::p4d::count_launch(), k_scale<<<r.gb, kBlock, 0, D->stream>>>(w, w, r.len, r.misc() + 2 * r.L.m + 2, 2);
+      }
+      P4D_TRY(cudaMemcpyAsync(c0->hs_h, r0.misc() + 2 * r0.L.m + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              D->stream));
+      P4D_TRY(cudaStreamSynchronize(D->stream));
+      for (int p = 0; p < P; ++p) fg_step_read(R[p], k, c0->hs_h);
+    }
+    // x += Z y on every slab (the same y)
+    for (int p = 0; p < P; ++p) {
+      FgRun& r = R[p];
+      p4d_ctx* c = r.c;
+      if (r.kk > 0) {
+        ::p4d::count_launch(), k_backsolve<<<1, 1, 0, D->stream>>>(c->hs, r.L, r.kk);
+        Reducer{c}.maxpy(c->Z, r.len, r.kk, c->hs + r.L.y, r.x, r.len, -1.0, nullptr, nullptr, r.gb);
+      }
+    }
+    if (r0.st == P4D_ERR_NONFINITE) break;
+    if (r0.st == P4D_OK) {
+      P4D_TRYS(residual_norm());
+      P4D_TRY(cudaMemcpyAsync(c0->hs_h, r0.misc() + 2 * r0.L.m + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                              D->stream));
+      P4D_TRY(cudaStreamSynchronize(D->stream));
+      share_host(1);
+      for (int p = 0; p < P; ++p) fg_cycle_end_read(R[p]);
+    }
+  }
+  // particle back-substitution, then the true residual of the full system
+  for (int p = 0; p < P; ++p) {
+    FgRun& r = R[p];
+    p4d_ctx* c = r.c;
+    ::p4d::count_launch(), k_surface_coupling<<<nblocks(std::max<int64_t>(1, c->NE)), kBlock, 0, D->stream>>>(
+        c->NE, r.tau, c->enode, r.nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, r.x, c->tloc, 0);
+    P4D_TRYS(particle_solve64(c, r.b + 3 * r.nn, r.x + 3 * r.nn, c->tloc, 0));
+  }
+  P4D_TRYS(dd_halo(D, x));
+  for (int p = 0; p < P; ++p) {
+    FgRun& r = R[p];
+    p4d_ctx* c = r.c;
+    double* m = r.misc() + 2 * r.L.m;
+    P4D_TRYS(jvp_full(c, r.x, c->r0, 0, r.b, true));
+    P4D_TRYS(dd_zero_ghost(D, p, c->r0, true));
+    ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, D->stream>>>(c->r0, r.nn, c->ndof, c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 128, 0, D->stream>>>(c->part, kRedBlocks, m + 24);
+    ::p4d::count_launch(), k_field_norms<<<kRedBlocks, kRedThreads, 0, D->stream>>>(c->r0, c->sqd, r.nn, c->ndof, c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 128, 0, D->stream>>>(c->part, kRedBlocks, m + 32);
+    ::p4d::count_launch(), k_field_norms_plain<<<kRedBlocks, kRedThreads, 0, D->stream>>>(r.b, r.nn, c->ndof, c->part);
+    ::p4d::count_launch(), k_sum4<<<1, 128, 0, D->stream>>>(c->part, kRedBlocks, m + 36);
+  }
+  P4D_TRYS(reduce(at_off(2, 24), 4));
+  P4D_TRYS(reduce(at_off(2, 32), 8));
+  P4D_TRY(cudaEventRecord(r0.ev1, D->stream));
+  P4D_TRY(cudaMemcpyAsync(c0->hs_h, r0.misc() + 2 * r0.L.m + 7, sizeof(double) * 33, cudaMemcpyDeviceToHost, D->stream));
+  P4D_TRY(cudaStreamSynchronize(D->stream));
+  fg_finish_read(r0, info);
+  return r0.st;
 }
 
 }  // namespace p4d

@@ -279,6 +279,27 @@ struct p4d_batch_ctx {
   std::vector<unsigned> gen;            // cells' graph generations when gk was built
 };
 
+// Slab domain decomposition of one cell along z: parts[p] is the handle of
+// slab p (bottom to top); consecutive slabs share one element layer, so a
+// slab's ghost node planes (local plane 0 above the bottom slab, the last
+// local plane below the top slab) are owned by its neighbours.  Slab p owns
+// its local node planes [own_lo, own_hi) and its electrode nodes
+// [cs_lo, cs_hi) (node order).
+constexpr int kDDRed = 256;   // largest allreduce (values)
+struct p4d_dd_ctx {
+  std::vector<p4d_ctx*> parts;          // not owned
+  cudaStream_t stream = nullptr;        // the parts' common stream
+  int64_t nxy = 0;                      // nodes per z plane
+  std::vector<int32_t> plan;            // halo messages [n][4]: src slab, src plane, dst slab, dst plane
+  std::vector<int> own_lo, own_hi;
+  std::vector<int64_t> cs_lo, cs_hi;
+  double* sbuf = nullptr;               // [n][3 nxy] packed planes (sender side)
+  double* rbuf = nullptr;               // [n][3 nxy] received planes
+  double* red = nullptr;                // [(P + 1)][kDDRed] allreduce staging; the sum in the last row
+  double* part = nullptr;               // block partial sums
+  std::vector<double*> bw;              // [P] right-hand sides with ghost rows zero
+};
+
 // ---------------------------------------------------------------- helpers
 namespace p4d {
 
@@ -468,5 +489,15 @@ p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int tr
 // Lockstep FGMRES over the cells of a batch (see p4d_batch_ctx).
 p4d_status fgmres_batched(p4d_batch_ctx* B, const double* const* b, double* const* x, p4d_info* info, int transpose);
 void batch_drop_graphs(p4d_batch_ctx* B);
+
+// ---- slab domain decomposition (dd.cu; the driver in krylov.cu)
+// Ghost planes of fields 0..2 of every slab's vector v[p] <- the owners' planes.
+p4d_status dd_halo(p4d_dd_ctx* D, double* const* v);
+// Zero slab p's ghost rows of v (fields 0..2; with cs_rows also the particle rows).
+p4d_status dd_zero_ghost(p4d_dd_ctx* D, int p, double* v, bool cs_rows);
+// ptrs[p][0..n) <- sum over the slabs of ptrs[q][0..n) (n <= kDDRed), on every slab.
+p4d_status dd_allreduce(p4d_dd_ctx* D, double* const* ptrs, int n);
+p4d_status dd_owned_sumsq(p4d_dd_ctx* D, int p, const double* const* v, const double* w, double* out);
+p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4d_info* info);
 
 }  // namespace p4d

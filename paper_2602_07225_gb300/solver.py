@@ -183,3 +183,77 @@ class P4DSolver:
             self.close()
         except Exception:
             pass
+
+
+def halo_plan(nplanes):
+    """Halo messages of z slabs with nplanes[p] local node planes:
+    [(src slab, src plane, dst slab, dst plane)] (p4d_dd_halo_plan; host only)."""
+    lib = N.load()
+    n = len(nplanes)
+    arr = (C.c_int32 * n)(*[int(v) for v in nplanes])
+    m = lib.p4d_dd_halo_plan(n, arr, None)
+    if m < 0:
+        raise ValueError("a slab without owned node planes")
+    out = (C.c_int32 * max(4 * m, 1))()
+    lib.p4d_dd_halo_plan(n, arr, out)
+    return [tuple(out[4 * i:4 * i + 4]) for i in range(m)]
+
+
+class SlabSolver:
+    """One cell cut into z slabs (``p4d_inputs.slab_cases``): one handle per
+    slab, all on one stream, grouped by p4d_dd_create.  Vectors are lists of
+    per-slab device tensors in each slab's full layout."""
+
+    def __init__(self, slabs, device="cuda", stream=None, **opts):
+        self.slabs = slabs
+        dev = torch.device(device)
+        stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.parts = [P4DSolver(s["case"], device=dev, stream=stream, **opts) for s in slabs]
+        self.lib = self.parts[0].lib
+        n = len(self.parts)
+        hs = (C.c_void_p * n)(*[p.h.value for p in self.parts])
+        out = C.c_void_p()
+        N.check(self.lib.p4d_dd_create(hs, n, C.byref(out)), "p4d_dd_create")
+        self.dd = out
+
+    def _ptrs(self, ts):
+        return (C.c_void_p * len(ts))(*[_dev(t).data_ptr() for t in ts])
+
+    def state_tensors(self):
+        return [p.state_tensors(s["case"]["state"]) for p, s in zip(self.parts, self.slabs)]
+
+    def residual(self, states):
+        return [p.residual(s) for p, s in zip(self.parts, states)]
+
+    def jacobian_update(self, states):
+        arr = (N.State * len(self.parts))(*[p._state(s) for p, s in zip(self.parts, states)])
+        N.check(self.lib.p4d_dd_jacobian_update(self.dd, arr), "p4d_dd_jacobian_update")
+
+    def jvp(self, xs):
+        """J x on the owned rows (the ghost planes of each x[p] receive the owners' values)."""
+        ys = [torch.empty_like(x) for x in xs]
+        N.check(self.lib.p4d_dd_jvp(self.dd, self._ptrs(xs), self._ptrs(ys)), "p4d_dd_jvp")
+        return ys
+
+    def solve(self, bs, xs=None, check=True):
+        xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
+        info = N.Info()
+        st = self.lib.p4d_dd_fgmres_solve(self.dd, self._ptrs(bs), self._ptrs(xs), C.byref(info))
+        if check and st != N.OK:
+            raise N.P4DError(st, "p4d_dd_fgmres_solve")
+        d = info.as_dict()
+        d["status"] = st
+        return xs, d
+
+    def close(self):
+        if getattr(self, "dd", None):
+            self.lib.p4d_dd_destroy(self.dd)
+            self.dd = None
+        for p in getattr(self, "parts", []):
+            p.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
