@@ -653,6 +653,78 @@ def ordering_study(args):
     print(json.dumps(out))
 
 
+def slab_study(args):
+    """cube128 (seeded linearization, seed 1002) cut into 1, 2, 4 and 8 z
+    slabs on this one GPU (p4d_dd_*): one handle per slab, ghost planes
+    exchanged before every operator application, every inner product reduced
+    over the slabs, block Jacobi across the slabs.  Iterations, time of one
+    Newton linear solve to 1e-8 and the solution's per-field difference from
+    the undecomposed solve; what one slab per GPU would add (the transfers
+    and allreduces over the interconnect) is not in these times."""
+    import torch
+    from p4d_inputs import make_case, slab_cases, slab_node_rows
+    from paper_2602_07225_gb300 import P4DSolver, SlabSolver
+    from paper_2602_07225_gb300 import build as pbuild
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    case = make_case("cube128")
+    m = case["mesh"]
+    nxy = (m["nx"] + 1) * (m["ny"] + 1)
+    opts = dict(precision=1, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0],
+                cheb_ratio=CHEB[1], cgs_refine=args.cgs_refine)
+
+    def timed(fn, reps=3):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / reps
+
+    s = P4DSolver(case, device=dev, **opts)
+    st = s.state_tensors(case["state"])
+    b = s.residual(st).neg_()
+    s.jacobian_update(st)
+    (x1, info1), ms1 = timed(lambda: s.solve(b))
+    x1 = x1.cpu().numpy()
+    nn = s.nn
+    s.close()
+    del st, b
+    torch.cuda.empty_cache()
+    rows = [{"slabs": 1, "driver": "single cell", "iters": info1["iters"], "ms_per_solve": ms1,
+             "rel_res": info1["rel_res"]}]
+    for nparts in (1, 2, 4, 8):
+        slabs = slab_cases(case, nparts)
+        dd = SlabSolver(slabs, device=dev, **opts)
+        sts = dd.state_tensors()
+        bs = [r.neg_() for r in dd.residual(sts)]
+        dd.jacobian_update(sts)
+        (xs, info), ms = timed(lambda: dd.solve(bs))
+        diff = 0.0
+        for i, (sl, xp) in enumerate(zip(slabs, xs)):
+            glob, loc = slab_node_rows(sl, nxy)
+            xv, nns = xp.cpu().numpy(), dd.parts[i].nn
+            for f in range(3):
+                ref = x1[f * nn:(f + 1) * nn]
+                diff = max(diff, float(np.abs(xv[f * nns + loc] - ref[glob]).max() / np.abs(ref).max()))
+        rows.append({"slabs": nparts, "driver": "decomposed", "iters": info["iters"], "ms_per_solve": ms,
+                     "rel_res": info["rel_res"], "rel_res_unscaled": info["rel_res_unscaled"],
+                     "max_field_diff_vs_cell": diff})
+        dd.close()
+        del dd, sts, bs, xs
+        torch.cuda.empty_cache()
+    out = {"study": "slab_decomposition", "metric": METRIC, "unit": "solves/s", "n_gpus": 1, "data": "synthetic",
+           "higher_is_better": True, "dtype": "f64 outer / f32 preconditioner", "results": rows,
+           "value": 1e3 / rows[2]["ms_per_solve"],
+           "config": {"workload": "cube128 seeded linearization (seed 1002) as 1-8 z slabs on one GPU, REDUCED, "
+                                  + CYCLE + ", FGMRES(30) rtol 1e-8, " + CGS_DESC[args.cgs_refine]
+                                  + "; value = two slabs (linear solve only)"}}
+    print(json.dumps(out))
+
+
 def slab_adjoint(args):
     """Adjoint of the flattened jelly-roll slab: 2048x16x48 elements
     (20/8/20), N_c = 15, tabs on the first 64 element columns (applied
@@ -740,6 +812,9 @@ def main():
     args = parse()
     if args.workload == "slab2048" and args.impl == "gpu":
         slab_adjoint(args)
+        return
+    if args.workload == "slabs128" and args.impl == "gpu":
+        slab_study(args)
         return
     if args.workload == "orderings" and args.impl == "gpu":
         ordering_study(args)

@@ -438,18 +438,6 @@ struct Reducer {
   }
 };
 
-// Runs Arnoldi step k of FGMRES through its captured graph (captured on
-// first use, per transpose and layout; dropped when the options change).
-template <typename F>
-p4d_status launch_step_graph(p4d_ctx* c, int trans, int k, F&& body) {
-  auto& vec = c->itg[trans ? 1 : 0][c->prm.mode == 0 ? 1 : 0];
-  if ((int)vec.size() <= k) vec.resize(k + 1);
-  p4d_ctx::PcGraph& g = vec[k];
-  if (!g.exec) P4D_TRYS(capture_graph(c, g, body));
-  count_launches(g.kernels);
-  P4D_TRY(cudaGraphLaunch(g.exec, c->stream));
-  return P4D_OK;
-}
 
 }  // namespace
 
@@ -475,6 +463,24 @@ __global__ void k_put_status(const double* __restrict__ src, double* __restrict_
 // Condition of a cell's conditional (IF) node in a batched step graph.
 __global__ void k_set_active(cudaGraphConditionalHandle h, const int* __restrict__ active) {
   if (threadIdx.x == 0) cudaGraphSetConditional(h, *active ? 1u : 0u);
+}
+
+// Device gate of a graph-driven restart cycle (in hs after the misc scalars):
+// [0] stop, [1] steps run, [2] residual estimate and [3] status of the last
+// step, [4] step limit of the cycle, [5] ||s.b_k||, [6] rtol.
+constexpr int kGateOff = 48;
+
+__global__ void k_gate(cudaGraphConditionalHandle h, const double* __restrict__ gate, int k) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, (gate[0] == 0.0 && (double)k < gate[4]) ? 1u : 0u);
+}
+
+// After Arnoldi step k (whose estimate and status k_put_status left in
+// gate[2..3]): the cycle stops on a breakdown, a non-finite scalar or a
+// converged estimate, the same tests the host applies to a step's status.
+__global__ void k_step_done(double* gate, int k) {
+  if (threadIdx.x != 0) return;
+  gate[1] = k + 1;
+  if (gate[3] != 0.0 || gate[2] / gate[5] <= gate[6]) gate[0] = 1.0;
 }
 
 struct FgRun;
@@ -749,44 +755,10 @@ void fg_finish_read(FgRun& r, p4d_info* info) {
   }
 }
 
-}  // namespace
-
-p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
-  FgRun r;
-  P4D_TRYS(fg_begin(r, c, b, x, trans));
-  P4D_TRY(cudaStreamSynchronize(c->stream));
-  P4D_TRYS(fg_bnorm(r));
-  while (r.active()) {
-    P4D_TRYS(fg_cycle_launch(r));
-    P4D_TRY(cudaStreamSynchronize(c->stream));
-    fg_cycle_read(r);
-    if (r.stop) break;
-    for (int k = 0; !r.cycle_done; ++k) {
-      if (c->prm.profile) P4D_TRYS(fg_step_body(r, k, true, nullptr));
-      else P4D_TRYS(launch_step_graph(c, trans, k, [&]() { return fg_step_body(r, k, false, nullptr); }));
-      P4D_TRY(cudaStreamSynchronize(c->stream));
-      fg_step_read(r, k, c->hs_h);
-    }
-    P4D_TRYS(fg_cycle_end_launch(r));
-    if (r.st == P4D_ERR_NONFINITE) break;
-    if (r.st == P4D_OK) {
-      P4D_TRY(cudaStreamSynchronize(c->stream));
-      fg_cycle_end_read(r);
-    }
-  }
-  P4D_TRYS(fg_finish_launch(r));
-  P4D_TRY(cudaStreamSynchronize(c->stream));
-  fg_finish_read(r, info);
-  return r.st;
-}
-
-// ---------------------------------------------------------------- batched driver
-namespace {
-
 // What body() launches on c->stream, captured into a new (not instantiated)
 // graph; kernels = its kernel launches.
 template <typename F>
-p4d_status capture_raw(p4d_ctx* c, cudaGraph_t* out, long long* kernels, F&& body) {
+p4d_status capture_body(p4d_ctx* c, cudaGraph_t* out, long long* kernels, F&& body) {
   cudaStream_t user = c->stream;
   c->stream = c->cap_stream;
   *kernels = 0;
@@ -808,6 +780,135 @@ p4d_status capture_raw(p4d_ctx* c, cudaGraph_t* out, long long* kernels, F&& bod
   return st;
 }
 
+// The restart cycle of r as one graph: for k < m, gate(k) -> IF { Arnoldi
+// step k; its status into the gate }.
+p4d_status cycle_graph(FgRun& r, p4d_ctx::CycleGraph*& out) {
+  p4d_ctx* c = r.c;
+  p4d_ctx::CycleGraph& cg = c->cyc[r.trans ? 1 : 0][r.full ? 1 : 0];
+  out = &cg;
+  if (cg.exec && cg.m == r.m) return P4D_OK;
+  if (cg.exec) cudaGraphExecDestroy(cg.exec);
+  cg.exec = nullptr;
+  cg.kernels.assign(r.m, 0);
+  double* gate = r.misc() + 2 * r.L.m + kGateOff;
+  cudaGraph_t G = nullptr;
+  P4D_TRY(cudaGraphCreate(&G, 0));
+  p4d_status st = P4D_OK;
+  cudaGraphNode_t prev = nullptr;
+  for (int k = 0; k < r.m && st == P4D_OK; ++k) {
+    cudaGraph_t step = nullptr;
+    long long kc = 0;
+    st = capture_body(c, &step, &kc, [&]() -> p4d_status {
+      P4D_TRYS(fg_step_body(r, k, false, gate + 2));
+      ::p4d::count_launch(), k_step_done<<<1, 32, 0, c->stream>>>(gate, k);
+      return P4D_OK;
+    });
+    if (st != P4D_OK) break;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t kn = nullptr, cn = nullptr, ch = nullptr;
+    const double* gc = gate;
+    int kk = k;
+    void* args[] = {&h, &gc, &kk};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_gate;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    if (cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+        cudaGraphAddKernelNode(&kn, G, prev ? &prev : nullptr, prev ? 1 : 0, &kp) != cudaSuccess)
+      st = P4D_ERR_CUDA;
+    cp.conditional.handle = h;
+    if (st == P4D_OK && cudaGraphAddNode(&cn, G, &kn, nullptr, 1, &cp) != cudaSuccess) st = P4D_ERR_CUDA;
+    if (st == P4D_OK && cudaGraphAddChildGraphNode(&ch, cp.conditional.phGraph_out[0], nullptr, 0, step) != cudaSuccess)
+      st = P4D_ERR_CUDA;
+    cudaGraphDestroy(step);
+    prev = cn;
+    cg.kernels[k] = kc;
+  }
+  if (st == P4D_OK && cudaGraphInstantiate(&cg.exec, G, 0) != cudaSuccess) st = P4D_ERR_CUDA;
+  cudaGraphDestroy(G);
+  if (st != P4D_OK) {
+    cudaGetLastError();
+    cg.exec = nullptr;
+    return st;
+  }
+  cg.m = r.m;
+  return P4D_OK;
+}
+
+// The Arnoldi steps of one restart cycle by its graph: the host uploads the
+// gate, launches the graph, and reads the gate once at the end.
+p4d_status fg_cycle_steps_graph(FgRun& r) {
+  p4d_ctx* c = r.c;
+  p4d_ctx::CycleGraph* cg = nullptr;
+  P4D_TRYS(cycle_graph(r, cg));
+  double* gate = r.misc() + 2 * r.L.m + kGateOff;
+  double* stage = c->hs_h + kGateOff;
+  stage[0] = 0.0;
+  stage[1] = 0.0;
+  stage[2] = 0.0;
+  stage[3] = 0.0;
+  stage[4] = (double)std::min(r.m, c->prm.maxit - r.iters);
+  stage[5] = r.bnorm;
+  stage[6] = c->prm.rtol;
+  P4D_TRY(cudaMemcpyAsync(gate, stage, 7 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  P4D_TRY(cudaGraphLaunch(cg->exec, c->stream));
+  P4D_TRY(cudaMemcpyAsync(c->hs_h, gate, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  const int nrun = (int)c->hs_h[1];
+  long long launched = cg->m;
+  for (int k = 0; k < nrun; ++k) launched += cg->kernels[k];
+  count_launches(launched);
+  if (nrun < 1) return P4D_ERR_CUDA;   // the first step always runs (limit >= 1, no stop)
+  const double s2[2] = {c->hs_h[2], c->hs_h[3]};
+  r.iters += nrun - 1;
+  fg_step_read(r, nrun - 1, s2);
+  return P4D_OK;
+}
+
+}  // namespace
+
+p4d_status fgmres(p4d_ctx* c, const double* b, double* x, p4d_info* info, int trans) {
+  FgRun r;
+  P4D_TRYS(fg_begin(r, c, b, x, trans));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  P4D_TRYS(fg_bnorm(r));
+  while (r.active()) {
+    P4D_TRYS(fg_cycle_launch(r));
+    P4D_TRY(cudaStreamSynchronize(c->stream));
+    fg_cycle_read(r);
+    if (r.stop) break;
+    if (c->prm.profile) {
+      // per-kernel events cannot sit inside a graph: step by step
+      for (int k = 0; !r.cycle_done; ++k) {
+        P4D_TRYS(fg_step_body(r, k, true, nullptr));
+        P4D_TRY(cudaStreamSynchronize(c->stream));
+        fg_step_read(r, k, c->hs_h);
+      }
+    } else {
+      P4D_TRYS(fg_cycle_steps_graph(r));
+    }
+    P4D_TRYS(fg_cycle_end_launch(r));
+    if (r.st == P4D_ERR_NONFINITE) break;
+    if (r.st == P4D_OK) {
+      P4D_TRY(cudaStreamSynchronize(c->stream));
+      fg_cycle_end_read(r);
+    }
+  }
+  P4D_TRYS(fg_finish_launch(r));
+  P4D_TRY(cudaStreamSynchronize(c->stream));
+  fg_finish_read(r, info);
+  return r.st;
+}
+
+// ---------------------------------------------------------------- batched driver
+namespace {
+
+
 // The batched graph of Krylov column k: for every cell whose restart length
 // exceeds k, set_active(cell) -> IF(cell active) { Arnoldi step k of the
 // cell }.  The cells' chains are independent nodes, so the GPU runs them
@@ -827,7 +928,7 @@ p4d_status batch_step_graph(p4d_batch_ctx* B, std::vector<FgRun>& R, int k, int 
     if (k >= r.m) continue;
     cudaGraph_t step = nullptr;
     long long kc = 0;
-    st = capture_raw(r.c, &step, &kc, [&]() { return fg_step_body(r, k, false, B->stat_dev + 2 * i); });
+    st = capture_body(r.c, &step, &kc, [&]() { return fg_step_body(r, k, false, B->stat_dev + 2 * i); });
     if (st != P4D_OK) break;
     cudaGraphConditionalHandle h;
     cudaGraphNode_t kn = nullptr, cn = nullptr, ch = nullptr;

@@ -250,7 +250,14 @@ struct p4d_ctx {
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;             // kernel nodes (added to the launch counter per launch)
   } pcg[2][2];
-  std::vector<PcGraph> itg[2][2];      // Arnoldi step k of FGMRES, [transpose][full][k]
+  // One FGMRES restart cycle as one graph, [transpose][full]: Arnoldi step k
+  // inside a conditional (IF) node whose condition a one-thread kernel sets
+  // from the device gate (no stop yet, k below the cycle's step limit).
+  struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    int m = 0;                         // steps in the graph
+    std::vector<long long> kernels;    // kernel launches of step k (gate kernels not included)
+  } cyc[2][2];
   unsigned graph_gen = 0;              // incremented whenever the captured graphs are dropped
   cudaStream_t cap_stream = nullptr;
   int* kdev = nullptr;                 // current Krylov column (device)

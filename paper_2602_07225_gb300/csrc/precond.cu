@@ -413,10 +413,12 @@ void drop_graphs(p4d_ctx* c) {
   };
   for (auto& row : c->pcg)
     for (auto& g : row) drop(g);
-  for (auto& row : c->itg)
-    for (auto& v : row) {
-      for (auto& g : v) drop(g);
-      v.clear();
+  for (auto& row : c->cyc)
+    for (auto& g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      g.m = 0;
+      g.kernels.clear();
     }
 }
 

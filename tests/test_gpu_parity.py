@@ -296,6 +296,23 @@ def test_set_params_refuses_assembled_physics():
     s.set_options(cheb_degree=3)
 
 
+@pytest.mark.parametrize("restart,maxit", [(4, 400), (5, 13), (30, 7)])
+def test_cycle_graph_matches_stepwise(restart, maxit):
+    # one graph per restart cycle (an IF node per Arnoldi step, stopped on the
+    # device) against the host stepping through the same kernels; the cycle's
+    # step limit comes from the restart length or the remaining maxit
+    case, d, ref, s, st = _setup("hetero", precision=1, mode=1, rtol=1e-10, maxit=maxit, restart=restart)
+    s.jacobian_update(st)
+    b = -s.residual(st)
+    x_graph, i1 = s.solve(b, check=False)
+    s.set_options(profile=1)
+    x_direct, i2 = s.solve(b, check=False)
+    for key in ("iters", "restarts", "status", "reorth"):
+        assert i1[key] == i2[key], (key, i1, i2)
+    assert i1["iters"] <= maxit
+    assert torch.equal(x_graph, x_direct)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_graph_and_direct_paths_agree(mode, adjoint):
