@@ -661,6 +661,7 @@ def slab_study(args):
     Newton linear solve to 1e-8 and the solution's per-field difference from
     the undecomposed solve; what one slab per GPU would add (the transfers
     and allreduces over the interconnect) is not in these times."""
+    import numpy as np
     import torch
     from p4d_inputs import make_case, slab_cases, slab_node_rows
     from paper_2602_07225_gb300 import P4DSolver, SlabSolver
