@@ -302,9 +302,20 @@ int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan);
    handle, mismatch, a slab without owned planes), OOM, CUDA. */
 p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out);
 
+/* Coarse space of the two-level preconditioner (default 2): 0 none (block
+   Jacobi across the slabs), 1 one constant per slab and block (phi_s of
+   each electrode, phi_e, c_e), 2 also one linear-in-z function per slab and
+   block.  The correction Z A_c^-1 Z^T, with the Galerkin matrix A_c = Z^T J Z
+   of the REDUCED operator, is added to every slab preconditioner's output;
+   A_c (at most 8 per slab) is built at p4d_dd_jacobian_update and solved in
+   FP64 redundantly on every slab.  Takes effect at the next update; a
+   singular A_c leaves the correction off. */
+p4d_status p4d_dd_set_coarse(p4d_dd dd, int32_t modes);
+
 /* Linearize every slab at states[p] (each the cell's state restricted to
    the slab, ghost planes included), then set the norm floor of the Krylov
-   weights from the owned rows of all slabs.  Synchronizes the stream. */
+   weights from the owned rows of all slabs and build the coarse space (one
+   decomposed JVP per coarse basis vector).  Synchronizes the stream. */
 p4d_status p4d_dd_jacobian_update(p4d_dd dd, const p4d_state* states);
 
 /* y = J x on the owned rows of every slab ([host] arrays of [device] slab
@@ -318,11 +329,11 @@ p4d_status p4d_dd_jvp(p4d_dd dd, double* const* x, double* const* y);
    every slab with the same rtol, restart, maxit and cgs_refine, profile
    off).  b[p], x[p] as p4d_fgmres_solve per slab; the ghost rows of b are
    ignored, the owned rows of x are the solution (its ghost planes hold the
-   owners' values).  The preconditioner of each slab is its own block
-   preconditioner on the slab: block Jacobi across the slabs, so the
-   iteration count grows with the number of slabs while the converged
-   solution is the cell's.  info (one report for the cell) as
-   p4d_fgmres_solve.  Synchronizes the stream. */
+   owners' values).  The preconditioner is each slab's own block
+   preconditioner on the slab (block Jacobi across the slabs) plus the
+   coarse correction of p4d_dd_set_coarse; the converged solution is the
+   cell's.  info (one report for the cell) as p4d_fgmres_solve.
+   Synchronizes the stream. */
 p4d_status p4d_dd_fgmres_solve(p4d_dd dd, const double* const* b, double* const* x, p4d_info* info);
 
 /* Release the decomposition (NULL is ignored); the slabs are untouched. */

@@ -91,6 +91,100 @@ __global__ void k_dd_sum(const double* __restrict__ red, int nparts, int n, doub
   }
 }
 
+// Coarse bin of owned node n of field f (-1: phi_s not an unknown there):
+// 2 g for the constant mode, 2 g + 1 for the linear one; g = 0 phi_s anode,
+// 1 phi_s cathode, 2 phi_e, 3 c_e.
+__device__ __forceinline__ int coarse_group(int f, uint8_t lab) {
+  if (f > 0) return f + 1;
+  if (!(lab & kLabActive)) return -1;
+  return (lab & kLabAnode) ? 0 : 1;
+}
+
+// zeta of local node plane k among the owned planes [lo, hi): the cell
+// centres of [-1, 1] cut into hi - lo equal parts
+__device__ __forceinline__ double coarse_zeta(int k, int lo, int hi) {
+  return (2.0 * (k - lo) + 1.0) / (double)(hi - lo) - 1.0;
+}
+
+// Block partials [block][8] of the coarse sums of a slab vector (fields
+// 0..2): bin 2g += u, bin 2g + 1 += u zeta, u = v (sqd iwf_f when scaled:
+// the unscaled s^-1 v of the Krylov space).
+__global__ void __launch_bounds__(kDDThreads) k_dd_crestrict(const double* __restrict__ v,
+                                                             const double* __restrict__ sqd,
+                                                             const double* __restrict__ iwf,
+                                                             const uint8_t* __restrict__ label, int64_t nn,
+                                                             int64_t nxy, int lo, int hi,
+                                                             double* __restrict__ partial) {
+  double acc[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) acc[b] = 0.0;
+  const int64_t nown = (int64_t)(hi - lo) * nxy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * nown;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(i / nown);
+    const int64_t n = (int64_t)lo * nxy + (i - f * nown);
+    const int g = coarse_group(f, label[n]);
+    if (g < 0) continue;
+    const int64_t row = f * nn + n;
+    const double u = sqd ? v[row] * sqd[row] * iwf[f] : v[row];
+    const double z = coarse_zeta((int)(n / nxy), lo, hi);
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg) {
+      const bool on = gg == g;
+      acc[2 * gg] += on ? u : 0.0;
+      acc[2 * gg + 1] += on ? u * z : 0.0;
+    }
+  }
+  double a4[4] = {acc[0], acc[1], acc[2], acc[3]};
+  block_sum4(a4, partial);
+  __syncthreads();
+  double b4[4] = {acc[4], acc[5], acc[6], acc[7]};
+  block_sum4(b4, partial + 4 * gridDim.x);
+}
+
+// bins[map[b]] = sum of the block partials of bin b (the other entries zero)
+__global__ void k_dd_cbins(const double* __restrict__ partial, int nblk, const int* __restrict__ map, int nb,
+                           double* __restrict__ bins) {
+  __shared__ double s8[8];
+  sum4_warps(partial, nblk, s8);
+  sum4_warps(partial + 4 * nblk, nblk, s8 + 4);
+  __syncthreads();
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) bins[j] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < 8 && map[threadIdx.x] >= 0) bins[map[threadIdx.x]] = s8[threadIdx.x];
+}
+
+// y = A^-1 bins (dense nb x nb, column-major), one block
+__global__ void k_dd_capply(const double* __restrict__ ainv, const double* __restrict__ bins, int nb,
+                            double* __restrict__ y) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nb; ++j) s = fma(ainv[(int64_t)j * nb + i], bins[j], s);
+    y[i] = s;
+  }
+}
+
+// z += sum_b y[map[b]] basis_b over the slab's owned nodes (fields 0..2)
+__global__ void k_dd_cprolong(double* __restrict__ z, const double* __restrict__ y, const int* __restrict__ map,
+                              const uint8_t* __restrict__ label, int64_t nn, int64_t nxy, int lo, int hi) {
+  const int64_t nown = (int64_t)(hi - lo) * nxy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * nown;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(i / nown);
+    const int64_t n = (int64_t)lo * nxy + (i - f * nown);
+    const int g = coarse_group(f, label[n]);
+    if (g < 0) continue;
+    const int j0 = map[2 * g], j1 = map[2 * g + 1];
+    double add = j0 >= 0 ? y[j0] : 0.0;
+    if (j1 >= 0) add += y[j1] * coarse_zeta((int)(n / nxy), lo, hi);
+    z[f * nn + n] += add;
+  }
+}
+
+__global__ void k_dd_unit(double* __restrict__ y, int nb, int j) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) y[i] = i == j ? 1.0 : 0.0;
+}
+
 }  // namespace
 
 p4d_status dd_halo(p4d_dd_ctx* D, double* const* v) {
@@ -163,6 +257,142 @@ p4d_status dd_owned_sumsq(p4d_dd_ctx* D, int p, const double* const* v, const do
   return P4D_OK;
 }
 
+namespace {
+
+// Coarse sums of slab p's vector v into row p of D->bins (scaled: of s^-1 v).
+p4d_status dd_coarse_sums(p4d_dd_ctx* D, int p, const double* v, bool scaled) {
+  p4d_ctx* c = D->parts[p];
+  ::p4d::count_launch(), k_dd_crestrict<<<kDDBlocks, kDDThreads, 0, D->stream>>>(
+      v, scaled ? c->sqd : nullptr, c->iwf, c->label, c->g.nn, D->nxy, D->own_lo[p], D->own_hi[p], D->cpart);
+  ::p4d::count_launch(), k_dd_cbins<<<1, 128, 0, D->stream>>>(D->cpart, kDDBlocks, D->cmap_dev + 8 * p, D->nb,
+                                                             D->bins + (int64_t)p * kDDRed);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+p4d_status dd_bins_allreduce(p4d_dd_ctx* D) {
+  const int P = (int)D->parts.size();
+  std::vector<double*> ptr(P);
+  for (int p = 0; p < P; ++p) ptr[p] = D->bins + (int64_t)p * kDDRed;
+  return dd_allreduce(D, ptr.data(), D->nb);
+}
+
+p4d_status dd_prolong(p4d_dd_ctx* D, int p, const double* y, double* z) {
+  p4d_ctx* c = D->parts[p];
+  const int64_t n = 3 * (int64_t)(D->own_hi[p] - D->own_lo[p]) * D->nxy;
+  ::p4d::count_launch(), k_dd_cprolong<<<std::min<int64_t>(nblocks(n), 4 * 152), kBlock, 0, D->stream>>>(
+      z, y, D->cmap_dev + 8 * p, c->label, c->g.nn, D->nxy, D->own_lo[p], D->own_hi[p]);
+  P4D_TRY(cudaGetLastError());
+  return P4D_OK;
+}
+
+// Inverse of the dense n x n column-major matrix a by Gauss-Jordan
+// elimination with partial pivoting (FP64); false when a pivot vanishes.
+bool dense_inverse(std::vector<double>& a, int n, std::vector<double>& inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  auto A = [&](int i, int j) -> double& { return a[(size_t)j * n + i]; };
+  auto I = [&](int i, int j) -> double& { return inv[(size_t)j * n + i]; };
+  double amax = 0.0;
+  for (double v : a) amax = std::max(amax, std::fabs(v));
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A(i, k)) > std::fabs(A(piv, k))) piv = i;
+    if (!(std::fabs(A(piv, k)) > 1e-14 * amax)) return false;
+    if (piv != k)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A(k, j), A(piv, j));
+        std::swap(I(k, j), I(piv, j));
+      }
+    const double d = 1.0 / A(k, k);
+    for (int j = 0; j < n; ++j) {
+      A(k, j) *= d;
+      I(k, j) *= d;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = A(i, k);
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A(i, j) -= f * A(k, j);
+        I(i, j) -= f * I(k, j);
+      }
+    }
+  }
+  return true;
+}
+
+// The coarse basis of the current linearization and A_c = Z^T J Z (REDUCED
+// operator, unscaled), inverted on the host in FP64 and kept on the device.
+p4d_status dd_coarse_build(p4d_dd_ctx* D) {
+  const int P = (int)D->parts.size();
+  D->nb = 0;
+  if (D->coarse_modes == 0 || P < 2) return P4D_OK;
+  // groups present on each slab (phi_s anode / cathode unknowns among the owned nodes)
+  D->cmap.assign(8 * (size_t)P, -1);
+  int nb = 0;
+  for (int p = 0; p < P; ++p) {
+    p4d_ctx* c = D->parts[p];
+    std::vector<uint8_t> lab((size_t)c->g.nn);
+    P4D_TRY(cudaMemcpy(lab.data(), c->label, lab.size(), cudaMemcpyDeviceToHost));
+    bool has[4] = {false, false, true, true};
+    for (int64_t n = (int64_t)D->own_lo[p] * D->nxy; n < (int64_t)D->own_hi[p] * D->nxy; ++n)
+      if (lab[n] & kLabActive) has[(lab[n] & kLabAnode) ? 0 : 1] = true;
+    const bool lin = D->coarse_modes >= 2 && D->own_hi[p] - D->own_lo[p] >= 2;
+    for (int g = 0; g < 4; ++g) {
+      if (!has[g]) continue;
+      D->cmap[8 * p + 2 * g] = nb++;
+      if (lin) D->cmap[8 * p + 2 * g + 1] = nb++;
+    }
+  }
+  if (nb > kDDRed) return P4D_ERR_INVALID_ARG;   // cannot happen: at most 8 per slab, at most 32 slabs
+  P4D_TRY(cudaMemcpyAsync(D->cmap_dev, D->cmap.data(), sizeof(int) * 8 * P, cudaMemcpyHostToDevice, D->stream));
+  D->nb = nb;
+  std::vector<double> ac((size_t)nb * nb), inv;
+  for (int j = 0; j < nb; ++j) {
+    // W = J Z_j over the slabs (halo exchange first), then Z^T W
+    for (int p = 0; p < P; ++p) {
+      p4d_ctx* c = D->parts[p];
+      P4D_TRY(cudaMemsetAsync(D->wx[p], 0, sizeof(double) * 3 * c->g.nn, D->stream));
+      ::p4d::count_launch(), k_dd_unit<<<1, 128, 0, D->stream>>>(D->cy + (int64_t)p * kDDRed, nb, j);
+      P4D_TRYS(dd_prolong(D, p, D->cy + (int64_t)p * kDDRed, D->wx[p]));
+    }
+    P4D_TRYS(dd_halo(D, D->wx.data()));
+    for (int p = 0; p < P; ++p) {
+      P4D_TRYS(jvp_reduced(D->parts[p], D->wx[p], D->wy[p], 0, nullptr, false));
+      P4D_TRYS(dd_zero_ghost(D, p, D->wy[p], false));
+      P4D_TRYS(dd_coarse_sums(D, p, D->wy[p], false));
+    }
+    P4D_TRYS(dd_bins_allreduce(D));
+    P4D_TRY(cudaMemcpyAsync(ac.data() + (size_t)j * nb, D->bins, sizeof(double) * nb, cudaMemcpyDeviceToHost,
+                            D->stream));
+  }
+  P4D_TRY(cudaStreamSynchronize(D->stream));
+  if (!dense_inverse(ac, nb, inv)) {
+    D->nb = 0;   // singular coarse matrix: one-level (block Jacobi) preconditioner
+    return P4D_OK;
+  }
+  P4D_TRY(cudaMemcpyAsync(D->ainv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, D->stream));
+  P4D_TRY(cudaStreamSynchronize(D->stream));
+  return P4D_OK;
+}
+
+}  // namespace
+
+p4d_status dd_coarse_correct(p4d_dd_ctx* D, const double* const* v, double* const* z) {
+  if (D->nb == 0) return P4D_OK;
+  const int P = (int)D->parts.size();
+  for (int p = 0; p < P; ++p) P4D_TRYS(dd_coarse_sums(D, p, v[p], true));
+  P4D_TRYS(dd_bins_allreduce(D));
+  for (int p = 0; p < P; ++p) {
+    double* y = D->cy + (int64_t)p * kDDRed;
+    ::p4d::count_launch(), k_dd_capply<<<1, 256, 0, D->stream>>>(D->ainv, D->bins + (int64_t)p * kDDRed, D->nb, y);
+    P4D_TRYS(dd_prolong(D, p, y, z[p]));
+  }
+  return P4D_OK;
+}
+
 }  // namespace p4d
 
 using namespace p4d;
@@ -191,7 +421,7 @@ int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan) 
 p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
   if (!out) return P4D_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!parts || nparts < 1) return P4D_ERR_INVALID_ARG;
+  if (!parts || nparts < 1 || nparts > 32) return P4D_ERR_INVALID_ARG;
   for (int i = 0; i < nparts; ++i) {
     if (!parts[i]) return P4D_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
@@ -233,12 +463,22 @@ p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
       (cudaMalloc(&D->sbuf, sizeof(double) * msg) != cudaSuccess ||
        cudaMalloc(&D->rbuf, sizeof(double) * msg) != cudaSuccess ||
        cudaMalloc(&D->red, sizeof(double) * (size_t)(nparts + 1) * kDDRed) != cudaSuccess ||
-       cudaMalloc(&D->part, sizeof(double) * 4 * 2 * 152) != cudaSuccess))
+       cudaMalloc(&D->part, sizeof(double) * 4 * kDDBlocks) != cudaSuccess ||
+       cudaMalloc(&D->cpart, sizeof(double) * 8 * kDDBlocks) != cudaSuccess ||
+       cudaMalloc(&D->cmap_dev, sizeof(int) * 8 * (size_t)nparts) != cudaSuccess ||
+       cudaMalloc(&D->bins, sizeof(double) * (size_t)nparts * kDDRed) != cudaSuccess ||
+       cudaMalloc(&D->cy, sizeof(double) * (size_t)nparts * kDDRed) != cudaSuccess ||
+       cudaMalloc(&D->ainv, sizeof(double) * (size_t)kDDRed * kDDRed) != cudaSuccess))
     st = P4D_ERR_OOM;
   for (int p = 0; p < nparts && st == P4D_OK; ++p) {
-    double* b = nullptr;
-    if (cudaMalloc(&b, sizeof(double) * (size_t)parts[p]->ndof) != cudaSuccess) st = P4D_ERR_OOM;
+    double *b = nullptr, *wx = nullptr, *wy = nullptr;
+    const size_t n3 = 3 * (size_t)parts[p]->g.nn;
+    if (cudaMalloc(&b, sizeof(double) * (size_t)parts[p]->ndof) != cudaSuccess ||
+        cudaMalloc(&wx, sizeof(double) * n3) != cudaSuccess || cudaMalloc(&wy, sizeof(double) * n3) != cudaSuccess)
+      st = P4D_ERR_OOM;
     D->bw.push_back(b);
+    D->wx.push_back(wx);
+    D->wy.push_back(wy);
   }
   if (dev_prev >= 0) cudaSetDevice(dev_prev);
   if (st != P4D_OK) {
@@ -255,9 +495,12 @@ void p4d_dd_destroy(p4d_dd D) {
   if (D->sbuf) cudaFree(D->sbuf);
   if (D->rbuf) cudaFree(D->rbuf);
   if (D->red) cudaFree(D->red);
-  if (D->part) cudaFree(D->part);
-  for (double* b : D->bw)
-    if (b) cudaFree(b);
+  for (void* q : {(void*)D->part, (void*)D->cpart, (void*)D->cmap_dev, (void*)D->bins, (void*)D->cy,
+                  (void*)D->ainv})
+    if (q) cudaFree(q);
+  for (auto* v : {&D->bw, &D->wx, &D->wy})
+    for (double* b : *v)
+      if (b) cudaFree(b);
   delete D;
 }
 
@@ -274,7 +517,15 @@ p4d_status p4d_dd_jacobian_update(p4d_dd D, const p4d_state* states) {
     ptr[p] = D->parts[p]->unorm2;
   }
   P4D_TRYS(dd_allreduce(D, ptr.data(), 4));
+  P4D_TRYS(dd_coarse_build(D));
   P4D_TRY(cudaStreamSynchronize(D->stream));
+  return P4D_OK;
+}
+
+p4d_status p4d_dd_set_coarse(p4d_dd D, int32_t modes) {
+  if (!D || modes < 0 || modes > 2) return P4D_ERR_INVALID_ARG;
+  D->coarse_modes = modes;
+  D->nb = 0;   // rebuilt by the next p4d_dd_jacobian_update
   return P4D_OK;
 }
 

@@ -1160,6 +1160,12 @@ p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4
       for (int p = 0; p < P; ++p) {
         P4D_TRYS(precond_column(D->parts[p], 0, true));
         vec[p] = D->parts[p]->Z + (int64_t)k * R[p].len;
+        ptr[p] = D->parts[p]->V + (int64_t)k * R[p].len;
+      }
+      // two-level: z_k += Z A_c^-1 Z^T (s^-1 v_k)
+      {
+        std::vector<const double*> vk(ptr.begin(), ptr.end());
+        P4D_TRYS(dd_coarse_correct(D, vk.data(), vec.data()));
       }
       P4D_TRYS(dd_halo(D, vec.data()));
       // w = s.J z_k on the owned rows; h = V^T w, ||w||^2

@@ -305,6 +305,20 @@ struct p4d_dd_ctx {
   double* red = nullptr;                // [(P + 1)][kDDRed] allreduce staging; the sum in the last row
   double* part = nullptr;               // block partial sums
   std::vector<double*> bw;              // [P] right-hand sides with ghost rows zero
+  // Two-level correction: coarse basis vectors per slab, field and group
+  // (phi_s: anode and cathode unknowns; phi_e, c_e: all nodes) and mode
+  // (constant, linear in z over the slab's owned planes); coarse bin b of a
+  // slab (0..7: phi_s anode 1, z; phi_s cathode 1, z; phi_e 1, z; c_e 1, z)
+  // is basis vector cmap[8 p + b] (-1: none).
+  int coarse_modes = 2;                 // 0 none, 1 constants, 2 constants and linear in z
+  int nb = 0;                           // coarse basis vectors (0: correction off)
+  std::vector<int> cmap;                // [P][8]
+  int* cmap_dev = nullptr;
+  double* bins = nullptr;               // [P][kDDRed] coarse sums, one row per slab
+  double* cy = nullptr;                 // [P][kDDRed] coarse solution, one row per slab
+  double* ainv = nullptr;               // [kDDRed^2 / ...] inverse coarse matrix (nb x nb), FP64
+  double* cpart = nullptr;              // block partials of the coarse sums
+  std::vector<double*> wx, wy;          // [P] vectors of the coarse matrix build (3 nn)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -506,5 +520,7 @@ p4d_status dd_zero_ghost(p4d_dd_ctx* D, int p, double* v, bool cs_rows);
 p4d_status dd_allreduce(p4d_dd_ctx* D, double* const* ptrs, int n);
 p4d_status dd_owned_sumsq(p4d_dd_ctx* D, int p, const double* const* v, const double* w, double* out);
 p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4d_info* info);
+// z_p += Z A_c^-1 Z^T (s^-1 v_p) on every slab (no-op when the correction is off).
+p4d_status dd_coarse_correct(p4d_dd_ctx* D, const double* const* v, double* const* z);
 
 }  // namespace p4d

@@ -204,7 +204,7 @@ class SlabSolver:
     slab, all on one stream, grouped by p4d_dd_create.  Vectors are lists of
     per-slab device tensors in each slab's full layout."""
 
-    def __init__(self, slabs, device="cuda", stream=None, **opts):
+    def __init__(self, slabs, device="cuda", stream=None, coarse=2, **opts):
         self.slabs = slabs
         dev = torch.device(device)
         stream = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -215,6 +215,11 @@ class SlabSolver:
         out = C.c_void_p()
         N.check(self.lib.p4d_dd_create(hs, n, C.byref(out)), "p4d_dd_create")
         self.dd = out
+        self.set_coarse(coarse)
+
+    def set_coarse(self, modes):
+        """Coarse space: 0 none, 1 constants, 2 constants and linear in z (next update)."""
+        N.check(self.lib.p4d_dd_set_coarse(self.dd, int(modes)), "p4d_dd_set_coarse")
 
     def _ptrs(self, ts):
         return (C.c_void_p * len(ts))(*[_dev(t).data_ptr() for t in ts])

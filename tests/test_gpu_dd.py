@@ -69,13 +69,13 @@ def _scatter(maps, g, parts):
     return xs
 
 
-def _setup(name, nparts, **opts):
+def _setup(name, nparts, coarse=2, **opts):
     from paper_2602_07225_gb300 import P4DSolver, SlabSolver
     case = CELLS[name]()
     okw, lkw = LAWS.get(name, ({}, {}))
     d = Disc(case["mesh"], case["params"], **okw)
     slabs = slab_cases(case, nparts)
-    dd = SlabSolver(slabs, **lkw, **opts)
+    dd = SlabSolver(slabs, coarse=coarse, **lkw, **opts)
     maps = _maps(case, slabs, dd.parts, d)
     cell = P4DSolver(case, **lkw, **opts)
     return case, d, slabs, dd, maps, cell
@@ -104,10 +104,11 @@ def test_dd_jvp_is_the_cells(name, nparts):
 @pytest.mark.parametrize("name,nparts", [("cube8", 2), ("cube8", 3), ("hetero", 2), ("tpms", 2), ("paper_laws", 2)])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("refine", [0, 1])
-def test_dd_fgmres_matches_direct(name, nparts, precision, refine):
+@pytest.mark.parametrize("coarse", [0, 2])
+def test_dd_fgmres_matches_direct(name, nparts, precision, refine, coarse):
     rtol = 1e-12 if precision == 0 else 1e-10
     case, d, slabs, dd, maps, cell = _setup(name, nparts, precision=precision, mode=1, rtol=rtol, maxit=1500,
-                                            cgs_refine=refine)
+                                            cgs_refine=refine, coarse=coarse)
     sts = dd.state_tensors()
     dd.jacobian_update(sts)
     bs = [-r for r in dd.residual(sts)]
@@ -121,6 +122,25 @@ def test_dd_fgmres_matches_direct(name, nparts, precision, refine):
     assert err <= (1e-9 if precision == 0 else 1e-7), (err, info)
     if refine == 0:
         assert info["reorth"] == 0
+
+
+def test_coarse_space_cuts_iterations():
+    # the slabs' block Jacobi leaves the long-range potential modes to
+    # FGMRES; the coarse space (constants and linear-in-z functions per slab
+    # and block) carries them
+    from paper_2602_07225_gb300 import SlabSolver
+    case = make_box_case(16, 16, (20, 8, 20), 100e-6, (100e-6, 25e-6, 100e-6), 6, 1007)
+    its = {}
+    for coarse in (0, 1, 2):
+        dd = SlabSolver(slab_cases(case, 4), coarse=coarse, precision=1, mode=1, rtol=1e-8, maxit=1500)
+        sts = dd.state_tensors()
+        dd.jacobian_update(sts)
+        _, info = dd.solve([-r for r in dd.residual(sts)])
+        assert info["status"] == 0, info
+        its[coarse] = info["iters"]
+        dd.close()
+    assert its[2] < its[0], its
+    assert its[1] <= its[0], its
 
 
 @pytest.mark.parametrize("name", ["cube8", "paper_laws"])
