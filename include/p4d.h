@@ -271,36 +271,38 @@ void p4d_batch_destroy(p4d_batch b);
 
 /* ---- Slab domain decomposition of one cell (paper section 5, the strong
    and weak scaling runs partition the cell over MPI ranks).  The cell is
-   cut along z into slabs, each built as its own handle from the sub-mesh of
-   its elements plus one element layer of each neighbour: consecutive slabs
-   share one element layer, so the lowest local node plane of every slab but
-   the first and the highest of every slab but the last are ghost planes,
-   owned by the neighbour (the slab's owned planes are the rest).  The slab
-   meshes and states are the cell's restricted to those elements and nodes;
-   Gamma_n and the z = 0 foil belong to the first slab only, Gamma_p and the
-   z = Lz foil to the last.  A stencil application exchanges the ghost
-   planes of its input with the owners (pack, transfer, unpack); every inner
-   product sums the slabs' owned-row partial sums.  In this library all
-   slabs of a decomposition live on one GPU and one stream (a transfer is a
-   device-to-device copy; the sum runs over the slabs' staged partials);
-   with one slab per rank the same steps are a send/recv pair per message
-   and an allreduce. */
+   cut along z into slabs; slab p owns a contiguous range of node planes
+   and is built as its own handle from the sub-mesh of the elements between
+   `ghosts` node planes below and above that range (clipped at the cell's
+   faces): the lowest `ghosts` local planes of every slab but the first and
+   the highest `ghosts` of every slab but the last are ghost planes, owned
+   by the neighbour.  The slab meshes and states are the cell's restricted
+   to those elements and nodes; Gamma_n and the z = 0 foil belong to the
+   first slab only, Gamma_p and the z = Lz foil to the last.  An operator
+   application exchanges the ghost planes of its input with the owners
+   (pack, transfer, unpack); every inner product sums the slabs' owned-row
+   partial sums.  In this library all slabs of a decomposition live on one
+   GPU and one stream (a transfer is a device-to-device copy; the sum runs
+   over the slabs' staged partials); with one slab per rank the same steps
+   are a send/recv pair per message and an allreduce. */
 typedef struct p4d_dd_ctx* p4d_dd;
 
-/* Halo messages of nparts slabs with nplanes[p] local node planes each
-   ([host], no device work, callable without a GPU): writes 4 int32 per
-   message to plan (if not NULL): source slab, source local plane,
-   destination slab, destination local plane (a ghost plane), and returns
-   the number of messages, 2 (nparts - 1); -1 when nparts < 1 or a slab has
-   no owned plane (nplanes[p] < 1 + its ghost planes). */
-int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan);
+/* Halo messages of nparts slabs with nplanes[p] local node planes each and
+   `ghosts` ghost planes per interior side ([host], no device work, callable
+   without a GPU): writes 4 int32 per message to plan (if not NULL): source
+   slab, first source plane, destination slab, first destination plane
+   (`ghosts` consecutive planes each), and returns the number of messages,
+   2 (nparts - 1); -1 when nparts < 1, ghosts < 1, or a slab owns no plane
+   or (nparts > 1) fewer planes than ghosts. */
+int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t ghosts, int32_t* plan);
 
-/* Group the slab handles parts[0..nparts) (bottom to top; not owned:
-   destroy the decomposition before them).  They must share the device, the
-   stream, nx, ny and nc.  Allocates the message buffers and one
-   right-hand-side copy per slab.  Errors: INVALID_ARG (NULL or repeated
-   handle, mismatch, a slab without owned planes), OOM, CUDA. */
-p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out);
+/* Group the slab handles parts[0..nparts) (bottom to top, 1 <= nparts <=
+   32, `ghosts` ghost planes per interior side; not owned: destroy the
+   decomposition before them).  They must share the device, the stream, nx,
+   ny and nc.  Allocates the message buffers, one right-hand-side copy and
+   two coarse-space work vectors per slab.  Errors: INVALID_ARG (NULL or
+   repeated handle, mismatch, a plan p4d_dd_halo_plan rejects), OOM, CUDA. */
+p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, int32_t ghosts, p4d_dd* out);
 
 /* Coarse space of the two-level preconditioner (default 2): 0 none (block
    Jacobi across the slabs), 1 one constant per slab and block (phi_s of
@@ -329,10 +331,11 @@ p4d_status p4d_dd_jvp(p4d_dd dd, double* const* x, double* const* y);
    every slab with the same rtol, restart, maxit and cgs_refine, profile
    off).  b[p], x[p] as p4d_fgmres_solve per slab; the ghost rows of b are
    ignored, the owned rows of x are the solution (its ghost planes hold the
-   owners' values).  The preconditioner is each slab's own block
-   preconditioner on the slab (block Jacobi across the slabs) plus the
-   coarse correction of p4d_dd_set_coarse; the converged solution is the
-   cell's.  info (one report for the cell) as p4d_fgmres_solve.
+   owners' values).  The preconditioner is restricted additive Schwarz
+   over the slabs: each slab applies its own block preconditioner to the
+   Krylov vector on its owned and ghost rows (the owners' values) and keeps
+   its owned rows; plus the coarse correction of p4d_dd_set_coarse.  The
+   converged solution is the cell's.  info (one report for the cell) as p4d_fgmres_solve.
    Synchronizes the stream. */
 p4d_status p4d_dd_fgmres_solve(p4d_dd dd, const double* const* b, double* const* x, p4d_info* info);
 

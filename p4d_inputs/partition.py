@@ -3,12 +3,12 @@ bookkeeping only: the slabs' meshes, parameters and states are slices of the
 cell's arrays).
 
 The node planes 0..nz are split into ``nparts`` contiguous owned ranges
-``[p_r, p_{r+1})`` of nearly equal size.  Slab r is built from the elements
-``[max(p_r - 1, 0), min(p_{r+1}, nz))``: its own elements plus one element
-layer of each neighbour, so its node planes run from ``max(p_r - 1, 0)`` to
-``min(p_{r+1}, nz)``.  The lowest of them is a ghost plane (owned by slab
-r - 1) for every slab but the first, the highest one (owned by slab r + 1)
-for every slab but the last.  Gamma_n, the grounded z = 0 face, and its
+``[p_r, p_{r+1})`` of nearly equal size.  With ``g`` ghost planes per
+interior side, slab r is built from the elements
+``[max(p_r - g, 0), min(p_{r+1} - 1 + g, nz))``, so its node planes run from
+``max(p_r - g, 0)`` to ``min(p_{r+1} - 1 + g, nz)``.  The lowest ``g`` of
+them are ghost planes (owned by slab r - 1) for every slab but the first,
+the highest ``g`` (owned by slab r + 1) for every slab but the last.  Gamma_n, the grounded z = 0 face, and its
 foil belong to the first slab; Gamma_p, the z = Lz face carrying the
 applied current, and its foil to the last.
 """
@@ -27,19 +27,22 @@ def owned_plane_bounds(nz, nparts):
     return [round(r * (nz + 1) / nparts) for r in range(nparts + 1)]
 
 
-def slab_cases(case, nparts):
-    """The cell ``case`` cut into ``nparts`` z slabs.  Returns a list of
-    dicts, bottom to top: ``case`` (mesh, params and state of the slab, same
-    keys as the cell's), ``e_lo`` (first element layer = first node plane of
-    the slab in the cell), ``own`` (owned local node planes [lo, hi)) and
-    ``nplanes``."""
+def slab_cases(case, nparts, ghosts=1):
+    """The cell ``case`` cut into ``nparts`` z slabs with ``ghosts`` ghost
+    planes per interior side.  Returns a list of dicts, bottom to top:
+    ``case`` (mesh, params and state of the slab, same keys as the cell's),
+    ``e_lo`` (first element layer = first node plane of the slab in the
+    cell), ``own`` (owned local node planes [lo, hi)), ``nplanes`` and
+    ``ghosts``."""
     m = case["mesh"]
     nx, ny, nz = int(m["nx"]), int(m["ny"]), int(m["nz"])
     nxy_e, nxy_n = nx * ny, (nx + 1) * (ny + 1)
     bounds = owned_plane_bounds(nz, nparts)
+    if ghosts < 1 or (nparts > 1 and min(b1 - b0 for b0, b1 in zip(bounds, bounds[1:])) < ghosts):
+        raise ValueError("every slab must own at least `ghosts` >= 1 node planes")
     out = []
     for r in range(nparts):
-        e_lo, e_hi = max(bounds[r] - 1, 0), min(bounds[r + 1], nz)
+        e_lo, e_hi = max(bounds[r] - ghosts, 0), min(bounds[r + 1] - 1 + ghosts, nz)
         sm = dict(m)
         sm["nz"] = e_hi - e_lo
         sm["hz"] = np.asarray(m["hz"], float)[e_lo:e_hi].copy()
@@ -60,7 +63,7 @@ def slab_cases(case, nparts):
         nplanes = e_hi - e_lo + 1
         own = (bounds[r] - e_lo, bounds[r + 1] - e_lo)
         out.append(dict(case=dict(mesh=sm, params=dict(case["params"]), state=sst), e_lo=e_lo, own=own,
-                        nplanes=nplanes))
+                        nplanes=nplanes, ghosts=ghosts))
     return out
 
 

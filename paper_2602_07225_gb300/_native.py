@@ -97,8 +97,8 @@ SIGNATURES = {
     "p4d_batch_fgmres_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(Info)]),
     "p4d_batch_adjoint_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(Info)]),
     "p4d_batch_destroy": (None, [C.c_void_p]),
-    "p4d_dd_halo_plan": (C.c_int32, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "p4d_dd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "p4d_dd_halo_plan": (C.c_int32, [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
+    "p4d_dd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "p4d_dd_set_coarse": (C.c_int, [C.c_void_p, C.c_int32]),
     "p4d_dd_jacobian_update": (C.c_int, [C.c_void_p, C.POINTER(State)]),
     "p4d_dd_jvp": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),

@@ -22,22 +22,23 @@ namespace {
 constexpr int kDDThreads = 256;
 constexpr int kDDBlocks = 2 * 152;
 
-// buf[f][j] = x[f nn + off + j], f = phi_s, phi_e, c_e
-__global__ void k_dd_pack(const double* __restrict__ x, int64_t nn, int64_t off, int64_t nxy,
-                          double* __restrict__ buf) {
-  const int64_t n = 3 * nxy;
+// buf[f][j] = x[f nn + off + j] (w: times w at the same row), j < len,
+// f = phi_s, phi_e, c_e
+__global__ void k_dd_pack(const double* __restrict__ x, const double* __restrict__ w, int64_t nn, int64_t off,
+                          int64_t len, double* __restrict__ buf) {
+  const int64_t n = 3 * len;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t f = i / nxy, j = i - f * nxy;
-    buf[i] = x[f * nn + off + j];
+    const int64_t f = i / len, row = f * nn + off + (i - f * len);
+    buf[i] = w ? x[row] * w[row] : x[row];
   }
 }
 
-__global__ void k_dd_unpack(double* __restrict__ x, int64_t nn, int64_t off, int64_t nxy,
-                            const double* __restrict__ buf) {
-  const int64_t n = 3 * nxy;
+__global__ void k_dd_unpack(double* __restrict__ x, const double* __restrict__ w, int64_t nn, int64_t off,
+                            int64_t len, const double* __restrict__ buf) {
+  const int64_t n = 3 * len;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t f = i / nxy, j = i - f * nxy;
-    x[f * nn + off + j] = buf[i];
+    const int64_t f = i / len, row = f * nn + off + (i - f * len);
+    x[row] = w ? buf[i] * w[row] : buf[i];
   }
 }
 
@@ -187,24 +188,24 @@ __global__ void k_dd_unit(double* __restrict__ y, int nb, int j) {
 
 }  // namespace
 
-p4d_status dd_halo(p4d_dd_ctx* D, double* const* v) {
+p4d_status dd_halo(p4d_dd_ctx* D, double* const* v, bool scaled) {
   const int nmsg = (int)D->plan.size() / 4;
-  const int64_t nxy = D->nxy;
-  const unsigned gb = nblocks(3 * nxy);
+  const int64_t nxy = D->nxy, len = (int64_t)D->ghosts * nxy;
+  const unsigned gb = std::min<unsigned>(nblocks(3 * len), 4 * 152);
   for (int m = 0; m < nmsg; ++m) {
     const int* q = &D->plan[4 * m];
     p4d_ctx* s = D->parts[q[0]];
-    ::p4d::count_launch(), k_dd_pack<<<gb, kBlock, 0, D->stream>>>(v[q[0]], s->g.nn, q[1] * nxy, nxy,
-                                                                  D->sbuf + (int64_t)m * 3 * nxy);
+    ::p4d::count_launch(), k_dd_pack<<<gb, kBlock, 0, D->stream>>>(v[q[0]], scaled ? s->sqd : nullptr, s->g.nn,
+                                                                  q[1] * nxy, len, D->sbuf + m * 3 * len);
   }
   for (int m = 0; m < nmsg; ++m)
-    P4D_TRY(cudaMemcpyAsync(D->rbuf + (int64_t)m * 3 * nxy, D->sbuf + (int64_t)m * 3 * nxy,
-                            sizeof(double) * 3 * nxy, cudaMemcpyDeviceToDevice, D->stream));
+    P4D_TRY(cudaMemcpyAsync(D->rbuf + m * 3 * len, D->sbuf + m * 3 * len, sizeof(double) * 3 * len,
+                            cudaMemcpyDeviceToDevice, D->stream));
   for (int m = 0; m < nmsg; ++m) {
     const int* q = &D->plan[4 * m];
     p4d_ctx* d = D->parts[q[2]];
-    ::p4d::count_launch(), k_dd_unpack<<<gb, kBlock, 0, D->stream>>>(v[q[2]], d->g.nn, q[3] * nxy, nxy,
-                                                                    D->rbuf + (int64_t)m * 3 * nxy);
+    ::p4d::count_launch(), k_dd_unpack<<<gb, kBlock, 0, D->stream>>>(v[q[2]], scaled ? d->rsqd : nullptr, d->g.nn,
+                                                                    q[3] * nxy, len, D->rbuf + m * 3 * len);
   }
   P4D_TRY(cudaGetLastError());
   return P4D_OK;
@@ -358,7 +359,7 @@ p4d_status dd_coarse_build(p4d_dd_ctx* D) {
       ::p4d::count_launch(), k_dd_unit<<<1, 128, 0, D->stream>>>(D->cy + (int64_t)p * kDDRed, nb, j);
       P4D_TRYS(dd_prolong(D, p, D->cy + (int64_t)p * kDDRed, D->wx[p]));
     }
-    P4D_TRYS(dd_halo(D, D->wx.data()));
+    P4D_TRYS(dd_halo(D, D->wx.data(), false));
     for (int p = 0; p < P; ++p) {
       P4D_TRYS(jvp_reduced(D->parts[p], D->wx[p], D->wy[p], 0, nullptr, false));
       P4D_TRYS(dd_zero_ghost(D, p, D->wy[p], false));
@@ -399,26 +400,28 @@ using namespace p4d;
 
 extern "C" {
 
-int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t* plan) {
-  if (nparts < 1 || !nplanes) return -1;
+int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t ghosts, int32_t* plan) {
+  if (nparts < 1 || !nplanes || ghosts < 1) return -1;
   for (int p = 0; p < nparts; ++p) {
-    const int ghosts = (p > 0) + (p < nparts - 1);
-    if (nplanes[p] < ghosts + 1) return -1;   // at least one owned plane
+    const int ng = ghosts * ((p > 0) + (p < nparts - 1));
+    // owned planes: at least one, and as many as a neighbour's ghost planes
+    const int own = nplanes[p] - ng;
+    if (own < 1 || (nparts > 1 && own < ghosts)) return -1;
   }
   int m = 0;
   for (int p = 0; p + 1 < nparts; ++p) {
     if (plan) {
-      // the upper slab's bottom ghost plane <- the lower slab's last owned plane
-      plan[4 * m + 0] = p; plan[4 * m + 1] = nplanes[p] - 2; plan[4 * m + 2] = p + 1; plan[4 * m + 3] = 0;
-      // the lower slab's top ghost plane <- the upper slab's first owned plane
-      plan[4 * m + 4] = p + 1; plan[4 * m + 5] = 1; plan[4 * m + 6] = p; plan[4 * m + 7] = nplanes[p] - 1;
+      // the upper slab's lowest ghost planes <- the lower slab's last owned planes
+      plan[4 * m + 0] = p; plan[4 * m + 1] = nplanes[p] - 2 * ghosts; plan[4 * m + 2] = p + 1; plan[4 * m + 3] = 0;
+      // the lower slab's highest ghost planes <- the upper slab's first owned planes
+      plan[4 * m + 4] = p + 1; plan[4 * m + 5] = ghosts; plan[4 * m + 6] = p; plan[4 * m + 7] = nplanes[p] - ghosts;
     }
     m += 2;
   }
   return m;
 }
 
-p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
+p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, int32_t ghosts, p4d_dd* out) {
   if (!out) return P4D_ERR_INVALID_ARG;
   *out = nullptr;
   if (!parts || nparts < 1 || nparts > 32) return P4D_ERR_INVALID_ARG;
@@ -434,7 +437,7 @@ p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
   }
   std::vector<int32_t> nz1(nparts);
   for (int i = 0; i < nparts; ++i) nz1[i] = parts[i]->g.nnz;
-  const int nmsg = p4d_dd_halo_plan(nparts, nz1.data(), nullptr);
+  const int nmsg = p4d_dd_halo_plan(nparts, nz1.data(), ghosts, nullptr);
   if (nmsg < 0) return P4D_ERR_INVALID_ARG;
   p4d_dd_ctx* D = new (std::nothrow) p4d_dd_ctx;
   if (!D) return P4D_ERR_OOM;
@@ -442,11 +445,12 @@ p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
   D->stream = parts[0]->stream;
   D->nxy = (int64_t)parts[0]->g.nnx * parts[0]->g.nny;
   D->plan.assign(4 * (size_t)nmsg, 0);
-  p4d_dd_halo_plan(nparts, nz1.data(), D->plan.data());
+  D->ghosts = ghosts;
+  p4d_dd_halo_plan(nparts, nz1.data(), ghosts, D->plan.data());
   for (int p = 0; p < nparts; ++p) {
     const p4d_ctx* c = parts[p];
-    D->own_lo.push_back(p > 0 ? 1 : 0);
-    D->own_hi.push_back(p < nparts - 1 ? nz1[p] - 1 : nz1[p]);
+    D->own_lo.push_back(p > 0 ? ghosts : 0);
+    D->own_hi.push_back(p < nparts - 1 ? nz1[p] - ghosts : nz1[p]);
     // electrode nodes are numbered in node order, so a slab's owned ones are
     // one contiguous range of its list
     const int64_t lo = (int64_t)D->own_lo[p] * D->nxy, hi = (int64_t)D->own_hi[p] * D->nxy;
@@ -458,7 +462,7 @@ p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, p4d_dd* out) {
   int dev_prev = -1;
   cudaGetDevice(&dev_prev);
   if (cudaSetDevice(parts[0]->device) != cudaSuccess) st = P4D_ERR_CUDA;
-  const size_t msg = (size_t)std::max(nmsg, 1) * 3 * D->nxy;
+  const size_t msg = (size_t)std::max(nmsg, 1) * 3 * ghosts * D->nxy;
   if (st == P4D_OK &&
       (cudaMalloc(&D->sbuf, sizeof(double) * msg) != cudaSuccess ||
        cudaMalloc(&D->rbuf, sizeof(double) * msg) != cudaSuccess ||
@@ -534,7 +538,7 @@ p4d_status p4d_dd_jvp(p4d_dd D, double* const* x, double* const* y) {
   const int P = (int)D->parts.size();
   for (int p = 0; p < P; ++p)
     if (!x[p] || !y[p] || x[p] == y[p] || !D->parts[p]->linearized) return P4D_ERR_INVALID_ARG;
-  P4D_TRYS(dd_halo(D, x));
+  P4D_TRYS(dd_halo(D, x, false));
   for (int p = 0; p < P; ++p) {
     P4D_TRYS(jvp_full(D->parts[p], x[p], y[p], 0, nullptr, false));
     P4D_TRYS(dd_zero_ghost(D, p, y[p], true));

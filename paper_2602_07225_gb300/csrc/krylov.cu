@@ -1132,7 +1132,7 @@ p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4
   };
   // V_0 = s.(b_k - J x), ||V_0|| and the true residual use the same sequence
   auto residual_norm = [&]() -> p4d_status {
-    P4D_TRYS(dd_halo(D, x));
+    P4D_TRYS(dd_halo(D, x, false));
     for (int p = 0; p < P; ++p) {
       p4d_ctx* c = D->parts[p];
       P4D_TRYS(jvp_reduced(c, x[p], c->V, 0, R[p].bk, true));
@@ -1157,17 +1157,23 @@ p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4
     if (r0.stop) break;
     for (int k = 0; !r0.cycle_done; ++k) {
       // z_k = P_slab^-1 (s^-1 v_k), then the owners' values in its ghost planes
+      // restricted additive Schwarz: every slab preconditions v_k on its
+      // owned and ghost rows (the owners' values), its owned rows are kept
       for (int p = 0; p < P; ++p) {
-        P4D_TRYS(precond_column(D->parts[p], 0, true));
         vec[p] = D->parts[p]->Z + (int64_t)k * R[p].len;
         ptr[p] = D->parts[p]->V + (int64_t)k * R[p].len;
+      }
+      P4D_TRYS(dd_halo(D, ptr.data(), true));
+      for (int p = 0; p < P; ++p) {
+        P4D_TRYS(precond_column(D->parts[p], 0, true));
+        P4D_TRYS(dd_zero_ghost(D, p, ptr[p], false));
       }
       // two-level: z_k += Z A_c^-1 Z^T (s^-1 v_k)
       {
         std::vector<const double*> vk(ptr.begin(), ptr.end());
         P4D_TRYS(dd_coarse_correct(D, vk.data(), vec.data()));
       }
-      P4D_TRYS(dd_halo(D, vec.data()));
+      P4D_TRYS(dd_halo(D, vec.data(), false));
       // w = s.J z_k on the owned rows; h = V^T w, ||w||^2
       for (int p = 0; p < P; ++p) {
         p4d_ctx* c = D->parts[p];
@@ -1250,7 +1256,7 @@ p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4
         c->NE, r.tau, c->enode, r.nn, c->label, c->Aj, c->Mj, c->betaj, c->ge, c->gc, c->gs, r.x, c->tloc, 0);
     P4D_TRYS(particle_solve64(c, r.b + 3 * r.nn, r.x + 3 * r.nn, c->tloc, 0));
   }
-  P4D_TRYS(dd_halo(D, x));
+  P4D_TRYS(dd_halo(D, x, false));
   for (int p = 0; p < P; ++p) {
     FgRun& r = R[p];
     p4d_ctx* c = r.c;

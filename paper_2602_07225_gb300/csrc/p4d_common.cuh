@@ -287,9 +287,10 @@ struct p4d_batch_ctx {
 };
 
 // Slab domain decomposition of one cell along z: parts[p] is the handle of
-// slab p (bottom to top); consecutive slabs share one element layer, so a
-// slab's ghost node planes (local plane 0 above the bottom slab, the last
-// local plane below the top slab) are owned by its neighbours.  Slab p owns
+// slab p (bottom to top); consecutive slabs overlap by 2 ghosts - 1 element
+// layers, so a slab's lowest `ghosts` node planes (above the bottom slab)
+// and highest `ghosts` planes (below the top slab) are ghost planes owned
+// by its neighbours.  Slab p owns
 // its local node planes [own_lo, own_hi) and its electrode nodes
 // [cs_lo, cs_hi) (node order).
 constexpr int kDDRed = 256;   // largest allreduce (values)
@@ -297,11 +298,13 @@ struct p4d_dd_ctx {
   std::vector<p4d_ctx*> parts;          // not owned
   cudaStream_t stream = nullptr;        // the parts' common stream
   int64_t nxy = 0;                      // nodes per z plane
-  std::vector<int32_t> plan;            // halo messages [n][4]: src slab, src plane, dst slab, dst plane
+  int ghosts = 1;                       // ghost node planes per interior side
+  std::vector<int32_t> plan;            // halo messages [n][4]: src slab, first src plane, dst slab, first dst plane
+                                        // (ghosts consecutive planes each)
   std::vector<int> own_lo, own_hi;
   std::vector<int64_t> cs_lo, cs_hi;
-  double* sbuf = nullptr;               // [n][3 nxy] packed planes (sender side)
-  double* rbuf = nullptr;               // [n][3 nxy] received planes
+  double* sbuf = nullptr;               // [n][3 ghosts nxy] packed planes (sender side)
+  double* rbuf = nullptr;               // [n][3 ghosts nxy] received planes
   double* red = nullptr;                // [(P + 1)][kDDRed] allreduce staging; the sum in the last row
   double* part = nullptr;               // block partial sums
   std::vector<double*> bw;              // [P] right-hand sides with ghost rows zero
@@ -512,8 +515,10 @@ p4d_status fgmres_batched(p4d_batch_ctx* B, const double* const* b, double* cons
 void batch_drop_graphs(p4d_batch_ctx* B);
 
 // ---- slab domain decomposition (dd.cu; the driver in krylov.cu)
-// Ghost planes of fields 0..2 of every slab's vector v[p] <- the owners' planes.
-p4d_status dd_halo(p4d_dd_ctx* D, double* const* v);
+// Ghost planes of fields 0..2 of every slab's vector v[p] <- the owners' planes
+// (scaled: Krylov-space vectors s.u, rescaled by the rows' sqrt(diag J) of
+// sender and receiver, so that the receiver holds s.u with its own s).
+p4d_status dd_halo(p4d_dd_ctx* D, double* const* v, bool scaled);
 // Zero slab p's ghost rows of v (fields 0..2; with cs_rows also the particle rows).
 p4d_status dd_zero_ghost(p4d_dd_ctx* D, int p, double* v, bool cs_rows);
 // ptrs[p][0..n) <- sum over the slabs of ptrs[q][0..n) (n <= kDDRed), on every slab.

@@ -185,17 +185,18 @@ class P4DSolver:
             pass
 
 
-def halo_plan(nplanes):
-    """Halo messages of z slabs with nplanes[p] local node planes:
-    [(src slab, src plane, dst slab, dst plane)] (p4d_dd_halo_plan; host only)."""
+def halo_plan(nplanes, ghosts=1):
+    """Halo messages of z slabs with nplanes[p] local node planes and `ghosts`
+    ghost planes per interior side: [(src slab, first src plane, dst slab,
+    first dst plane)], `ghosts` planes each (p4d_dd_halo_plan; host only)."""
     lib = N.load()
     n = len(nplanes)
     arr = (C.c_int32 * n)(*[int(v) for v in nplanes])
-    m = lib.p4d_dd_halo_plan(n, arr, None)
+    m = lib.p4d_dd_halo_plan(n, arr, int(ghosts), None)
     if m < 0:
-        raise ValueError("a slab without owned node planes")
+        raise ValueError("a slab owns no node plane, or fewer than the ghost planes")
     out = (C.c_int32 * max(4 * m, 1))()
-    lib.p4d_dd_halo_plan(n, arr, out)
+    lib.p4d_dd_halo_plan(n, arr, int(ghosts), out)
     return [tuple(out[4 * i:4 * i + 4]) for i in range(m)]
 
 
@@ -213,7 +214,7 @@ class SlabSolver:
         n = len(self.parts)
         hs = (C.c_void_p * n)(*[p.h.value for p in self.parts])
         out = C.c_void_p()
-        N.check(self.lib.p4d_dd_create(hs, n, C.byref(out)), "p4d_dd_create")
+        N.check(self.lib.p4d_dd_create(hs, n, int(slabs[0]["ghosts"]), C.byref(out)), "p4d_dd_create")
         self.dd = out
         self.set_coarse(coarse)
 

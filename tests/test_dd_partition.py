@@ -1,8 +1,8 @@
 """Slab domain decomposition on the host.
 
 The decomposed solve rests on one fact: the rows a slab owns, assembled on
-the slab's own sub-mesh (its elements plus one element layer of each
-neighbour), are the cell's rows.  The oracle checks that here for the
+the slab's own sub-mesh (its elements plus the element layers of its ghost
+planes), are the cell's rows.  The oracle checks that here for the
 residual and the Jacobian of several cells (section 4 eqs.), so that a
 wrong slice (an element layer too few, Gamma_n or Gamma_p on the wrong
 slab, a shifted node plane) fails.  The library's halo plan is checked
@@ -56,9 +56,9 @@ def _row_maps(d_cell, d_slab, slab, nxy):
 
 
 @pytest.mark.parametrize("name", list(CELLS))
-@pytest.mark.parametrize("nparts", [2, 3])
+@pytest.mark.parametrize("nparts,ghosts", [(2, 1), (3, 1), (2, 2)])
 @pytest.mark.parametrize("material", [None, "paper"])
-def test_owned_rows_of_a_slab_are_the_cells(name, nparts, material):
+def test_owned_rows_of_a_slab_are_the_cells(name, nparts, ghosts, material):
     case = CELLS[name]()
     kw = dict(material="paper", ocp="paper") if material else {}
     d = Disc(case["mesh"], case["params"], **kw)
@@ -67,7 +67,7 @@ def test_owned_rows_of_a_slab_are_the_cells(name, nparts, material):
     J = d.jacobian(st).tocsr()
     m = case["mesh"]
     nxy = (m["nx"] + 1) * (m["ny"] + 1)
-    slabs = slab_cases(case, nparts)
+    slabs = slab_cases(case, nparts, ghosts)
     covered = np.zeros(d.ndof, int)
     for sl in slabs:
         ds = Disc(sl["case"]["mesh"], sl["case"]["params"], **kw)
@@ -91,23 +91,27 @@ def test_slabs_partition_the_node_planes(nz, nparts):
     assert b[0] == 0 and b[-1] == nz + 1 and all(b[r + 1] > b[r] for r in range(nparts))
 
 
-def test_plan_matches_partition():
+@pytest.mark.parametrize("ghosts", [1, 2, 3])
+def test_plan_matches_partition(ghosts):
     from paper_2602_07225_gb300 import halo_plan
     case = make_case("cube8")
     for nparts in (1, 2, 3, 5):
-        slabs = slab_cases(case, nparts)
-        plan = halo_plan([s["nplanes"] for s in slabs])
+        slabs = slab_cases(case, nparts, ghosts)
+        plan = halo_plan([s["nplanes"] for s in slabs], ghosts)
         assert len(plan) == 2 * (nparts - 1)
-        ghosts = set()
+        got = set()
         for src, sp, dst, dp in plan:
-            lo, hi = slabs[src]["own"]
-            assert lo <= sp < hi                                   # an owned plane ...
-            assert not slabs[dst]["own"][0] <= dp < slabs[dst]["own"][1]  # ... into a ghost plane
-            assert slabs[src]["e_lo"] + sp == slabs[dst]["e_lo"] + dp    # of the same cell plane
-            ghosts.add((dst, dp))
+            for t in range(ghosts):
+                lo, hi = slabs[src]["own"]
+                assert lo <= sp + t < hi                                      # an owned plane ...
+                assert not slabs[dst]["own"][0] <= dp + t < slabs[dst]["own"][1]  # ... into a ghost plane
+                assert slabs[src]["e_lo"] + sp + t == slabs[dst]["e_lo"] + dp + t  # of the same cell plane
+                got.add((dst, dp + t))
         want = {(r, p) for r, s in enumerate(slabs) for p in range(s["nplanes"])
                 if not s["own"][0] <= p < s["own"][1]}
-        assert ghosts == want
+        assert got == want
+        for r, s in enumerate(slabs):                       # the library's ownership rule
+            assert s["own"] == (ghosts if r > 0 else 0, s["nplanes"] - (ghosts if r < nparts - 1 else 0))
 
 
 def test_plan_rejects_slabs_without_owned_planes():
@@ -116,6 +120,12 @@ def test_plan_rejects_slabs_without_owned_planes():
         halo_plan([1, 3])
     with pytest.raises(ValueError):
         halo_plan([3, 2, 3])
+    with pytest.raises(ValueError):
+        halo_plan([5, 5], ghosts=4)        # one owned plane each, fewer than the neighbour's ghosts
+    with pytest.raises(ValueError):
+        halo_plan([5, 5], ghosts=0)
+    with pytest.raises(ValueError):
+        slab_cases(make_case("cube8"), 8, ghosts=4)
 
 
 def _free_port():
@@ -124,7 +134,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, ghosts):
     sys.path.insert(0, ROOT)
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -139,7 +149,7 @@ def _rank(rank, world, port, q):
         nn = nxy * (m["nz"] + 1)
         rng = np.random.default_rng(5)
         g = rng.standard_normal(3 * nn)                     # a cell vector (fields 0..2)
-        slabs = slab_cases(case, world)
+        slabs = slab_cases(case, world, ghosts)
         me = slabs[rank]
         nns = me["nplanes"] * nxy
         off = me["e_lo"] * nxy
@@ -147,18 +157,19 @@ def _rank(rank, world, port, q):
         glob, loc = slab_node_rows(me, nxy)
         for f in range(3):
             x[f * nns + loc] = g[f * nn + glob]             # owned rows only
-        plan = halo_plan([s["nplanes"] for s in slabs])
+        plan = halo_plan([s["nplanes"] for s in slabs], ghosts)
+        ln = ghosts * nxy                                   # `ghosts` consecutive planes per message
         reqs = []
         for src, sp, dst, dp in plan:                       # pack and send
             if src == rank:
-                buf = torch.tensor(np.concatenate([x[f * nns + sp * nxy:f * nns + (sp + 1) * nxy] for f in range(3)]))
+                buf = torch.tensor(np.concatenate([x[f * nns + sp * nxy:f * nns + sp * nxy + ln] for f in range(3)]))
                 reqs.append(dist.isend(buf, dst))
         for src, sp, dst, dp in plan:                       # receive and unpack
             if dst == rank:
-                buf = torch.empty(3 * nxy, dtype=torch.float64)
+                buf = torch.empty(3 * ln, dtype=torch.float64)
                 dist.recv(buf, src)
                 for f in range(3):
-                    x[f * nns + dp * nxy:f * nns + (dp + 1) * nxy] = buf[f * nxy:(f + 1) * nxy].numpy()
+                    x[f * nns + dp * nxy:f * nns + dp * nxy + ln] = buf[f * ln:(f + 1) * ln].numpy()
         for r in reqs:
             r.wait()
         want = np.concatenate([g[f * nn + off:f * nn + off + nns] for f in range(3)])
@@ -171,11 +182,12 @@ def _rank(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_two_ranks_exchange_ghost_planes_and_reduce():
+@pytest.mark.parametrize("ghosts", [1, 2])
+def test_two_ranks_exchange_ghost_planes_and_reduce(ghosts):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q, ghosts)) for r in range(2)]
     for p in procs:
         p.start()
     out = sorted(q.get(timeout=240) for _ in procs)

@@ -69,22 +69,23 @@ def _scatter(maps, g, parts):
     return xs
 
 
-def _setup(name, nparts, coarse=2, **opts):
+def _setup(name, nparts, coarse=2, ghosts=1, **opts):
     from paper_2602_07225_gb300 import P4DSolver, SlabSolver
     case = CELLS[name]()
     okw, lkw = LAWS.get(name, ({}, {}))
     d = Disc(case["mesh"], case["params"], **okw)
-    slabs = slab_cases(case, nparts)
+    slabs = slab_cases(case, nparts, ghosts)
     dd = SlabSolver(slabs, coarse=coarse, **lkw, **opts)
     maps = _maps(case, slabs, dd.parts, d)
     cell = P4DSolver(case, **lkw, **opts)
     return case, d, slabs, dd, maps, cell
 
 
-@pytest.mark.parametrize("name,nparts", [("cube8", 2), ("cube8", 3), ("hetero", 2), ("tabshell", 2), ("tpms", 2),
-                                         ("paper_laws", 2), ("paper_laws", 4)])
-def test_dd_jvp_is_the_cells(name, nparts):
-    case, d, slabs, dd, maps, cell = _setup(name, nparts, precision=0)
+@pytest.mark.parametrize("name,nparts,ghosts", [("cube8", 2, 1), ("cube8", 3, 1), ("cube8", 3, 3), ("hetero", 2, 1),
+                                                ("tabshell", 2, 1), ("tpms", 2, 2), ("paper_laws", 2, 1),
+                                                ("paper_laws", 4, 2)])
+def test_dd_jvp_is_the_cells(name, nparts, ghosts):
+    case, d, slabs, dd, maps, cell = _setup(name, nparts, ghosts=ghosts, precision=0)
     sts = dd.state_tensors()
     dd.jacobian_update(sts)
     stc = cell.state_tensors(case["state"])
@@ -101,14 +102,15 @@ def test_dd_jvp_is_the_cells(name, nparts):
     assert np.abs(r - rc).max() <= 1e-14 * np.abs(rc).max()
 
 
-@pytest.mark.parametrize("name,nparts", [("cube8", 2), ("cube8", 3), ("hetero", 2), ("tpms", 2), ("paper_laws", 2)])
+@pytest.mark.parametrize("name,nparts,ghosts", [("cube8", 2, 1), ("cube8", 3, 1), ("cube8", 3, 2), ("hetero", 2, 1),
+                                                ("tpms", 2, 2), ("paper_laws", 2, 1)])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("refine", [0, 1])
 @pytest.mark.parametrize("coarse", [0, 2])
-def test_dd_fgmres_matches_direct(name, nparts, precision, refine, coarse):
+def test_dd_fgmres_matches_direct(name, nparts, ghosts, precision, refine, coarse):
     rtol = 1e-12 if precision == 0 else 1e-10
-    case, d, slabs, dd, maps, cell = _setup(name, nparts, precision=precision, mode=1, rtol=rtol, maxit=1500,
-                                            cgs_refine=refine, coarse=coarse)
+    case, d, slabs, dd, maps, cell = _setup(name, nparts, ghosts=ghosts, precision=precision, mode=1, rtol=rtol,
+                                            maxit=1500, cgs_refine=refine, coarse=coarse)
     sts = dd.state_tensors()
     dd.jacobian_update(sts)
     bs = [-r for r in dd.residual(sts)]
@@ -132,7 +134,7 @@ def test_coarse_space_cuts_iterations():
     case = make_box_case(16, 16, (20, 8, 20), 100e-6, (100e-6, 25e-6, 100e-6), 6, 1007)
     its = {}
     for coarse in (0, 1, 2):
-        dd = SlabSolver(slab_cases(case, 4), coarse=coarse, precision=1, mode=1, rtol=1e-8, maxit=1500)
+        dd = SlabSolver(slab_cases(case, 4, 2), coarse=coarse, precision=1, mode=1, rtol=1e-8, maxit=1500)
         sts = dd.state_tensors()
         dd.jacobian_update(sts)
         _, info = dd.solve([-r for r in dd.residual(sts)])
@@ -158,6 +160,21 @@ def test_one_slab_is_the_cell_solve(name):
     assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
 
 
+def test_wider_overlap_cuts_iterations():
+    from paper_2602_07225_gb300 import SlabSolver
+    case = make_box_case(16, 16, (20, 8, 20), 100e-6, (100e-6, 25e-6, 100e-6), 6, 1007)
+    its = {}
+    for ghosts in (1, 4):
+        dd = SlabSolver(slab_cases(case, 4, ghosts), coarse=2, precision=1, mode=1, rtol=1e-8, maxit=1500)
+        sts = dd.state_tensors()
+        dd.jacobian_update(sts)
+        _, info = dd.solve([-r for r in dd.residual(sts)])
+        assert info["status"] == 0, info
+        its[ghosts] = info["iters"]
+        dd.close()
+    assert its[4] < its[1], its
+
+
 def test_dd_rejects_mismatched_slabs():
     from paper_2602_07225_gb300 import P4DSolver, _native as N
     import ctypes as C
@@ -166,6 +183,6 @@ def test_dd_rejects_mismatched_slabs():
     lib = a.lib
     out = C.c_void_p()
     hs = (C.c_void_p * 2)(a.h.value, b.h.value)
-    assert lib.p4d_dd_create(hs, 2, C.byref(out)) == N.INVALID_ARG
+    assert lib.p4d_dd_create(hs, 2, 1, C.byref(out)) == N.INVALID_ARG
     hs = (C.c_void_p * 2)(a.h.value, a.h.value)
-    assert lib.p4d_dd_create(hs, 2, C.byref(out)) == N.INVALID_ARG
+    assert lib.p4d_dd_create(hs, 2, 1, C.byref(out)) == N.INVALID_ARG
