@@ -657,8 +657,8 @@ def slab_study(args):
     """cube128 (seeded linearization, seed 1002) cut into 1, 2, 4 and 8 z
     slabs on this one GPU (p4d_dd_*): one handle per slab, ghost planes
     exchanged before every operator application, every inner product reduced
-    over the slabs, restricted additive Schwarz over the slabs (1 or 4 ghost
-    planes) with and without the two-level coarse correction.  Iterations,
+    over the slabs, restricted additive Schwarz over the slabs (1, 4 or 8
+    ghost planes) with and without the two-level coarse correction.  Iterations,
     time of one
     Newton linear solve to 1e-8 and the solution's per-field difference from
     the undecomposed solve; what one slab per GPU would add (the transfers
@@ -699,8 +699,8 @@ def slab_study(args):
     torch.cuda.empty_cache()
     rows = [{"slabs": 1, "driver": "single cell", "iters": info1["iters"], "ms_per_solve": ms1,
              "rel_res": info1["rel_res"]}]
-    for nparts, coarse, ghosts in ((1, 0, 1), (2, 0, 1), (2, 2, 1), (2, 2, 4), (4, 2, 1), (4, 2, 4), (8, 2, 1),
-                                   (8, 2, 4)):
+    for nparts, coarse, ghosts in ((1, 0, 1), (2, 0, 1), (2, 0, 4), (2, 2, 4), (4, 0, 4), (4, 2, 4), (4, 2, 8),
+                                   (8, 0, 4), (8, 2, 4), (8, 2, 8)):
         slabs = slab_cases(case, nparts, ghosts)
         dd = SlabSolver(slabs, device=dev, coarse=coarse, **opts)
         sts = dd.state_tensors()
@@ -727,8 +727,8 @@ def slab_study(args):
            "value": 1e3 / rows[4]["ms_per_solve"],
            "config": {"workload": "cube128 seeded linearization (seed 1002) as 1-8 z slabs on one GPU, REDUCED, "
                                   + CYCLE + ", FGMRES(30) rtol 1e-8, " + CGS_DESC[args.cgs_refine]
-                                  + "; restricted additive Schwarz over the slabs with 1 or 4 ghost planes, with or "
-                                    "without the coarse correction; value = two slabs, 4 ghost planes, coarse "
+                                  + "; restricted additive Schwarz over the slabs with 1, 4 or 8 ghost planes, with "
+                                    "or without the coarse correction; value = two slabs, 4 ghost planes, coarse "
                                     "correction (linear solve only)"}}
     print(json.dumps(out))
 

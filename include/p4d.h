@@ -334,7 +334,8 @@ p4d_status p4d_dd_jvp(p4d_dd dd, double* const* x, double* const* y);
    owners' values).  The preconditioner is restricted additive Schwarz
    over the slabs: each slab applies its own block preconditioner to the
    Krylov vector on its owned and ghost rows (the owners' values) and keeps
-   its owned rows; plus the coarse correction of p4d_dd_set_coarse.  The
+   its owned rows; with ghosts = 1 the ghost rows are zero instead (block
+   Jacobi across the slabs); plus the coarse correction of p4d_dd_set_coarse.  The
    converged solution is the cell's.  info (one report for the cell) as p4d_fgmres_solve.
    Synchronizes the stream. */
 p4d_status p4d_dd_fgmres_solve(p4d_dd dd, const double* const* b, double* const* x, p4d_info* info);

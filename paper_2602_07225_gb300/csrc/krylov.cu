@@ -1158,12 +1158,15 @@ p4d_status fgmres_dd(p4d_dd_ctx* D, const double* const* b, double* const* x, p4
     for (int k = 0; !r0.cycle_done; ++k) {
       // z_k = P_slab^-1 (s^-1 v_k), then the owners' values in its ghost planes
       // restricted additive Schwarz: every slab preconditions v_k on its
-      // owned and ghost rows (the owners' values), its owned rows are kept
+      // owned and ghost rows (the owners' values) and keeps its owned rows.
+      // With a single ghost plane, whose rows miss the elements beyond the
+      // slab, its rows stay zero (block Jacobi across the slabs): fed the
+      // owners' residual there the iteration counts grow several times.
       for (int p = 0; p < P; ++p) {
         vec[p] = D->parts[p]->Z + (int64_t)k * R[p].len;
         ptr[p] = D->parts[p]->V + (int64_t)k * R[p].len;
       }
-      P4D_TRYS(dd_halo(D, ptr.data(), true));
+      if (D->ghosts > 1) P4D_TRYS(dd_halo(D, ptr.data(), true));
       for (int p = 0; p < P; ++p) {
         P4D_TRYS(precond_column(D->parts[p], 0, true));
         P4D_TRYS(dd_zero_ghost(D, p, ptr[p], false));
