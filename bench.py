@@ -673,7 +673,7 @@ def slab_study(args):
     case = make_case("cube128")
     m = case["mesh"]
     nxy = (m["nx"] + 1) * (m["ny"] + 1)
-    opts = dict(precision=1, mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0],
+    opts = dict(precision=1, mode=1, combine=0, rtol=1e-8, restart=30, maxit=1000, cheb_degree=CHEB[0],
                 cheb_ratio=CHEB[1], cgs_refine=args.cgs_refine)
 
     def timed(fn, reps=3):
@@ -706,7 +706,7 @@ def slab_study(args):
         sts = dd.state_tensors()
         bs = [r.neg_() for r in dd.residual(sts)]
         dd.jacobian_update(sts)
-        (xs, info), ms = timed(lambda: dd.solve(bs))
+        (xs, info), ms = timed(lambda: dd.solve(bs, check=False), reps=2)
         diff = 0.0
         for i, (sl, xp) in enumerate(zip(slabs, xs)):
             glob, loc = slab_node_rows(sl, nxy)
@@ -715,10 +715,12 @@ def slab_study(args):
                 ref = x1[f * nn:(f + 1) * nn]
                 diff = max(diff, float(np.abs(xv[f * nns + loc] - ref[glob]).max() / np.abs(ref).max()))
         rows.append({"slabs": nparts, "driver": "decomposed", "ghost_planes": ghosts,
-                     "coarse": ["none", "constants", "constants + z"][coarse],
+                     "coarse": ["none", "constants", "constants + z"][coarse], "status": info["status"],
                      "iters": info["iters"], "ms_per_solve": ms,
                      "rel_res": info["rel_res"], "rel_res_unscaled": info["rel_res_unscaled"],
                      "max_field_diff_vs_cell": diff})
+        print("slabs %d ghosts %d coarse %d: %d iterations, status %d" % (nparts, ghosts, coarse, info["iters"],
+                                                                         info["status"]), file=sys.stderr)
         dd.close()
         del dd, sts, bs, xs
         torch.cuda.empty_cache()
