@@ -28,7 +28,7 @@
 // (the multigrid never writes them).
 //
 // Layout of a launch: each block owns a tile of W x H nodes (nominally
-// 32 x 8; the last tile of an axis takes the remainder, at most one more)
+// 15 x 15; the last tile of an axis takes the remainder, at most one more)
 // and marches in z over a chunk of node planes.  Per plane it stages the
 // (W+2) x (H+2) tile of x in shared memory, evaluates the (W+1) x (H+1)
 // elements between that plane and the next (their lower-corner outputs go
@@ -43,8 +43,14 @@
 namespace p4d {
 namespace {
 
-constexpr int kTX = 32, kTY = 8;        // nominal node tile (one thread per node)
-constexpr int kMfThreads = kTX * kTY;
+// Nominal node tile: 15 x 15 nodes have (15 + 1)^2 = 256 elements, one per
+// thread, so that no warp evaluates a second element before the per-plane
+// barrier (only the remainder tiles of an axis, up to 16 nodes wide, do).
+constexpr int kTX = 15, kTY = 15;
+constexpr int kMfThreads = 256;
+static_assert((kTX + 3) * (kTY + 3) <= 2 * kMfThreads, "two x entries per thread at most");
+static_assert((kTX + 2) * (kTY + 2) <= 2 * kMfThreads, "two elements per thread at most");
+static_assert((kTX + 1) * (kTY + 1) <= 2 * kMfThreads, "two nodes per thread at most");
 constexpr int kDefaultZChunk = 8;      // node planes per block (tunable: P4D_MF_ZCHUNK)
 
 template <typename T>
@@ -116,12 +122,12 @@ __device__ __forceinline__ void element_apply(T (&v)[8], const T (&lam)[8]) {
 //
 // Tiles are at most (kTX + 1) x (kTY + 1) nodes, so every thread owns at
 // most two x loads, two elements and two nodes of a plane (slot r: index
-// tid + 256 r).  The global loads of the next plane (x of plane k + 2, the
+// tid + 256 r; the nominal tile: one element and at most one node).  The global loads of the next plane (x of plane k + 2, the
 // element coefficients of element plane k + 1, the node data of plane
 // k + 1) are issued into registers one iteration ahead, so their latency
 // overlaps the current plane's element and node work.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
+__global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 it = a.items[blockIdx.x];
   const int f = it.x;
@@ -133,11 +139,14 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   const int k0 = it.z, k1 = it.w;
   const int XW = W + 2, XH = H + 2, EW = W + 1, EH = H + 1;
   const int XN = XW * XH, EN = EW * EH, NN = W * H;
-  // ring buffers: x planes [4][XN]; element planes' lower-corner outputs
-  // [2][4][EN] and upper-corner outputs [3][4][EN]
+  // shared-memory layout with the largest tile's strides (compile-time
+  // constants, so that every shared access is a base plus an immediate):
+  // x planes [4][XP] with rows of XS; element planes' lower-corner outputs
+  // [2][4][EP] and upper-corner outputs [3][4][EP] with rows of ES
+  constexpr int XS = kTX + 3, XP = XS * (kTY + 3), ES = kTX + 2, EP = ES * (kTY + 2);
   T* xs = reinterpret_cast<T*>(smem_raw);
-  T* Lb = xs + 4 * XN;
-  T* Ub = Lb + 8 * EN;
+  T* Lb = xs + 4 * XP;
+  T* Ub = Lb + 8 * EP;
   // the block's field pointers, selected once (not per access)
   const T* __restrict__ Fx = fsel(a, f).x;
   T* __restrict__ Fxo = fsel(a, f).xo;
@@ -169,20 +178,22 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   for (int r = 0; r < 2; ++r) {
     const int q = tid + r * kMfThreads;
     xoff[r] = -1;
-    xsm[r] = q < XN ? q : -1;
+    xsm[r] = -1;
     if (q < XN) {
       const int jj = q / XW, ii = q - jj * XW;
+      xsm[r] = ii + XS * jj;
       const int gi = i0 - 1 + ii, gj = j0 - 1 + jj;
       if (gi >= 0 && gi < a.nnx && gj >= 0 && gj < a.nny) xoff[r] = gi + a.nnx * gj;
     }
     eoff[r] = -1;
-    eq[r] = q < EN ? q : -1;
+    eq[r] = -1;
     ebase[r] = 0;
 #pragma unroll
     for (int t = 0; t < 3; ++t) ex[r][t] = ey[r][t] = (T)0;
     if (q < EN) {
       const int ej = q / EW, ei = q - ej * EW;
-      ebase[r] = ei + XW * ej;
+      eq[r] = ei + ES * ej;
+      ebase[r] = ei + XS * ej;
       const int gi = i0 - 1 + ei, gj = j0 - 1 + ej;
       if (gi >= 0 && gi < a.nx && gj >= 0 && gj < a.ny) {
         eoff[r] = gi + a.nx * gj;
@@ -199,8 +210,8 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     if (q < NN) {
       const int jj = q / W, ii = q - jj * W;
       noff[r] = (i0 + ii) + a.nnx * (j0 + jj);
-      nq[r] = ii + EW * jj;
-      nsm[r] = (ii + 1) + XW * (jj + 1);
+      nq[r] = ii + ES * jj;
+      nsm[r] = (ii + 1) + XS * (jj + 1);
     }
   }
   // Chebyshev coefficients of the block's hierarchies (phi_s: both electrodes)
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     if (wx2) xr[1] = (kin && xoff[1] >= 0) ? Fx[xoff[1] + base] : (T)0;
   };
   auto store_x = [&](int slot) {
-    T* dst = xs + slot * XN;
+    T* dst = xs + slot * XP;
     if (xsm[0] >= 0) dst[xsm[0]] = xr[0];
     if (wx2 && xsm[1] >= 0) dst[xsm[1]] = xr[1];
   };
@@ -262,10 +273,10 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
   // element plane ke between x planes ke and ke + 1 of the ring,
   // coefficients in kr / mr: lower corners to L[ke & 1], upper to U[ke % 3]
   auto element_plane = [&](int ke) {
-    const T* xl = xs + ((ke + 4) & 3) * XN;
-    const T* xu = xs + ((ke + 5) & 3) * XN;
-    T* lo = Lb + ((ke + 2) & 1) * 4 * EN;
-    T* up = Ub + ((ke + 3) % 3) * 4 * EN;
+    const T* xl = xs + ((ke + 4) & 3) * XP;
+    const T* xu = xs + ((ke + 5) & 3) * XP;
+    T* lo = Lb + ((ke + 2) & 1) * 4 * EP;
+    T* up = Ub + ((ke + 3) % 3) * 4 * EP;
     T Ksz = 0, Msz = 0, Mdz = 0;
     if (ke >= 0 && ke < a.nz) {
       Ksz = a.gz[ke];
@@ -282,12 +293,12 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
       const int base = ebase[r];
       v[0] = xl[base];
       v[1] = xl[base + 1];
-      v[2] = xl[base + XW];
-      v[3] = xl[base + XW + 1];
+      v[2] = xl[base + XS];
+      v[3] = xl[base + XS + 1];
       v[4] = xu[base];
       v[5] = xu[base + 1];
-      v[6] = xu[base + XW];
-      v[7] = xu[base + XW + 1];
+      v[6] = xu[base + XS];
+      v[7] = xu[base + XS + 1];
       // eigenvalues (the x factors carry the 1/8); per (y, z) component
       // b + 2c: P = My Mz, Q = Ky Mz + My Kz
       const T Kdx = ex[r][0], Msx = ex[r][1], Mdx = ex[r][2];
@@ -308,8 +319,8 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
       element_apply<T>(v, lam);
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        lo[l * EN + q] = v[l];
-        up[l * EN + q] = v[4 + l];
+        lo[l * EP + q] = v[l];
+        up[l * EP + q] = v[4 + l];
       }
     }
   };
@@ -344,9 +355,9 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
     fetch_x(k + 4);
     element_plane(k + 1);       // zero outputs beyond the last element plane
     fetch_coef(k + 2);
-    const T* xk = xs + ((k + 4) & 3) * XN;
-    const T* lo = Lb + ((k + 2) & 1) * 4 * EN;
-    const T* upPrev = Ub + ((k + 2) % 3) * 4 * EN;
+    const T* xk = xs + ((k + 4) & 3) * XP;
+    const T* lo = Lb + ((k + 2) & 1) * 4 * EP;
+    const T* upPrev = Ub + ((k + 2) % 3) * 4 * EP;
     const int base = k * sxy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -360,8 +371,8 @@ __global__ void __launch_bounds__(kMfThreads, 3) k_mf_level0(MfArgs<T> a) {
       const int e = nq[r];
       const T xn = xk[nsm[r]];
       T ax = sr[r] * xn;
-      ax += (lo[3 * EN + e] + upPrev[3 * EN + e]) + (lo[2 * EN + e + 1] + upPrev[2 * EN + e + 1]);
-      ax += (lo[1 * EN + e + EW] + upPrev[1 * EN + e + EW]) + (lo[e + EW + 1] + upPrev[e + EW + 1]);
+      ax += (lo[3 * EP + e] + upPrev[3 * EP + e]) + (lo[2 * EP + e + 1] + upPrev[2 * EP + e + 1]);
+      ax += (lo[1 * EP + e + ES] + upPrev[1 * EP + e + ES]) + (lo[e + ES + 1] + upPrev[e + ES + 1]);
       const T res = br[r] - ax;
       const int n = noff[r] + base;
       if (MODE == 1) {
@@ -478,8 +489,9 @@ p4d_status mf_setup(p4d_ctx* c) {
   P4D_TRYS(dalloc_t(c, &d, std::max<size_t>(1, items.size())));
   if (!items.empty()) P4D_TRY(cudaMemcpy(d, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   c->mf_items = d;
+  // the kernel lays shared memory out with the largest tile's strides
   const size_t ts = sizeof(float);
-  const size_t xn = (size_t)(mw + 2) * (mh + 2), en = (size_t)(mw + 1) * (mh + 1);
+  const size_t xn = (size_t)(kTX + 3) * (kTY + 3), en = (size_t)(kTX + 2) * (kTY + 2);
   c->mf_smem = ts * (4 * xn + 20 * en);
   if (mw > kTX + 1 || mh > kTY + 1 || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
   // The kernels' shared-memory limit is a process-wide attribute shared by
