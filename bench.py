@@ -479,7 +479,7 @@ def batched_leg(args, rank=0, world=1, local=0):
     cells = [allc[i] for i in shard(len(allc), rank, world)]
     t0 = time.perf_counter()
     bs = BatchSolver(cells, threads=16, device=torch.device("cuda", local), precision=1, mode=1, rtol=1e-8,
-                     maxit=600)
+                     maxit=600, cgs_refine=args.cgs_refine, tune_setup=True)
     setup_s = time.perf_counter() - t0
     ndof = sum(s.ndof for s in bs.solvers)
     lib = bs.solvers[0].lib
@@ -850,7 +850,9 @@ def main():
                "dtype": "f64 outer / f32 preconditioner", "data": "synthetic",
                "config": {"workload": "gyroid64: 64 gyroid cells 16x16x24..64x64x96, N_c 10-20, one Newton "
                                       "linear solve per cell per step, lockstep batch (one CUDA graph per "
-                                      "Krylov column over all cells), autotuned Chebyshev",
+                                      "Krylov column over all cells), autotuned smoother, block combination, "
+                                      "coarsening threshold and level-0 tile depth per shape, "
+                                      + CGS_DESC[args.cgs_refine],
                           "unknowns": r["ndof"], "l2": "inputs larger than L2"},
                "fgmres_iters_per_s": r["its"] / r["lock_s"], **seq, "setup_s": r["setup_s"], "tuned": r["tuned"],
                "failed_cells": r["failed"], "gpu_launches": r["launches"], "clocks": r["clocks"]}

@@ -136,6 +136,8 @@ typedef struct {
                            parameters" keep the default classical Gram-Schmidt without
                            refinement), 1 when the first pass leaves ||w|| < 0.7 ||w_0||
                            (default), 2 always */
+  int32_t mf_zchunk;    /* node planes per block of the matrix-free level-0 kernel (the
+                           z depth of its tile; 0 = 8, at most 64).  Fixed at p4d_setup */
 } p4d_params;
 
 /* A linearization state.  All [device], FP64; cs / cs_prev are [nelec][nc]. */
@@ -192,9 +194,10 @@ p4d_status p4d_get_sizes(p4d_handle h, int64_t* nnode, int64_t* nelec, int64_t* 
 p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out);
 
 /* Change solver options (combine, order, restart, maxit, rtol, cheb_ratio,
-   cheb_degree, mode, profile) and the kinetics constants.  precision,
-   coarse_max and the parameters assembled at setup (dt, F, brug, De, kappa,
-   sigma_n, sigma_p, transport_model) cannot change (INVALID_ARG). */
+   cheb_degree, mode, profile, cgs_refine) and the kinetics constants.
+   precision, coarse_max, mf_zchunk and the parameters assembled at setup
+   (dt, F, brug, De, kappa, sigma_n, sigma_p, transport_model) cannot
+   change (INVALID_ARG). */
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* params);
 
 /* Nonlinear residual R(u) (paper section 4, block residual [R_phis; R_phie;

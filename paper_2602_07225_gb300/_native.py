@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("restart", C.c_int32), ("maxit", C.c_int32), ("mode", C.c_int32),
                 ("cheb_degree", C.c_int32), ("coarse_max", C.c_int32), ("cheb_ratio", C.c_double),
                 ("rtol", C.c_double), ("profile", C.c_int32), ("ocp_model", C.c_int32),
-                ("transport_model", C.c_int32), ("cgs_refine", C.c_int32)]
+                ("transport_model", C.c_int32), ("cgs_refine", C.c_int32), ("mf_zchunk", C.c_int32)]
 
 
 class State(C.Structure):

@@ -10,9 +10,13 @@ synchronizes once per column for the whole batch.  The "threads" mode
 for comparison.  An autotuner picks the
 Chebyshev degree and interval per (mesh shape, precision) by timing one
 solve of the first cell of each grid shape (N_c does not enter the
-multigrid: the particle blocks are eliminated exactly), then the block combination (block Jacobi or block Gauss-Seidel
-in each order of the fields) with that smoother; results are cached in
-memory and optionally in a JSON file.
+multigrid: the particle blocks are eliminated exactly), then the block
+combination (block Jacobi or block Gauss-Seidel in each order of the fields)
+with that smoother, then the two options fixed when a handle is set up: the
+coarsening threshold coarse_max (the multigrid's level count) and the z
+depth of the matrix-free level-0 tile (mf_zchunk), each candidate on a
+handle built for it; results are cached in memory and optionally in a JSON
+file.
 """
 import concurrent.futures as cf
 import ctypes as C
@@ -30,6 +34,9 @@ CANDIDATES = ((1, 4.0), (2, 10.0), (3, 10.0), (3, 20.0), (4, 20.0))
 # Gauss-Seidel in every order of the fields (0 phi_s, 1 phi_e, 2 c_e)
 BJ = (0, (1, 0, 2))
 COMBOS = (BJ,) + tuple((1, o) for o in itertools.permutations((0, 1, 2)))
+# (coarse_max, mf_zchunk), the library defaults first
+SETUP_DEFAULT = (128, 8)
+SETUP_CANDIDATES = (SETUP_DEFAULT, (32, 8), (512, 8), (128, 4), (128, 16))
 
 
 class Autotuner:
@@ -74,44 +81,90 @@ class Autotuner:
                 best, best_ms = best_s + (combine, order), ms
         return best
 
-    def get(self, solver, case, state, b):
+    def tune_setup(self, build, runtime):
+        """(coarse_max, mf_zchunk): build(coarse_max, mf_zchunk) returns a
+        linearized solver of the shape and its right-hand side; each
+        candidate runs with the runtime options chosen before."""
+        best, best_ms = SETUP_DEFAULT, float("inf")
+        for cm, zc in SETUP_CANDIDATES:
+            s, b = build(cm, zc)
+            s.set_options(**runtime)
+            ms = self._time(s, b)
+            if hasattr(s, "close"):
+                s.close()
+            if ms < best_ms:
+                best, best_ms = (cm, zc), ms
+        return best
+
+    def get(self, solver, case, state, b, build=None):
+        """(cheb_degree, cheb_ratio, combine, order, coarse_max, mf_zchunk);
+        without build the setup options stay at the library defaults."""
         k = self.key(solver, case)
-        if k not in self.cache:
-            self.cache[k] = self.tune(solver, state, b)
+        if k not in self.cache or (build is not None and len(self.cache[k]) < 6):
+            got = self.cache[k][:4] if k in self.cache else self.tune(solver, state, b)
+            deg, ratio, combine, order = got
+            setup = SETUP_DEFAULT
+            if build is not None:
+                setup = self.tune_setup(build, dict(cheb_degree=deg, cheb_ratio=ratio, combine=combine,
+                                                    order=tuple(order)))
+            self.cache[k] = tuple(got) + tuple(setup)
             if self.path:
                 with open(self.path, "w") as fh:
                     json.dump({json.dumps(list(kk)): list(v) for kk, v in self.cache.items()}, fh)
-        return self.cache[k]
+        v = self.cache[k]
+        return tuple(v) + (tuple(SETUP_DEFAULT) if len(v) < 6 else ())
 
 
 class BatchSolver:
-    """cases: list of generator cases; opts: P4DSolver options."""
+    """cases: list of generator cases; opts: P4DSolver options.  With
+    tune_setup the autotuner also searches coarse_max and mf_zchunk (each
+    candidate builds a handle of the shape's first cell)."""
 
-    def __init__(self, cases, threads=16, autotune=True, tuner=None, device="cuda", **opts):
+    def __init__(self, cases, threads=16, autotune=True, tuner=None, device="cuda", tune_setup=False, **opts):
         self.cases = cases
         self.threads = threads
+        self.opts = dict(opts)
+        self.device = device
         self.solvers, self.states = [], []
         for c in cases:
-            st = torch.cuda.Stream(device=device)
-            with torch.cuda.stream(st):
-                s = P4DSolver(c, device=device, stream=st, **opts)
-                self.solvers.append(s)
-                self.states.append(s.state_tensors(c["state"]))
+            s, stt = self._make(c, opts)
+            self.solvers.append(s)
+            self.states.append(stt)
         torch.cuda.synchronize()
         self._batch = None
         self.tuner = tuner or (Autotuner() if autotune else None)
         self.tuned = {}
         if self.tuner:
-            for i, (s, c) in enumerate(zip(self.solvers, self.cases)):
+            for i, c in enumerate(self.cases):
+                s = self.solvers[i]
                 k = Autotuner.key(s, c)
                 if k not in self.tuned:
                     with torch.cuda.stream(s.stream):
                         b = s.residual(self.states[i]).neg_()
                         s.jacobian_update(self.states[i])
-                        self.tuned[k] = self.tuner.get(s, c, self.states[i], b)
-                deg, ratio, combine, order = self.tuned[k]
+                        build = (lambda cm, zc, c=c: self._build_linearized(c, cm, zc)) if tune_setup else None
+                        self.tuned[k] = self.tuner.get(s, c, self.states[i], b, build=build)
+                deg, ratio, combine, order, cm, zc = self.tuned[k]
+                want = dict(coarse_max=cm, mf_zchunk=zc)
+                if (int(s.params.coarse_max), int(s.params.mf_zchunk) or SETUP_DEFAULT[1]) != (cm, zc):
+                    s.close()
+                    s, self.states[i] = self._make(c, {**opts, **want})
+                    self.solvers[i] = s
                 s.set_options(cheb_degree=deg, cheb_ratio=ratio, combine=combine, order=tuple(order))
         torch.cuda.synchronize()
+
+    def _make(self, c, opts):
+        st = torch.cuda.Stream(device=self.device)
+        with torch.cuda.stream(st):
+            s = P4DSolver(c, device=self.device, stream=st, **opts)
+            return s, s.state_tensors(c["state"])
+
+    def _build_linearized(self, c, coarse_max, mf_zchunk):
+        s, stt = self._make(c, {**self.opts, "coarse_max": coarse_max, "mf_zchunk": mf_zchunk})
+        with torch.cuda.stream(s.stream):
+            b = s.residual(stt).neg_()
+            s.jacobian_update(stt)
+        return s, b
 
     def _linearize(self, i):
         s, st = self.solvers[i], self.states[i]

@@ -125,6 +125,7 @@ bool valid_params(const p4d_params* p) {
   if (p->ocp_model < 0 || p->ocp_model > 1) return false;
   if (p->transport_model < 0 || p->transport_model > 1) return false;
   if (p->cgs_refine < 0 || p->cgs_refine > 2) return false;
+  if (p->mf_zchunk < 0 || p->mf_zchunk > 64) return false;
   bool seen[3] = {false, false, false};
   for (int i = 0; i < 3; ++i) {
     if (p->order[i] < 0 || p->order[i] > 2 || seen[p->order[i]]) return false;
@@ -360,6 +361,7 @@ void p4d_params_default(p4d_params* p) {
   p->restart = 30; p->maxit = 500; p->mode = 1; p->cheb_degree = 2; p->coarse_max = 128;
   p->cheb_ratio = 10.0; p->rtol = 1e-8; p->profile = 0; p->ocp_model = 0; p->transport_model = 0;
   p->cgs_refine = 1;
+  p->mf_zchunk = 0;
 }
 
 p4d_status p4d_setup(const p4d_mesh* m, const p4d_params* prm, const p4d_state* st, void* stream,
@@ -415,7 +417,8 @@ p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out) {
 
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
   if (!h || !p || !valid_params(p)) return P4D_ERR_INVALID_ARG;
-  if (p->precision != h->prm.precision || p->coarse_max != h->prm.coarse_max) return P4D_ERR_INVALID_ARG;
+  if (p->precision != h->prm.precision || p->coarse_max != h->prm.coarse_max || p->mf_zchunk != h->prm.mf_zchunk)
+    return P4D_ERR_INVALID_ARG;
   if (p->profile != 0 && p->profile != 1) return P4D_ERR_INVALID_ARG;
   if (p->restart > h->mcap) return P4D_ERR_INVALID_ARG;
   // parameters baked into the assembled stencils, the particle factors and

@@ -36,7 +36,6 @@
 // updates its nodes.  The phi_s work list covers only the node planes that
 // hold phi_s unknowns.
 #include <algorithm>
-#include <cstdlib>
 #include <vector>
 #include "p4d_common.cuh"
 
@@ -51,7 +50,7 @@ constexpr int kMfThreads = 256;
 static_assert((kTX + 3) * (kTY + 3) <= 2 * kMfThreads, "two x entries per thread at most");
 static_assert((kTX + 2) * (kTY + 2) <= 2 * kMfThreads, "two elements per thread at most");
 static_assert((kTX + 1) * (kTY + 1) <= 2 * kMfThreads, "two nodes per thread at most");
-constexpr int kDefaultZChunk = 8;      // node planes per block (tunable: P4D_MF_ZCHUNK)
+constexpr int kDefaultZChunk = 8;      // node planes per block when p4d_params.mf_zchunk = 0
 
 template <typename T>
 struct MfField {
@@ -463,8 +462,7 @@ p4d_status mf_setup(p4d_ctx* c) {
   // or the last tile's remainder (which can be smaller or one larger)
   const int mw = c->mf_ntx == 1 ? nnx : std::max(kTX, nnx - (c->mf_ntx - 1) * kTX);
   const int mh = c->mf_nty == 1 ? nny : std::max(kTY, nny - (c->mf_nty - 1) * kTY);
-  int zc = kDefaultZChunk;
-  if (const char* s = std::getenv("P4D_MF_ZCHUNK")) zc = std::max(1, std::atoi(s));
+  const int zc = c->prm.mf_zchunk > 0 ? c->prm.mf_zchunk : kDefaultZChunk;
   // planes holding phi_s unknowns
   std::vector<uint8_t> lab(c->g.nn);
   P4D_TRY(cudaMemcpy(lab.data(), c->label, c->g.nn, cudaMemcpyDeviceToHost));

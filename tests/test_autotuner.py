@@ -2,7 +2,9 @@
 candidate is solved once to capture its graphs and timed on a second solve;
 the smoother is chosen under block Jacobi first, then the block combination
 with that smoother; non-converging candidates never win; results are cached
-per shape and precision and round-trip through the JSON cache file."""
+per shape and precision and round-trip through the JSON cache file; the
+setup-time options (coarse_max, mf_zchunk) are searched last, each on a
+handle built for it."""
 import json
 import os
 import sys
@@ -10,7 +12,8 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
-from paper_2602_07225_gb300.batch import BJ, CANDIDATES, COMBOS, Autotuner  # noqa: E402
+from paper_2602_07225_gb300.batch import (BJ, CANDIDATES, COMBOS, SETUP_CANDIDATES, SETUP_DEFAULT,  # noqa: E402
+                                          Autotuner)
 
 
 class _Params:
@@ -73,7 +76,7 @@ def test_failed_candidates_never_win_and_cache_round_trip(tmp_path):
     path = str(tmp_path / "tune.json")
     tuner = Autotuner(path)
     got = tuner.get(fs, _case(), None, None)
-    assert got[:2] != (1, 4.0) and got[2:] == BJ
+    assert got[:2] != (1, 4.0) and got[2:4] == BJ and got[4:] == SETUP_DEFAULT
     # cached: no further solves for the same shape and precision
     n = len(fs.calls)
     assert tuner.get(fs, _case(), None, None) == got and len(fs.calls) == n
@@ -82,3 +85,48 @@ def test_failed_candidates_never_win_and_cache_round_trip(tmp_path):
     key = Autotuner.key(fs, _case())
     assert list(again.cache[key][:3]) == list(got[:3]) and list(again.cache[key][3]) == list(got[3])
     json.load(open(path))
+
+
+def test_setup_stage_builds_each_candidate_and_keeps_the_runtime_choice(tmp_path):
+    ms = {s + BJ: 9.0 for s in CANDIDATES}
+    ms[(3, 10.0) + BJ] = 5.0
+    fs = FakeSolver(ms)
+    built, closed = [], []
+
+    class Built(FakeSolver):
+        def close(self):
+            closed.append(self.setup)
+
+    speed = {c: 7.0 for c in SETUP_CANDIDATES}
+    speed[(512, 8)] = 3.0
+    speed[(32, 8)] = 2.0
+    fail = (32, 8)                                 # the fastest does not converge: never chosen
+
+    def build(cm, zc):
+        b = Built({}, fail={(3, 10.0) + BJ} if (cm, zc) == fail else ())
+        b.setup = (cm, zc)
+        b.ms = {(3, 10.0) + BJ: speed[(cm, zc)]}
+        built.append((cm, zc))
+        return b, None
+
+    tuner = Autotuner(str(tmp_path / "t.json"))
+    got = tuner.get(fs, _case(24), None, None, build=build)
+    assert got == (3, 10.0) + BJ + (512, 8)
+    assert built == list(SETUP_CANDIDATES) and closed == built
+
+
+def test_cached_runtime_choice_gains_setup_options(tmp_path):
+    path = str(tmp_path / "old.json")
+    key = [16, 16, 24, 1]
+    json.dump({json.dumps(key): [2, 10.0, 0, [1, 0, 2]]}, open(path, "w"))
+    tuner = Autotuner(path)
+    fs = FakeSolver({})
+    assert tuner.get(fs, _case(), None, None) == (2, 10.0, 0, [1, 0, 2]) + SETUP_DEFAULT
+    assert fs.calls == []                          # no runtime search for a cached shape
+
+    def build(cm, zc):
+        b = FakeSolver({(2, 10.0, 0, (1, 0, 2)): 1.0 if (cm, zc) == (128, 16) else 4.0})
+        return b, None
+
+    got = tuner.get(fs, _case(), None, None, build=build)
+    assert got[:4] == (2, 10.0, 0, [1, 0, 2]) and got[4:] == (128, 16) and fs.calls == []
