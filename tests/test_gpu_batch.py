@@ -26,16 +26,22 @@ def _cells():
             make_gyroid_cell(16, 0.25, 3, 12, 7), make_gyroid_cell(16, -0.05, 1, 17, 8)]
 
 
-def test_batch_matches_oracle_and_sequential():
+@pytest.mark.parametrize("tune_setup", [False, True])
+def test_batch_matches_oracle_and_sequential(tune_setup):
     from paper_2602_07225_gb300 import BatchSolver
+    from paper_2602_07225_gb300.batch import SETUP_CANDIDATES, SETUP_DEFAULT
     from oracle.fe import Disc
     from oracle.krylov import LinearSolve, per_field_error
     cells = _cells()
-    bs = BatchSolver(cells, threads=4, precision=1, rtol=1e-11, maxit=800)
+    bs = BatchSolver(cells, threads=4, precision=1, rtol=1e-11, maxit=800, tune_setup=tune_setup)
     assert len(bs.tuned) == len({c["gyroid"]["n"] for c in cells})   # one tuning per grid shape
-    for deg, ratio, combine, order in bs.tuned.values():
+    for deg, ratio, combine, order, cm, zc in bs.tuned.values():
         assert deg in (1, 2, 3, 4) and ratio > 1
         assert combine in (0, 1) and sorted(order) == [0, 1, 2]
+        assert (cm, zc) in SETUP_CANDIDATES if tune_setup else (cm, zc) == SETUP_DEFAULT
+    for s, c in zip(bs.solvers, cells):            # every handle built with its shape's setup options
+        cm, zc = bs.tuned[(c["mesh"]["nx"], c["mesh"]["ny"], c["mesh"]["nz"], 1)][4:]
+        assert int(s.params.coarse_max) == cm and (int(s.params.mf_zchunk) or 8) == zc
     lock = bs.solve_all("lockstep")
     thr = bs.solve_all("threads")
     seq = bs.solve_all("sequential")
