@@ -98,7 +98,7 @@ def test_setup_stage_builds_each_candidate_and_keeps_the_runtime_choice(tmp_path
             closed.append(self.setup)
 
     speed = {c: 7.0 for c in SETUP_CANDIDATES}
-    speed[(512, 8)] = 3.0
+    speed[(64, 8)] = 3.0
     speed[(32, 8)] = 2.0
     fail = (32, 8)                                 # the fastest does not converge: never chosen
 
@@ -111,7 +111,7 @@ def test_setup_stage_builds_each_candidate_and_keeps_the_runtime_choice(tmp_path
 
     tuner = Autotuner(str(tmp_path / "t.json"))
     got = tuner.get(fs, _case(24), None, None, build=build)
-    assert got == (3, 10.0) + BJ + (512, 8)
+    assert got == (3, 10.0) + BJ + (64, 8)
     assert built == list(SETUP_CANDIDATES) and closed == built
 
 
