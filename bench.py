@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--slab-nx", type=int, default=2048, help="slab2048: elements along the long axis")
     ap.add_argument("--slab-steps", type=int, default=30, help="slab2048: backward-Euler steps")
     ap.add_argument("--slab-fd", type=int, default=6, help="slab2048: directional finite-difference checks")
+    ap.add_argument("--slab-geometry", default="cube", choices=["cube", "paper"],
+                    help="slab2048: the cube's element scale without collector foils, or the paper's jelly roll "
+                         "(1 m x 5 cm, 50/20/50 um layers) with aluminium and copper foils as collector shells")
     return ap.parse_args()
 
 
@@ -757,7 +760,13 @@ def slab_adjoint(args):
     nx = args.slab_nx
     nsteps = args.slab_steps
     tab = max(1, 64 * nx // 2048)
-    case = make_slab_case(nx=nx, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=tab, crate=2.0)
+    if args.slab_geometry == "paper":
+        # the paper's jelly roll: 1 m x 5 cm, 50/20/50 um layers; the foils as thin
+        # shells: aluminium 3.77e7 S/m x 15 um (cathode), copper 5.96e7 S/m x 10 um (anode)
+        geo = dict(h_lat=1.0 / nx, width=0.05, L_layers=(50e-6, 20e-6, 50e-6), shell=(565.5, 596.0))
+    else:
+        geo = {}
+    case = make_slab_case(nx=nx, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=tab, crate=2.0, **geo)
     m, p = case["mesh"], case["params"]
     region = m["region"]
     nz = int(m["nz"])
@@ -812,7 +821,10 @@ def slab_adjoint(args):
     out = {"study": "adjoint_slab", "metric": METRIC, "unit": "gradients/s", "value": 1.0 / t_grad, "n_gpus": 1,
            "higher_is_better": True, "data": "synthetic", "dtype": "f64 outer / f32 preconditioner",
            "config": {"workload": "jelly-roll slab %dx16x48 (20/8/20), N_c=15, tabs on %d columns, 2C, %d BE steps "
-                                  "x 10 s, checkpoints every 5" % (nx, tab, nsteps),
+                                  "x 10 s, checkpoints every 5" % (nx, tab, nsteps)
+                                  + (", the paper's geometry (1 m x 5 cm, 50/20/50 um) with collector foils "
+                                     "(565.5 and 596 S shells)" if args.slab_geometry == "paper" else
+                                     ", 0.78 um lateral elements, 100/25/100 um layers, no foils"),
                       "unknowns": int(3 * (nx + 1) * 17 * 49 + 15 * (nx + 1) * 17 * 42)},
            "V_final": V0, "forward_s": t_fwd, "gradient_s": t_grad, "fd_checks": checks,
            "max_rel_err": max(c["rel_err"] for c in checks) if checks else None}

@@ -218,7 +218,7 @@ def _hetero_fields(nx, ny, nz, hx, hy, hz, region, rng, corr=8, mean=0.3, cv=0.2
 
 def make_slab_case(nx=2048, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=64, crate=2.0,
                    h_lat=100e-6 / 128, L_layers=(100e-6, 25e-6, 100e-6), shell=(0.0, 0.0),
-                   state="initial"):
+                   state="initial", width=None):
     """Flattened jelly-roll-like slab: nx x ny elements of h_lat x h_lat
     laterally, anode/separator/cathode layers in z.  The tabs are the
     strips of the first `tab` element columns along x: gamma_p (applied
@@ -228,14 +228,15 @@ def make_slab_case(nx=2048, ny=16, layers=(20, 8, 20), nc=15, seed=1005, tab=64,
     area.  shell = (cathode, anode) collector-foil surface conductances in S
     (0: none); real foils (aluminium 3.77e7 S/m x 15 um = 565 S, copper
     5.96e7 S/m x 10 um = 596 S) are ~1e8 times the bulk conductance of a
-    sub-micron element."""
-    case = make_box_case(nx, ny, layers, (nx * h_lat, ny * h_lat), L_layers, nc, seed, state=state)
+    sub-micron element.  width: the slab's extent along y (default ny h_lat)."""
+    Ly = ny * h_lat if width is None else width
+    case = make_box_case(nx, ny, layers, (nx * h_lat, Ly), L_layers, nc, seed, state=state)
     m, p = case["mesh"], case["params"]
     col = np.arange(nx * ny) % nx
     m["gamma_p"] = (col < tab).astype(np.uint8)
     m["gamma_n"] = (col < tab).astype(np.uint8)
     m["shell_sigma_t_p"], m["shell_sigma_t_n"] = float(shell[0]), float(shell[1])
-    p["i_app"] = crate * theoretical_iapp(nx * h_lat, ny * h_lat, L_layers[0], L_layers[2], 0.6, 0.5,
+    p["i_app"] = crate * theoretical_iapp(nx * h_lat, Ly, L_layers[0], L_layers[2], 0.6, 0.5,
                                           p["cmax_n"], p["cmax_p"], p["F"]) * nx / tab
     return case
 
