@@ -30,11 +30,12 @@
 // Layout of a launch: each block owns a tile of W x H nodes (nominally
 // 15 x 15; the last tile of an axis takes the remainder, at most one more)
 // and marches in z over a chunk of node planes.  Per plane it stages the
-// (W+2) x (H+2) tile of x in shared memory, evaluates the (W+1) x (H+1)
-// elements between that plane and the next (their lower-corner outputs go
-// to this plane, the upper-corner outputs are kept for the next), and
-// updates its nodes.  The phi_s work list covers only the node planes that
-// hold phi_s unknowns.
+// (W+2) x (H+2) tile of x, the element coefficients and the node data in
+// shared memory (asynchronous copies a few planes ahead), evaluates the
+// (W+1) x (H+1) elements between that plane and the next (their
+// lower-corner outputs go to this plane, the upper-corner outputs are kept
+// for the next), and updates its nodes.  The phi_s work list covers only
+// the node planes that hold phi_s unknowns.
 #include <algorithm>
 #include <vector>
 #include "p4d_common.cuh"
@@ -47,6 +48,10 @@ namespace {
 // barrier (only the remainder tiles of an axis, up to 16 nodes wide, do).
 constexpr int kTX = 15, kTY = 15;
 constexpr int kMfThreads = 256;
+// planes of asynchronous copies in flight ahead of their use: one keeps the
+// rings small enough for four blocks per SM, which measured faster than
+// deeper rings at three blocks per SM
+constexpr int kMfDepth = 1;
 static_assert((kTX + 3) * (kTY + 3) <= 2 * kMfThreads, "two x entries per thread at most");
 static_assert((kTX + 2) * (kTY + 2) <= 2 * kMfThreads, "two elements per thread at most");
 static_assert((kTX + 1) * (kTY + 1) <= 2 * kMfThreads, "two nodes per thread at most");
@@ -116,15 +121,27 @@ __device__ __forceinline__ void element_apply(T (&v)[8], const T (&lam)[8]) {
       }
 }
 
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid; the
+// source is then not read).
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // MODE 0: Chebyshev step on a nonzero x: d = c0 D^-1 (b - A x) (step 0) or
 // d = ca d + cb D^-1 (b - A x), then x_out = x + d.  MODE 1: r = b - A x.
 //
 // Tiles are at most (kTX + 1) x (kTY + 1) nodes, so every thread owns at
-// most two x loads, two elements and two nodes of a plane (slot r: index
-// tid + 256 r; the nominal tile: one element and at most one node).  The global loads of the next plane (x of plane k + 2, the
-// element coefficients of element plane k + 1, the node data of plane
-// k + 1) are issued into registers one iteration ahead, so their latency
-// overlaps the current plane's element and node work.
+// most two x entries, two elements and two nodes of a plane (slot r: index
+// tid + 256 r).  The global data of the march (x planes, the element
+// coefficients, the node data b, diag, 1/diag, d) reach shared memory by
+// asynchronous copies kMfDepth planes ahead of their use, in rings
+// counted from the first step ks = k0 - 2 of the march (plane j in slot
+// (j - ks) mod the ring size): the loads in flight hold no registers, and
+// the x tile is not copied through registers into shared memory.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,13 +155,18 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   const int k0 = it.z, k1 = it.w;
   const int XW = W + 2, XH = H + 2, EW = W + 1, EH = H + 1;
   const int XN = XW * XH, EN = EW * EH, NN = W * H;
-  // shared-memory layout with the largest tile's strides (compile-time
-  // constants, so that every shared access is a base plus an immediate):
-  // x planes [4][XP] with rows of XS; element planes' lower-corner outputs
-  // [2][4][EP] and upper-corner outputs [3][4][EP] with rows of ES
+  // shared memory, laid out with the largest tile's strides (compile-time
+  // constants): rings of x planes [RX][XP] (rows of XS), element
+  // coefficients [RC][2][EP] (rows of ES), node data [RN][4][NP] (rows of
+  // NW), then the element planes' lower-corner outputs [2][4][EP] and
+  // upper-corner outputs [3][4][EP]
   constexpr int XS = kTX + 3, XP = XS * (kTY + 3), ES = kTX + 2, EP = ES * (kTY + 2);
+  constexpr int NW = kTX + 1, NP = NW * (kTY + 1);
+  constexpr int DP = kMfDepth, RX = DP + 4, RC = DP + 2, RN = DP + 2;
   T* xs = reinterpret_cast<T*>(smem_raw);
-  T* Lb = xs + 4 * XP;
+  T* cs = xs + RX * XP;
+  T* ns = cs + RC * 2 * EP;
+  T* Lb = ns + RN * 4 * NP;
   T* Ub = Lb + 8 * EP;
   // the block's field pointers, selected once (not per access)
   const T* __restrict__ Fx = fsel(a, f).x;
@@ -170,9 +192,9 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   // elements and nodes), computed once for the whole z march
   int xoff[2], xsm[2];       // x entry: in-plane offset (-1 outside the grid), tile index (-1: none)
   int eoff[2], ebase[2];     // element: in-plane offset (-1 outside), x-tile index of its lower-left node
-  int eq[2];                 // element slot (-1: none)
+  int eq[2];                 // element tile index (-1: none)
   T ex[2][3], ey[2][3];      // element: x factors (2/h, h/2, h/6)/8 and y factors (2/h, h/2, h/6)
-  int noff[2], nq[2], nsm[2];
+  int noff[2], nq[2], nsm[2], nid[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int q = tid + r * kMfThreads;
@@ -206,11 +228,13 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
     noff[r] = -1;
     nq[r] = 0;
     nsm[r] = 0;
+    nid[r] = 0;
     if (q < NN) {
       const int jj = q / W, ii = q - jj * W;
       noff[r] = (i0 + ii) + a.nnx * (j0 + jj);
       nq[r] = ii + ES * jj;
       nsm[r] = (ii + 1) + XS * (jj + 1);
+      nid[r] = ii + NW * jj;
     }
   }
   // Chebyshev coefficients of the block's hierarchies (phi_s: both electrodes)
@@ -225,57 +249,71 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
     }
   }
 
-  T xr[2];                         // prefetched x of one plane
-  T kr[2], mr[2];                  // prefetched element coefficients of one element plane
-  T br[2], dr[2], ir[2], sr[2];    // prefetched node data (b, d, 1/diag, variable diagonal)
-  int lr[2];
-  auto fetch_x = [&](int k) {
-    const bool kin = k >= 0 && k < a.nnz;
-    const int base = k * sxy;
-    xr[0] = (kin && xoff[0] >= 0) ? Fx[xoff[0] + base] : (T)0;
-    if (wx2) xr[1] = (kin && xoff[1] >= 0) ? Fx[xoff[1] + base] : (T)0;
+  const int ks = k0 - 2;   // first step of the march (element plane k0 - 1)
+  // asynchronous copies of x plane j (planes outside the grid: zeros)
+  auto issue_x = [&](int j) {
+    if (j > k1 + 1) return;   // beyond the last element plane's upper x plane
+    T* dst = xs + ((j - ks) % RX) * XP;
+    const bool kin = j >= 0 && j < a.nnz;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !wx2) break;
+      if (xsm[r] < 0) continue;
+      const bool on = kin && xoff[r] >= 0;
+      cp_async4(dst + xsm[r], on ? Fx + (xoff[r] + j * sxy) : Fx, on);
+    }
   };
-  auto store_x = [&](int slot) {
-    T* dst = xs + slot * XP;
-    if (xsm[0] >= 0) dst[xsm[0]] = xr[0];
-    if (wx2 && xsm[1] >= 0) dst[xsm[1]] = xr[1];
-  };
-  auto fetch_coef = [&](int ke) {
+  // element coefficients of element plane ke (outside the grid: zeros)
+  auto issue_coef = [&](int ke) {
+    if (ke > k1) return;
+    T* dst = cs + ((ke - ks) % RC) * 2 * EP;
     const bool kin = ke >= 0 && ke < a.nz;
-    const int base = ke * sexy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (r == 1 && !we2) break;
+      if (eq[r] < 0) continue;
       const bool on = kin && eoff[r] >= 0;
-      kr[r] = on ? Fkc[eoff[r] + base] : (T)0;
-      mr[r] = (on && mass) ? Fmc[eoff[r] + base] : (T)0;
+      const int e = eoff[r] + ke * sexy;
+      cp_async4(dst + eq[r], on ? Fkc + e : Fkc, on);
+      if (mass) cp_async4(dst + EP + eq[r], on ? Fmc + e : Fmc, on);
     }
   };
-  auto fetch_nodes = [&](int k) {
-    const bool kin = k < k1;
-    const int base = k * sxy;
+  // node data of node plane k (only the march's planes [k0, k1))
+  auto issue_nodes = [&](int k) {
+    if (k < k0 || k >= k1) return;
+    T* dst = ns + ((k - ks) % RN) * 4 * NP;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (r == 1 && !wn2) break;
-      const bool on = kin && noff[r] >= 0;
-      const int n = noff[r] + base;
-      lr[r] = (on && f == 0) ? (int)a.label[n] : 0;
-      br[r] = on ? Fb[n] : (T)0;
-      sr[r] = on ? Fsvs[n] : (T)0;
+      if (noff[r] < 0) continue;
+      const int n = noff[r] + k * sxy;
+      cp_async4(dst + nid[r], Fb + n, true);
+      cp_async4(dst + NP + nid[r], Fsvs + n, true);
       if (MODE == 0) {
-        ir[r] = on ? Fdinv[n] : (T)0;
-        dr[r] = (on && a.step != 0) ? Fd[n] : (T)0;
+        cp_async4(dst + 2 * NP + nid[r], Fdinv + n, true);
+        cp_async4(dst + 3 * NP + nid[r], a.step != 0 ? Fd + n : Fd, a.step != 0);
       }
     }
   };
+  int lr[2] = {0, 0};   // labels of the next node plane (phi_s), in registers
+  auto fetch_labels = [&](int k) {
+    if (f != 0) return;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !wn2) break;
+      lr[r] = (k < k1 && noff[r] >= 0) ? (int)a.label[noff[r] + k * sxy] : 0;
+    }
+  };
 
-  // element plane ke between x planes ke and ke + 1 of the ring,
-  // coefficients in kr / mr: lower corners to L[ke & 1], upper to U[ke % 3]
+  // element plane ke between x planes ke and ke + 1: lower corners to
+  // L[(ke - ks) & 1], upper corners to U[(ke - ks) % 3]
   auto element_plane = [&](int ke) {
-    const T* xl = xs + ((ke + 4) & 3) * XP;
-    const T* xu = xs + ((ke + 5) & 3) * XP;
-    T* lo = Lb + ((ke + 2) & 1) * 4 * EP;
-    T* up = Ub + ((ke + 3) % 3) * 4 * EP;
+    const int rx = ke - ks;
+    const T* xl = xs + (rx % RX) * XP;
+    const T* xu = xs + ((rx + 1) % RX) * XP;
+    const T* cf = cs + (rx % RC) * 2 * EP;
+    T* lo = Lb + (rx & 1) * 4 * EP;
+    T* up = Ub + (rx % 3) * 4 * EP;
     T Ksz = 0, Msz = 0, Mdz = 0;
     if (ke >= 0 && ke < a.nz) {
       Ksz = a.gz[ke];
@@ -287,7 +325,7 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       if (r == 1 && !we2) break;
       const int q = eq[r];
       if (q < 0) continue;
-      const T kc = kr[r], mc = mr[r];
+      const T kc = cf[q], mc = mass ? cf[EP + q] : (T)0;
       T v[8];
       const int base = ebase[r];
       v[0] = xl[base];
@@ -324,39 +362,40 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
     }
   };
 
-  // Software pipeline, one barrier per node plane p: x plane p + 3 goes to
-  // the ring, element plane p + 1 is evaluated and node plane p updated
-  // from element planes p (lower corners) and p - 1 (upper corners), with
-  // the loads for the next plane in flight.  Within a phase the writes
-  // (x slot (p+3) & 3, L[(p+1) & 1], U[(p+1) % 3]) and the reads (x slots of
-  // planes p .. p+2, L[p & 1], U[(p-1) % 3]) never overlap.
-  auto store_plane = [&](int k) { store_x((k + 4) & 3); };
-  fetch_x(k0 - 1);
-  store_plane(k0 - 1);
-  fetch_x(k0);
-  store_plane(k0);
-  fetch_x(k0 + 1);
-  store_plane(k0 + 1);
-  fetch_x(k0 + 2);
-  store_plane(k0 + 2);
-  fetch_coef(k0 - 1);
-  __syncthreads();
-  element_plane(k0 - 1);   // zero outputs when k0 = 0; its lower corners are never read
-  fetch_coef(k0);
-  element_plane(k0);
-  fetch_coef(k0 + 1);
-  fetch_x(k0 + 3);
-  fetch_nodes(k0);
-  __syncthreads();
-
-  for (int k = k0; k < k1; ++k) {
-    store_plane(k + 3);         // the slot of plane k - 1, no longer read
-    fetch_x(k + 4);
-    element_plane(k + 1);       // zero outputs beyond the last element plane
-    fetch_coef(k + 2);
-    const T* xk = xs + ((k + 4) & 3) * XP;
-    const T* lo = Lb + ((k + 2) & 1) * 4 * EP;
-    const T* upPrev = Ub + ((k + 2) % 3) * 4 * EP;
+  // Step k of the march (k = ks .. k1 - 1): issue the copies of x plane
+  // k + 2 + DP, coefficients k + 1 + DP and node data k + DP; wait for the
+  // copies issued DP steps earlier; one barrier; evaluate element plane
+  // k + 1 (x planes k + 1, k + 2) and, for k >= k0, update node plane k
+  // from element planes k (lower corners) and k - 1 (upper corners).
+  // Between two barriers the slots written (x plane k + 1 + DP + 2 of a
+  // thread already in the next step: the slot of plane k - 1; L and U of
+  // element plane k + 1; the coefficient and node slots of planes k and
+  // k - 1) and the slots read (x planes k .. k + 2, coefficients k + 1,
+  // node data k, L of element plane k, U of element plane k - 1) differ.
+  issue_x(ks + 1);
+#pragma unroll
+  for (int g = 0; g < DP; ++g) {
+    const int k = ks - DP + g;
+    issue_x(k + 2 + DP);
+    issue_coef(k + 1 + DP);
+    issue_nodes(k + DP);
+    cp_async_commit();
+  }
+  fetch_labels(k0);
+  for (int k = ks; k < k1; ++k) {
+    issue_x(k + 2 + DP);
+    issue_coef(k + 1 + DP);
+    issue_nodes(k + DP);
+    cp_async_commit();
+    cp_async_wait<DP>();
+    __syncthreads();
+    element_plane(k + 1);   // zero outputs when k + 1 is outside the element planes
+    if (k < k0) continue;
+    const int rk = k - ks;
+    const T* xk = xs + (rk % RX) * XP;
+    const T* nd = ns + (rk % RN) * 4 * NP;
+    const T* lo = Lb + (rk & 1) * 4 * EP;
+    const T* upPrev = Ub + ((rk + 2) % 3) * 4 * EP;
     const int base = k * sxy;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -367,24 +406,32 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
         if (!(lr[r] & kLabActive)) continue;
         hsel = (lr[r] & kLabAnode) ? 0 : 1;
       }
-      const int e = nq[r];
+      const int e = nq[r], id = nid[r];
       const T xn = xk[nsm[r]];
-      T ax = sr[r] * xn;
+      T ax = nd[NP + id] * xn;
       ax += (lo[3 * EP + e] + upPrev[3 * EP + e]) + (lo[2 * EP + e + 1] + upPrev[2 * EP + e + 1]);
       ax += (lo[1 * EP + e + ES] + upPrev[1 * EP + e + ES]) + (lo[e + ES + 1] + upPrev[e + ES + 1]);
-      const T res = br[r] - ax;
+      const T res = nd[id] - ax;
       const int n = noff[r] + base;
       if (MODE == 1) {
         Fr[n] = res;
       } else {
-        const T dn = (hsel ? cA[1] : cA[0]) * dr[r] + (hsel ? cB[1] : cB[0]) * (ir[r] * res);
+        const T dn = (hsel ? cA[1] : cA[0]) * nd[3 * NP + id] + (hsel ? cB[1] : cB[0]) * (nd[2 * NP + id] * res);
         Fd[n] = dn;
         Fxo[n] = xn + dn;
       }
     }
-    fetch_nodes(k + 1);
-    __syncthreads();
+    fetch_labels(k + 1);
   }
+  cp_async_wait<0>();   // no copy into this block's shared memory outlives it
+}
+
+// Shared memory of k_mf_level0 (FP32): the x, coefficient and node-data
+// rings and the element planes' corner outputs.
+constexpr size_t mf_smem_bytes() {
+  return sizeof(float) * ((size_t)(kMfDepth + 4) * (kTX + 3) * (kTY + 3) +
+                          (size_t)(kMfDepth + 2) * 2 * (kTX + 2) * (kTY + 2) +
+                          (size_t)(kMfDepth + 2) * 4 * (kTX + 1) * (kTY + 1) + (size_t)20 * (kTX + 2) * (kTY + 2));
 }
 
 template <typename T>
@@ -488,16 +535,13 @@ p4d_status mf_setup(p4d_ctx* c) {
   if (!items.empty()) P4D_TRY(cudaMemcpy(d, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   c->mf_items = d;
   // the kernel lays shared memory out with the largest tile's strides
-  const size_t ts = sizeof(float);
-  const size_t xn = (size_t)(kTX + 3) * (kTY + 3), en = (size_t)(kTX + 2) * (kTY + 2);
-  c->mf_smem = ts * (4 * xn + 20 * en);
+  c->mf_smem = mf_smem_bytes();
   if (mw > kTX + 1 || mh > kTY + 1 || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
   // The kernels' shared-memory limit is a process-wide attribute shared by
   // every handle: set it to the largest tile any grid can have (64 x 16
   // nodes), never to this handle's size, which would fail the launches of
   // larger handles set up before.
-  const size_t smax = sizeof(float) * (4 * (kTX + 3) * (kTY + 3) + 20 * (kTX + 2) * (kTY + 2));
-  if (c->mf_smem > smax) return P4D_ERR_INVALID_ARG;   // cannot happen: tiles are at most (kTX+1) x (kTY+1) nodes
+  const size_t smax = mf_smem_bytes();
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   return mf_setup_t<float>(c);
