@@ -53,6 +53,7 @@ WORKLOAD_DESC = {"cube128": "cube128: Q1 hex 128x128x96 (anode/sep/cathode 40/16
 CUBE128_DOF = 3 * 129 * 129 * 97 + 20 * 82 * 129 * 129
 
 
+COMBINE_DESC = {"bj": "block Jacobi", "bgs": "block Gauss-Seidel in the order phi_e, phi_s, c_e"}
 CGS_DESC = {0: "classical Gram-Schmidt without refinement", 1: "classical Gram-Schmidt, second pass when needed",
             2: "classical Gram-Schmidt twice"}
 
@@ -69,6 +70,8 @@ def parse():
     ap.add_argument("--laws", default="linear", choices=["linear", "paper"],
                     help="material laws: linear OCP and constant transport (the workload definition), or the "
                          "paper's OCP curves and kappa(c_e), D_e(c_e)")
+    ap.add_argument("--combine", default="bj", choices=["bj", "bgs"],
+                    help="block Jacobi, or block Gauss-Seidel in the paper's order (phi_e, phi_s, c_e; c_s eliminated)")
     ap.add_argument("--cgs-refine", type=int, default=0, choices=[0, 1, 2],
                     help="second Gram-Schmidt pass: 0 never (the paper's GMRES setting), 1 when needed, 2 always")
     ap.add_argument("--slab-nx", type=int, default=2048, help="slab2048: elements along the long axis")
@@ -231,8 +234,8 @@ def gpu_leg(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case = make_workload(args.workload, rank, state="initial")
-    opts = dict(mode=1, combine=0, rtol=1e-8, restart=30, maxit=600, cheb_degree=CHEB[0], cheb_ratio=CHEB[1],
-                cgs_refine=args.cgs_refine)
+    opts = dict(mode=1, combine=0 if args.combine == "bj" else 1, order=(1, 0, 2), rtol=1e-8, restart=30, maxit=600,
+                cheb_degree=CHEB[0], cheb_ratio=CHEB[1], cgs_refine=args.cgs_refine)
     if args.laws == "paper":
         opts.update(ocp_model=1, transport_model=1)
     s = P4DSolver(case, device=dev, precision=1, **opts)
@@ -422,7 +425,7 @@ def roofline_jvp(s, st, dev):
             "gbs": bytes_ / (ms * 1e-3) / 1e9}
 
 
-def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0):
+def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0, combine="bj"):
     """The oracle's plain Newton method with block-preconditioned FGMRES
     linear solves (same V(2,2) cycle, rtol 1e-8) on a bounded sample of the
     workload: the first backward-Euler step from rest of a 16x16 lateral
@@ -453,7 +456,8 @@ def cpu_oracle_leg(full_dof, sample_lat=16, seconds_hint=30.0):
     ok.LinearSolve = Counting
     try:
         while True:
-            st, _ = time_step(d, st, rtol=NEWTON_RTOL, linear="fgmres", degree=CHEB[0], ratio=CHEB[1])
+            st, _ = time_step(d, st, rtol=NEWTON_RTOL, linear="fgmres", degree=CHEB[0], ratio=CHEB[1],
+                              combine="additive" if combine == "bj" else "multiplicative", order=(1, 0, 2))
             steps += 1
             if time.perf_counter() - t0 > seconds_hint * 0.5 or steps >= 2:
                 break
@@ -897,7 +901,7 @@ def main():
     if not args.no_cpu and world == 1:
         try:
             cores = os.cpu_count()
-            c = cpu_oracle_leg(r["ndof"])
+            c = cpu_oracle_leg(r["ndof"], combine=args.combine)
             cpu = {"value": c["scaled_solves_per_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
                    "sample": "oracle Newton with FGMRES linear solves (BJ, " + CYCLE + ", FP64) for %d backward-"
                              "Euler step(s) from rest of a 16x16x96 column block of the cube128 workload "
@@ -926,7 +930,8 @@ def main():
         "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload) +
                                ", 1C discharge from rest (theta_n 0.8, theta_p 0.6, c_e 1000), "
                                "one step = one backward-Euler step of 10 s by Newton (scaled residual 1e-8), "
-                               "REDUCED Schur mode, block Jacobi, " + CYCLE + ", FGMRES(30) rtol 1e-8, "
+                               "REDUCED Schur mode, " + COMBINE_DESC[args.combine] + ", " + CYCLE
+                               + ", FGMRES(30) rtol 1e-8, "
                                + CGS_DESC[args.cgs_refine]
                                + (", the paper's OCP curves and kappa(c_e), D_e(c_e)" if args.laws == "paper" else ""),
                    "time_steps": args.steps, "unknowns": r["ndof"],
@@ -980,7 +985,7 @@ def reference_main(args):
     vals = []
     its = []
     for _ in range(max(1, args.steps)):
-        c = cpu_oracle_leg(CUBE128_DOF, seconds_hint=10.0)
+        c = cpu_oracle_leg(CUBE128_DOF, seconds_hint=10.0, combine=args.combine)
         vals.append(c["scaled_solves_per_s"])
         its.append(c["iters_per_solve"])
         if time.perf_counter() - t0 > 150:
