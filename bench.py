@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--laws", default="linear", choices=["linear", "paper"],
                     help="material laws: linear OCP and constant transport (the workload definition), or the "
                          "paper's OCP curves and kappa(c_e), D_e(c_e)")
+    ap.add_argument("--stepwise", action="store_true",
+                    help="launch every solve kernel by kernel instead of through CUDA graphs (the same work; for "
+                         "profilers that cannot see kernels inside conditional graph nodes)")
     ap.add_argument("--combine", default="bj", choices=["bj", "bgs"],
                     help="block Jacobi, or block Gauss-Seidel in the paper's order (phi_e, phi_s, c_e; c_s eliminated)")
     ap.add_argument("--cgs-refine", type=int, default=0, choices=[0, 1, 2],
@@ -235,7 +238,7 @@ def gpu_leg(args, rank, world, local):
     dev = torch.device("cuda", local)
     case = make_workload(args.workload, rank, state="initial")
     opts = dict(mode=1, combine=0 if args.combine == "bj" else 1, order=(1, 0, 2), rtol=1e-8, restart=30, maxit=600,
-                cheb_degree=CHEB[0], cheb_ratio=CHEB[1], cgs_refine=args.cgs_refine)
+                cheb_degree=CHEB[0], cheb_ratio=CHEB[1], cgs_refine=args.cgs_refine, profile=int(args.stepwise))
     if args.laws == "paper":
         opts.update(ocp_model=1, transport_model=1)
     s = P4DSolver(case, device=dev, precision=1, **opts)
