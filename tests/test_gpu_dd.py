@@ -3,9 +3,11 @@ slabs, one handle per slab on one stream, ghost planes exchanged before
 every operator application and every inner product reduced over the slabs.
 
 * The decomposed JVP is the cell's JVP on every owned row.
-* The decomposed FGMRES (block Jacobi across the slabs) converges to the
-  cell's solution: the oracle's direct solve, within the bounds of the
-  single-cell parity tests.
+* The decomposed FGMRES (restricted additive Schwarz over the slabs, with
+  or without the two-level coarse correction) converges to the cell's
+  solution: the oracle's direct solve, within the bounds of the single-cell
+  parity tests.
+* The coarse space and a wider overlap cut the iteration count.
 * One slab is the single-cell solve."""
 import numpy as np
 import pytest
@@ -127,7 +129,7 @@ def test_dd_fgmres_matches_direct(name, nparts, ghosts, precision, refine, coars
 
 
 def test_coarse_space_cuts_iterations():
-    # the slabs' block Jacobi leaves the long-range potential modes to
+    # the slab preconditioners leave the long-range potential modes to
     # FGMRES; the coarse space (constants and linear-in-z functions per slab
     # and block) carries them
     from paper_2602_07225_gb300 import SlabSolver
