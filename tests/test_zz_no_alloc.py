@@ -55,6 +55,37 @@ def test_noalloc_jvp_matches_jvp_twice(lib, name, transpose):
         assert _field_rel(s, y.cpu().numpy(), y_ref.cpu().numpy()) < 1e-11, call
 
 
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_noalloc_jvp_under_stream_capture(lib, transpose):
+    """The use the entry point exists for: a call captured into a CUDA graph
+    on the handle's stream (after one eager call), the graph replayed on new
+    contents of the captured input buffer."""
+    from paper_2602_07225_gb300 import P4DSolver
+    case = make_case("cube8")
+    cs = torch.cuda.Stream()
+    s = P4DSolver(case, precision=1, stream=cs)
+    with torch.cuda.stream(cs):
+        st = s.state_tensors(case["state"])
+        s.jacobian_update(st)
+        x = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+        y = torch.zeros_like(x)
+        assert lib.p4d_jvp_noalloc(s.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), transpose) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs):
+        rc = lib.p4d_jvp_noalloc(s.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), transpose)
+    assert rc == 0, rc
+    rng = np.random.default_rng(22)
+    for _ in range(2):
+        x.copy_(torch.tensor(rng.standard_normal(s.ndof), device="cuda"))
+        y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        y_ref = s.jvp(x, transpose=bool(transpose))
+        torch.cuda.synchronize()
+        assert _field_rel(s, y.cpu().numpy(), y_ref.cpu().numpy()) < 1e-11
+
+
 def test_noalloc_rejects_too_many_electrode_nodes(lib):
     """cube128 has 1,364,562 electrode nodes > P4D_NOALLOC_MAX_NELEC = 2^20."""
     from paper_2602_07225_gb300 import P4DSolver
