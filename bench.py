@@ -344,8 +344,7 @@ def measure_fp64(s):
 
 # Algorithmic bytes of one level-0 Chebyshev step per node and field: the
 # method's minimum for a matrix-free fine-level smoothing step (read x, b,
-# 1/diag and d, write d and x_out: 6 x 4 B of FP32 vectors), the per-unit
-# figure of the survey's measurement plan.
+# 1/diag and d, write d and x_out: 6 x 4 B of FP32 vectors).
 ALG_BYTES_SMOOTH0 = 24
 # Bytes the matrix-free level-0 step reads and writes per node and field:
 # x, b, 1/diag, d and the variable diagonal in, d and x_out out (7 x 4 B),
@@ -958,7 +957,7 @@ def main():
                      "traffic_source": TRAFFIC_SOURCE,
                      "kernel": roof["kernel"], "peak_source": src, "ms_per_launch": roof["ms"],
                      "bytes_per_launch": roof["bytes"],
-                     "bytes_note": "%d B per node and field (the survey's algorithmic bytes of a fine-level "
+                     "bytes_note": "%d B per node and field (the method's algorithmic bytes of a fine-level "
                                    "Chebyshev step: x, b, 1/diag, d in, d and x out) x %d rows"
                                    % (ALG_BYTES_SMOOTH0, roof["rows"]),
                      "kernel_bytes_per_launch": roof["kernel_bytes"],
