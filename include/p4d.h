@@ -304,7 +304,9 @@ int32_t p4d_dd_halo_plan(int32_t nparts, const int32_t* nplanes, int32_t ghosts,
    decomposition before them).  They must share the device, the stream, nx,
    ny and nc.  Allocates the message buffers, one right-hand-side copy and
    two coarse-space work vectors per slab.  Errors: INVALID_ARG (NULL or
-   repeated handle, mismatch, a plan p4d_dd_halo_plan rejects), OOM, CUDA. */
+   repeated handle, mismatch, a plan p4d_dd_halo_plan rejects), OOM, CUDA.
+   The calls below return INVALID_ARG when the slabs' device is not the
+   current device. */
 p4d_status p4d_dd_create(const p4d_handle* parts, int32_t nparts, int32_t ghosts, p4d_dd* out);
 
 /* Coarse space of the two-level preconditioner (default 2): 0 none (block

@@ -394,6 +394,17 @@ p4d_status dd_coarse_correct(p4d_dd_ctx* D, const double* const* v, double* cons
   return P4D_OK;
 }
 
+// The slabs' kernels run on the current device with the slabs' memory:
+// refuse a call made with another device current.
+bool dd_on_device(const p4d_dd_ctx* D) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == D->parts[0]->device;
+}
+
 }  // namespace p4d
 
 using namespace p4d;
@@ -510,6 +521,7 @@ void p4d_dd_destroy(p4d_dd D) {
 
 p4d_status p4d_dd_jacobian_update(p4d_dd D, const p4d_state* states) {
   if (!D || !states) return P4D_ERR_INVALID_ARG;
+  if (!dd_on_device(D)) return P4D_ERR_INVALID_ARG;
   const int P = (int)D->parts.size();
   for (int p = 0; p < P; ++p) P4D_TRYS(p4d_jacobian_update(D->parts[p], &states[p]));
   // the norm floor of the Krylov weights uses ||sqrt(d) u_f|| of the whole
@@ -535,6 +547,7 @@ p4d_status p4d_dd_set_coarse(p4d_dd D, int32_t modes) {
 
 p4d_status p4d_dd_jvp(p4d_dd D, double* const* x, double* const* y) {
   if (!D || !x || !y) return P4D_ERR_INVALID_ARG;
+  if (!dd_on_device(D)) return P4D_ERR_INVALID_ARG;
   const int P = (int)D->parts.size();
   for (int p = 0; p < P; ++p)
     if (!x[p] || !y[p] || x[p] == y[p] || !D->parts[p]->linearized) return P4D_ERR_INVALID_ARG;
@@ -548,6 +561,7 @@ p4d_status p4d_dd_jvp(p4d_dd D, double* const* x, double* const* y) {
 
 p4d_status p4d_dd_fgmres_solve(p4d_dd D, const double* const* b, double* const* x, p4d_info* info) {
   if (!D || !b || !x) return P4D_ERR_INVALID_ARG;
+  if (!dd_on_device(D)) return P4D_ERR_INVALID_ARG;
   const int P = (int)D->parts.size();
   const p4d_params& p0 = D->parts[0]->prm;
   for (int p = 0; p < P; ++p) {
