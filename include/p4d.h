@@ -46,6 +46,8 @@
  *    P4D_ERR_CUDA the handle should be destroyed.
  *  - Threads: a handle is used by one host thread at a time; distinct
  *    handles are independent.
+ *  - Devices: a handle lives on the device current at p4d_setup; a call that
+ *    launches work with another device current returns INVALID_ARG.
  */
 #ifndef P4D_H
 #define P4D_H

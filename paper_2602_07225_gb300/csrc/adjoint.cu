@@ -201,6 +201,7 @@ extern "C" {
 p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce, double* cs,
                             const double* ce_prev, const double* cs_prev, double rtol, int32_t maxit,
                             int32_t* iters_out, p4d_info* info) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !phis || !phie || !ce || !cs || !ce_prev || !cs_prev || maxit < 1 || !(rtol > 0))
     return P4D_ERR_INVALID_ARG;
   const int64_t nn = h->g.nn, ndof = h->ndof, ncs = h->NE * h->nc;
@@ -291,6 +292,7 @@ p4d_status p4d_newton_solve(p4d_handle h, double* phis, double* phie, double* ce
 }
 
 p4d_status p4d_voltage_weights(p4d_handle h, double* q) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !q || !(h->gp_area > 0)) return P4D_ERR_INVALID_ARG;
   ::p4d::count_launch(), k_voltage_weights<<<nblocks(h->ndof), kBlock, 0, h->stream>>>(h->g.nn, h->ndof, h->gpw, 1.0 / h->gp_area, q);
   P4D_TRY(cudaGetLastError());
@@ -298,6 +300,7 @@ p4d_status p4d_voltage_weights(p4d_handle h, double* q) {
 }
 
 p4d_status p4d_terminal_voltage(p4d_handle h, const double* phis, double* v) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !phis || !v || !(h->gp_area > 0)) return P4D_ERR_INVALID_ARG;
   ::p4d::count_launch(), k_terminal_voltage<<<1, 256, 0, h->stream>>>(h->g.nn, h->gpw, phis, 1.0 / h->gp_area, v);
   P4D_TRY(cudaGetLastError());
@@ -306,6 +309,7 @@ p4d_status p4d_terminal_voltage(p4d_handle h, const double* phis, double* v) {
 
 p4d_status p4d_param_grad(p4d_handle h, const p4d_state* st, const double* lam, double* g_sigma, double* g_Ds,
                           double* g_eps) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !st || !lam || !st->phis || !st->phie || !st->ce || !st->cs || !st->ce_prev) return P4D_ERR_INVALID_ARG;
   double* P = h->tloc;   // per electrode node particle term
   if (h->NE > 0)
@@ -324,6 +328,7 @@ p4d_status p4d_param_grad(p4d_handle h, const p4d_state* st, const double* lam, 
 }
 
 p4d_status p4d_adjoint_prev(p4d_handle h, const double* lam, double* out) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !lam || !out || lam == out) return P4D_ERR_INVALID_ARG;
   ::p4d::count_launch(), k_adjoint_prev<<<nblocks(h->g.nn + h->NE * h->nc), kBlock, 0, h->stream>>>(
       h->g, h->NE, h->nc, 1.0 / h->prm.dt, h->Jst + (size_t)3 * 27 * h->g.nn, h->Mj, lam, out);

@@ -416,6 +416,7 @@ p4d_status p4d_electrode_nodes(p4d_handle h, int32_t* out) {
 }
 
 p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !p || !valid_params(p)) return P4D_ERR_INVALID_ARG;
   if (p->precision != h->prm.precision || p->coarse_max != h->prm.coarse_max || p->mf_zchunk != h->prm.mf_zchunk)
     return P4D_ERR_INVALID_ARG;
@@ -437,12 +438,14 @@ p4d_status p4d_set_params(p4d_handle h, const p4d_params* p) {
 }
 
 p4d_status p4d_residual(p4d_handle h, const p4d_state* st, double* r) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !st || !r || !st->phis || !st->phie || !st->ce || !st->cs || !st->ce_prev || !st->cs_prev)
     return P4D_ERR_INVALID_ARG;
   return residual(h, st, r);
 }
 
 p4d_status p4d_jacobian_update(p4d_handle h, const p4d_state* st) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !st || !st->phis || !st->phie || !st->ce || !st->cs || !st->ce_prev || !st->cs_prev)
     return P4D_ERR_INVALID_ARG;
   h->linearized = false;
@@ -455,24 +458,28 @@ p4d_status p4d_jacobian_update(p4d_handle h, const p4d_state* st) {
 }
 
 p4d_status p4d_jvp(p4d_handle h, const double* x, double* y, int transpose) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !x || !y || x == y) return P4D_ERR_INVALID_ARG;
   if (!h->linearized) return P4D_ERR_INVALID_ARG;
   return jvp_full(h, x, y, transpose ? 1 : 0, nullptr, false);
 }
 
 p4d_status p4d_precond_apply(p4d_handle h, const double* r, double* z, int transpose) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !r || !z || r == z) return P4D_ERR_INVALID_ARG;
   if (!h->linearized) return P4D_ERR_INVALID_ARG;
   return precond_full(h, r, z, transpose ? 1 : 0, false);
 }
 
 p4d_status p4d_fgmres_solve(p4d_handle h, const double* b, double* x, p4d_info* info) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !b || !x || b == x) return P4D_ERR_INVALID_ARG;
   if (!h->linearized) return P4D_ERR_INVALID_ARG;
   return fgmres(h, b, x, info, 0);
 }
 
 p4d_status p4d_adjoint_solve(p4d_handle h, const double* g, double* lam, p4d_info* info) {
+  if (h && !::p4d::on_device(h)) return P4D_ERR_INVALID_ARG;
   if (!h || !g || !lam || g == lam) return P4D_ERR_INVALID_ARG;
   if (!h->linearized) return P4D_ERR_INVALID_ARG;
   return fgmres(h, g, lam, info, 1);
@@ -531,6 +538,7 @@ p4d_status batch_solve(p4d_batch B, const double* const* b, double* const* x, p4
   for (size_t i = 0; i < B->cells.size(); ++i) {
     const p4d_ctx* c = B->cells[i];
     if (!b[i] || !x[i] || b[i] == x[i] || !c->linearized || c->prm.profile) return P4D_ERR_INVALID_ARG;
+    if (!::p4d::on_device(c)) return P4D_ERR_INVALID_ARG;
   }
   return fgmres_batched(B, b, x, info, trans);
 }

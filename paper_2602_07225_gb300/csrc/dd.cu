@@ -394,16 +394,8 @@ p4d_status dd_coarse_correct(p4d_dd_ctx* D, const double* const* v, double* cons
   return P4D_OK;
 }
 
-// The slabs' kernels run on the current device with the slabs' memory:
-// refuse a call made with another device current.
-bool dd_on_device(const p4d_dd_ctx* D) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return dev == D->parts[0]->device;
-}
+// The slabs' kernels run on the current device with the slabs' memory.
+bool dd_on_device(const p4d_dd_ctx* D) { return on_device(D->parts[0]); }
 
 }  // namespace p4d
 

@@ -335,6 +335,17 @@ inline p4d_status dalloc_t(p4d_ctx* c, T** p, size_t count) {
 
 inline unsigned nblocks(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
+// A handle's kernels run on the current device with the handle's memory:
+// the calls that launch work refuse another device current.
+inline bool on_device(const p4d_ctx* c) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == c->device;
+}
+
 // Process-wide count of kernel launches issued by the library (every launch
 // site is written "count_launch(), kernel<<<...>>>(...)").
 void count_launch();
