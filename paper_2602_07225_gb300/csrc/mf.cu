@@ -37,6 +37,7 @@
 // for the next), and updates its nodes.  The phi_s work list covers only
 // the node planes that hold phi_s unknowns.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 #include "p4d_common.cuh"
 
@@ -130,6 +131,46 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool val
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The same operator with packed FP32x2 arithmetic (float): the pair m =
+// b + 2c holds the local nodes (a = 0, 1) of one (y, z) position, so the y
+// and z butterfly stages, the eigenvalues and the scaling are lane-wise
+// pair operations and only the x stage is scalar.  Every lane rounds as the
+// scalar operation; a - b is formed as fma(b, -1, a), exact like a
+// subtraction.  P[m], Q[m]: the (y, z) factors of pair m (Q[0] = 0).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void f2_butterfly(float2& a, float2& b) {
+  const float2 t = a;
+  a = __fadd2_rn(t, b);
+  b = f2_sub(t, b);
+}
+__device__ __forceinline__ void element_apply_x2(float (&v)[8], float As, float Ad, float Bs, float Bd,
+                                                 const float (&P)[4], const float (&Q)[4]) {
+  float2 w[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float p = v[2 * m], q = v[2 * m + 1];
+    w[m] = make_float2(p + q, p - q);
+  }
+  f2_butterfly(w[0], w[1]);
+  f2_butterfly(w[2], w[3]);
+  f2_butterfly(w[0], w[2]);
+  f2_butterfly(w[1], w[3]);
+  const float2 A2 = make_float2(As, Ad), B2 = make_float2(Bs, Bd);
+  w[0] = __fmul2_rn(w[0], __fmul2_rn(A2, make_float2(P[0], P[0])));
+#pragma unroll
+  for (int m = 1; m < 4; ++m)
+    w[m] = __fmul2_rn(w[m], __ffma2_rn(B2, make_float2(Q[m], Q[m]), __fmul2_rn(A2, make_float2(P[m], P[m]))));
+  f2_butterfly(w[0], w[2]);
+  f2_butterfly(w[1], w[3]);
+  f2_butterfly(w[0], w[1]);
+  f2_butterfly(w[2], w[3]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[2 * m] = w[m].x + w[m].y;
+    v[2 * m + 1] = w[m].x - w[m].y;
+  }
+}
 
 // MODE 0: Chebyshev step on a nonzero x: d = c0 D^-1 (b - A x) (step 0) or
 // d = ca d + cb D^-1 (b - A x), then x_out = x + d.  MODE 1: r = b - A x.
@@ -344,16 +385,21 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       const T Q1 = Kdy * Msz, Q2 = Msy * Ksz, Q3 = Kdy * Mdz + Mdy * Ksz;
       const T As = Msx * mc, Bs = Msx * kc;            // lambda(s, .) = As P + Bs Q
       const T Ad = kc * Kdx + mc * Mdx, Bd = kc * Mdx; // lambda(d, .) = Ad P + Bd Q
-      T lam[8];
-      lam[0] = As * P0;
-      lam[1] = Ad * P0;
-      lam[2] = As * P1 + Bs * Q1;
-      lam[3] = Ad * P1 + Bd * Q1;
-      lam[4] = As * P2 + Bs * Q2;
-      lam[5] = Ad * P2 + Bd * Q2;
-      lam[6] = As * P3 + Bs * Q3;
-      lam[7] = Ad * P3 + Bd * Q3;
-      element_apply<T>(v, lam);
+      if constexpr (std::is_same<T, float>::value) {
+        const float Pm[4] = {P0, P1, P2, P3}, Qm[4] = {0.f, Q1, Q2, Q3};
+        element_apply_x2(v, As, Ad, Bs, Bd, Pm, Qm);
+      } else {
+        T lam[8];
+        lam[0] = As * P0;
+        lam[1] = Ad * P0;
+        lam[2] = As * P1 + Bs * Q1;
+        lam[3] = Ad * P1 + Bd * Q1;
+        lam[4] = As * P2 + Bs * Q2;
+        lam[5] = Ad * P2 + Bd * Q2;
+        lam[6] = As * P3 + Bs * Q3;
+        lam[7] = Ad * P3 + Bd * Q3;
+        element_apply<T>(v, lam);
+      }
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         lo[l * EP + q] = v[l];
