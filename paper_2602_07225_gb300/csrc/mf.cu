@@ -63,12 +63,11 @@ struct MfField {
   const T* x;      // level-0 iterate (guarded vector)
   T* xo;           // Chebyshev output x + d
   const T* b;
-  const T* dinv;
   T* d;
   T* r;            // residual output
-  const T* svs;    // sc_f * variable node diagonal
-  const T* kc;     // [nelem] sc_f * stiffness coefficient
-  const T* mc;     // [nelem] sc_f * mass coefficient / dt, or nullptr
+  const float2* sd;   // [nn] (sc_f * variable node diagonal, 1/diag)
+  const float2* kcm;  // [nelem] (sc_f * stiffness coefficient, sc_f * mass coefficient / dt or 0)
+  bool mass;          // the field has a mass term
 };
 
 template <typename T>
@@ -127,6 +126,10 @@ __device__ __forceinline__ void element_apply(T (&v)[8], const T (&lam)[8]) {
 __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -198,9 +201,10 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   const int XN = XW * XH, EN = EW * EH, NN = W * H;
   // shared memory, laid out with the largest tile's strides (compile-time
   // constants): rings of x planes [RX][XP] (rows of XS), element
-  // coefficients [RC][2][EP] (rows of ES), node data [RN][4][NP] (rows of
-  // NW), then the element planes' lower-corner outputs [2][4][EP] and
-  // upper-corner outputs [3][4][EP]
+  // coefficient pairs [RC][EP][2] (rows of ES), node data [RN][NP + 2 NP +
+  // NP] (b, the (variable diagonal, 1/diag) pairs, d; rows of NW), then the
+  // element planes' lower-corner outputs [2][4][EP] and upper-corner outputs
+  // [3][4][EP]
   constexpr int XS = kTX + 3, XP = XS * (kTY + 3), ES = kTX + 2, EP = ES * (kTY + 2);
   constexpr int NW = kTX + 1, NP = NW * (kTY + 1);
   constexpr int DP = kMfDepth, RX = DP + 4, RC = DP + 2, RN = DP + 2;
@@ -213,17 +217,15 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   const T* __restrict__ Fx = fsel(a, f).x;
   T* __restrict__ Fxo = fsel(a, f).xo;
   const T* __restrict__ Fb = fsel(a, f).b;
-  const T* __restrict__ Fdinv = fsel(a, f).dinv;
   T* __restrict__ Fd = fsel(a, f).d;
   T* __restrict__ Fr = fsel(a, f).r;
-  const T* __restrict__ Fsvs = fsel(a, f).svs;
-  const T* __restrict__ Fkc = fsel(a, f).kc;
-  const T* __restrict__ Fmc = fsel(a, f).mc;
+  const float2* __restrict__ Fsd = fsel(a, f).sd;
+  const float2* __restrict__ Fkcm = fsel(a, f).kcm;
   const int tid = threadIdx.x;
   // 32-bit offsets: every level-0 array has fewer than 2^31 entries
   const int sxy = a.nnx * a.nny;
   const int sexy = a.nx * a.ny;
-  const bool mass = Fmc != nullptr;
+  const bool mass = fsel(a, f).mass;
 
   // warp-uniform: does any lane of this warp own a second x entry, element
   // or node (most warps do not; they skip the second slot's code)
@@ -315,8 +317,7 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       if (eq[r] < 0) continue;
       const bool on = kin && eoff[r] >= 0;
       const int e = eoff[r] + ke * sexy;
-      cp_async4(dst + eq[r], on ? Fkc + e : Fkc, on);
-      if (mass) cp_async4(dst + EP + eq[r], on ? Fmc + e : Fmc, on);
+      cp_async8(dst + 2 * eq[r], on ? Fkcm + e : Fkcm, on);
     }
   };
   // node data of node plane k (only the march's planes [k0, k1))
@@ -329,9 +330,8 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       if (noff[r] < 0) continue;
       const int n = noff[r] + k * sxy;
       cp_async4(dst + nid[r], Fb + n, true);
-      cp_async4(dst + NP + nid[r], Fsvs + n, true);
+      cp_async8(dst + NP + 2 * nid[r], Fsd + n, true);
       if (MODE == 0) {
-        cp_async4(dst + 2 * NP + nid[r], Fdinv + n, true);
         cp_async4(dst + 3 * NP + nid[r], a.step != 0 ? Fd + n : Fd, a.step != 0);
       }
     }
@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       if (r == 1 && !we2) break;
       const int q = eq[r];
       if (q < 0) continue;
-      const T kc = cf[q], mc = mass ? cf[EP + q] : (T)0;
+      const float2 km = *reinterpret_cast<const float2*>(cf + 2 * q);   // (kc, mc); mc = 0 without mass
+      const T kc = km.x, mc = km.y;
       T v[8];
       const int base = ebase[r];
       v[0] = xl[base];
@@ -454,7 +455,8 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       }
       const int e = nq[r], id = nid[r];
       const T xn = xk[nsm[r]];
-      T ax = nd[NP + id] * xn;
+      const float2 sdv = *reinterpret_cast<const float2*>(nd + NP + 2 * id);   // (variable diagonal, 1/diag)
+      T ax = sdv.x * xn;
       ax += (lo[3 * EP + e] + upPrev[3 * EP + e]) + (lo[2 * EP + e + 1] + upPrev[2 * EP + e + 1]);
       ax += (lo[1 * EP + e + ES] + upPrev[1 * EP + e + ES]) + (lo[e + ES + 1] + upPrev[e + ES + 1]);
       const T res = nd[id] - ax;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       if (MODE == 1) {
         Fr[n] = res;
       } else {
-        const T dn = (hsel ? cA[1] : cA[0]) * nd[3 * NP + id] + (hsel ? cB[1] : cB[0]) * (nd[2 * NP + id] * res);
+        const T dn = (hsel ? cA[1] : cA[0]) * nd[3 * NP + id] + (hsel ? cB[1] : cB[0]) * (sdv.y * res);
         Fd[n] = dn;
         Fxo[n] = xn + dn;
       }
@@ -480,28 +482,29 @@ constexpr size_t mf_smem_bytes() {
                           (size_t)(kMfDepth + 2) * 4 * (kTX + 1) * (kTY + 1) + (size_t)20 * (kTX + 2) * (kTY + 2));
 }
 
-template <typename T>
+// Per field and element the (stiffness, mass) coefficient pair; only c_e
+// has a mass term.
 __global__ void k_mf_coef(int64_t nelem, const uint8_t* __restrict__ region, const double* __restrict__ eps,
                           const double* __restrict__ eps_s, const double* __restrict__ sig_e, double brug,
-                          double kappa, double De, double dt, double s0, double s1, double s2, T* __restrict__ out) {
+                          double kappa, double De, double dt, double s0, double s1, double s2,
+                          float2* __restrict__ out) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nelem) return;
   const uint8_t r = region[e];
   const double sig = (r == 0 || r == 2) ? pow(eps_s[e], brug) * sig_e[e] : 0.0;
   const double epb = pow(eps[e], brug);
-  out[e] = (T)(s0 * sig);
-  out[nelem + e] = (T)(s1 * epb * kappa);
-  out[2 * nelem + e] = (T)(s2 * epb * De);
-  out[3 * nelem + e] = (T)(s2 * eps[e] / dt);
+  out[e] = make_float2((float)(s0 * sig), 0.f);
+  out[nelem + e] = make_float2((float)(s1 * epb * kappa), 0.f);
+  out[2 * nelem + e] = make_float2((float)(s2 * epb * De), (float)(s2 * eps[e] / dt));
 }
 
 template <typename T>
 p4d_status mf_setup_t(p4d_ctx* c) {
   const int nx = c->nx, ny = c->ny, nz = c->nz;
   const int64_t nelem = c->nelem;
-  T* coef = nullptr;
-  P4D_TRYS(dalloc_t(c, &coef, (size_t)4 * nelem));
-  ::p4d::count_launch(), k_mf_coef<T><<<nblocks(nelem), kBlock, 0, c->stream>>>(
+  float2* coef = nullptr;
+  P4D_TRYS(dalloc_t(c, &coef, (size_t)3 * nelem));
+  ::p4d::count_launch(), k_mf_coef<<<nblocks(nelem), kBlock, 0, c->stream>>>(
       nelem, c->region, c->eps_e, c->epss_e, c->sig_e, c->prm.brug, c->kappa_fix, c->De_fix, c->prm.dt,
       c->scale_f[0], c->scale_f[1], c->scale_f[2], coef);
   c->mf_coef = coef;
@@ -528,9 +531,9 @@ p4d_status mf_setup_t(p4d_ctx* c) {
   P4D_TRYS(dalloc_t(c, &gd, g.size()));
   P4D_TRY(cudaMemcpy(gd, g.data(), g.size() * sizeof(T), cudaMemcpyHostToDevice));
   c->mf_geo = gd;
-  T* svs = nullptr;
+  float2* svs = nullptr;   // (variable diagonal, 1/diag) pairs, written per linearization
   P4D_TRYS(dalloc_t(c, &svs, (size_t)3 * c->g.nn));
-  P4D_TRY(cudaMemset(svs, 0, sizeof(T) * 3 * c->g.nn));
+  P4D_TRY(cudaMemset(svs, 0, sizeof(float2) * 3 * c->g.nn));
   c->mf_svs = svs;
   return P4D_OK;
 }
@@ -607,17 +610,17 @@ p4d_status mf_launch(p4d_ctx* c, int fmask, int step) {
   a.gx = g; a.gy = g + 3 * c->nx; a.gz = g + 3 * (c->nx + c->ny);
   a.label = c->label;
   a.items = c->mf_items;
-  const T* coef = (const T*)c->mf_coef;
+  const float2* coef = (const float2*)c->mf_coef;
   const int64_t ne = c->nelem, nn = c->g.nn;
   const int hof[3] = {0, 2, 3};
   for (int f = 0; f < 3; ++f) {
     const int h = hof[f];
     MfField<T>& F = a.f[f];
-    F.x = (const T*)L.x[h]; F.xo = (T*)L.x2[h]; F.b = (const T*)L.b[h]; F.dinv = (const T*)L.dinv[h];
+    F.x = (const T*)L.x[h]; F.xo = (T*)L.x2[h]; F.b = (const T*)L.b[h];
     F.d = (T*)L.d[h]; F.r = (T*)L.r[h];
-    F.svs = (const T*)c->mf_svs + f * nn;
-    F.kc = coef + f * ne;
-    F.mc = f == 2 ? coef + 3 * ne : nullptr;
+    F.sd = (const float2*)c->mf_svs + f * nn;
+    F.kcm = coef + f * ne;
+    F.mass = f == 2;
   }
   a.ctab = sizeof(T) == sizeof(double) ? (const T*)c->cheb_dev : (const T*)c->cheb_dev32;
   a.step = step;

@@ -386,7 +386,7 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
                                 const double* __restrict__ Aj, const double* __restrict__ ge,
                                 const double* __restrict__ gc, const double* __restrict__ zeta, double s0,
                                 double s1, double s2, TS* st0, TS* st1, TS* st2, T* di0, T* di1, T* di2,
-                                double* __restrict__ svar, double* lam, T* __restrict__ svs) {
+                                double* __restrict__ svar, double* lam, float2* __restrict__ sd) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nn = g.nn;
   double gl[kNH] = {0.0, 0.0, 0.0, 0.0};
@@ -410,10 +410,12 @@ __global__ void k_level0_update(Grid g, double tau, const double* __restrict__ s
       const double ab = absoff[f * nn + n];
       if (!(diag > 0.0)) diag = fmax(ab, 1e-300);   // keep the smoother finite on a degenerate row
       svar[f * nn + n] = sv[f];
-      if (svs) svs[f * nn + n] = (T)(sc[f] * sv[f]);   // the matrix-free level 0 adds it to the element part
       sts[f][13 * nn + n] = fromd<TS>(sc[f] * s);
       const T dsc = (T)(sc[f] * diag);
       dis[f][n] = (T)1 / dsc;
+      // the matrix-free level 0 adds the variable diagonal to the element part;
+      // it reads it with 1/diag as one pair
+      if (sd) sd[f * nn + n] = make_float2((float)(T)(sc[f] * sv[f]), (float)((T)1 / dsc));
       int h = f + 1;
       if (f == 0) {
         if (!act) continue;
@@ -1438,12 +1440,12 @@ p4d_status mg_update(p4d_ctx* c) {
     ::p4d::count_launch(), k_level0_update<double, double><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (double*)l0.st[0], (double*)l0.st[2], (double*)l0.st[3], (double*)l0.dinv[0], (double*)l0.dinv[2],
-        (double*)l0.dinv[3], svar, l0.lam, (double*)nullptr);
+        (double*)l0.dinv[3], svar, l0.lam, (float2*)nullptr);
   else
     ::p4d::count_launch(), k_level0_update<float, float><<<nblocks(nn), kBlock, 0, c->stream>>>(
         c->g, tau, c->sfix, c->offsum, c->absoff, c->label, c->eidx, c->Aj, c->ge, c->gc, c->zeta, sf[0], sf[1], sf[2],
         (float*)l0.st[0], (float*)l0.st[2], (float*)l0.st[3], (float*)l0.dinv[0], (float*)l0.dinv[2],
-        (float*)l0.dinv[3], svar, l0.lam, (float*)c->mf_svs);
+        (float*)l0.dinv[3], svar, l0.lam, (float2*)c->mf_svs);
   if (prec == 0) P4D_TRYS(mg_update_levels<double>(c, svar, sch));
   else P4D_TRYS(mg_update_levels<float>(c, svar, sch));
   P4D_TRY(cudaGetLastError());

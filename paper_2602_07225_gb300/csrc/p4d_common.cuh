@@ -215,9 +215,10 @@ struct p4d_ctx {
   double* tr_rows = nullptr;           // [2][nn] transport rows of the last residual evaluation
 
   // matrix-free level 0 (mf.cu), compute precision of the preconditioner
-  void* mf_coef = nullptr;             // [4][nelem] sc_0 sigma_eff, sc_1 kappa_eff, sc_2 D_eff, sc_2 eps/dt
+  void* mf_coef = nullptr;             // [3][nelem] float2 (stiffness, mass) per field: sc_0 sigma_eff,
+                                       // sc_1 kappa_eff, (sc_2 D_eff, sc_2 eps/dt)
   void* mf_geo = nullptr;              // per-axis factors (2/h, h/2, h/6) [3][nx] / 8, [3][ny], [3][nz]
-  void* mf_svs = nullptr;              // [3][nn] sc_f * variable node diagonal (per linearization)
+  void* mf_svs = nullptr;              // [3][nn] float2 (sc_f * variable node diagonal, 1/diag) (per linearization)
   int4* mf_items = nullptr;            // work items (field, tile, k0, k1), phi_s then phi_e then c_e
   int mf_off[3] = {0, 0, 0}, mf_cnt[3] = {0, 0, 0};
   int mf_ntx = 0, mf_nty = 0;          // node tiles per axis
