@@ -78,7 +78,28 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(const double* __restrict__
 #pragma unroll
   for (int i = 0; i < P; ++i) acc[i] = 0.0;
   const double* Vg = V + (int64_t)g0 * ldv;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < len; n += stride) {
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // two elements per trip, all their loads issued before the FMAs (twice the
+  // loads in flight); each accumulator still takes n, n + stride, ... in order
+  for (; n + stride < len; n += 2 * stride) {
+    const double w0 = w[n], w1 = w[n + stride];
+    double a0[NG > 0 ? NG : 1], a1[NG > 0 ? NG : 1];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      a0[i] = Vg[(int64_t)i * ldv + n];
+      a1[i] = Vg[(int64_t)i * ldv + n + stride];
+    }
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      acc[i] = fma(a0[i], w0, acc[i]);
+      acc[i] = fma(a1[i], w1, acc[i]);
+    }
+    if (WW) {
+      acc[NG] = fma(w0, w0, acc[NG]);
+      acc[NG] = fma(w1, w1, acc[NG]);
+    }
+  }
+  for (; n < len; n += stride) {
     const double wn = w[n];
 #pragma unroll
     for (int i = 0; i < NG; ++i) acc[i] = fma(Vg[(int64_t)i * ldv + n], wn, acc[i]);
