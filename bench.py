@@ -33,10 +33,10 @@ WORKLOAD = "cube128"
 # the 82 electrode node layers (41 anode + 41 cathode)
 # DRAM bytes per row of one level-0 Chebyshev step (k_mf_level0, all four
 # hierarchies), from an ncu capture of that launch on cube128 itself
-# (dram__bytes_read.sum + dram__bytes_write.sum = 111.01 + 17.48 MB for
+# (dram__bytes_read.sum + dram__bytes_write.sum = 110.79 + 16.98 MB for
 # 4,576,275 rows; a one-pass metric set, so the full-size capture is safe)
-TRAFFIC_PER_ROW = (111.01e6 + 17.48e6) / 4576275
-TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of one level-0 k_mf_level0 launch on cube128 (1.17 x the "
+TRAFFIC_PER_ROW = (110.79e6 + 16.98e6) / 4576275
+TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of one level-0 k_mf_level0 launch on cube128 (1.16 x the "
                   "24 B/row algorithmic bytes), per row x rows")
 FP64_TFLOPS = 1.25    # GB300 nominal non-tensor FP64
 CHEB = (2, 10.0)      # Chebyshev degree (V(d,d) cycles) and eigenvalue ratio, both arms

@@ -44,18 +44,18 @@
 namespace p4d {
 namespace {
 
-// Nominal node tile: 15 x 15 nodes have (15 + 1)^2 = 256 elements, one per
-// thread, so that no warp evaluates a second element before the per-plane
-// barrier (only the remainder tiles of an axis, up to 16 nodes wide, do).
+// Node tile: at most 15 x 15 nodes, which have at most (15 + 1)^2 = 256
+// elements: one element and one node of a plane per thread, so that no
+// warp evaluates a second element before the per-plane barrier.  The last
+// tile of an axis takes the remainder (1 to 15 nodes).
 constexpr int kTX = 15, kTY = 15;
 constexpr int kMfThreads = 256;
 // planes of asynchronous copies in flight ahead of their use: one keeps the
-// rings small enough for four blocks per SM, which measured faster than
-// deeper rings at three blocks per SM
+// rings small (35 KB of shared memory per block) for five blocks per SM,
+// which measured faster than deeper rings at fewer blocks per SM
 constexpr int kMfDepth = 1;
-static_assert((kTX + 3) * (kTY + 3) <= 2 * kMfThreads, "two x entries per thread at most");
-static_assert((kTX + 2) * (kTY + 2) <= 2 * kMfThreads, "two elements per thread at most");
-static_assert((kTX + 1) * (kTY + 1) <= 2 * kMfThreads, "two nodes per thread at most");
+static_assert((kTX + 2) * (kTY + 2) <= 2 * kMfThreads, "two x entries per thread at most");
+static_assert((kTX + 1) * (kTY + 1) <= kMfThreads, "one element per thread");
 constexpr int kDefaultZChunk = 8;      // node planes per block when p4d_params.mf_zchunk = 0
 
 template <typename T>
@@ -178,16 +178,19 @@ __device__ __forceinline__ void element_apply_x2(float (&v)[8], float As, float 
 // MODE 0: Chebyshev step on a nonzero x: d = c0 D^-1 (b - A x) (step 0) or
 // d = ca d + cb D^-1 (b - A x), then x_out = x + d.  MODE 1: r = b - A x.
 //
-// Tiles are at most (kTX + 1) x (kTY + 1) nodes, so every thread owns at
-// most two x entries, two elements and two nodes of a plane (slot r: index
-// tid + 256 r).  The global data of the march (x planes, the element
-// coefficients, the node data b, diag, 1/diag, d) reach shared memory by
-// asynchronous copies kMfDepth planes ahead of their use, in rings
-// counted from the first step ks = k0 - 2 of the march (plane j in slot
-// (j - ks) mod the ring size): the loads in flight hold no registers, and
-// the x tile is not copied through registers into shared memory.
+// Every thread owns at most two x entries, one element and one node of a
+// plane (x entry slot r: index tid + 256 r).  The global data of the march
+// (x planes, the element coefficients, the node data b, diag, 1/diag, d)
+// reach shared memory by asynchronous copies kMfDepth planes ahead of their
+// use, in rings counted from the first step ks = k0 - 2 of the march (plane
+// j in slot (j - ks) mod the ring size): the loads in flight hold no
+// registers, and the x tile is not copied through registers into shared
+// memory.  Each thread evaluates the same element column in every plane, so
+// it keeps the upper-corner outputs of element plane ke - 1 in registers and
+// adds them to the lower-corner outputs of element plane ke: the sums S
+// (per corner, lower + upper) are what node plane ke gathers.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
+__global__ void __launch_bounds__(kMfThreads, 5) k_mf_level0(MfArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 it = a.items[blockIdx.x];
   const int f = it.x;
@@ -203,16 +206,14 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   // constants): rings of x planes [RX][XP] (rows of XS), element
   // coefficient pairs [RC][EP][2] (rows of ES), node data [RN][NP + 2 NP +
   // NP] (b, the (variable diagonal, 1/diag) pairs, d; rows of NW), then the
-  // element planes' lower-corner outputs [2][4][EP] and upper-corner outputs
-  // [3][4][EP]
+  // element planes' corner sums [2][4][EP]
   constexpr int XS = kTX + 3, XP = XS * (kTY + 3), ES = kTX + 2, EP = ES * (kTY + 2);
   constexpr int NW = kTX + 1, NP = NW * (kTY + 1);
-  constexpr int DP = kMfDepth, RX = DP + 4, RC = DP + 2, RN = DP + 2;
+  constexpr unsigned DP = kMfDepth, RX = DP + 4, RC = DP + 2, RN = DP + 2;
   T* xs = reinterpret_cast<T*>(smem_raw);
   T* cs = xs + RX * XP;
   T* ns = cs + RC * 2 * EP;
-  T* Lb = ns + RN * 4 * NP;
-  T* Ub = Lb + 8 * EP;
+  T* Sb = ns + RN * 4 * NP;
   // the block's field pointers, selected once (not per access)
   const T* __restrict__ Fx = fsel(a, f).x;
   T* __restrict__ Fxo = fsel(a, f).xo;
@@ -225,19 +226,12 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   // 32-bit offsets: every level-0 array has fewer than 2^31 entries
   const int sxy = a.nnx * a.nny;
   const int sexy = a.nx * a.ny;
-  const bool mass = fsel(a, f).mass;
 
-  // warp-uniform: does any lane of this warp own a second x entry, element
-  // or node (most warps do not; they skip the second slot's code)
-  const int wb = (tid & ~31) + kMfThreads;
-  const bool wx2 = wb < XN, we2 = wb < EN, wn2 = wb < NN;
-  // per-slot constants (slot r: index tid + 256 r of the plane's x entries,
-  // elements and nodes), computed once for the whole z march
-  int xoff[2], xsm[2];       // x entry: in-plane offset (-1 outside the grid), tile index (-1: none)
-  int eoff[2], ebase[2];     // element: in-plane offset (-1 outside), x-tile index of its lower-left node
-  int eq[2];                 // element tile index (-1: none)
-  T ex[2][3], ey[2][3];      // element: x factors (2/h, h/2, h/6)/8 and y factors (2/h, h/2, h/6)
-  int noff[2], nq[2], nsm[2], nid[2];
+  // warp-uniform: does any lane of this warp own a second x entry (most
+  // warps do not; they skip the second slot's code)
+  const bool wx2 = (tid & ~31) + kMfThreads < XN;
+  // per-thread constants, computed once for the whole z march
+  int xoff[2], xsm[2];   // x entry: in-plane offset (-1 outside the grid), tile index (-1: none)
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int q = tid + r * kMfThreads;
@@ -249,36 +243,35 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
       const int gi = i0 - 1 + ii, gj = j0 - 1 + jj;
       if (gi >= 0 && gi < a.nnx && gj >= 0 && gj < a.nny) xoff[r] = gi + a.nnx * gj;
     }
-    eoff[r] = -1;
-    eq[r] = -1;
-    ebase[r] = 0;
+  }
+  // element: in-plane offset (-1 outside the grid), x-tile index of its
+  // lower-left node, element tile index (-1: none), x factors (2/h, h/2,
+  // h/6)/8 and y factors (2/h, h/2, h/6)
+  int eoff = -1, ebase = 0, eq = -1;
+  T ex[3] = {0, 0, 0}, ey[3] = {0, 0, 0};
+  if (tid < EN) {
+    const int ej = tid / EW, ei = tid - ej * EW;
+    eq = ei + ES * ej;
+    ebase = ei + XS * ej;
+    const int gi = i0 - 1 + ei, gj = j0 - 1 + ej;
+    if (gi >= 0 && gi < a.nx && gj >= 0 && gj < a.ny) {
+      eoff = gi + a.nx * gj;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) ex[r][t] = ey[r][t] = (T)0;
-    if (q < EN) {
-      const int ej = q / EW, ei = q - ej * EW;
-      eq[r] = ei + ES * ej;
-      ebase[r] = ei + XS * ej;
-      const int gi = i0 - 1 + ei, gj = j0 - 1 + ej;
-      if (gi >= 0 && gi < a.nx && gj >= 0 && gj < a.ny) {
-        eoff[r] = gi + a.nx * gj;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          ex[r][t] = a.gx[t * a.nx + gi];
-          ey[r][t] = a.gy[t * a.ny + gj];
-        }
+      for (int t = 0; t < 3; ++t) {
+        ex[t] = a.gx[t * a.nx + gi];
+        ey[t] = a.gy[t * a.ny + gj];
       }
     }
-    noff[r] = -1;
-    nq[r] = 0;
-    nsm[r] = 0;
-    nid[r] = 0;
-    if (q < NN) {
-      const int jj = q / W, ii = q - jj * W;
-      noff[r] = (i0 + ii) + a.nnx * (j0 + jj);
-      nq[r] = ii + ES * jj;
-      nsm[r] = (ii + 1) + XS * (jj + 1);
-      nid[r] = ii + NW * jj;
-    }
+  }
+  // node: in-plane offset (-1: none), element tile index of the element it
+  // is the upper corner of, x-tile index, node-data tile index
+  int noff = -1, nq = 0, nsm = 0, nid = 0;
+  if (tid < NN) {
+    const int jj = tid / W, ii = tid - jj * W;
+    noff = (i0 + ii) + a.nnx * (j0 + jj);
+    nq = ii + ES * jj;
+    nsm = (ii + 1) + XS * (jj + 1);
+    nid = ii + NW * jj;
   }
   // Chebyshev coefficients of the block's hierarchies (phi_s: both electrodes)
   T cA[2], cB[2];
@@ -293,10 +286,13 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   }
 
   const int ks = k0 - 2;   // first step of the march (element plane k0 - 1)
+  // The march evaluates element planes k0 - 1 .. k1 - 1 (node planes k0 ..
+  // k1 - 1 need no other), so it reads x planes k0 - 1 .. k1 and the
+  // coefficients of element planes k0 - 1 .. k1 - 1.
   // asynchronous copies of x plane j (planes outside the grid: zeros)
   auto issue_x = [&](int j) {
-    if (j > k1 + 1) return;   // beyond the last element plane's upper x plane
-    T* dst = xs + ((j - ks) % RX) * XP;
+    if (j > k1) return;
+    T* dst = xs + ((unsigned)(j - ks) % RX) * XP;
     const bool kin = j >= 0 && j < a.nnz;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -308,121 +304,98 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
   };
   // element coefficients of element plane ke (outside the grid: zeros)
   auto issue_coef = [&](int ke) {
-    if (ke > k1) return;
-    T* dst = cs + ((ke - ks) % RC) * 2 * EP;
-    const bool kin = ke >= 0 && ke < a.nz;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r == 1 && !we2) break;
-      if (eq[r] < 0) continue;
-      const bool on = kin && eoff[r] >= 0;
-      const int e = eoff[r] + ke * sexy;
-      cp_async8(dst + 2 * eq[r], on ? Fkcm + e : Fkcm, on);
-    }
+    if (ke >= k1 || eq < 0) return;
+    T* dst = cs + ((unsigned)(ke - ks) % RC) * 2 * EP;
+    const bool on = ke >= 0 && ke < a.nz && eoff >= 0;
+    cp_async8(dst + 2 * eq, on ? Fkcm + (eoff + ke * sexy) : Fkcm, on);
   };
   // node data of node plane k (only the march's planes [k0, k1))
   auto issue_nodes = [&](int k) {
-    if (k < k0 || k >= k1) return;
-    T* dst = ns + ((k - ks) % RN) * 4 * NP;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r == 1 && !wn2) break;
-      if (noff[r] < 0) continue;
-      const int n = noff[r] + k * sxy;
-      cp_async4(dst + nid[r], Fb + n, true);
-      cp_async8(dst + NP + 2 * nid[r], Fsd + n, true);
-      if (MODE == 0) {
-        cp_async4(dst + 3 * NP + nid[r], a.step != 0 ? Fd + n : Fd, a.step != 0);
-      }
-    }
+    if (k < k0 || k >= k1 || noff < 0) return;
+    T* dst = ns + ((unsigned)(k - ks) % RN) * 4 * NP;
+    const int n = noff + k * sxy;
+    cp_async4(dst + nid, Fb + n, true);
+    cp_async8(dst + NP + 2 * nid, Fsd + n, true);
+    if (MODE == 0) cp_async4(dst + 3 * NP + nid, a.step != 0 ? Fd + n : Fd, a.step != 0);
   };
-  int lr[2] = {0, 0};   // labels of the next node plane (phi_s), in registers
+  int lr = 0;   // label of the next node plane (phi_s), in a register
   auto fetch_labels = [&](int k) {
     if (f != 0) return;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r == 1 && !wn2) break;
-      lr[r] = (k < k1 && noff[r] >= 0) ? (int)a.label[noff[r] + k * sxy] : 0;
-    }
+    lr = (k < k1 && noff >= 0) ? (int)a.label[noff + k * sxy] : 0;
   };
 
-  // element plane ke between x planes ke and ke + 1: lower corners to
-  // L[(ke - ks) & 1], upper corners to U[(ke - ks) % 3]
+  // element plane ke between x planes ke and ke + 1: corner sums (lower
+  // corners of ke + upper corners of ke - 1) to S[(ke - ks) & 1]; the upper
+  // corners of ke stay in up[] for element plane ke + 1
+  T up[4] = {0, 0, 0, 0};
   auto element_plane = [&](int ke) {
-    const int rx = ke - ks;
+    if (eq < 0) return;
+    const unsigned rx = (unsigned)(ke - ks);
     const T* xl = xs + (rx % RX) * XP;
     const T* xu = xs + ((rx + 1) % RX) * XP;
     const T* cf = cs + (rx % RC) * 2 * EP;
-    T* lo = Lb + (rx & 1) * 4 * EP;
-    T* up = Ub + (rx % 3) * 4 * EP;
+    T* so = Sb + (rx & 1) * 4 * EP;
     T Ksz = 0, Msz = 0, Mdz = 0;
     if (ke >= 0 && ke < a.nz) {
       Ksz = a.gz[ke];
       Msz = a.gz[a.nz + ke];
       Mdz = a.gz[2 * a.nz + ke];
     }
+    const float2 km = *reinterpret_cast<const float2*>(cf + 2 * eq);   // (kc, mc); mc = 0 without mass
+    const T kc = km.x, mc = km.y;
+    T v[8];
+    v[0] = xl[ebase];
+    v[1] = xl[ebase + 1];
+    v[2] = xl[ebase + XS];
+    v[3] = xl[ebase + XS + 1];
+    v[4] = xu[ebase];
+    v[5] = xu[ebase + 1];
+    v[6] = xu[ebase + XS];
+    v[7] = xu[ebase + XS + 1];
+    // eigenvalues (the x factors carry the 1/8); per (y, z) component
+    // b + 2c: P = My Mz, Q = Ky Mz + My Kz
+    const T Kdx = ex[0], Msx = ex[1], Mdx = ex[2];
+    const T Kdy = ey[0], Msy = ey[1], Mdy = ey[2];
+    const T P0 = Msy * Msz, P1 = Mdy * Msz, P2 = Msy * Mdz, P3 = Mdy * Mdz;
+    const T Q1 = Kdy * Msz, Q2 = Msy * Ksz, Q3 = Kdy * Mdz + Mdy * Ksz;
+    const T As = Msx * mc, Bs = Msx * kc;            // lambda(s, .) = As P + Bs Q
+    const T Ad = kc * Kdx + mc * Mdx, Bd = kc * Mdx; // lambda(d, .) = Ad P + Bd Q
+    if constexpr (std::is_same<T, float>::value) {
+      const float Pm[4] = {P0, P1, P2, P3}, Qm[4] = {0.f, Q1, Q2, Q3};
+      element_apply_x2(v, As, Ad, Bs, Bd, Pm, Qm);
+    } else {
+      T lam[8];
+      lam[0] = As * P0;
+      lam[1] = Ad * P0;
+      lam[2] = As * P1 + Bs * Q1;
+      lam[3] = Ad * P1 + Bd * Q1;
+      lam[4] = As * P2 + Bs * Q2;
+      lam[5] = Ad * P2 + Bd * Q2;
+      lam[6] = As * P3 + Bs * Q3;
+      lam[7] = Ad * P3 + Bd * Q3;
+      element_apply<T>(v, lam);
+    }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r == 1 && !we2) break;
-      const int q = eq[r];
-      if (q < 0) continue;
-      const float2 km = *reinterpret_cast<const float2*>(cf + 2 * q);   // (kc, mc); mc = 0 without mass
-      const T kc = km.x, mc = km.y;
-      T v[8];
-      const int base = ebase[r];
-      v[0] = xl[base];
-      v[1] = xl[base + 1];
-      v[2] = xl[base + XS];
-      v[3] = xl[base + XS + 1];
-      v[4] = xu[base];
-      v[5] = xu[base + 1];
-      v[6] = xu[base + XS];
-      v[7] = xu[base + XS + 1];
-      // eigenvalues (the x factors carry the 1/8); per (y, z) component
-      // b + 2c: P = My Mz, Q = Ky Mz + My Kz
-      const T Kdx = ex[r][0], Msx = ex[r][1], Mdx = ex[r][2];
-      const T Kdy = ey[r][0], Msy = ey[r][1], Mdy = ey[r][2];
-      const T P0 = Msy * Msz, P1 = Mdy * Msz, P2 = Msy * Mdz, P3 = Mdy * Mdz;
-      const T Q1 = Kdy * Msz, Q2 = Msy * Ksz, Q3 = Kdy * Mdz + Mdy * Ksz;
-      const T As = Msx * mc, Bs = Msx * kc;            // lambda(s, .) = As P + Bs Q
-      const T Ad = kc * Kdx + mc * Mdx, Bd = kc * Mdx; // lambda(d, .) = Ad P + Bd Q
-      if constexpr (std::is_same<T, float>::value) {
-        const float Pm[4] = {P0, P1, P2, P3}, Qm[4] = {0.f, Q1, Q2, Q3};
-        element_apply_x2(v, As, Ad, Bs, Bd, Pm, Qm);
-      } else {
-        T lam[8];
-        lam[0] = As * P0;
-        lam[1] = Ad * P0;
-        lam[2] = As * P1 + Bs * Q1;
-        lam[3] = Ad * P1 + Bd * Q1;
-        lam[4] = As * P2 + Bs * Q2;
-        lam[5] = Ad * P2 + Bd * Q2;
-        lam[6] = As * P3 + Bs * Q3;
-        lam[7] = Ad * P3 + Bd * Q3;
-        element_apply<T>(v, lam);
-      }
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        lo[l * EP + q] = v[l];
-        up[l * EP + q] = v[4 + l];
-      }
+    for (int l = 0; l < 4; ++l) {
+      so[l * EP + eq] = v[l] + up[l];
+      up[l] = v[4 + l];
     }
   };
 
   // Step k of the march (k = ks .. k1 - 1): issue the copies of x plane
   // k + 2 + DP, coefficients k + 1 + DP and node data k + DP; wait for the
   // copies issued DP steps earlier; one barrier; evaluate element plane
-  // k + 1 (x planes k + 1, k + 2) and, for k >= k0, update node plane k
-  // from element planes k (lower corners) and k - 1 (upper corners).
-  // Between two barriers the slots written (x plane k + 1 + DP + 2 of a
-  // thread already in the next step: the slot of plane k - 1; L and U of
-  // element plane k + 1; the coefficient and node slots of planes k and
-  // k - 1) and the slots read (x planes k .. k + 2, coefficients k + 1,
-  // node data k, L of element plane k, U of element plane k - 1) differ.
+  // k + 1 (x planes k + 1, k + 2; none at the last step) and, for k >= k0,
+  // update node plane k from the corner sums of element plane k.  Between
+  // two barriers the slots written (x plane k + 1 + DP + 2 of a thread
+  // already in the next step: the slot of plane k - 1; S of element plane
+  // k + 1; the coefficient and node slots of planes k and k - 1) and the
+  // slots read (x planes k .. k + 2, coefficients k + 1, node data k, S of
+  // element plane k) differ.
   issue_x(ks + 1);
 #pragma unroll
-  for (int g = 0; g < DP; ++g) {
-    const int k = ks - DP + g;
+  for (int g = 0; g < (int)DP; ++g) {
+    const int k = ks - (int)DP + g;
     issue_x(k + 2 + DP);
     issue_coef(k + 1 + DP);
     issue_nodes(k + DP);
@@ -436,37 +409,34 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
     cp_async_commit();
     cp_async_wait<DP>();
     __syncthreads();
-    element_plane(k + 1);   // zero outputs when k + 1 is outside the element planes
+    if (k + 1 < k1) element_plane(k + 1);   // zero outputs when k + 1 is outside the element planes
     if (k < k0) continue;
-    const int rk = k - ks;
-    const T* xk = xs + (rk % RX) * XP;
-    const T* nd = ns + (rk % RN) * 4 * NP;
-    const T* lo = Lb + (rk & 1) * 4 * EP;
-    const T* upPrev = Ub + ((rk + 2) % 3) * 4 * EP;
-    const int base = k * sxy;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r == 1 && !wn2) break;
-      if (noff[r] < 0) continue;
+    if (noff >= 0) {
       int hsel = 0;
+      bool act = true;
       if (f == 0) {
-        if (!(lr[r] & kLabActive)) continue;
-        hsel = (lr[r] & kLabAnode) ? 0 : 1;
+        act = lr & kLabActive;
+        hsel = (lr & kLabAnode) ? 0 : 1;
       }
-      const int e = nq[r], id = nid[r];
-      const T xn = xk[nsm[r]];
-      const float2 sdv = *reinterpret_cast<const float2*>(nd + NP + 2 * id);   // (variable diagonal, 1/diag)
-      T ax = sdv.x * xn;
-      ax += (lo[3 * EP + e] + upPrev[3 * EP + e]) + (lo[2 * EP + e + 1] + upPrev[2 * EP + e + 1]);
-      ax += (lo[1 * EP + e + ES] + upPrev[1 * EP + e + ES]) + (lo[e + ES + 1] + upPrev[e + ES + 1]);
-      const T res = nd[id] - ax;
-      const int n = noff[r] + base;
-      if (MODE == 1) {
-        Fr[n] = res;
-      } else {
-        const T dn = (hsel ? cA[1] : cA[0]) * nd[3 * NP + id] + (hsel ? cB[1] : cB[0]) * (sdv.y * res);
-        Fd[n] = dn;
-        Fxo[n] = xn + dn;
+      if (act) {
+        const unsigned rk = (unsigned)(k - ks);
+        const T* xk = xs + (rk % RX) * XP;
+        const T* nd = ns + (rk % RN) * 4 * NP;
+        const T* S = Sb + (rk & 1) * 4 * EP;
+        const T xn = xk[nsm];
+        const float2 sdv = *reinterpret_cast<const float2*>(nd + NP + 2 * nid);   // (variable diagonal, 1/diag)
+        T ax = sdv.x * xn;
+        ax += S[3 * EP + nq] + S[2 * EP + nq + 1];
+        ax += S[1 * EP + nq + ES] + S[nq + ES + 1];
+        const T res = nd[nid] - ax;
+        const int n = noff + k * sxy;
+        if (MODE == 1) {
+          Fr[n] = res;
+        } else {
+          const T dn = (hsel ? cA[1] : cA[0]) * nd[3 * NP + nid] + (hsel ? cB[1] : cB[0]) * (sdv.y * res);
+          Fd[n] = dn;
+          Fxo[n] = xn + dn;
+        }
       }
     }
     fetch_labels(k + 1);
@@ -475,11 +445,11 @@ __global__ void __launch_bounds__(kMfThreads, 4) k_mf_level0(MfArgs<T> a) {
 }
 
 // Shared memory of k_mf_level0 (FP32): the x, coefficient and node-data
-// rings and the element planes' corner outputs.
+// rings and the element planes' corner sums.
 constexpr size_t mf_smem_bytes() {
   return sizeof(float) * ((size_t)(kMfDepth + 4) * (kTX + 3) * (kTY + 3) +
                           (size_t)(kMfDepth + 2) * 2 * (kTX + 2) * (kTY + 2) +
-                          (size_t)(kMfDepth + 2) * 4 * (kTX + 1) * (kTY + 1) + (size_t)20 * (kTX + 2) * (kTY + 2));
+                          (size_t)(kMfDepth + 2) * 4 * (kTX + 1) * (kTY + 1) + (size_t)8 * (kTX + 2) * (kTY + 2));
 }
 
 // Per field and element the (stiffness, mass) coefficient pair; only c_e
@@ -550,14 +520,11 @@ p4d_status mf_setup(p4d_ctx* c) {
   if (c->prm.precision == 0) return P4D_OK;
   const int nnx = c->g.nnx, nny = c->g.nny, nnz = c->g.nnz;
   c->mf_phis = !(c->shell_p > 0.0) && !(c->shell_n > 0.0);
-  // tiles of kTX x kTY nodes; the last of an axis takes the remainder, at
-  // most kTX + 1 (kTY + 1) nodes: nnx - 1 elements need ceil((nnx - 1) / kTX) tiles
-  c->mf_ntx = std::max(1, (nnx - 2) / kTX + 1);
-  c->mf_nty = std::max(1, (nny - 2) / kTY + 1);
-  // largest tile: a single tile spans the axis; otherwise the nominal size
-  // or the last tile's remainder (which can be smaller or one larger)
-  const int mw = c->mf_ntx == 1 ? nnx : std::max(kTX, nnx - (c->mf_ntx - 1) * kTX);
-  const int mh = c->mf_nty == 1 ? nny : std::max(kTY, nny - (c->mf_nty - 1) * kTY);
+  // tiles of kTX x kTY nodes; the last of an axis takes the remainder (1 to
+  // kTX nodes)
+  c->mf_ntx = (nnx + kTX - 1) / kTX;
+  c->mf_nty = (nny + kTY - 1) / kTY;
+  const int mw = nnx - (c->mf_ntx - 1) * kTX, mh = nny - (c->mf_nty - 1) * kTY;
   const int zc = c->prm.mf_zchunk > 0 ? c->prm.mf_zchunk : kDefaultZChunk;
   // planes holding phi_s unknowns
   std::vector<uint8_t> lab(c->g.nn);
@@ -585,11 +552,11 @@ p4d_status mf_setup(p4d_ctx* c) {
   c->mf_items = d;
   // the kernel lays shared memory out with the largest tile's strides
   c->mf_smem = mf_smem_bytes();
-  if (mw > kTX + 1 || mh > kTY + 1 || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
+  if (mw > kTX || mh > kTY || mw < 1 || mh < 1) return P4D_ERR_INVALID_ARG;   // cannot happen
   // The kernels' shared-memory limit is a process-wide attribute shared by
-  // every handle: set it to the largest tile any grid can have (64 x 16
-  // nodes), never to this handle's size, which would fail the launches of
-  // larger handles set up before.
+  // every handle: set it to the kernel's fixed layout (the largest tile's),
+  // never to a size of this handle's, which could fail the launches of
+  // handles set up before.
   const size_t smax = mf_smem_bytes();
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   P4D_TRY(cudaFuncSetAttribute(k_mf_level0<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));

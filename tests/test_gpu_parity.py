@@ -22,6 +22,9 @@ CASES = {
     # anisotropic elements: the first multigrid level(s) coarsen x and y only
     "aniso": lambda: make_box_case(13, 11, (7, 3, 7), 30e-6, (40e-6, 15e-6, 40e-6), 5, 124),
     "aniso2": lambda: make_box_case(16, 16, (6, 3, 6), 24e-6, (40e-6, 15e-6, 40e-6), 4, 125),
+    # 16 x 31 nodes: the matrix-free level 0's last tile of each axis is one
+    # node wide (tiles of at most 15 nodes)
+    "tile1": lambda: make_box_case(15, 30, (4, 2, 4), 40e-6, (40e-6, 15e-6, 40e-6), 4, 127),
     # particles on the paper's graded radial mesh (spacings shrink toward the
     # surface, last/first = 0.5) with lognormal radii
     "graded": lambda: make_box_case(6, 5, (4, 2, 4), 30e-6, (40e-6, 15e-6, 40e-6), 8, 126, rs_cv=0.3,
@@ -43,9 +46,10 @@ LIB_KW = {"paper_ocp": dict(ocp_model=1), "paper_laws": dict(ocp_model=1, transp
 # coarse grids keep half-width last elements (an odd element count along an
 # axis) and on the anisotropic boxes (measured 2.3e-9 at rtol 1e-10 on
 # "odd", 2.0e-9 on "graded", 2.1e-7 at rtol 1e-8 on "aniso"), so those
-# meshes are solved to a 100x tighter rtol.  The error bounds are the same
+# meshes (and "tile1", odd along x and anisotropic) are solved to a 100x
+# tighter rtol.  The error bounds are the same
 # for every mesh: 1e-9 for the FP64 path, 1e-7 for the mixed paths.
-TIGHT = {"odd", "oddcoarse", "aniso", "aniso2", "graded"}
+TIGHT = {"odd", "oddcoarse", "aniso", "aniso2", "graded", "tile1"}
 RTOL_FP64 = {name: (1e-12 if name in TIGHT else 1e-10) for name in CASES}
 RTOL_MIXED = {name: (1e-10 if name in TIGHT else 1e-8) for name in CASES}
 
@@ -136,6 +140,28 @@ def test_precond_fp64_matches_oracle_algorithm(name, combine, transpose, cheb):
     # through the back substitution, and BGS passes it on to later fields.
     tol = [1e-7, 1e-11 if combine == "additive" else 1e-7, 1e-11 if combine == "additive" else 1e-7, 1e-7]
     assert all(e < t for e, t in zip(errs, tol)), errs
+
+
+@pytest.mark.parametrize("name", ["cube8", "odd", "oddcoarse", "aniso", "aniso2", "tile1", "hetero", "tabshell", "tpms"])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_precond_mixed_matches_oracle_algorithm(name, precision):
+    """FP32 preconditioner (matrix-free level 0, FP32 levels >= 1, FP32
+    particle solves; precision 2: BF16 storage of levels >= 1) = the
+    oracle's FP64 algorithm (block Jacobi over V(2,2) Chebyshev cycles) up to
+    the storage precision's rounding.  The bound is ~170 FP32 unit roundoffs
+    (BF16: below one BF16 unit roundoff, 2^-8): rounding of the stored
+    operators and of ~10 Chebyshev passes per level over 3-7 levels, with the
+    residuals' cancellation."""
+    case, d, ref, s, st = _setup(name, precision=precision, combine=0, mode=0, cheb_degree=2, cheb_ratio=10.0)
+    s.jacobian_update(st)
+    J = d.jacobian(ref)
+    P = BlockPrecond(d, J, combine="additive", order=(1, 0, 2), degree=2, ratio=10.0)
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(d.ndof) * np.sqrt(J.diagonal())
+    z = s.precond(torch.tensor(r, device="cuda")).cpu().numpy()
+    z_ref = P.apply(r)
+    errs = [np.linalg.norm(z[sl] - z_ref[sl]) / np.linalg.norm(z_ref[sl]) for sl in d.field_slices()]
+    assert max(errs) < (1e-5 if precision == 1 else 3e-3), errs
 
 
 @pytest.mark.parametrize("name", ["cube8", "hetero"])
