@@ -27,14 +27,14 @@
 // phi_s is lifted by its zero values at the nodes without a phi_s unknown
 // (the multigrid never writes them).
 //
-// Layout of a launch: each block owns a tile of W x H nodes (nominally
-// 15 x 15; the last tile of an axis takes the remainder, at most one more)
-// and marches in z over a chunk of node planes.  Per plane it stages the
-// (W+2) x (H+2) tile of x, the element coefficients and the node data in
-// shared memory (asynchronous copies a few planes ahead), evaluates the
-// (W+1) x (H+1) elements between that plane and the next (their
-// lower-corner outputs go to this plane, the upper-corner outputs are kept
-// for the next), and updates its nodes.  The phi_s work list covers only
+// Layout of a launch: each block owns a tile of W x H nodes (15 x 15; the
+// last tile of an axis takes the remainder, 1 to 15 nodes) and marches in z
+// over a chunk of node planes.  Per plane it stages the (W+2) x (H+2) tile
+// of x, the element coefficients and the node data in shared memory
+// (asynchronous copies one plane ahead), evaluates the (W+1) x (H+1)
+// elements between that plane and the next (their lower-corner outputs go
+// to this plane, the upper-corner outputs are kept in registers for the
+// next), and updates its nodes.  The phi_s work list covers only
 // the node planes that hold phi_s unknowns.
 #include <algorithm>
 #include <type_traits>
