@@ -419,3 +419,35 @@ def test_tpms_cell_charge_balance():
     an = d.etype == 0
     assert np.sum(d.A[~an] * i_n[~an]) == pytest.approx(I, rel=1e-8)
     assert np.sum(d.A[an] * i_n[an]) == pytest.approx(-I, rel=1e-8)
+
+
+@pytest.mark.parametrize("cell", ["cube8", "tpms"])
+def test_masked_galerkin_operator_rank(cell):
+    """The phi_s multigrid of one electrode (masked to its unknowns): the
+    Galerkin operator P^T A P of the symmetric positive definite fine block
+    is symmetric positive semidefinite, and definite exactly when the
+    masked prolongation has full column rank.  On the layered cube it has;
+    on the voxelised gyroid the anode's grounded nodes leave coarse columns
+    that reach the anode only where it is one element thick, the columns
+    become dependent and the coarse operator singular."""
+    from p4d_inputs import make_tpms_cell
+    from oracle.blocks import BlockPrecond
+    case = make_case("cube8") if cell == "cube8" else make_tpms_cell(8, 8, 6)
+    d, st = _disc(case)
+    A = BlockPrecond(d, d.jacobian(st), coarse_max=16).blocks[0][0]
+    node_elec = np.full(d.nn, -1)
+    node_elec[d.enodes] = d.etype
+    mask = d.act & (node_elec == 0)
+    Af = A[mask][:, mask].toarray()
+    assert np.abs(Af - Af.T).max() <= 1e-12 * np.abs(Af).max()
+    assert np.linalg.eigvalsh(Af).min() > 0
+    mg = GMG(A, (d.nnx, d.nny, d.nnz), mask=mask, coarse_max=16, lengths=d.lengths)
+    P = mg.P[0].tocsc()
+    cols = np.flatnonzero(np.asarray(abs(P).sum(axis=0)).ravel() > 0)
+    Ac = mg.A[1][cols][:, cols].toarray()
+    ev = np.linalg.eigvalsh(0.5 * (Ac + Ac.T))
+    assert np.abs(Ac - Ac.T).max() <= 1e-12 * np.abs(Ac).max()
+    assert ev.min() >= -1e-12 * ev.max()
+    full_rank = np.linalg.matrix_rank(P[:, cols].toarray()[mask]) == len(cols)
+    assert full_rank == (cell == "cube8")
+    assert (ev.min() > 1e-10 * ev.max()) == full_rank, (ev.min() / ev.max(), full_rank)
